@@ -1,0 +1,369 @@
+/*
+ * Plain FP64 CPU oracle for the leave-one-out cross-validated log-likelihood
+ * of the double-kernel (Nadaraya-Watson) conditional density estimator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file; only the test suite, the smoke check and the benchmark's CPU
+ * baseline use it.  It shares no code, header, table or helper with the CUDA
+ * library.
+ *
+ * Conventions (Holmes, Gray & Isbell, Sec. 2 and Sec. 3):
+ *   h1 = bandwidth on x (d dimensions), h2 = bandwidth on y (1 dimension);
+ *   K_h(t) = h^{-d} K(t/h) with K the standard normal density (Sec. 2 scaling).
+ *   A_j(h1,h2) = sum_{i != j} K_h1(|x_j - x_i|) K_h2(y_j - y_i)     (Sec. 3.2)
+ *   B_j(h1)    = sum_{i != j} K_h1(|x_j - x_i|)                     (Sec. 3.2)
+ *   ell_j      = ln A_j - ln B_j = ln fhat^{-j}(y_j | x_j)          (Eq. 1)
+ *   L_cond     = sum_j ell_j                (conditional LOO log-likelihood)
+ *   L_eq3      = (1/n) sum_j ln(fhat^{-j}(y_j|x_j) fhat^{-j}(x_j))   (Eq. 3)
+ *              = (1/n) sum_j ln A_j - ln(n-1)                       (Sec. 3.2)
+ * Every sum over i is evaluated with a log-sum-exp (max, then sum of shifted
+ * exponentials) so that no bandwidth underflows; every loop is a straight loop
+ * over all i != j (exclusion by index).  Rows j are split across threads;
+ * sums over j are Neumaier-compensated in a fixed block order, so results do
+ * not depend on the thread count.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define LN_SQRT_2PI 0.91893853320467274178 /* ln sqrt(2 pi) */
+#define ROW_BLOCK 256
+
+typedef struct { double s, c; } neumaier_t;
+
+static void nm_add(neumaier_t *a, double v) {
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+    else a->c += (v - t) + a->s;
+    a->s = t;
+}
+static double nm_val(const neumaier_t *a) { return a->s + a->c; }
+
+/* Standardisation used on the paper's data (Sec. 4): each x dimension is
+ * centred and divided by its sample standard deviation (ddof = 1).
+ * x is N x d row-major (FP32 values widened to FP64).  Returns -1 when a
+ * dimension has zero spread. */
+int oracle_standardize(const double *x, int64_t N, int d, double *out) {
+    for (int c = 0; c < d; ++c) {
+        neumaier_t m = {0, 0};
+        for (int64_t i = 0; i < N; ++i) nm_add(&m, x[i * d + c]);
+        double mean = nm_val(&m) / (double)N;
+        neumaier_t v = {0, 0};
+        for (int64_t i = 0; i < N; ++i) {
+            double t = x[i * d + c] - mean;
+            nm_add(&v, t * t);
+        }
+        double sd = sqrt(nm_val(&v) / (double)(N - 1));
+        if (!(sd > 0.0)) return -1;
+        for (int64_t i = 0; i < N; ++i) out[i * d + c] = (x[i * d + c] - mean) / sd;
+    }
+    return 0;
+}
+
+static double sqdist(const double *a, const double *b, int d) {
+    double s = 0.0;
+    for (int c = 0; c < d; ++c) {
+        double t = a[c] - b[c];
+        s += t * t;
+    }
+    return s;
+}
+
+/* ln sum_{i != j} exp(e_i), by max then shifted sum. */
+static double lse_excl(const double *e, int64_t N, int64_t j) {
+    double m = -INFINITY;
+    for (int64_t i = 0; i < N; ++i)
+        if (i != j && e[i] > m) m = e[i];
+    if (m == -INFINITY) return -INFINITY;
+    double s = 0.0;
+    for (int64_t i = 0; i < N; ++i)
+        if (i != j) s += exp(e[i] - m);
+    return m + log(s);
+}
+
+/* ------------------------------------------------------------------ */
+/* Per-row LOO log terms                                               */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const double *x, *y, *h1, *h2;
+    int64_t N;
+    int d, G1, G2;
+    const int64_t *rows;      /* NULL: all rows */
+    int64_t n_rows;
+    double *ell;              /* optional: n_rows x G1 x G2 */
+    double *lnA;              /* optional: n_rows x G1 x G2 */
+    neumaier_t *blk_cond;     /* optional: n_blocks x G1 x G2 */
+    neumaier_t *blk_lnA;      /* optional: n_blocks x G1 x G2 */
+    int64_t next_block;
+    pthread_mutex_t mu;
+} rows_job_t;
+
+static void row_terms(const rows_job_t *J, int64_t j, double *dx2, double *dy2, double *e,
+                      double *ell_out, double *lnA_out) {
+    const int d = J->d;
+    for (int64_t i = 0; i < J->N; ++i) {
+        dx2[i] = sqdist(J->x + j * d, J->x + i * d, d);
+        double t = J->y[j] - J->y[i];
+        dy2[i] = t * t;
+    }
+    for (int k = 0; k < J->G1; ++k) {
+        const double h1 = J->h1[k];
+        for (int64_t i = 0; i < J->N; ++i) e[i] = -dx2[i] / (2.0 * h1 * h1);
+        /* ln B_j = ln sum K_h1 */
+        const double lnB = lse_excl(e, J->N, j) - d * (LN_SQRT_2PI + log(h1));
+        for (int l = 0; l < J->G2; ++l) {
+            const double h2 = J->h2[l];
+            for (int64_t i = 0; i < J->N; ++i)
+                e[i] = -dx2[i] / (2.0 * h1 * h1) - dy2[i] / (2.0 * h2 * h2);
+            const double lnA = lse_excl(e, J->N, j) - d * (LN_SQRT_2PI + log(h1))
+                               - (LN_SQRT_2PI + log(h2));
+            ell_out[k * J->G2 + l] = lnA - lnB;
+            lnA_out[k * J->G2 + l] = lnA;
+        }
+    }
+}
+
+static void *rows_worker(void *arg) {
+    rows_job_t *J = (rows_job_t *)arg;
+    const int64_t G = (int64_t)J->G1 * J->G2;
+    double *dx2 = malloc(sizeof(double) * J->N);
+    double *dy2 = malloc(sizeof(double) * J->N);
+    double *e = malloc(sizeof(double) * J->N);
+    double *ell = malloc(sizeof(double) * G);
+    double *lnA = malloc(sizeof(double) * G);
+    for (;;) {
+        pthread_mutex_lock(&J->mu);
+        int64_t b = J->next_block++;
+        pthread_mutex_unlock(&J->mu);
+        int64_t r0 = b * ROW_BLOCK;
+        if (r0 >= J->n_rows) break;
+        int64_t r1 = r0 + ROW_BLOCK < J->n_rows ? r0 + ROW_BLOCK : J->n_rows;
+        for (int64_t r = r0; r < r1; ++r) {
+            int64_t j = J->rows ? J->rows[r] : r;
+            row_terms(J, j, dx2, dy2, e, ell, lnA);
+            if (J->ell) memcpy(J->ell + r * G, ell, sizeof(double) * G);
+            if (J->lnA) memcpy(J->lnA + r * G, lnA, sizeof(double) * G);
+            if (J->blk_cond)
+                for (int64_t c = 0; c < G; ++c) {
+                    nm_add(&J->blk_cond[b * G + c], ell[c]);
+                    nm_add(&J->blk_lnA[b * G + c], lnA[c]);
+                }
+        }
+    }
+    free(dx2); free(dy2); free(e); free(ell); free(lnA);
+    return NULL;
+}
+
+static void run_rows(rows_job_t *J, int n_threads) {
+    if (n_threads < 1) n_threads = 1;
+    pthread_mutex_init(&J->mu, NULL);
+    J->next_block = 0;
+    pthread_t *th = malloc(sizeof(pthread_t) * n_threads);
+    for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, rows_worker, J);
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&J->mu);
+}
+
+/* ell_j(k,l) and ln A_j(k,l) for the listed rows (rows == NULL: 0..n_rows-1).
+ * Outputs are n_rows x G1 x G2, row-major with h1 major. */
+void oracle_loo_rows(const double *x, const double *y, int64_t N, int d,
+                     const double *h1, int G1, const double *h2, int G2,
+                     const int64_t *rows, int64_t n_rows, double *ell, double *lnA,
+                     int n_threads) {
+    rows_job_t J;
+    memset(&J, 0, sizeof(J));
+    J.x = x; J.y = y; J.h1 = h1; J.h2 = h2; J.N = N; J.d = d; J.G1 = G1; J.G2 = G2;
+    J.rows = rows; J.n_rows = n_rows; J.ell = ell; J.lnA = lnA;
+    run_rows(&J, n_threads);
+}
+
+/* Whole-grid scores: L_cond[k][l] = sum_j ell_j, L_eq3[k][l] = (1/N) sum_j ln A_j - ln(N-1). */
+void oracle_loo_grid(const double *x, const double *y, int64_t N, int d,
+                     const double *h1, int G1, const double *h2, int G2,
+                     double *L_cond, double *L_eq3, int n_threads) {
+    const int64_t G = (int64_t)G1 * G2;
+    const int64_t n_blocks = (N + ROW_BLOCK - 1) / ROW_BLOCK;
+    rows_job_t J;
+    memset(&J, 0, sizeof(J));
+    J.x = x; J.y = y; J.h1 = h1; J.h2 = h2; J.N = N; J.d = d; J.G1 = G1; J.G2 = G2;
+    J.rows = NULL; J.n_rows = N;
+    J.blk_cond = calloc((size_t)(n_blocks * G), sizeof(neumaier_t));
+    J.blk_lnA = calloc((size_t)(n_blocks * G), sizeof(neumaier_t));
+    run_rows(&J, n_threads);
+    for (int64_t c = 0; c < G; ++c) {
+        neumaier_t a = {0, 0}, b = {0, 0};
+        for (int64_t bl = 0; bl < n_blocks; ++bl) {
+            nm_add(&a, nm_val(&J.blk_cond[bl * G + c]));
+            nm_add(&b, nm_val(&J.blk_lnA[bl * G + c]));
+        }
+        L_cond[c] = nm_val(&a);
+        L_eq3[c] = nm_val(&b) / (double)N - log((double)(N - 1));
+    }
+    free(J.blk_cond);
+    free(J.blk_lnA);
+}
+
+/* ------------------------------------------------------------------ */
+/* Gradient of L_cond with respect to (ln h1, ln h2) at one bandwidth  */
+/* ------------------------------------------------------------------ */
+/* Derivation (the paper gives none; it follows from the Gaussian K):
+ *   d ln K_h1(r)/d ln h1 = r^2/h1^2 - d,   d ln K_h2(t)/d ln h2 = t^2/h2^2 - 1,
+ *   d ell_j/d ln h1 = (E_Aj[dx2] - E_Bj[dx2]) / h1^2,
+ *   d ell_j/d ln h2 = E_Aj[dy2] / h2^2 - 1,
+ * where E_Aj weights i by K_h1 K_h2 and E_Bj by K_h1 (i != j). */
+typedef struct {
+    const double *x, *y;
+    int64_t N;
+    int d;
+    double h1, h2;
+    const int64_t *rows;
+    int64_t n_rows;
+    double *row_out;          /* optional n_rows x 3: ell, d/dlnh1, d/dlnh2 */
+    neumaier_t *blk;          /* n_blocks x 3 */
+    int64_t next_block;
+    pthread_mutex_t mu;
+} grad_job_t;
+
+static void grad_row(const grad_job_t *J, int64_t j, double *dx2, double *dy2, double out[3]) {
+    const int d = J->d;
+    const double a1 = 1.0 / (2.0 * J->h1 * J->h1), a2 = 1.0 / (2.0 * J->h2 * J->h2);
+    double mA = -INFINITY, mB = -INFINITY;
+    for (int64_t i = 0; i < J->N; ++i) {
+        dx2[i] = sqdist(J->x + j * d, J->x + i * d, d);
+        double t = J->y[j] - J->y[i];
+        dy2[i] = t * t;
+        if (i == j) continue;
+        double eA = -a1 * dx2[i] - a2 * dy2[i], eB = -a1 * dx2[i];
+        if (eA > mA) mA = eA;
+        if (eB > mB) mB = eB;
+    }
+    double sA = 0, sAx = 0, sAy = 0, sB = 0, sBx = 0;
+    for (int64_t i = 0; i < J->N; ++i) {
+        if (i == j) continue;
+        double wA = exp(-a1 * dx2[i] - a2 * dy2[i] - mA);
+        double wB = exp(-a1 * dx2[i] - mB);
+        sA += wA; sAx += wA * dx2[i]; sAy += wA * dy2[i];
+        sB += wB; sBx += wB * dx2[i];
+    }
+    double lnA = mA + log(sA) - d * (LN_SQRT_2PI + log(J->h1)) - (LN_SQRT_2PI + log(J->h2));
+    double lnB = mB + log(sB) - d * (LN_SQRT_2PI + log(J->h1));
+    out[0] = lnA - lnB;
+    out[1] = (sAx / sA - sBx / sB) / (J->h1 * J->h1);
+    out[2] = (sAy / sA) / (J->h2 * J->h2) - 1.0;
+}
+
+static void *grad_worker(void *arg) {
+    grad_job_t *J = (grad_job_t *)arg;
+    double *dx2 = malloc(sizeof(double) * J->N);
+    double *dy2 = malloc(sizeof(double) * J->N);
+    for (;;) {
+        pthread_mutex_lock(&J->mu);
+        int64_t b = J->next_block++;
+        pthread_mutex_unlock(&J->mu);
+        int64_t r0 = b * ROW_BLOCK;
+        if (r0 >= J->n_rows) break;
+        int64_t r1 = r0 + ROW_BLOCK < J->n_rows ? r0 + ROW_BLOCK : J->n_rows;
+        for (int64_t r = r0; r < r1; ++r) {
+            double o[3];
+            grad_row(J, J->rows ? J->rows[r] : r, dx2, dy2, o);
+            if (J->row_out) memcpy(J->row_out + 3 * r, o, sizeof(o));
+            for (int c = 0; c < 3; ++c) nm_add(&J->blk[b * 3 + c], o[c]);
+        }
+    }
+    free(dx2); free(dy2);
+    return NULL;
+}
+
+/* L_cond and its gradient (d/d ln h1, d/d ln h2) over the listed rows
+ * (rows == NULL: all N rows).  out3 = {L, dL/dlnh1, dL/dlnh2}. */
+void oracle_grad(const double *x, const double *y, int64_t N, int d, double h1, double h2,
+                 const int64_t *rows, int64_t n_rows, double *row_out, double *out3,
+                 int n_threads) {
+    grad_job_t J;
+    memset(&J, 0, sizeof(J));
+    J.x = x; J.y = y; J.N = N; J.d = d; J.h1 = h1; J.h2 = h2;
+    J.rows = rows; J.n_rows = n_rows; J.row_out = row_out;
+    const int64_t n_blocks = (n_rows + ROW_BLOCK - 1) / ROW_BLOCK;
+    J.blk = calloc((size_t)(n_blocks * 3 + 3), sizeof(neumaier_t));
+    pthread_mutex_init(&J.mu, NULL);
+    if (n_threads < 1) n_threads = 1;
+    pthread_t *th = malloc(sizeof(pthread_t) * n_threads);
+    for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, grad_worker, &J);
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&J.mu);
+    for (int c = 0; c < 3; ++c) {
+        neumaier_t a = {0, 0};
+        for (int64_t b = 0; b < n_blocks; ++b) nm_add(&a, nm_val(&J.blk[b * 3 + c]));
+        out3[c] = nm_val(&a);
+    }
+    free(J.blk);
+}
+
+/* ------------------------------------------------------------------ */
+/* Conditional density at query points (Eq. 1, no leave-one-out)       */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const double *x, *y, *xq, *yg;
+    int64_t N, Q;
+    int d, G;
+    double h1, h2;
+    double *f;
+    int64_t next;
+    pthread_mutex_t mu;
+} dens_job_t;
+
+static void *dens_worker(void *arg) {
+    dens_job_t *J = (dens_job_t *)arg;
+    double *ex = malloc(sizeof(double) * J->N);
+    double *e = malloc(sizeof(double) * J->N);
+    const double a1 = 1.0 / (2.0 * J->h1 * J->h1), a2 = 1.0 / (2.0 * J->h2 * J->h2);
+    for (;;) {
+        pthread_mutex_lock(&J->mu);
+        int64_t q = J->next++;
+        pthread_mutex_unlock(&J->mu);
+        if (q >= J->Q) break;
+        double mB = -INFINITY;
+        for (int64_t i = 0; i < J->N; ++i) {
+            ex[i] = -a1 * sqdist(J->xq + q * J->d, J->x + i * J->d, J->d);
+            if (ex[i] > mB) mB = ex[i];
+        }
+        double sB = 0;
+        for (int64_t i = 0; i < J->N; ++i) sB += exp(ex[i] - mB);
+        const double lnB = mB + log(sB);
+        for (int g = 0; g < J->G; ++g) {
+            double mA = -INFINITY;
+            for (int64_t i = 0; i < J->N; ++i) {
+                double t = J->yg[g] - J->y[i];
+                e[i] = ex[i] - a2 * t * t;
+                if (e[i] > mA) mA = e[i];
+            }
+            double sA = 0;
+            for (int64_t i = 0; i < J->N; ++i) sA += exp(e[i] - mA);
+            double lnf = mA + log(sA) - lnB - (LN_SQRT_2PI + log(J->h2));
+            J->f[q * J->G + g] = exp(lnf);
+        }
+    }
+    free(ex); free(e);
+    return NULL;
+}
+
+/* f[q][g] = fhat(yg[g] | xq[q]) of Eq. 1 with Gaussian kernels, all N points. */
+void oracle_density(const double *x, const double *y, int64_t N, int d, double h1, double h2,
+                    const double *xq, int64_t Q, const double *yg, int G, double *f,
+                    int n_threads) {
+    dens_job_t J;
+    memset(&J, 0, sizeof(J));
+    J.x = x; J.y = y; J.xq = xq; J.yg = yg; J.N = N; J.Q = Q; J.d = d; J.G = G;
+    J.h1 = h1; J.h2 = h2; J.f = f;
+    pthread_mutex_init(&J.mu, NULL);
+    if (n_threads < 1) n_threads = 1;
+    pthread_t *th = malloc(sizeof(pthread_t) * n_threads);
+    for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, dens_worker, &J);
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&J.mu);
+}

@@ -1,0 +1,202 @@
+"""Pins for the FP64 CPU oracle against facts fixed by the paper's definitions
+and by mathematics, independent of the oracle's own code: brute force from
+Eq. 1 / Eq. 3 on tiny inputs, closed forms (N = 2, h1 -> inf, h1 -> 0),
+invariances, kernel-sum symmetry checked with scipy's pair distances,
+the unit integral and Gaussian convolution of fhat(.|x), and finite
+differences of the score for the gradient."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+from scipy.spatial.distance import pdist
+
+from oracle import brute, oracle
+from paper_1206_5278_gb300 import synth
+
+
+def _small(N, d, seed, scale=1.0):
+    return synth.random_small(N, d, seed, scale)
+
+
+@pytest.mark.parametrize("N,d,seed", [(5, 1, 0), (9, 2, 1), (12, 3, 2), (7, 1, 3)])
+def test_oracle_matches_brute_force(N, d, seed):
+    """Sec. 3.2 expansion (oracle, log-sum-exp) equals Eq. 1/Eq. 3 evaluated
+    directly, including the explicit fhat^{-j}(x_j) factor of Eq. 3."""
+    x, y = _small(N, d, seed)
+    rng = np.random.default_rng(seed)
+    h1 = np.sort(rng.uniform(0.3, 2.0, 3))
+    h2 = np.sort(rng.uniform(0.2, 1.5, 4))
+    Lc, Le = oracle.loo_grid(x, y, h1, h2, n_threads=2)
+    xl, yl = x.astype(np.float64).tolist(), y.astype(np.float64).tolist()
+    for k in range(h1.size):
+        for l in range(h2.size):
+            bc = brute.L_cond(xl, yl, h1[k], h2[l])
+            be = brute.L_eq3(xl, yl, h1[k], h2[l])
+            assert abs(Lc[k, l] - bc) <= 1e-11 * max(1.0, abs(bc))
+            assert abs(Le[k, l] - be) <= 1e-11 * max(1.0, abs(be))
+
+
+def test_rows_sum_to_grid():
+    x, y = _small(40, 2, 5)
+    h1, h2 = np.array([0.3, 0.9]), np.array([0.2, 0.5, 1.1])
+    Lc, Le = oracle.loo_grid(x, y, h1, h2)
+    ell, lnA = oracle.loo_rows(x, y, h1, h2)
+    np.testing.assert_allclose(ell.sum(0), Lc, rtol=1e-12)
+    np.testing.assert_allclose(lnA.mean(0) - math.log(39), Le, rtol=1e-12)
+    sub = [3, 17, 0, 39]
+    ell_s, _ = oracle.loo_rows(x, y, h1, h2, rows=sub)
+    np.testing.assert_allclose(ell_s, ell[sub], rtol=1e-13)
+
+
+@pytest.mark.parametrize("d", [1, 3])
+def test_two_points_closed_form(d):
+    """N=2: A_j/B_j = K_h2(y1-y2) for any h1, so L_cond = 2 ln K_h2(y1-y2)."""
+    x, y = _small(2, d, 11)
+    h1 = np.array([0.01, 0.7, 50.0])
+    h2 = np.array([0.3, 2.0])
+    Lc, Le = oracle.loo_grid(x, y, h1, h2)
+    dy = float(y[0]) - float(y[1])
+    for l, hh in enumerate(h2):
+        want = 2.0 * stats.norm.logpdf(dy, scale=hh)
+        np.testing.assert_allclose(Lc[:, l], want, rtol=1e-12, atol=1e-12)
+
+
+def test_h1_infinite_limit_is_loo_kde_of_y():
+    """h1 -> inf: every x weight is equal, so L_cond is the LOO KDE
+    log-likelihood of y alone (checked with scipy's gaussian_kde)."""
+    x, y = _small(30, 2, 12)
+    h2 = 0.4
+    Lc, _ = oracle.loo_grid(x, y, np.array([1e7]), np.array([h2]))
+    yd = y.astype(np.float64)
+    want = 0.0
+    for j in range(yd.size):
+        rest = np.delete(yd, j)
+        kde = stats.gaussian_kde(rest, bw_method=h2 / rest.std(ddof=1))
+        want += math.log(kde(yd[j:j + 1])[0])
+    assert abs(Lc[0, 0] - want) <= 1e-9 * abs(want)
+
+
+def test_h1_zero_limit_is_nearest_neighbour():
+    """h1 -> 0: all x weight moves to the x-nearest neighbour nn(j), so
+    ell_j -> ln K_h2(y_j - y_nn(j))."""
+    x, y = _small(50, 2, 13)
+    h2 = 0.35
+    ell, _ = oracle.loo_rows(x, y, np.array([1e-3]), np.array([h2]))
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    D = ((xd[:, None, :] - xd[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(D, np.inf)
+    nn = D.argmin(1)
+    want = stats.norm.logpdf(yd - yd[nn], scale=h2)
+    np.testing.assert_allclose(ell[:, 0, 0], want, rtol=1e-9, atol=1e-9)
+
+
+def test_invariances():
+    x, y = _small(25, 2, 14)
+    h1, h2 = np.array([0.4, 1.3]), np.array([0.25, 0.8])
+    L0, _ = oracle.loo_grid(x, y, h1, h2)
+    perm = np.random.default_rng(0).permutation(25)
+    Lp, _ = oracle.loo_grid(x[perm], y[perm], h1, h2)
+    np.testing.assert_allclose(Lp, L0, rtol=1e-12)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    Lt, _ = oracle.loo_grid(xd + 3.25, yd - 7.5, h1, h2)
+    np.testing.assert_allclose(Lt, L0, rtol=1e-10)
+    c = 2.5
+    Lx, _ = oracle.loo_grid(c * xd, yd, c * h1, h2)
+    np.testing.assert_allclose(Lx, L0, rtol=1e-11)
+    Ly, _ = oracle.loo_grid(xd, c * yd, h1, c * h2)
+    np.testing.assert_allclose(Ly, L0 - 25 * math.log(c), rtol=1e-11)
+
+
+def test_kernel_sums_symmetric_with_pair_distances():
+    """v(i,j) = v(j,i): sum_j A_j and sum_j B_j equal twice the sum over
+    unordered pairs, computed here from scipy's pdist (normalisation
+    constants K_h(t) = h^-d K(t/h) included)."""
+    N, d = 60, 3
+    x, y = _small(N, d, 15)
+    h1, h2 = 0.8, 0.45
+    ell, lnA = oracle.loo_rows(x, y, np.array([h1]), np.array([h2]))
+    lnB = lnA - ell
+    px = pdist(x.astype(np.float64), "sqeuclidean")
+    py = pdist(y.astype(np.float64)[:, None], "sqeuclidean")
+    kx = np.exp(-px / (2 * h1 * h1)) / (math.sqrt(2 * math.pi) * h1) ** d
+    ky = np.exp(-py / (2 * h2 * h2)) / (math.sqrt(2 * math.pi) * h2)
+    np.testing.assert_allclose(np.exp(lnB[:, 0, 0]).sum(), 2 * kx.sum(), rtol=1e-12)
+    np.testing.assert_allclose(np.exp(lnA[:, 0, 0]).sum(), 2 * (kx * ky).sum(), rtol=1e-12)
+
+
+def test_standardize_matches_numpy():
+    x, _ = synth.gmm_sine(500, 4, seed=3)
+    z = oracle.standardize(x)
+    xd = x.astype(np.float64)
+    np.testing.assert_allclose(z, (xd - xd.mean(0)) / xd.std(0, ddof=1), rtol=1e-12, atol=1e-13)
+    with pytest.raises(ValueError):
+        oracle.standardize(np.ones((10, 2)))
+
+
+def test_gradient_matches_finite_differences():
+    x, y = _small(80, 2, 16)
+    h1, h2 = 0.6, 0.4
+    out = oracle.grad(x, y, h1, h2)
+    Lc, _ = oracle.loo_grid(x, y, np.array([h1]), np.array([h2]))
+    assert abs(out[0] - Lc[0, 0]) < 1e-10 * abs(Lc[0, 0])
+    s = 1e-3
+    e = math.exp
+    f = lambda a, b: oracle.loo_grid(x, y, np.array([a]), np.array([b]))[0][0, 0]
+    g1 = (f(h1 * e(s), h2) - f(h1 * e(-s), h2)) / (2 * s)
+    g2 = (f(h1, h2 * e(s)) - f(h1, h2 * e(-s))) / (2 * s)
+    # central differences are O(s^2) accurate
+    assert abs(out[1] - g1) <= 1e-5 * (abs(g1) + 1)
+    assert abs(out[2] - g2) <= 1e-5 * (abs(g2) + 1)
+
+
+def test_gradient_matches_brute_fd_tiny():
+    x, y = _small(8, 1, 17)
+    out = oracle.grad(x, y, 0.7, 0.5)
+    g1, g2 = brute.grad_fd(x.astype(np.float64).tolist(), y.astype(np.float64).tolist(), 0.7, 0.5)
+    assert abs(out[1] - g1) < 1e-6 and abs(out[2] - g2) < 1e-6
+
+
+def test_gradient_rows():
+    x, y = _small(30, 3, 18)
+    tot, rows = oracle.grad(x, y, 0.9, 0.3, per_row=True)
+    np.testing.assert_allclose(rows.sum(0), tot, rtol=1e-12)
+
+
+def test_density_matches_brute():
+    x, y = _small(10, 2, 19)
+    xq = synth.random_small(3, 2, 20)[0]
+    yg = np.linspace(-2, 2, 5)
+    f = oracle.density(x, y, 0.6, 0.4, xq, yg)
+    xl, yl = x.astype(np.float64).tolist(), y.astype(np.float64).tolist()
+    for q in range(3):
+        for g in range(5):
+            want = brute.density(xl, yl, xq[q].astype(np.float64).tolist(), yg[g], 0.6, 0.4)
+            assert abs(f[q, g] - want) <= 1e-12 * want + 1e-300
+
+
+def test_density_integrates_to_one_and_convolves():
+    """int fhat(y|x) dy = 1, and int fhat(y|x) N(y; m, s^2) dy equals
+    sum_i u_i N(y_i; m, s^2 + h2^2) / sum_i u_i (Gaussian convolution)."""
+    x, y = synth.gmm_sine(300, 2, seed=21)
+    h1, h2 = 0.3, 0.15
+    xs = oracle.standardize(x)
+    xq = xs[:4] + 0.05
+    yd = y.astype(np.float64)
+    grid = np.linspace(yd.min() - 12 * h2, yd.max() + 12 * h2, 20001)
+    f = oracle.density(xs, yd, h1, h2, xq, grid)
+    integ = np.trapezoid(f, grid, axis=1)
+    np.testing.assert_allclose(integ, 1.0, atol=1e-8)
+    m, s = 0.2, 0.5
+    lhs = np.trapezoid(f * stats.norm.pdf(grid, m, s)[None, :], grid, axis=1)
+    for q in range(4):
+        u = np.exp(-((xs - xq[q]) ** 2).sum(1) / (2 * h1 * h1))
+        rhs = (u * stats.norm.pdf(yd, m, math.sqrt(s * s + h2 * h2))).sum() / u.sum()
+        assert abs(lhs[q] - rhs) <= 1e-8 * rhs
+
+
+def test_bandwidth_grid_inclusive_log_spaced():
+    g = synth.bandwidth_grid(0.05, 2.0, 32)
+    assert g[0] == 0.05 and abs(g[-1] - 2.0) < 1e-15
+    r = g[1:] / g[:-1]
+    np.testing.assert_allclose(r, r[0], rtol=1e-12)
