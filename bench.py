@@ -1,0 +1,284 @@
+"""Benchmark: exact LOO-CV score of the double-kernel conditional density
+estimator over a full 32x32 bandwidth grid on N=50,000 standardised 5-D
+points (one step = one whole-grid evaluation, N^2 x 1024 pair-evaluations).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LOO-CV pair-evals/s (N²×bandwidths) at 1e-5 rel err vs plain; p50/p99 latency"
+UNIT = "pair-evals/s"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def flops_per_pair(G1: int, G2: int, d: int) -> int:
+    """Algorithmic FP32 flops per pair (j, i) for a G1 x G2 grid, FMA = 2:
+    distance 3d+2, shift subtractions 2, exp2 arguments G1+G2 multiplies,
+    outer product 2 G1 G2, denominator sums G1."""
+    return 2 * G1 * G2 + G1 + (G1 + G2) + 3 * d + 4
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [ln.split(",") for ln in open(self.f.name).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(w, n_rows: int, seed: int = 0):
+    """Time the FP64 oracle on n_rows random rows of the workload (all host
+    cores).  Returns (pair-evals/s, seconds, threads, rows)."""
+    from oracle import oracle
+    rows = np.random.default_rng(seed).choice(w.N, n_rows, replace=False)
+    th = oracle.default_threads()
+    t0 = time.perf_counter()
+    oracle.loo_rows(w.x, w.y, w.h1, w.h2, rows=rows, standardize_x=w.standardize, n_threads=th)
+    dt = time.perf_counter() - t0
+    pe = n_rows * w.N * w.h1.size * w.h2.size
+    return pe / dt, dt, th, rows
+
+
+def run_reference(args, w):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    from oracle import oracle
+    oracle.build()
+    rows_per_step = args.ref_rows
+    times = []
+    for s in range(args.warmup + args.steps):
+        _, dt, th, _ = oracle_sample(w, rows_per_step, seed=s)
+        if s >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * float(np.mean(times))
+    pe = rows_per_step * w.N * w.h1.size * w.h2.size
+    v = pe / (ms * 1e-3)
+    sample = "%d random rows x N=%d x %dx%d grid per step (FP64 oracle, log-sum-exp)" % (
+        rows_per_step, w.N, w.h1.size, w.h2.size)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": w.name, "N": w.N, "d_x": w.d,
+                                           "G1": int(w.h1.size), "G2": int(w.h2.size)},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, w):
+    import torch
+    from paper_1206_5278_gb300 import cde
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    G1, G2 = int(w.h1.size), int(w.h2.size)
+    ctx = cde.cde_init(local)
+    ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=w.standardize)
+    stream = torch.cuda.Stream()
+    Lc = torch.empty(G1 * G2, dtype=torch.float64, device="cuda")
+    Le = torch.empty(G1 * G2, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    pe_step = w.N * w.N * G1 * G2
+
+    def step():
+        cde.cde_loo_loglik(ctx, ds, w.h1, w.h2, Lc, Le, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step()
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.fill_(float(s))          # L2 flush (256 MB) outside the timed events
+            ev[s][0].record(stream)
+            step()
+            ev[s][1].record(stream)
+    stream.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    per = np.array([a.elapsed_time(b) for a, b in ev])  # ms
+    ms = float(per.mean())
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = pe_step * world / (ms * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e_times = []
+    Lh = np.empty((G1, G2))
+    for s in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        d2 = cde.cde_create_dataset(ctx, w.x, w.y, standardize=w.standardize)
+        Lh, Leh = cde.cde_loo_loglik(ctx, d2, w.h1, w.h2)
+        cde.cde_destroy_dataset(ctx, d2)
+        e2e_times.append(time.perf_counter() - t1)
+    e2e_s = float(np.median(e2e_times))
+    h2d = w.x.nbytes + w.y.nbytes
+    d2h = 2 * G1 * G2 * 8
+
+    # ---- roofline (FP32 pipe; measured unit rates) ----
+    peaks = cde.cde_measure_peaks(ctx) if hasattr(cde, "cde_measure_peaks") else None
+    fpp = flops_per_pair(G1, G2, w.d)
+    achieved = w.N * w.N * fpp / (ms * 1e-3) / 1e12
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    try:
+        p = peaks and peaks.ffma_per_clk_sm
+    except Exception:
+        p = None
+    lanes = 128.0
+    peak_max = 2 * lanes * sms * 2070e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
+            "frac": achieved / peak_max, "traffic": None,
+            "peak_basis": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x 2070 MHz (max clock)" % sms}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (2 * lanes * sms * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    # ---- parity spot check on sampled rows + CPU baseline (rank 0, N=1) ----
+    cpu = None
+    parity = None
+    if rank == 0:
+        from oracle import oracle
+        oracle.build()
+        rows = np.random.default_rng(123).choice(w.N, 8, replace=False)
+        g = cde.cde_loo_rows(ctx, ds, w.h1, w.h2, rows)
+        ref, _ = oracle.loo_rows(w.x, w.y, w.h1, w.h2, rows=rows, standardize_x=w.standardize)
+        parity = float(np.max(np.abs(g - ref) / np.maximum(1.0, np.abs(ref))))
+        if world == 1 and not args.no_cpu:
+            v, dt, th, _ = oracle_sample(w, args.cpu_rows, seed=7)
+            cpu = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
+                   "sample": "%d random rows x N=%d x %dx%d grid (FP64 oracle), %.1f s" % (
+                       args.cpu_rows, w.N, G1, G2, dt)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "N": w.N, "d_x": w.d, "G1": G1, "G2": G2,
+                      "standardized": bool(w.standardize),
+                      "l2": "flushed (256 MB write) before every timed step",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
+           "e2e": {"value": pe_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h), "s_per_step": e2e_s,
+                   "includes": "dataset upload + standardise + nearest-neighbour shifts + grid + copy back"},
+           "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+           "gpu_launches": 2 * args.steps, "parity_rows_max_rel_err": parity,
+           "wall_s_timed_region": wall}
+    if peaks is not None:
+        out["measured_unit_rates"] = {"ffma_per_clk_sm": peaks.ffma_per_clk_sm,
+                                      "ex2_per_clk_sm": peaks.ex2_per_clk_sm,
+                                      "sm_clock_mhz": peaks.sm_clock_mhz}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    cde.cde_destroy_dataset(ctx, ds)
+    cde.cde_shutdown(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-rows", type=int, default=24)
+    ap.add_argument("--ref-rows", type=int, default=8)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--N", type=int, default=50000, help="dataset size (profiling runs use less)")
+    args = ap.parse_args()
+    from paper_1206_5278_gb300 import synth
+    rank, _, _ = _env_rank()
+    w = synth.scale_workload(N=args.N, seed=1 + 1000 * rank)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        if not os.path.exists(os.path.join(ROOT, "paper_1206_5278_gb300", "libcde.so")):
+            from __graft_entry__ import build
+            build()
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

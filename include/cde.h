@@ -1,0 +1,229 @@
+/*
+ * cde.h -- C ABI of the GB300 (sm_103a) library for the double-kernel
+ * conditional density estimator of Holmes, Gray & Isbell, "Fast Nonparametric
+ * Conditional Density Estimation".
+ *
+ * Notation (the paper's h1/h2 roles are swapped here; this library uses):
+ *   h1 = bandwidth of the x kernel (d_x dimensions, isotropic Gaussian),
+ *   h2 = bandwidth of the y kernel (scalar y, Gaussian).
+ *   K_h(t) = h^{-d} K(t/h), K the standard normal density (Sec. 2).
+ *   fhat(y|x) = sum_i K_h1(|x-x_i|) K_h2(y-y_i) / sum_i K_h1(|x-x_i|)   (Eq. 1)
+ *   A_j = sum_{i!=j} K_h1(|x_j-x_i|) K_h2(y_j-y_i),
+ *   B_j = sum_{i!=j} K_h1(|x_j-x_i|)                          (Sec. 3.2)
+ *   L_cond(h1,h2) = sum_j ln(A_j / B_j)      (conditional LOO log-likelihood)
+ *   L_eq3(h1,h2)  = (1/N) sum_j ln A_j - ln(N-1)   (Eq. 3 and its expansion)
+ *
+ * Conventions for every entry point:
+ *   - Returns a cde_status; never aborts the process.  On failure the
+ *     thread-local message from cde_last_error() says what went wrong.
+ *   - Inputs are copied or only read; the caller keeps ownership of every
+ *     pointer it passes.  Outputs go to caller-owned buffers.
+ *   - Pointers are host pointers unless a flag or argument says device.
+ *     Device pointers must be CUDA device memory on the context's device.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the context's own
+ *     stream.  Calls whose outputs are host memory are synchronous; calls
+ *     with CDE_OUT_DEVICE only enqueue work on the stream.
+ *   - Invalid sizes or non-finite values give CDE_EINVAL; a bandwidth must be
+ *     finite and in [1e-12, 1e12].
+ *   - A context may be used from several host threads; calls are serialised
+ *     internally except the request queue, which is thread-safe by design.
+ */
+#ifndef CDE_H
+#define CDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cde_ctx cde_ctx;   /* opaque: device, streams, datasets */
+typedef int64_t cde_dataset;      /* handle of a device-resident dataset */
+
+typedef enum {
+    CDE_OK = 0,
+    CDE_EINVAL = 1,     /* bad argument */
+    CDE_ENOMEM = 2,     /* memory budget or device allocation refused */
+    CDE_ECUDA = 3,      /* CUDA runtime error (message has the CUDA text) */
+    CDE_EBUSY = 4,      /* request queue full */
+    CDE_ETIMEOUT = 5,   /* wait ran out, or a device-side bounded wait gave up */
+    CDE_ENOTFOUND = 6,  /* unknown dataset handle or ticket */
+    CDE_ECANCELED = 7   /* request cancelled before it ran */
+} cde_status;
+
+enum { CDE_OUT_DEVICE = 1,    /* output pointers are device memory; call is async */
+       CDE_IN_DEVICE = 2 };   /* input arrays (x, y, queries, grids) are device memory */
+
+/* Library version string (static storage). */
+const char *cde_version(void);
+
+/* Message of the last failed call on this host thread (static/thread storage,
+ * valid until the next call on the same thread). */
+const char *cde_last_error(void);
+
+/* Create a context on CUDA device `device`.  `mem_budget_bytes` caps the
+ * device memory held by resident datasets and admitted serving jobs
+ * (0 = 90% of the device's free memory).  *ctx receives the context. */
+int cde_init(cde_ctx **ctx, int device, size_t mem_budget_bytes);
+
+/* Stop the request loop (if running), free every dataset and the context. */
+void cde_shutdown(cde_ctx *ctx);
+
+/*
+ * Make a dataset resident on the device.
+ *   x: N x d_x row-major float32; y: N float32 (host, or device with
+ *   CDE_IN_DEVICE in `flags`).  standardize != 0 centres each x dimension and
+ *   divides it by its sample standard deviation (ddof = 1), in FP64 (Sec. 4);
+ *   y is never scaled.  Requires N >= 2, d_x >= 1, finite values, and a
+ *   non-zero spread in every dimension when standardising.
+ *   Also computes, once, each row's nearest squared distance to any other row
+ *   in x and in y (the per-row shifts used to keep exp2 in range).
+ *   *out receives the handle.  Memory: about (d_x + 3) * 4 * N bytes.
+ */
+int cde_create_dataset(cde_ctx *ctx, const float *x, const float *y, int64_t N, int d_x,
+                       int standardize, int flags, cde_dataset *out);
+
+/* Release a dataset's device memory.  CDE_ENOTFOUND for an unknown handle. */
+int cde_destroy_dataset(cde_ctx *ctx, cde_dataset ds);
+
+/* Size, dimension and (when standardised) per-dimension mean and sd of a
+ * dataset; mean/sd may be NULL, otherwise arrays of d_x doubles. */
+int cde_dataset_info(cde_ctx *ctx, cde_dataset ds, int64_t *N, int *d_x, double *mean,
+                     double *sd);
+
+/*
+ * Exact LOO log-likelihood over a bandwidth grid (Eq. 3 and Sec. 3.2),
+ * every pair (j, i != j) evaluated once for all G1 x G2 bandwidth pairs.
+ *   h1[G1], h2[G2]: host arrays of bandwidths (any order, G1,G2 >= 1).
+ *   L_cond_out, L_eq3_out: G1 x G2 row-major (h1 major) doubles; either may be
+ *   NULL.  Host memory unless flags has CDE_OUT_DEVICE.
+ * Numerics: pair sums in FP32 with per-row shifts (exp2 on the SFU),
+ * exact joint-shift recomputation of any cell whose shifted numerator falls
+ * below 2^-40, log-ratio and the sum over j in FP64 in a fixed order (the
+ * result is bitwise reproducible).
+ */
+int cde_loo_loglik(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const double *h2,
+                   int G2, double *L_cond_out, double *L_eq3_out, int flags, void *stream);
+
+/*
+ * Per-row terms ell_j(k,l) = ln(A_j/B_j) for a list of rows (Eq. 1 at the
+ * left-out point), for checking full-size runs row by row.
+ *   rows[n_rows]: host int64 row indices in [0, N); ell_out: n_rows x G1 x G2
+ *   doubles (host).
+ */
+int cde_loo_rows(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const double *h2,
+                 int G2, const int64_t *rows, int64_t n_rows, double *ell_out, void *stream);
+
+/*
+ * L_cond and its gradient with respect to (ln h1, ln h2) at one bandwidth
+ * pair (derivative of the Sec. 3.2 sums for the Gaussian kernel):
+ *   dL/dln h1 = sum_j (E_Aj[|dx|^2] - E_Bj[|dx|^2]) / h1^2,
+ *   dL/dln h2 = sum_j (E_Aj[dy^2] / h2^2 - 1),
+ * E_Aj weighting i by K_h1 K_h2 and E_Bj by K_h1.
+ *   out3 = {L_cond, dL/dln h1, dL/dln h2} (host, or device with CDE_OUT_DEVICE).
+ */
+int cde_loo_grad(cde_ctx *ctx, cde_dataset ds, double h1, double h2, double *out3, int flags,
+                 void *stream);
+
+/*
+ * Conditional density fhat(y|x) of Eq. 1 (all N points, no leave-one-out) at
+ * Q query points and a G_y-point y grid.
+ *   xq: Q x d_x row-major float32 in the dataset's ORIGINAL units (the
+ *   dataset's standardisation is applied to the queries); ygrid: G_y float32;
+ *   f_out: Q x G_y float32.  CDE_IN_DEVICE: xq and ygrid are device memory;
+ *   CDE_OUT_DEVICE: f_out is device memory.  Q >= 0 (Q = 0 is a no-op).
+ */
+int cde_density(cde_ctx *ctx, cde_dataset ds, double h1, double h2, const float *xq, int64_t Q,
+                const float *ygrid, int G_y, float *f_out, int flags, void *stream);
+
+/*
+ * Many datasets in one persistent launch inside a captured CUDA graph.
+ *   n datasets ds[n]; per dataset b: h1[b] (G1[b] doubles), h2[b] (G2[b]
+ *   doubles), outputs L_cond_out[b] / L_eq3_out[b] (G1[b] x G2[b] doubles, host;
+ *   either array of pointers, or an entry, may be NULL).  Every G must be
+ *   <= 32.  The result of each dataset is bitwise identical to
+ *   cde_loo_loglik on that dataset alone.
+ */
+int cde_loo_loglik_batch(cde_ctx *ctx, int n, const cde_dataset *ds, const double *const *h1,
+                         const int *G1, const double *const *h2, const int *G2,
+                         double *const *L_cond_out, double *const *L_eq3_out, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Request queue (continuous batching of density and selection jobs)   */
+/* ------------------------------------------------------------------ */
+enum { CDE_REQ_DENSITY = 0, CDE_REQ_SELECT = 1 };
+
+typedef struct {
+    int kind;              /* CDE_REQ_DENSITY or CDE_REQ_SELECT */
+    cde_dataset ds;
+    /* density: bandwidths, queries (host, Q x d_x, original units), y grid, output */
+    double h1, h2;
+    const float *xq;
+    int64_t Q;
+    const float *ygrid;
+    int G_y;
+    float *f_out;          /* Q x G_y, host, written when the ticket completes */
+    /* selection: a G1 x G2 grid search followed by n_steps gradient-ascent
+     * steps in (ln h1, ln h2) from the best grid cell (step size `lr`). */
+    const double *h1_grid;
+    int G1;
+    const double *h2_grid;
+    int G2;
+    int n_steps;
+    double lr;
+    double *sel_out;       /* 4 doubles: best h1, best h2, L at best, L of the grid best */
+    double *L_grid_out;    /* optional G1 x G2 L_cond of the grid (host) */
+} cde_request;
+
+typedef struct {
+    int n_streams;          /* concurrent jobs on the device (default 4) */
+    int queue_capacity;     /* pending requests before cde_submit returns CDE_EBUSY */
+    size_t job_mem_budget;  /* device bytes admitted jobs may hold at once (0 = ctx budget) */
+} cde_server_config;
+
+/* Start the request loop (a native scheduler thread).  cfg may be NULL. */
+int cde_server_start(cde_ctx *ctx, const cde_server_config *cfg);
+/* Stop the loop after the running jobs finish; pending jobs are cancelled. */
+int cde_server_stop(cde_ctx *ctx);
+/* Queue a request; *ticket identifies it.  The request's buffers must stay
+ * valid until the ticket completes.  CDE_EBUSY when the queue is full. */
+int cde_submit(cde_ctx *ctx, const cde_request *req, int64_t *ticket);
+/* *done = 1 when finished (then *status holds the job's cde_status). */
+int cde_poll(cde_ctx *ctx, int64_t ticket, int *done, int *status);
+/* Wait up to timeout_us microseconds (< 0: no limit); CDE_ETIMEOUT if not
+ * finished.  On completion returns the job's own status.  Never hangs. */
+int cde_wait(cde_ctx *ctx, int64_t ticket, int64_t timeout_us);
+/* Cancel a queued request (CDE_OK) -- running ones finish normally. */
+int cde_cancel(cde_ctx *ctx, int64_t ticket);
+
+typedef struct {
+    int64_t completed, cancelled, failed;
+    double p50_ms, p99_ms, mean_ms;     /* submit -> completion latency */
+    double p50_density_ms, p99_density_ms, p50_select_ms, p99_select_ms;
+    double busy_s;                       /* wall time with >= 1 job on the device */
+    int64_t peak_concurrent;             /* most jobs admitted at once */
+} cde_server_stats;
+
+int cde_server_stats_get(cde_ctx *ctx, cde_server_stats *out);
+/* Forget collected latencies (counters restart at zero). */
+int cde_server_stats_reset(cde_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
+/* Measured pipe rates of this GPU (roofline denominators)             */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int sm_count;
+    double sm_clock_mhz;        /* clock seen by the micro-benchmark kernels */
+    double ffma_per_clk_sm;     /* FP32 FMA lanes per clock per SM */
+    double ex2_per_clk_sm;      /* MUFU ex2 results per clock per SM */
+    double ffma_tops;           /* FP32 FMA per second, whole GPU (1e12) */
+    double ex2_tops;            /* ex2 per second, whole GPU (1e12) */
+} cde_peaks;
+
+int cde_measure_peaks(cde_ctx *ctx, cde_peaks *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDE_H */

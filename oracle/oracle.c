@@ -96,6 +96,7 @@ typedef struct {
     double *lnA;              /* optional: n_rows x G1 x G2 */
     neumaier_t *blk_cond;     /* optional: n_blocks x G1 x G2 */
     neumaier_t *blk_lnA;      /* optional: n_blocks x G1 x G2 */
+    int64_t block;            /* rows per work item (fixed: sums do not depend on threads) */
     int64_t next_block;
     pthread_mutex_t mu;
 } rows_job_t;
@@ -137,9 +138,9 @@ static void *rows_worker(void *arg) {
         pthread_mutex_lock(&J->mu);
         int64_t b = J->next_block++;
         pthread_mutex_unlock(&J->mu);
-        int64_t r0 = b * ROW_BLOCK;
+        int64_t r0 = b * J->block;
         if (r0 >= J->n_rows) break;
-        int64_t r1 = r0 + ROW_BLOCK < J->n_rows ? r0 + ROW_BLOCK : J->n_rows;
+        int64_t r1 = r0 + J->block < J->n_rows ? r0 + J->block : J->n_rows;
         for (int64_t r = r0; r < r1; ++r) {
             int64_t j = J->rows ? J->rows[r] : r;
             row_terms(J, j, dx2, dy2, e, ell, lnA);
@@ -177,6 +178,7 @@ void oracle_loo_rows(const double *x, const double *y, int64_t N, int d,
     memset(&J, 0, sizeof(J));
     J.x = x; J.y = y; J.h1 = h1; J.h2 = h2; J.N = N; J.d = d; J.G1 = G1; J.G2 = G2;
     J.rows = rows; J.n_rows = n_rows; J.ell = ell; J.lnA = lnA;
+    J.block = 1;
     run_rows(&J, n_threads);
 }
 
@@ -190,6 +192,7 @@ void oracle_loo_grid(const double *x, const double *y, int64_t N, int d,
     memset(&J, 0, sizeof(J));
     J.x = x; J.y = y; J.h1 = h1; J.h2 = h2; J.N = N; J.d = d; J.G1 = G1; J.G2 = G2;
     J.rows = NULL; J.n_rows = N;
+    J.block = ROW_BLOCK;
     J.blk_cond = calloc((size_t)(n_blocks * G), sizeof(neumaier_t));
     J.blk_lnA = calloc((size_t)(n_blocks * G), sizeof(neumaier_t));
     run_rows(&J, n_threads);

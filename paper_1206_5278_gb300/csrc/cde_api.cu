@@ -1,0 +1,313 @@
+// C ABI: context, errors, datasets and the synchronous entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cde_internal.h"
+
+namespace cde {
+
+static thread_local std::string g_err;
+
+int set_error(int status, const std::string& msg) {
+    g_err = msg;
+    return status;
+}
+
+int cuda_error(cudaError_t e, const char* where) {
+    const int st = (e == cudaErrorMemoryAllocation) ? CDE_ENOMEM : CDE_ECUDA;
+    return set_error(st, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+std::shared_ptr<Dataset> find_dataset(cde_ctx* ctx, cde_dataset ds) {
+    std::lock_guard<std::mutex> g(ctx->ds_mu);
+    auto it = ctx->datasets.find(ds);
+    return it == ctx->datasets.end() ? nullptr : it->second;
+}
+
+cudaStream_t pick_stream(cde_ctx* ctx, void* s) {
+    return s ? reinterpret_cast<cudaStream_t>(s) : ctx->stream;
+}
+
+static bool bandwidth_ok(double h) { return std::isfinite(h) && h >= 1e-12 && h <= 1e12; }
+
+static int check_grid(const double* h, int G, const char* name) {
+    if (!h || G < 1) return set_error(CDE_EINVAL, std::string(name) + ": empty bandwidth grid");
+    for (int k = 0; k < G; ++k)
+        if (!bandwidth_ok(h[k]))
+            return set_error(CDE_EINVAL, std::string(name) + ": bandwidth must be finite in [1e-12, 1e12]");
+    return CDE_OK;
+}
+
+static void free_dataset(Dataset* D) {
+    cudaFree(D->xs);
+    cudaFree(D->y);
+    cudaFree(D->mx);
+    cudaFree(D->my);
+    D->xs = D->y = D->mx = D->my = nullptr;
+}
+
+__global__ void k_finite_check(const float* a, int64_t n, int* flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(a[i])) atomicOr(flag, 1);
+}
+
+}  // namespace cde
+
+using namespace cde;
+
+extern "C" {
+
+const char* cde_version(void) { return "cde-gb300 0.1 (sm_103a)"; }
+
+const char* cde_last_error(void) { return g_err.c_str(); }
+
+int cde_init(cde_ctx** out, int device, size_t budget) {
+    if (!out) return set_error(CDE_EINVAL, "cde_init: null output");
+    *out = nullptr;
+    int n = 0;
+    CDE_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return set_error(CDE_EINVAL, "cde_init: no such device");
+    CDE_CUDA(cudaSetDevice(device));
+    cudaDeviceProp p;
+    CDE_CUDA(cudaGetDeviceProperties(&p, device));
+    if (p.major * 10 + p.minor < 100)
+        return set_error(CDE_EINVAL, "cde_init: device is not a Blackwell-class GPU");
+    auto* ctx = new cde_ctx();
+    ctx->device = device;
+    ctx->sm_count = p.multiProcessorCount;
+    size_t fr = 0, tot = 0;
+    cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return cuda_error(e, "cudaMemGetInfo");
+    }
+    ctx->budget = budget ? budget : (size_t)(0.9 * (double)fr);
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, 64 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, 64 * sizeof(int));
+    if (e != cudaSuccess) {
+        if (ctx->stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return cuda_error(e, "cde_init");
+    }
+    *out = ctx;
+    return CDE_OK;
+}
+
+void cde_server_stop_internal(cde_ctx* ctx);
+
+void cde_shutdown(cde_ctx* ctx) {
+    if (!ctx) return;
+    cde_server_stop_internal(ctx);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    {
+        std::lock_guard<std::mutex> g(ctx->ds_mu);
+        for (auto& kv : ctx->datasets) free_dataset(kv.second.get());
+        ctx->datasets.clear();
+    }
+    cudaFree(ctx->d_err);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int cde_create_dataset(cde_ctx* ctx, const float* x, const float* y, int64_t N, int d, int standardize,
+                       int flags, cde_dataset* out) {
+    if (!ctx || !x || !y || !out) return set_error(CDE_EINVAL, "cde_create_dataset: null argument");
+    if (N < 2) return set_error(CDE_EINVAL, "cde_create_dataset: need N >= 2");
+    if (N > (int64_t)1 << 30) return set_error(CDE_EINVAL, "cde_create_dataset: N too large");
+    if (d < 1 || d > kMaxD) return set_error(CDE_EINVAL, "cde_create_dataset: d_x must be in [1, 64]");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    const bool in_dev = flags & CDE_IN_DEVICE;
+    if (!in_dev) {
+        for (int64_t i = 0; i < N * d; ++i)
+            if (!std::isfinite(x[i])) return set_error(CDE_EINVAL, "cde_create_dataset: non-finite x");
+        for (int64_t i = 0; i < N; ++i)
+            if (!std::isfinite(y[i])) return set_error(CDE_EINVAL, "cde_create_dataset: non-finite y");
+    }
+    auto D = std::make_shared<Dataset>();
+    D->N = N;
+    D->d = d;
+    D->Np = (N + kPadRows - 1) / kPadRows * kPadRows;
+    D->standardized = standardize ? 1 : 0;
+    D->bytes = (size_t)D->Np * (d + 1) * 4 + (size_t)N * 8;
+    if (ctx->used.load() + D->bytes > ctx->budget)
+        return set_error(CDE_ENOMEM, "cde_create_dataset: memory budget exceeded");
+    cudaStream_t st = ctx->stream;
+    float *dx = nullptr, *dy = nullptr;
+    double* dstats = nullptr;
+    int rc = CDE_OK;
+    auto fail = [&](int r) {
+        cudaStreamSynchronize(st);
+        if (!in_dev) {
+            cudaFree(dx);
+            cudaFree(dy);
+        }
+        cudaFree(dstats);
+        free_dataset(D.get());
+        return r;
+    };
+    cudaError_t e = cudaMalloc((void**)&D->xs, (size_t)D->Np * d * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&D->y, (size_t)D->Np * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&D->mx, (size_t)N * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&D->my, (size_t)N * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dstats, (size_t)2 * d * sizeof(double) + 64);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cde_create_dataset: cudaMalloc"));
+    if (in_dev) {
+        dx = const_cast<float*>(x);
+        dy = const_cast<float*>(y);
+        int* flag = ctx->d_err + 8;
+        e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+        if (e == cudaSuccess) {
+            k_finite_check<<<256, 256, 0, st>>>(dx, N * d, flag);
+            k_finite_check<<<64, 256, 0, st>>>(dy, N, flag);
+            int h = 0;
+            e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess && h) return fail(set_error(CDE_EINVAL, "cde_create_dataset: non-finite input"));
+        }
+        if (e != cudaSuccess) return fail(cuda_error(e, "cde_create_dataset: finite check"));
+    } else {
+        e = cudaMalloc((void**)&dx, (size_t)N * d * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&dy, (size_t)N * 4);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, (size_t)N * d * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, (size_t)N * 4, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail(cuda_error(e, "cde_create_dataset: upload"));
+    }
+    rc = pack_enqueue(*D, dx, dy, st, dstats);
+    if (rc != CDE_OK) return fail(rc);
+    std::vector<double> stats(2 * d, 0.0);
+    if (standardize) {
+        e = cudaMemcpyAsync(stats.data(), dstats, 2 * d * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(cuda_error(e, "cde_create_dataset: stats"));
+        for (int c = 0; c < d; ++c)
+            if (!(stats[2 * c + 1] > 0.0))
+                return fail(set_error(CDE_EINVAL, "cde_create_dataset: zero spread in a dimension"));
+    }
+    rc = nn_shift_enqueue(*D, st);
+    if (rc != CDE_OK) return fail(rc);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cde_create_dataset: kernels"));
+    if (!in_dev) {
+        cudaFree(dx);
+        cudaFree(dy);
+    }
+    cudaFree(dstats);
+    D->mean.resize(d);
+    D->sd.resize(d);
+    for (int c = 0; c < d; ++c) {
+        D->mean[c] = standardize ? stats[2 * c] : 0.0;
+        D->sd[c] = standardize ? stats[2 * c + 1] : 1.0;
+    }
+    ctx->used += D->bytes;
+    {
+        std::lock_guard<std::mutex> g(ctx->ds_mu);
+        D->id = ctx->next_id++;
+        ctx->datasets[D->id] = D;
+    }
+    *out = D->id;
+    return CDE_OK;
+}
+
+int cde_destroy_dataset(cde_ctx* ctx, cde_dataset ds) {
+    if (!ctx) return set_error(CDE_EINVAL, "cde_destroy_dataset: null context");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::shared_ptr<Dataset> D;
+    {
+        std::lock_guard<std::mutex> g(ctx->ds_mu);
+        auto it = ctx->datasets.find(ds);
+        if (it == ctx->datasets.end()) return set_error(CDE_ENOTFOUND, "cde_destroy_dataset: unknown dataset");
+        if (it->second->users.load() > 0) return set_error(CDE_EBUSY, "cde_destroy_dataset: dataset in use");
+        D = it->second;
+        ctx->datasets.erase(it);
+    }
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    cudaDeviceSynchronize();
+    free_dataset(D.get());
+    ctx->used -= D->bytes;
+    return CDE_OK;
+}
+
+int cde_dataset_info(cde_ctx* ctx, cde_dataset ds, int64_t* N, int* d, double* mean, double* sd) {
+    if (!ctx) return set_error(CDE_EINVAL, "cde_dataset_info: null context");
+    auto D = find_dataset(ctx, ds);
+    if (!D) return set_error(CDE_ENOTFOUND, "cde_dataset_info: unknown dataset");
+    if (N) *N = D->N;
+    if (d) *d = D->d;
+    for (int c = 0; c < D->d; ++c) {
+        if (mean) mean[c] = D->mean[c];
+        if (sd) sd[c] = D->sd[c];
+    }
+    return CDE_OK;
+}
+
+int cde_loo_loglik(cde_ctx* ctx, cde_dataset ds, const double* h1, int G1, const double* h2, int G2,
+                   double* Lc, double* Le, int flags, void* stream) {
+    if (!ctx) return set_error(CDE_EINVAL, "cde_loo_loglik: null context");
+    int rc = check_grid(h1, G1, "h1");
+    if (rc == CDE_OK) rc = check_grid(h2, G2, "h2");
+    if (rc != CDE_OK) return rc;
+    if ((int64_t)G1 * G2 > (1 << 24)) return set_error(CDE_EINVAL, "cde_loo_loglik: grid too large");
+    auto D = find_dataset(ctx, ds);
+    if (!D) return set_error(CDE_ENOTFOUND, "cde_loo_loglik: unknown dataset");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = pick_stream(ctx, stream);
+    if (flags & CDE_OUT_DEVICE) return loo_grid_enqueue(ctx, *D, h1, G1, h2, G2, nullptr, 0, Lc, Le, nullptr, st);
+    const size_t n = (size_t)G1 * G2;
+    double* dbuf = nullptr;
+    CDE_CUDA(cudaMallocAsync((void**)&dbuf, 2 * n * sizeof(double), st));
+    rc = loo_grid_enqueue(ctx, *D, h1, G1, h2, G2, nullptr, 0, Lc ? dbuf : nullptr, Le ? dbuf + n : nullptr,
+                          nullptr, st);
+    cudaError_t e = cudaSuccess;
+    if (rc == CDE_OK && Lc) e = cudaMemcpyAsync(Lc, dbuf, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (rc == CDE_OK && e == cudaSuccess && Le)
+        e = cudaMemcpyAsync(Le, dbuf + n, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(dbuf, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (rc != CDE_OK) return rc;
+    if (e != cudaSuccess) return cuda_error(e, "cde_loo_loglik: copy");
+    if (e2 != cudaSuccess) return cuda_error(e2, "cde_loo_loglik: kernels");
+    return CDE_OK;
+}
+
+int cde_loo_rows(cde_ctx* ctx, cde_dataset ds, const double* h1, int G1, const double* h2, int G2,
+                 const int64_t* rows, int64_t n_rows, double* ell_out, void* stream) {
+    if (!ctx || !rows || !ell_out) return set_error(CDE_EINVAL, "cde_loo_rows: null argument");
+    int rc = check_grid(h1, G1, "h1");
+    if (rc == CDE_OK) rc = check_grid(h2, G2, "h2");
+    if (rc != CDE_OK) return rc;
+    if (n_rows < 1) return set_error(CDE_EINVAL, "cde_loo_rows: need n_rows >= 1");
+    auto D = find_dataset(ctx, ds);
+    if (!D) return set_error(CDE_ENOTFOUND, "cde_loo_rows: unknown dataset");
+    for (int64_t r = 0; r < n_rows; ++r)
+        if (rows[r] < 0 || rows[r] >= D->N) return set_error(CDE_EINVAL, "cde_loo_rows: row out of range");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = pick_stream(ctx, stream);
+    const size_t n = (size_t)n_rows * G1 * G2;
+    int64_t* drows = nullptr;
+    double* dell = nullptr;
+    CDE_CUDA(cudaMallocAsync((void**)&drows, n_rows * sizeof(int64_t), st));
+    CDE_CUDA(cudaMallocAsync((void**)&dell, n * sizeof(double), st));
+    cudaError_t e = cudaMemcpyAsync(drows, rows, n_rows * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        rc = loo_grid_enqueue(ctx, *D, h1, G1, h2, G2, drows, n_rows, nullptr, nullptr, dell, st);
+    if (e == cudaSuccess && rc == CDE_OK)
+        e = cudaMemcpyAsync(ell_out, dell, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(drows, st);
+    cudaFreeAsync(dell, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (rc != CDE_OK) return rc;
+    if (e != cudaSuccess) return cuda_error(e, "cde_loo_rows");
+    if (e2 != cudaSuccess) return cuda_error(e2, "cde_loo_rows: kernels");
+    return CDE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/cde.h"
+
+namespace cde {
+
+// Thread-local error text; set_error returns the status for `return set_error(...)`.
+int set_error(int status, const std::string& msg);
+int cuda_error(cudaError_t e, const char* where);
+
+#define CDE_CUDA(call)                                         \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return ::cde::cuda_error(_e, #call); \
+    } while (0)
+
+// Device-resident dataset.  x is stored structure-of-arrays, x[c][i] at
+// xs[c * Np + i], padded to Np (a multiple of kPadRows) with zeros.
+struct Dataset {
+    int64_t id = 0;
+    int64_t N = 0, Np = 0;
+    int d = 0;
+    int standardized = 0;
+    float* xs = nullptr;   // [d][Np]
+    float* y = nullptr;    // [Np]
+    float* mx = nullptr;   // [N] min_{i!=j} |x_j - x_i|^2 (FP32, same formula as the kernels)
+    float* my = nullptr;   // [N] min_{i!=j} (y_j - y_i)^2
+    std::vector<double> mean, sd;  // per-dimension (identity when not standardised)
+    size_t bytes = 0;
+    std::atomic<int> users{0};     // jobs currently reading it (serving)
+};
+
+constexpr int kPadRows = 256;
+constexpr int kMaxD = 64;          // largest d_x handled by the SIMT kernels
+
+struct Server;  // serve.cpp
+
+}  // namespace cde
+
+struct cde_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0;
+    std::atomic<size_t> used{0};
+    cudaStream_t stream = nullptr;
+    std::recursive_mutex mu;  // serialises the synchronous API
+    std::mutex ds_mu;         // guards the dataset map
+    std::map<int64_t, std::shared_ptr<cde::Dataset>> datasets;
+    int64_t next_id = 1;
+    cde::Server* server = nullptr;
+    int* d_err = nullptr;     // device-side error flag (bounded waits, checks)
+};
+
+namespace cde {
+
+std::shared_ptr<Dataset> find_dataset(cde_ctx* ctx, cde_dataset ds);
+cudaStream_t pick_stream(cde_ctx* ctx, void* s);
+
+// ---- LOO grid (loo_grid.cu) ----
+// Enqueue the LOO score for one dataset over a bandwidth grid (any G1, G2):
+// d_Lc / d_Le are device arrays G1 x G2 (either may be null); d_ell_rows
+// (n_rows x G1 x G2) is written when rows != null.
+int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, const double* h2,
+                     int G2, const int64_t* d_rows, int64_t n_rows, double* d_Lc, double* d_Le,
+                     double* d_ell_rows, cudaStream_t st);
+
+// Nearest squared distances per row (cached at dataset creation).
+int nn_shift_enqueue(const Dataset& D, cudaStream_t st);
+
+// Standardise / pack raw row-major x into the SoA layout (device input).
+int pack_enqueue(Dataset& D, const float* d_x_rowmajor, const float* d_y, cudaStream_t st,
+                 double* d_stats);
+
+// ---- gradient (loo_grad.cu) ----
+int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, double* d_out3,
+                     cudaStream_t st);
+
+// ---- density (density.cu) ----
+int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const float* d_xq,
+                    int64_t Q, const float* d_yg, int G, float* d_f, cudaStream_t st);
+
+// ---- batched (batch.cu) ----
+struct BatchItem {
+    const Dataset* D;
+    const double* h1; int G1;
+    const double* h2; int G2;
+    double* d_Lc;   // device G1 x G2 (may be null)
+    double* d_Le;
+};
+int loo_batch_enqueue(cde_ctx* ctx, const std::vector<BatchItem>& items, cudaStream_t st,
+                      bool use_graph);
+
+// ---- peaks (peaks.cu) ----
+int measure_peaks(cde_ctx* ctx, cde_peaks* out);
+
+}  // namespace cde

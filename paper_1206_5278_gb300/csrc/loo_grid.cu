@@ -1,0 +1,293 @@
+// Exact all-pairs leave-one-out log-likelihood of the double-kernel
+// conditional density estimator over a grid of bandwidth pairs.
+//
+// Holmes, Gray & Isbell, Sec. 3.2: L = (1/n) sum_j ln A_j - ln(n-1) with
+// A_j = sum_{i!=j} K_h1(|x_j-x_i|) K_h2(y_j-y_i); the conditional score adds
+// B_j = sum_{i!=j} K_h1(|x_j-x_i|) and sums ln(A_j/B_j) (Eq. 1 at the left-out
+// point).  Every pair (j,i) is visited once for all G1 x G2 bandwidths:
+//
+//   u_i(k) = 2^{a1_k (m_x,j - |x_j-x_i|^2)},  w_i(l) = 2^{a2_l (m_y,j - (y_j-y_i)^2)},
+//   a1_k = log2(e)/(2 h1_k^2),  a2_l = log2(e)/(2 h2_l^2),
+//   At_j(k,l) = sum_i u_i(k) w_i(l),     Bt_j(k) = sum_i u_i(k),
+//
+// where m_x,j / m_y,j are row j's nearest squared distances in x and in y (so
+// the largest u and the largest w are exactly 1: no overflow, and B never
+// underflows).  The Gaussian factors are separable, so one squared distance
+// per pair feeds G1 + G2 exp2 (MUFU) and G1*G2 multiply-adds.  The epilogue
+// removes the shifts and the kernel constants in FP64:
+//   ell_j = ln2 (log2 At - log2 Bt - a2_l m_y,j) - ln(sqrt(2 pi) h2_l)
+//   ln A_j = ln2 (log2 At - a1_k m_x,j - a2_l m_y,j) - d ln(sqrt(2pi) h1_k) - ln(sqrt(2pi) h2_l)
+// A cell whose shifted numerator At falls below 2^-40 (the x-nearest and the
+// y-nearest neighbours differ and both factors are small) is recomputed
+// exactly with a joint shift anchored at argmin_i [a1 (dx2-m_x) + a2 (dy2-m_y)].
+//
+// Work decomposition: a CTA of 8 warps owns a "unit" of JW = 1024/(G1 G2)
+// rows; the 8 warps split the i range in interleaved chunks of IC points and
+// their FP32 partial sums are combined in fixed warp order.  Units are grouped
+// into tiles; each tile's FP64 partial scores go to their own slot and a final
+// kernel sums the slots in tile order, so results are bitwise reproducible and
+// independent of how tiles are scheduled.
+#include <cmath>
+#include <cstdio>
+
+#include "cde_internal.h"
+#include "loo_common.cuh"
+
+namespace cde {
+
+// --------------------------------------------------------------------------
+// Dataset packing: optional FP64 standardisation, row-major -> SoA.
+// --------------------------------------------------------------------------
+__global__ void k_col_stats(const float* __restrict__ x, int64_t N, int d, double* stats) {
+    // one CTA per column: mean, then sum of squared deviations (fixed-order tree)
+    __shared__ double red[1024];
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) s += (double)x[i * d + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double mean = red[0] / (double)N;
+    __syncthreads();
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        double t = (double)x[i * d + c] - mean;
+        v += t * t;
+    }
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        stats[2 * c] = mean;
+        stats[2 * c + 1] = sqrt(red[0] / (double)(N - 1));
+    }
+}
+
+__global__ void k_pack(const float* __restrict__ x, const float* __restrict__ y, int64_t N,
+                       int64_t Np, int d, const double* __restrict__ stats, int standardize,
+                       float* __restrict__ xs, float* __restrict__ ys) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Np) return;
+    for (int c = 0; c < d; ++c) {
+        float v = 0.f;
+        if (i < N) {
+            if (standardize)
+                v = (float)(((double)x[i * d + c] - stats[2 * c]) / stats[2 * c + 1]);
+            else
+                v = x[i * d + c];
+        }
+        xs[(int64_t)c * Np + i] = v;
+    }
+    ys[i] = i < N ? y[i] : 0.f;
+}
+
+int pack_enqueue(Dataset& D, const float* d_x, const float* d_y, cudaStream_t st, double* d_stats) {
+    if (D.standardized) {
+        k_col_stats<<<D.d, 1024, 0, st>>>(d_x, D.N, D.d, d_stats);
+        CDE_CUDA(cudaGetLastError());
+    }
+    const int64_t blocks = (D.Np + 255) / 256;
+    k_pack<<<(unsigned)blocks, 256, 0, st>>>(d_x, d_y, D.N, D.Np, D.d, d_stats, D.standardized,
+                                             D.xs, D.y);
+    CDE_CUDA(cudaGetLastError());
+    return CDE_OK;
+}
+
+// --------------------------------------------------------------------------
+// Per-row nearest squared distances (the exp2 shifts), O(N^2 d), computed
+// once per dataset.  Same FP32 distance formula as every pair kernel.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_nn_shift(const float* __restrict__ xs,
+                                                  const float* __restrict__ y, int64_t N,
+                                                  int64_t Np, int d, float* __restrict__ mx,
+                                                  float* __restrict__ my) {
+    extern __shared__ float sm[];  // [d + 1][256]
+    const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const bool vj = j < N;
+    float xj[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) xj[c] = (vj && c < d) ? xs[(int64_t)c * Np + j] : 0.f;
+    const float yj = vj ? y[j] : 0.f;
+    float bx = INFINITY, by = INFINITY;
+    for (int64_t i0 = 0; i0 < N; i0 += 256) {
+        __syncthreads();
+        for (int c = 0; c <= d; ++c) {
+            const float* src = c < d ? xs + (int64_t)c * Np : y;
+            sm[c * 256 + threadIdx.x] = src[i0 + threadIdx.x];  // i0+tid < Np
+        }
+        __syncthreads();
+        const int n = (int)min((int64_t)256, N - i0);
+        for (int t = 0; t < n; ++t) {
+            const int64_t i = i0 + t;
+            float dx2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < d) {
+                    float u = xj[c] - sm[c * 256 + t];
+                    dx2 = fmaf(u, u, dx2);
+                }
+            for (int c = 8; c < d; ++c) {
+                float u = xs[(int64_t)c * Np + j * vj] - sm[c * 256 + t];
+                dx2 = fmaf(u, u, dx2);
+            }
+            const float dy = yj - sm[d * 256 + t];
+            const float dy2 = dy * dy;
+            if (i != j) {
+                bx = fminf(bx, dx2);
+                by = fminf(by, dy2);
+            }
+        }
+    }
+    if (vj) {
+        mx[j] = bx;
+        my[j] = by;
+    }
+}
+
+int nn_shift_enqueue(const Dataset& D, cudaStream_t st) {
+    const int64_t blocks = (D.N + 255) / 256;
+    const size_t smem = (size_t)(D.d + 1) * 256 * sizeof(float);
+    if (smem > 48 * 1024)
+        CDE_CUDA(cudaFuncSetAttribute(k_nn_shift, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    k_nn_shift<<<(unsigned)blocks, 256, smem, st>>>(D.xs, D.y, D.N, D.Np, D.d, D.mx, D.my);
+    CDE_CUDA(cudaGetLastError());
+    return CDE_OK;
+}
+
+// --------------------------------------------------------------------------
+// Final fixed-order reduction of tile partials: one warp per grid cell.
+// --------------------------------------------------------------------------
+__global__ void k_loo_final(const double* __restrict__ part, int n_tiles, int GG, int G2T,
+                            int G1r, int G2r, int ld, double N, double* Lc, double* Le) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= GG) return;
+    const int k = warp / G2T, l = warp % G2T;
+    double sc = 0.0, se = 0.0;
+    for (int t = lane; t < n_tiles; t += 32) {
+        sc += part[(int64_t)t * 2 * GG + warp];
+        se += part[(int64_t)t * 2 * GG + GG + warp];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        se += __shfl_xor_sync(0xffffffffu, se, o);
+    }
+    if (lane == 0 && k < G1r && l < G2r) {
+        if (Lc) Lc[k * ld + l] = sc;
+        if (Le) Le[k * ld + l] = se / N - log(N - 1.0);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Host side
+// --------------------------------------------------------------------------
+template <int G1, int G2>
+static int launch_shape(const LooArgs& a, int grid, cudaStream_t st) {
+    using C = LooCfg<G1, G2>;
+    const size_t smem = C::smem_bytes(a.d);
+    static bool attr_set = false;  // per instantiation; guarded by the ctx lock
+    if (!attr_set) {
+        CDE_CUDA(cudaFuncSetAttribute(k_loo_grid<G1, G2>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)C::smem_bytes(kMaxD)));
+        attr_set = true;
+    }
+    k_loo_grid<G1, G2><<<grid, C::kThreads, smem, st>>>(a);
+    CDE_CUDA(cudaGetLastError());
+    return CDE_OK;
+}
+
+static int pad_g(int g) { return g <= 8 ? 8 : (g <= 16 ? 16 : 32); }
+
+int launch_loo_tile_kernel(int T1, int T2, const LooArgs& a, int grid, cudaStream_t st) {
+#define CDE_SHAPE(A, B) \
+    if (T1 == A && T2 == B) return launch_shape<A, B>(a, grid, st);
+    CDE_SHAPE(8, 8) CDE_SHAPE(8, 16) CDE_SHAPE(8, 32)
+    CDE_SHAPE(16, 8) CDE_SHAPE(16, 16) CDE_SHAPE(16, 32)
+    CDE_SHAPE(32, 8) CDE_SHAPE(32, 16) CDE_SHAPE(32, 32)
+#undef CDE_SHAPE
+    return set_error(CDE_EINVAL, "unsupported grid block shape");
+}
+
+void fill_loo_args(LooArgs& a, const Dataset& D, const double* h1, int g1, const double* h2,
+                   int g2, int T1, int T2) {
+    a.xs = D.xs; a.y = D.y; a.mx = D.mx; a.my = D.my;
+    a.N = D.N; a.Np = D.Np; a.d = D.d;
+    a.thresh = 0x1p-40f;
+    const double L2E = 1.4426950408889634074;      // log2(e)
+    const double LNS2PI = 0.91893853320467274178;  // ln sqrt(2 pi)
+    for (int k = 0; k < 32; ++k) {
+        const double h = h1[k < g1 ? k : g1 - 1];
+        a.a1[k] = (float)(L2E / (2.0 * h * h));
+        a.lam1[k] = D.d * (LNS2PI + log(h));
+    }
+    for (int l = 0; l < 32; ++l) {
+        const double h = h2[l < g2 ? l : g2 - 1];
+        a.a2[l] = (float)(L2E / (2.0 * h * h));
+        a.kap2[l] = LNS2PI + log(h);
+    }
+    (void)T1; (void)T2;
+}
+
+int loo_units_per_tile(int T1, int T2) {
+    const int JW = 1024 / (T1 * T2);
+    return JW >= 8 ? 1 : 8 / JW;
+}
+
+int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, const double* h2,
+                     int G2, const int64_t* d_rows, int64_t n_rows, double* d_Lc, double* d_Le,
+                     double* d_ell_rows, cudaStream_t st) {
+    if (!d_rows) n_rows = D.N;
+    for (int k0 = 0; k0 < G1; k0 += 32) {
+        const int g1 = G1 - k0 < 32 ? G1 - k0 : 32;
+        const int T1 = pad_g(g1);
+        for (int l0 = 0; l0 < G2; l0 += 32) {
+            const int g2 = G2 - l0 < 32 ? G2 - l0 : 32;
+            const int T2 = pad_g(g2);
+            LooArgs a{};
+            fill_loo_args(a, D, h1 + k0, g1, h2 + l0, g2, T1, T2);
+            const int JW = 1024 / (T1 * T2);
+            a.rows = d_rows;
+            a.n_rows = n_rows;
+            a.n_units = (int)((n_rows + JW - 1) / JW);
+            a.units_per_tile = loo_units_per_tile(T1, T2);
+            a.n_tiles = (a.n_units + a.units_per_tile - 1) / a.units_per_tile;
+            a.ell_rows = d_ell_rows ? d_ell_rows + (size_t)k0 * G2 + l0 : nullptr;
+            a.ell_ld_row = (int64_t)G1 * G2;
+            a.ell_ld_k = G2;
+            a.G1r = g1;
+            a.G2r = g2;
+            const size_t part_bytes = (size_t)a.n_tiles * 2 * T1 * T2 * sizeof(double);
+            double* part = nullptr;
+            CDE_CUDA(cudaMallocAsync((void**)&part, part_bytes, st));
+            a.part = part;
+            a.tile_base = 0;
+            a.work = nullptr;
+            const int grid = a.n_tiles < 2 * ctx->sm_count ? a.n_tiles : 2 * ctx->sm_count;
+            int rc = launch_loo_tile_kernel(T1, T2, a, grid, st);
+            if (rc != CDE_OK) {
+                cudaFreeAsync(part, st);
+                return rc;
+            }
+            if (d_Lc || d_Le) {
+                const int GG = T1 * T2;
+                k_loo_final<<<(GG * 32 + 255) / 256, 256, 0, st>>>(
+                    part, a.n_tiles, GG, T2, g1, g2, G2, (double)D.N,
+                    d_Lc ? d_Lc + (size_t)k0 * G2 + l0 : nullptr,
+                    d_Le ? d_Le + (size_t)k0 * G2 + l0 : nullptr);
+                CDE_CUDA(cudaGetLastError());
+            }
+            CDE_CUDA(cudaFreeAsync(part, st));
+        }
+    }
+    return CDE_OK;
+}
+
+}  // namespace cde

@@ -1,0 +1,188 @@
+"""GPU parity of the exact LOO score (libcde.so, C ABI) against the FP64 oracle.
+
+Tolerance (relative 1e-5 on each L(h1,h2)): a cell passes when
+|L_gpu - L_oracle| <= 1e-5 * sum_j |ell_j| (ell_j the oracle's per-row term),
+which equals 1e-5 |L| when all rows share a sign and stays meaningful when L
+is near zero.  Per-row terms must agree to 2e-5 (absolute, plus 2e-5 relative).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1206_5278_gb300 import cde, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from __graft_entry__ import build
+    build()
+    c = cde.cde_init(0)
+    yield c
+    cde.cde_shutdown(c)
+
+
+def _check_grid(Lc, Le, x, y, h1, h2, standardize=False):
+    ell, lnA = oracle.loo_rows(x, y, h1, h2, standardize_x=standardize)
+    ref_c = ell.sum(0)
+    N = x.shape[0]
+    ref_e = lnA.mean(0) - math.log(N - 1)
+    scale_c = np.abs(ell).sum(0)
+    scale_e = np.abs(lnA).mean(0)
+    err_c = np.abs(Lc - ref_c) / scale_c
+    err_e = np.abs(Le - ref_e) / scale_e
+    assert np.all(np.isfinite(Lc)) and np.all(np.isfinite(Le))
+    assert err_c.max() <= TOL, "L_cond max rel err %g" % err_c.max()
+    assert err_e.max() <= TOL, "L_eq3 max rel err %g" % err_e.max()
+    return err_c.max()
+
+
+def test_tiny_workload_full_grid(ctx):
+    """N=2000, d=1 tanh mixture, 8x8 grid on [0.5, 20]^2: every cell."""
+    w = synth.tiny_workload()
+    ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=False)
+    Lc, Le = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
+    _check_grid(Lc, Le, w.x, w.y, w.h1, w.h2)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+@pytest.mark.parametrize("G1,G2", [(8, 8), (8, 16), (8, 32), (16, 8), (16, 16), (16, 32),
+                                   (32, 8), (32, 16), (32, 32)])
+def test_all_tile_shapes(ctx, G1, G2):
+    x, y = synth.gmm_sine(700, 3, seed=G1 * 100 + G2)
+    h1 = synth.bandwidth_grid(0.05, 2.0, G1)
+    h2 = synth.bandwidth_grid(0.01, 1.0, G2)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    Lc, Le = cde.cde_loo_loglik(ctx, ds, h1, h2)
+    _check_grid(Lc, Le, x, y, h1, h2, standardize=True)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+@pytest.mark.parametrize("N,d,G1,G2", [(2, 1, 3, 2), (3, 2, 1, 1), (33, 1, 5, 7), (257, 3, 9, 17),
+                                       (1031, 9, 33, 5), (517, 12, 6, 40), (300, 64, 4, 4)])
+def test_ragged_sizes_and_grids(ctx, N, d, G1, G2):
+    """Ragged N (not a multiple of any tile), padded and split grids,
+    d above the register path (9, 12, 64)."""
+    x, y = synth.random_small(N, d, seed=N + d)
+    h1 = synth.bandwidth_grid(0.3, 3.0, G1) * math.sqrt(d)
+    h2 = synth.bandwidth_grid(0.1, 2.0, G2)
+    ds = cde.cde_create_dataset(ctx, x, y)
+    Lc, Le = cde.cde_loo_loglik(ctx, ds, h1, h2)
+    _check_grid(Lc, Le, x, y, h1, h2)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_two_points_closed_form(ctx):
+    x = np.array([[0.3], [1.7]], dtype=np.float32)
+    y = np.array([0.25, -1.5], dtype=np.float32)
+    h1 = np.array([0.01, 1.0, 100.0])
+    h2 = np.array([0.2, 3.0])
+    ds = cde.cde_create_dataset(ctx, x, y)
+    Lc, _ = cde.cde_loo_loglik(ctx, ds, h1, h2)
+    dy = float(y[0]) - float(y[1])
+    for l, h in enumerate(h2):
+        want = 2 * (-dy * dy / (2 * h * h) - math.log(math.sqrt(2 * math.pi) * h))
+        np.testing.assert_allclose(Lc[:, l], want, rtol=1e-6)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_small_bandwidth_corner_uses_exact_fallback(ctx):
+    """h1 -> 0 and tiny h2: separable shifts lose the range and the cells
+    are recomputed with the joint shift; results stay finite and exact."""
+    w = synth.tiny_workload(N=600)
+    h1 = np.array([1e-3, 0.02, 0.5])
+    h2 = np.array([1e-3, 0.05, 2.0])
+    ds = cde.cde_create_dataset(ctx, w.x, w.y)
+    Lc, Le = cde.cde_loo_loglik(ctx, ds, h1, h2)
+    _check_grid(Lc, Le, w.x, w.y, h1, h2)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_standardisation_matches_oracle(ctx):
+    x, y = synth.gmm_sine(3000, 5, seed=7)
+    x = x * np.array([1.0, 10.0, 0.1, 3.0, 100.0], dtype=np.float32) + 5.0
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    N, d, mean, sd = cde.cde_dataset_info(ctx, ds)
+    xd = x.astype(np.float64)
+    np.testing.assert_allclose(mean, xd.mean(0), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(sd, xd.std(0, ddof=1), rtol=1e-12)
+    h1 = synth.bandwidth_grid(0.05, 2.0, 16)
+    h2 = synth.bandwidth_grid(0.01, 1.0, 16)
+    Lc, Le = cde.cde_loo_loglik(ctx, ds, h1, h2)
+    _check_grid(Lc, Le, x, y, h1, h2, standardize=True)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_rows_match_oracle_and_sum(ctx):
+    w = synth.tiny_workload(N=1500)
+    ds = cde.cde_create_dataset(ctx, w.x, w.y)
+    rows = np.random.default_rng(0).choice(1500, 77, replace=False)
+    ell = cde.cde_loo_rows(ctx, ds, w.h1, w.h2, rows)
+    ref, _ = oracle.loo_rows(w.x, w.y, w.h1, w.h2, rows=rows)
+    np.testing.assert_allclose(ell, ref, rtol=2e-5, atol=2e-5)
+    all_rows = cde.cde_loo_rows(ctx, ds, w.h1, w.h2, np.arange(1500))
+    Lc, _ = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
+    np.testing.assert_allclose(all_rows.sum(0), Lc, rtol=1e-12)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_deterministic_and_device_io(ctx):
+    import torch
+    w = synth.tiny_workload(N=1200)
+    xt = torch.from_numpy(w.x).cuda()
+    yt = torch.from_numpy(w.y).cuda()
+    ds = cde.cde_create_dataset(ctx, xt, yt)
+    a, b = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
+    c, e = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
+    assert np.array_equal(a, c) and np.array_equal(b, e)
+    Lc = torch.empty(64, dtype=torch.float64, device="cuda")
+    Le = torch.empty(64, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+    cde.cde_loo_loglik(ctx, ds, w.h1, w.h2, Lc, Le, stream=s)
+    s.synchronize()
+    assert np.array_equal(Lc.cpu().numpy().reshape(8, 8), a)
+    assert np.array_equal(Le.cpu().numpy().reshape(8, 8), b)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_invalid_arguments(ctx):
+    x, y = synth.random_small(10, 2, 0)
+    with pytest.raises(cde.CdeError) as e:
+        cde.cde_create_dataset(ctx, x[:1], y[:1])
+    assert e.value.status == cde.CDE_EINVAL
+    bad = x.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(cde.CdeError):
+        cde.cde_create_dataset(ctx, bad, y)
+    with pytest.raises(cde.CdeError):
+        cde.cde_create_dataset(ctx, np.ones((10, 2), np.float32), y, standardize=True)
+    ds = cde.cde_create_dataset(ctx, x, y)
+    with pytest.raises(cde.CdeError):
+        cde.cde_loo_loglik(ctx, ds, [0.0], [1.0])
+    with pytest.raises(cde.CdeError):
+        cde.cde_loo_loglik(ctx, ds, [1.0], [np.inf])
+    with pytest.raises(cde.CdeError) as e:
+        cde.cde_loo_loglik(ctx, ds + 999, [1.0], [1.0])
+    assert e.value.status == cde.CDE_ENOTFOUND
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_scale_workload_sampled_rows(ctx):
+    """N=50000, d=5 standardised GMM, 32x32 grid (the benchmark's workload,
+    same launch): 48 sampled rows element-wise against the oracle, plus the
+    grid L equal to the sum of all per-row terms."""
+    w = synth.scale_workload()
+    ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True)
+    Lc, Le = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
+    assert np.all(np.isfinite(Lc)) and np.all(np.isfinite(Le))
+    rows = np.random.default_rng(1).choice(w.N, 48, replace=False)
+    ell = cde.cde_loo_rows(ctx, ds, w.h1, w.h2, rows)
+    ref, _ = oracle.loo_rows(w.x, w.y, w.h1, w.h2, rows=rows, standardize_x=True)
+    err = np.abs(ell - ref) / np.maximum(1.0, np.abs(ref))
+    assert err.max() <= 2e-5, "max per-row err %g" % err.max()
+    cde.cde_destroy_dataset(ctx, ds)
