@@ -40,7 +40,7 @@ struct LooCfg {
     static constexpr int PPL = IC * JW / 32;           // phase-1 pairs per lane
     static constexpr int NKQ = G1 / 4, NLQ = G2 / 8;   // phase-2 lane tile: 4 k x 8 l
     static constexpr int LPJ = NKQ * NLQ;              // lanes per row in phase 2
-    static constexpr int UCH = JW * G1 / 2;            // 16-B chunks of a u row (duplicated pairs)
+    static constexpr int UCH = JW * G1 / 4;            // 16-B chunks of a u row
     static constexpr int WCH = JW * G2 / 4;            // 16-B chunks of a w row
     static constexpr int UROW = UCH * 4 + 4;           // floats per u row (+16 B pad: no bank conflicts)
     static constexpr int WROW = WCH * 4 + 4;
@@ -50,7 +50,8 @@ struct LooCfg {
     static constexpr int BIG = BIG0 > 2048 ? BIG0 : 2048;  // also holds 1024 doubles
     static constexpr int NKL = GG >= 256 ? GG / 256 : 1;
     static_assert(LPJ * JW == 32, "lane tiling");
-    static_assert(UCH >= 16 && WCH >= 8, "row chunks");
+    static_assert(UCH >= 8 && WCH >= 8, "row chunks");
+    static constexpr int FB = 8;                       // flagged cells per fallback pass
 
     __host__ __device__ static int dpad(int d) { return (d * JW + 3) & ~3; }
     // float offsets of the per-unit area
@@ -63,8 +64,9 @@ struct LooCfg {
     __host__ __device__ static int off_btl(int d) { return off_yj(d) + 96; }   // JW*G1 doubles
     __host__ __device__ static int off_flag(int d) { return off_btl(d) + 2 * JW * G1; }  // 1024 int
     __host__ __device__ static int off_nflag(int d) { return off_flag(d) + 1024; }
-    __host__ __device__ static int off_red(int d) { return off_nflag(d) + 4; }   // 64 words
-    static size_t smem_bytes(int d) { return (size_t)(off_red(d) + 64) * sizeof(float); }
+    __host__ __device__ static int off_red(int d) { return off_nflag(d) + 4; }   // 8 warps x FB x 2 words
+    __host__ __device__ static int off_fb(int d) { return off_red(d) + 2 * kWarps * FB; }  // FB x 2 words
+    static size_t smem_bytes(int d) { return (size_t)(off_fb(d) + 2 * FB + 8) * sizeof(float); }
 };
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -88,13 +90,179 @@ struct CoefParam {
     __device__ __forceinline__ float a2(int l) const { return a.a2[l]; }
 };
 
+// Exact joint-shift recomputation of the flagged cells of one unit (whole
+// CTA).  For a cell (row j, k, l) with e_i = a1_k (dx2_i - m_x,j) + a2_l (dy2_i - m_y,j):
+// pass 1 finds i* = argmin e_i, pass 2 sums 2^{-(a1_k (dx2_i - dx2_*) + a2_l (dy2_i - dy2_*))},
+// so the dominant term is exactly 1 and log2 At = -e_* + log2 S.  Cells are
+// sorted, grouped by row and processed FB at a time, each pass visiting every
+// point once for the whole group.
+template <int G1, int G2, class Coef>
+__device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, float* sm, int nfl) {
+    using C = LooCfg<G1, G2>;
+    constexpr int GG = C::GG, FB = C::FB;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int d = a.d;
+    const int64_t N = a.N, Np = a.Np;
+    float* xj_s = sm + C::off_xj();
+    float* yj_s = sm + C::off_yj(d);
+    float* mx_s = sm + C::off_mx(d);
+    float* my_s = sm + C::off_my(d);
+    const long long* ji_s = reinterpret_cast<const long long*>(sm + C::off_ji(d));
+    int* flag_s = reinterpret_cast<int*>(sm + C::off_flag(d));
+    float* redf = sm + C::off_red(d);
+    int* redi = reinterpret_cast<int*>(sm + C::off_red(d) + C::kWarps * FB);
+    int* fbi = reinterpret_cast<int*>(sm + C::off_fb(d));
+    double* la2 = reinterpret_cast<double*>(sm);
+
+    // sort the (distinct) flagged cell ids in place: each thread ranks its entries
+    int mine[4], rank[4];
+    int nm = 0;
+    for (int q = tid; q < nfl; q += C::kThreads) {
+        const int v = flag_s[q];
+        int r = 0;
+        for (int t = 0; t < nfl; ++t) r += flag_s[t] < v;
+        mine[nm] = v;
+        rank[nm] = r;
+        ++nm;
+    }
+    __syncthreads();
+    for (int m = 0; m < nm; ++m) flag_s[rank[m]] = mine[m];
+    __syncthreads();
+
+    int q0 = 0;
+    while (q0 < nfl) {
+        // group: up to FB consecutive cells of the same row
+        const int jl = flag_s[q0] / GG;
+        int nb = 0;
+        while (nb < FB && q0 + nb < nfl && flag_s[q0 + nb] / GG == jl) ++nb;
+        float A[FB], B[FB];
+#pragma unroll
+        for (int f = 0; f < FB; ++f) {
+            const int c = flag_s[q0 + (f < nb ? f : 0)];
+            const int kl = c - jl * GG, k = kl / G2, l = kl - k * G2;
+            A[f] = cf.a1(k);
+            B[f] = cf.a2(l);
+        }
+        const float mxj = mx_s[jl], myj = my_s[jl], yj = yj_s[jl];
+        const long long j = ji_s[jl];
+        const float* xjr = xj_s + jl * d;
+        // pass 1: argmin over i of e_i for each cell
+        float best[FB];
+        int bi[FB];
+#pragma unroll
+        for (int f = 0; f < FB; ++f) {
+            best[f] = INFINITY;
+            bi[f] = 0x7fffffff;
+        }
+        for (int64_t i = tid; i < N; i += C::kThreads) {
+            if (i == j) continue;
+            float dx2 = 0.f;
+            for (int cc = 0; cc < d; ++cc) {
+                const float t = xjr[cc] - a.xs[(int64_t)cc * Np + i];
+                dx2 = fmaf(t, t, dx2);
+            }
+            const float dy = yj - a.y[i];
+            const float ex = dx2 - mxj, ey = dy * dy - myj;
+#pragma unroll
+            for (int f = 0; f < FB; ++f) {
+                const float e = A[f] * ex + B[f] * ey;
+                if (e < best[f]) {   // i increases: first minimum kept
+                    best[f] = e;
+                    bi[f] = (int)i;
+                }
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < FB; ++f) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best[f], o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi[f], o);
+                if (ob < best[f] || (ob == best[f] && oi < bi[f])) {
+                    best[f] = ob;
+                    bi[f] = oi;
+                }
+            }
+            if (lane == 0) {
+                redf[warp * FB + f] = best[f];
+                redi[warp * FB + f] = bi[f];
+            }
+        }
+        __syncthreads();
+        if (tid < FB) {
+            float b = redf[tid];
+            int ix = redi[tid];
+            for (int w = 1; w < C::kWarps; ++w) {
+                const float ob = redf[w * FB + tid];
+                const int oi = redi[w * FB + tid];
+                if (ob < b || (ob == b && oi < ix)) {
+                    b = ob;
+                    ix = oi;
+                }
+            }
+            if (ix < 0 || (int64_t)ix >= N) ix = (j == 0) ? 1 : 0;  // every e infinite
+            fbi[tid] = ix;
+        }
+        __syncthreads();
+        float dxs[FB], dys[FB];
+#pragma unroll
+        for (int f = 0; f < FB; ++f) {
+            const int is = fbi[f];
+            float t2 = 0.f;
+            for (int cc = 0; cc < d; ++cc) {
+                const float t = xjr[cc] - a.xs[(int64_t)cc * Np + is];
+                t2 = fmaf(t, t, t2);
+            }
+            dxs[f] = t2;
+            const float t = yj - a.y[is];
+            dys[f] = t * t;
+        }
+        // pass 2: shifted sums
+        float S[FB];
+#pragma unroll
+        for (int f = 0; f < FB; ++f) S[f] = 0.f;
+        for (int64_t i = tid; i < N; i += C::kThreads) {
+            if (i == j) continue;
+            float dx2 = 0.f;
+            for (int cc = 0; cc < d; ++cc) {
+                const float t = xjr[cc] - a.xs[(int64_t)cc * Np + i];
+                dx2 = fmaf(t, t, dx2);
+            }
+            const float dy = yj - a.y[i];
+            const float dy2 = dy * dy;
+#pragma unroll
+            for (int f = 0; f < FB; ++f)
+                S[f] += ex2_approx(-(A[f] * (dx2 - dxs[f]) + B[f] * (dy2 - dys[f])));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int f = 0; f < FB; ++f) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) S[f] += __shfl_xor_sync(0xffffffffu, S[f], o);
+            if (lane == 0) redf[warp * FB + f] = S[f];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int f = 0; f < FB; ++f)
+            if (tid == f && f < nb) {
+                float tot = 0.f;
+                for (int w = 0; w < C::kWarps; ++w) tot += redf[w * FB + f];
+                const double es = (double)A[f] * ((double)dxs[f] - (double)mxj) +
+                                  (double)B[f] * ((double)dys[f] - (double)myj);
+                la2[flag_s[q0 + f]] = -es + log2_wide(tot);
+            }
+        __syncthreads();
+        q0 += nb;
+    }
+}
+
 // One tile of units: units [tile*UPT, min(n_units, (tile+1)*UPT)).
 template <int G1, int G2, class Coef>
 __device__ __forceinline__ void loo_tile(const LooArgs& a, const Coef& cf, int tile, float* sm) {
     using C = LooCfg<G1, G2>;
     constexpr int JW = C::JW, IC = C::IC, PPL = C::PPL, NKQ = C::NKQ, NLQ = C::NLQ;
     constexpr int LPJ = C::LPJ, GG = C::GG, UROW = C::UROW, WROW = C::WROW;
-    constexpr int UH = C::UCH / 2, WH = C::WCH / 2;
+    constexpr int WH = C::WCH / 2;
     constexpr double LN2 = 0.69314718055994530942;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int d = a.d;
@@ -108,9 +276,6 @@ __device__ __forceinline__ void loo_tile(const LooArgs& a, const Coef& cf, int t
     double* btl_s = reinterpret_cast<double*>(sm + C::off_btl(d));
     int* flag_s = reinterpret_cast<int*>(sm + C::off_flag(d));
     int* nflag_s = reinterpret_cast<int*>(sm + C::off_nflag(d));
-    float* redf = sm + C::off_red(d);
-    int* redi = reinterpret_cast<int*>(sm + C::off_red(d) + 32);
-
     const int u_begin = tile * a.units_per_tile;
     const int u_end = min(a.n_units, u_begin + a.units_per_tile);
     const int64_t N = a.N, Np = a.Np;
@@ -213,8 +378,7 @@ __device__ __forceinline__ void loo_tile(const LooArgs& a, const Coef& cf, int t
                     const float u1 = ex2_approx(cf.a1(4 * kq + 1) * t1);
                     const float u2 = ex2_approx(cf.a1(4 * kq + 2) * t1);
                     const float u3 = ex2_approx(cf.a1(4 * kq + 3) * t1);
-                    *reinterpret_cast<float4*>(ub + 4 * kq) = make_float4(u0, u0, u1, u1);
-                    *reinterpret_cast<float4*>(ub + 4 * (UH + kq)) = make_float4(u2, u2, u3, u3);
+                    *reinterpret_cast<float4*>(ub + 4 * kq) = make_float4(u0, u1, u2, u3);
                 }
                 float* wb = wst + il * WROW + 4 * jl * NLQ;
 #pragma unroll
@@ -239,11 +403,10 @@ __device__ __forceinline__ void loo_tile(const LooArgs& a, const Coef& cf, int t
 #pragma unroll
             for (int ii = 0; ii < IC; ++ii) {
                 const float4 ua = *reinterpret_cast<const float4*>(urd + ii * UROW);
-                const float4 ub = *reinterpret_cast<const float4*>(urd + ii * UROW + 4 * UH);
                 const float4 wa = *reinterpret_cast<const float4*>(wrd + ii * WROW);
                 const float4 wb = *reinterpret_cast<const float4*>(wrd + ii * WROW + 4 * WH);
-                const float2 U[4] = {make_float2(ua.x, ua.y), make_float2(ua.z, ua.w),
-                                     make_float2(ub.x, ub.y), make_float2(ub.z, ub.w)};
+                const float2 U[4] = {make_float2(ua.x, ua.x), make_float2(ua.y, ua.y),
+                                     make_float2(ua.z, ua.z), make_float2(ua.w, ua.w)};
                 const float2 W[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w),
                                      make_float2(wb.x, wb.y), make_float2(wb.z, wb.w)};
 #pragma unroll
@@ -251,14 +414,17 @@ __device__ __forceinline__ void loo_tile(const LooArgs& a, const Coef& cf, int t
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc[p][q] = __ffma2_rn(U[p], W[q], acc[p][q]);
                 if constexpr (NLQ == 1) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) bt[q] += U[q].x;
+                    bt[0] += ua.x;
+                    bt[1] += ua.y;
+                    bt[2] += ua.z;
+                    bt[3] += ua.w;
                 } else if constexpr (NLQ == 2) {
-                    const float4 h = lq2 ? ub : ua;
-                    bt[0] += h.x;
-                    bt[1] += h.z;
+                    bt[0] += lq2 ? ua.z : ua.x;
+                    bt[1] += lq2 ? ua.w : ua.y;
                 } else {
-                    bt[0] += urd[ii * UROW + (lq2 >> 1) * 4 * UH + (lq2 & 1) * 2];
+                    const float lo = (lq2 & 1) ? ua.y : ua.x;
+                    const float hi = (lq2 & 1) ? ua.w : ua.z;
+                    bt[0] += (lq2 & 2) ? hi : lo;
                 }
             }
             __syncwarp();
@@ -314,89 +480,7 @@ __device__ __forceinline__ void loo_tile(const LooArgs& a, const Coef& cf, int t
         }
         __syncthreads();
         const int nfl = *nflag_s;
-        for (int q = 0; q < nfl; ++q) {
-            // exact joint-shift recomputation of one cell, whole CTA
-            const int c = flag_s[q];
-            const int jl = c / GG, kl = c - jl * GG, k = kl / G2, l = kl - k * G2;
-            const float A = cf.a1(k), B = cf.a2(l);
-            const float mxj = mx_s[jl], myj = my_s[jl], yj = yj_s[jl];
-            const long long j = ji_s[jl];
-            const float* xjr = xj_s + jl * d;
-            float best = INFINITY;
-            int bi = 0x7fffffff;
-            for (int64_t i = tid; i < N; i += C::kThreads) {
-                if (i == j) continue;
-                float dx2 = 0.f;
-                for (int cc = 0; cc < d; ++cc) {
-                    const float t = xjr[cc] - a.xs[(int64_t)cc * Np + i];
-                    dx2 = fmaf(t, t, dx2);
-                }
-                const float dy = yj - a.y[i];
-                const float e = A * (dx2 - mxj) + B * (dy * dy - myj);
-                if (e < best || (e == best && (int)i < bi)) {
-                    best = e;
-                    bi = (int)i;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob < best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            if (lane == 0) {
-                redf[warp] = best;
-                redi[warp] = bi;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                float b = redf[0];
-                int ix = redi[0];
-                for (int w = 1; w < C::kWarps; ++w)
-                    if (redf[w] < b || (redf[w] == b && redi[w] < ix)) {
-                        b = redf[w];
-                        ix = redi[w];
-                    }
-                redi[8] = ix;
-            }
-            __syncthreads();
-            int is = redi[8];
-            if (is < 0 || (int64_t)is >= N) is = (j == 0) ? 1 : 0;  // all e infinite: any i != j
-            float dxs = 0.f;
-            for (int cc = 0; cc < d; ++cc) {
-                const float t = xjr[cc] - a.xs[(int64_t)cc * Np + is];
-                dxs = fmaf(t, t, dxs);
-            }
-            const float dys0 = yj - a.y[is];
-            const float dys = dys0 * dys0;
-            float s = 0.f;
-            for (int64_t i = tid; i < N; i += C::kThreads) {
-                if (i == j) continue;
-                float dx2 = 0.f;
-                for (int cc = 0; cc < d; ++cc) {
-                    const float t = xjr[cc] - a.xs[(int64_t)cc * Np + i];
-                    dx2 = fmaf(t, t, dx2);
-                }
-                const float dy = yj - a.y[i];
-                s += ex2_approx(-(A * (dx2 - dxs) + B * (dy * dy - dys)));
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            __syncthreads();
-            if (lane == 0) redf[warp] = s;
-            __syncthreads();
-            if (tid == 0) {
-                float S = 0.f;
-                for (int w = 0; w < C::kWarps; ++w) S += redf[w];
-                const double es = (double)A * ((double)dxs - (double)mxj) +
-                                  (double)B * ((double)dys - (double)myj);
-                la2[c] = -es + log2_wide(S);
-            }
-            __syncthreads();
-        }
+        if (nfl > 0) loo_fallback<G1, G2>(a, cf, sm, nfl);
         __syncthreads();
 
         // ---- FP64 log-ratio; each thread owns whole grid cells (all rows of
@@ -439,12 +523,21 @@ __device__ __forceinline__ void loo_tile(const LooArgs& a, const Coef& cf, int t
     }
 }
 
+// Tiles are taken from a counter (a.work, zeroed before the launch) so that
+// units needing the exact fallback do not leave other SMs idle; each tile's
+// partial has its own slot, so the schedule does not change the result.
 template <int G1, int G2>
 __global__ void __launch_bounds__(256, 2) k_loo_grid(const LooArgs a) {
     extern __shared__ float4 sm4[];
+    __shared__ int next_tile;
     const CoefParam cf{a};
-    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x)
+    for (int t0 = blockIdx.x;; t0 += gridDim.x) {
+        if (threadIdx.x == 0) next_tile = a.work ? atomicAdd(a.work, 1) : t0;
+        __syncthreads();
+        const int t = next_tile;
+        if (t >= a.n_tiles) break;
         loo_tile<G1, G2>(a, cf, t, reinterpret_cast<float*>(sm4));
+    }
 }
 
 int launch_loo_tile_kernel(int T1, int T2, const LooArgs& a, int grid, cudaStream_t st);

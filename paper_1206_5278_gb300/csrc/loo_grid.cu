@@ -266,10 +266,11 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
             a.G2r = g2;
             const size_t part_bytes = (size_t)a.n_tiles * 2 * T1 * T2 * sizeof(double);
             double* part = nullptr;
-            CDE_CUDA(cudaMallocAsync((void**)&part, part_bytes, st));
+            CDE_CUDA(cudaMallocAsync((void**)&part, part_bytes + 256, st));
             a.part = part;
             a.tile_base = 0;
-            a.work = nullptr;
+            a.work = reinterpret_cast<int*>(reinterpret_cast<char*>(part) + part_bytes);
+            CDE_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));
             const int grid = a.n_tiles < 2 * ctx->sm_count ? a.n_tiles : 2 * ctx->sm_count;
             int rc = launch_loo_tile_kernel(T1, T2, a, grid, st);
             if (rc != CDE_OK) {
