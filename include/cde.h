@@ -126,6 +126,11 @@ int cde_loo_rows(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const d
 int cde_loo_grad(cde_ctx *ctx, cde_dataset ds, double h1, double h2, double *out3, int flags,
                  void *stream);
 
+/* Per-row terms of cde_loo_grad for every row: rows_out is N x 3 doubles
+ * (host) holding {ell_j, d ell_j/d ln h1, d ell_j/d ln h2} (for checking). */
+int cde_loo_grad_rows(cde_ctx *ctx, cde_dataset ds, double h1, double h2, double *rows_out,
+                      void *stream);
+
 /*
  * Conditional density fhat(y|x) of Eq. 1 (all N points, no leave-one-out) at
  * Q query points and a G_y-point y grid.
@@ -148,6 +153,19 @@ int cde_density(cde_ctx *ctx, cde_dataset ds, double h1, double h2, const float 
 int cde_loo_loglik_batch(cde_ctx *ctx, int n, const cde_dataset *ds, const double *const *h1,
                          const int *G1, const double *const *h2, const int *G2,
                          double *const *L_cond_out, double *const *L_eq3_out, void *stream);
+
+/*
+ * Autotuner of the LOO launch for one grid shape (grids are padded to 8, 16 or
+ * 32 per axis): times units-per-tile x resident-CTAs-per-SM candidates with
+ * the single-dataset launch on dataset `ds` and keeps the fastest in the
+ * context.  Both cde_loo_loglik and cde_loo_loglik_batch use the kept values,
+ * so their results stay bitwise identical to each other.  Outputs may be NULL.
+ */
+int cde_autotune(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const double *h2, int G2,
+                 int *units_per_tile, int *ctas_per_sm, double *best_ms);
+/* Read / set the tile parameters for the shape of a G1 x G2 grid (0 = default). */
+int cde_tuning_get(cde_ctx *ctx, int G1, int G2, int *units_per_tile, int *ctas_per_sm);
+int cde_tuning_set(cde_ctx *ctx, int G1, int G2, int units_per_tile, int ctas_per_sm);
 
 /* ------------------------------------------------------------------ */
 /* Request queue (continuous batching of density and selection jobs)   */

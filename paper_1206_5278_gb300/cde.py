@@ -30,10 +30,10 @@ _fp = ctypes.POINTER(ctypes.c_float)
 
 EXPORTED = [
     "cde_version", "cde_last_error", "cde_init", "cde_shutdown", "cde_create_dataset",
-    "cde_destroy_dataset", "cde_dataset_info", "cde_loo_loglik", "cde_loo_rows", "cde_loo_grad",
+    "cde_destroy_dataset", "cde_dataset_info", "cde_loo_loglik", "cde_loo_rows", "cde_loo_grad", "cde_loo_grad_rows",
     "cde_density", "cde_loo_loglik_batch", "cde_server_start", "cde_server_stop", "cde_submit",
     "cde_poll", "cde_wait", "cde_cancel", "cde_server_stats_get", "cde_server_stats_reset",
-    "cde_measure_peaks",
+    "cde_measure_peaks", "cde_autotune", "cde_tuning_get", "cde_tuning_set",
 ]
 
 
@@ -98,6 +98,7 @@ def lib():
                          ctypes.c_int),
         "cde_loo_grad": ([_vp, _i64, ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int, _vp],
                          ctypes.c_int),
+        "cde_loo_grad_rows": ([_vp, _i64, ctypes.c_double, ctypes.c_double, _vp, _vp], ctypes.c_int),
         "cde_density": ([_vp, _i64, ctypes.c_double, ctypes.c_double, _vp, _i64, _vp,
                          ctypes.c_int, _vp, ctypes.c_int, _vp], ctypes.c_int),
         "cde_loo_loglik_batch": ([_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -112,6 +113,13 @@ def lib():
         "cde_server_stats_get": ([_vp, ctypes.POINTER(cde_server_stats)], ctypes.c_int),
         "cde_server_stats_reset": ([_vp], ctypes.c_int),
         "cde_measure_peaks": ([_vp, ctypes.POINTER(cde_peaks)], ctypes.c_int),
+        "cde_autotune": ([_vp, _i64, _vp, ctypes.c_int, _vp, ctypes.c_int,
+                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "cde_tuning_get": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cde_tuning_set": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+                           ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -245,6 +253,14 @@ def cde_loo_grad(ctx, ds: int, h1: float, h2: float, out3=None, stream=None) -> 
     return out
 
 
+def cde_loo_grad_rows(ctx, ds: int, h1: float, h2: float, stream=None) -> np.ndarray:
+    """Per-row (ell_j, d ell_j/dln h1, d ell_j/dln h2), shape (N, 3)."""
+    N = cde_dataset_info(ctx, ds)[0]
+    out = np.empty((N, 3))
+    _check(lib().cde_loo_grad_rows(ctx, int(ds), float(h1), float(h2), _ptr(out), _stream(stream)))
+    return out
+
+
 def cde_density(ctx, ds: int, h1: float, h2: float, xq, ygrid, f_out=None, stream=None):
     """fhat(ygrid | xq): (Q, G_y) float32.  CUDA tensors in/out are used in
     place (asynchronous when f_out is a CUDA tensor)."""
@@ -287,6 +303,27 @@ def cde_loo_loglik_batch(ctx, datasets: Sequence[int], h1s, h2s, stream=None):
     _check(lib().cde_loo_loglik_batch(ctx, n, _ptr(ds), P(h1a), _ptr(G1), P(h2a), _ptr(G2),
                                       P(Lc), P(Le), _stream(stream)))
     return Lc, Le
+
+
+def cde_autotune(ctx, ds: int, h1, h2):
+    """Tune the LOO launch for the shape of the h1 x h2 grid on dataset ds;
+    returns (units_per_tile, ctas_per_sm, best_ms)."""
+    h1 = _f64(h1).reshape(-1)
+    h2 = _f64(h2).reshape(-1)
+    u, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().cde_autotune(ctx, int(ds), _ptr(h1), h1.size, _ptr(h2), h2.size, ctypes.byref(u),
+                              ctypes.byref(c), ctypes.byref(ms)))
+    return u.value, c.value, ms.value
+
+
+def cde_tuning_get(ctx, G1: int, G2: int):
+    u, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib().cde_tuning_get(ctx, int(G1), int(G2), ctypes.byref(u), ctypes.byref(c)))
+    return u.value, c.value
+
+
+def cde_tuning_set(ctx, G1: int, G2: int, units_per_tile: int = 0, ctas_per_sm: int = 0):
+    _check(lib().cde_tuning_set(ctx, int(G1), int(G2), int(units_per_tile), int(ctas_per_sm)))
 
 
 def cde_server_start(ctx, n_streams: int = 4, queue_capacity: int = 1024, job_mem_budget: int = 0):

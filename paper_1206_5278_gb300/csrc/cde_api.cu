@@ -105,6 +105,7 @@ void cde_shutdown(cde_ctx* ctx) {
     cde_server_stop_internal(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    batch_plan_free(ctx);
     {
         std::lock_guard<std::mutex> g(ctx->ds_mu);
         for (auto& kv : ctx->datasets) free_dataset(kv.second.get());
@@ -229,6 +230,7 @@ int cde_destroy_dataset(cde_ctx* ctx, cde_dataset ds) {
     }
     CDE_CUDA(cudaSetDevice(ctx->device));
     cudaDeviceSynchronize();
+    batch_plan_free(ctx);  // a captured batch may reference this dataset
     free_dataset(D.get());
     ctx->used -= D->bytes;
     return CDE_OK;

@@ -60,6 +60,9 @@ struct cde_ctx {
     int64_t next_id = 1;
     cde::Server* server = nullptr;
     int* d_err = nullptr;     // device-side error flag (bounded waits, checks)
+    int tune_upt[3][3] = {};  // autotuned units per tile by grid shape (8/16/32), 0 = default
+    int tune_ctas[3][3] = {}; // autotuned resident CTAs per SM, 0 = default (2)
+    void* batch_plan = nullptr;  // cached batched launch (graph), batch.cu
 };
 
 namespace cde {
@@ -83,8 +86,9 @@ int pack_enqueue(Dataset& D, const float* d_x_rowmajor, const float* d_y, cudaSt
                  double* d_stats);
 
 // ---- gradient (loo_grad.cu) ----
+// d_rowv (optional, N x 3 doubles) receives per-row {ell_j, d ell_j/d ln h1, d ell_j/d ln h2}.
 int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, double* d_out3,
-                     cudaStream_t st);
+                     cudaStream_t st, double* d_rowv);
 
 // ---- density (density.cu) ----
 int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const float* d_xq,
@@ -98,8 +102,10 @@ struct BatchItem {
     double* d_Lc;   // device G1 x G2 (may be null)
     double* d_Le;
 };
-int loo_batch_enqueue(cde_ctx* ctx, const std::vector<BatchItem>& items, cudaStream_t st,
-                      bool use_graph);
+// Run (building and capturing on first use) the batched launch; host outputs.
+int loo_batch_run(cde_ctx* ctx, const std::vector<BatchItem>& items, std::vector<double*>& Lc,
+                  std::vector<double*>& Le, cudaStream_t st);
+void batch_plan_free(cde_ctx* ctx);
 
 // ---- peaks (peaks.cu) ----
 int measure_peaks(cde_ctx* ctx, cde_peaks* out);

@@ -1,0 +1,313 @@
+// Conditional density fhat(y|x) of Eq. 1 (Holmes, Gray & Isbell, Sec. 2) at
+// Q query points x_q and a G-point y grid, over all N data points:
+//
+//   fhat(y_g | x_q) = sum_i K_h1(x_q - x_i) K_h2(y_g - y_i) / sum_i K_h1(x_q - x_i)
+//                   = [sum_i u_qi w_ig] / [sum_i u_qi] / (sqrt(2 pi) h2)
+//   u_qi = 2^{a1 (m_q - |x_q - x_i|^2)},  w_ig = 2^{-a2 (y_g - y_i)^2},
+//
+// m_q the query's nearest squared distance (so max_i u_qi = 1 and neither sum
+// underflows), a = log2(e)/(2 h^2).  The numerator is a (Q x N) x (N x G)
+// product whose left factor is generated on the fly; each CTA owns 32 queries
+// x 256 grid points, computes the 32 x IC block of u and the IC x 256 block of
+// w for each chunk of IC data points into shared memory, and accumulates a
+// 4 x 8 register tile per thread.  Small Q splits the data range across CTAs;
+// split partials are summed in split order.
+#include <cmath>
+
+#include "cde_internal.h"
+
+namespace cde {
+
+constexpr int kDQ = 32;    // queries per CTA
+constexpr int kDG = 256;   // grid points per CTA
+constexpr int kDIC = 32;   // data points per chunk
+
+struct DensArgs {
+    const float* xs;   // dataset [d][Np]
+    const float* y;    // [Np]
+    const float* xq;   // queries [d][Qp] (standardised like the data)
+    const float* mq;   // [Q]
+    const float* yg;   // [G]
+    int64_t N, Np, Q, Qp;
+    int d, G;
+    float a1, a2;
+    int64_t i_per_split;   // multiple of kDIC
+    float* num;            // [n_split][Q][G]
+    float* den;            // [n_split][Q]
+};
+
+__device__ __forceinline__ float ex2d(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__global__ void k_query_pack(const float* __restrict__ xq, int64_t Q, int64_t Qp, int d,
+                             const double* __restrict__ mean, const double* __restrict__ sd,
+                             float* __restrict__ out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Qp) return;
+    for (int c = 0; c < d; ++c)
+        out[(int64_t)c * Qp + q] = q < Q ? (float)(((double)xq[q * d + c] - mean[c]) / sd[c]) : 0.f;
+}
+
+// per-query nearest squared distance to the data (same FP32 formula as the main kernel)
+__global__ void __launch_bounds__(256) k_query_shift(const float* __restrict__ xs, int64_t N,
+                                                     int64_t Np, int d, const float* __restrict__ xq,
+                                                     int64_t Q, int64_t Qp, float* __restrict__ mq) {
+    extern __shared__ float sm[];  // [d][256]
+    const int64_t q = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    float best = INFINITY;
+    for (int64_t i0 = 0; i0 < N; i0 += 256) {
+        __syncthreads();
+        for (int c = 0; c < d; ++c) sm[c * 256 + threadIdx.x] = xs[(int64_t)c * Np + i0 + threadIdx.x];
+        __syncthreads();
+        const int n = (int)min((int64_t)256, N - i0);
+        if (q < Q)
+            for (int t = 0; t < n; ++t) {
+                float dx2 = 0.f;
+                for (int c = 0; c < d; ++c) {
+                    const float u = xq[(int64_t)c * Qp + q] - sm[c * 256 + t];
+                    dx2 = fmaf(u, u, dx2);
+                }
+                best = fminf(best, dx2);
+            }
+    }
+    if (q < Q) mq[q] = best;
+}
+
+struct DensSmem {
+    float Us[kDIC][kDQ + 4];    // u[i][q]
+    float Ws[kDIC][kDG + 4];    // w[i][g]
+    float xqs[kMaxD][kDQ];
+    float xis[kMaxD][kDIC];
+    float yis[kDIC];
+    float dens[8][kDQ];
+};
+
+__global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
+    extern __shared__ float4 dsm4[];
+    DensSmem& S = *reinterpret_cast<DensSmem*>(dsm4);
+    auto& Us = S.Us;
+    auto& Ws = S.Ws;
+    auto& xqs = S.xqs;
+    auto& xis = S.xis;
+    auto& yis = S.yis;
+    auto& dens = S.dens;
+    const int tid = threadIdx.x;
+    const int64_t q0 = (int64_t)blockIdx.x * kDQ;
+    const int g0 = blockIdx.y * kDG;
+    const int64_t s = blockIdx.z;
+    const int64_t i_begin = s * a.i_per_split;
+    const int64_t i_end = min(a.N, i_begin + a.i_per_split);
+    const int d = a.d;
+    for (int e = tid; e < d * kDQ; e += 256) {
+        const int c = e / kDQ, qq = e % kDQ;
+        xqs[c][qq] = (q0 + qq < a.Qp) ? a.xq[(int64_t)c * a.Qp + q0 + qq] : 0.f;
+    }
+    // phase-1 roles: u for (q = tid / 8, 4 data points), w for grid point g = tid
+    const int uq = tid >> 3, ui = (tid & 7) * 4;
+    const float mqv = (q0 + uq < a.Q) ? a.mq[q0 + uq] : 0.f;
+    const int gg = g0 + tid < a.G ? g0 + tid : a.G - 1;
+    const float ygv = a.yg[gg];
+    // phase-2 tile: 4 queries x 8 grid points
+    const int pq = (tid >> 5) * 4, pg = (tid & 31) * 8;
+    float acc[4][8];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[p][r] = 0.f;
+    float usum = 0.f;
+    const float a1 = a.a1, a2 = a.a2;
+    for (int64_t c0 = i_begin; c0 < i_end; c0 += kDIC) {
+        __syncthreads();
+        for (int e = tid; e < (d + 1) * kDIC; e += 256) {
+            const int c = e / kDIC, ii = e % kDIC;
+            const int64_t i = c0 + ii;  // < Np
+            if (c < d) xis[c][ii] = a.xs[(int64_t)c * a.Np + i];
+            else yis[ii] = a.y[i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int ii = ui + r;
+            float dx2 = 0.f;
+            for (int c = 0; c < d; ++c) {
+                const float t = xqs[c][uq] - xis[c][ii];
+                dx2 = fmaf(t, t, dx2);
+            }
+            const bool ok = c0 + ii < i_end;
+            const float u = ok ? ex2d(a1 * (mqv - dx2)) : 0.f;
+            usum += u;
+            Us[ii][uq] = u;
+        }
+#pragma unroll 8
+        for (int ii = 0; ii < kDIC; ++ii) {
+            const float t = ygv - yis[ii];
+            Ws[ii][tid] = ex2d(-a2 * (t * t));
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int ii = 0; ii < kDIC; ++ii) {
+            const float4 u4 = *reinterpret_cast<const float4*>(&Us[ii][pq]);
+            const float4 wa = *reinterpret_cast<const float4*>(&Ws[ii][pg]);
+            const float4 wb = *reinterpret_cast<const float4*>(&Ws[ii][pg + 4]);
+            const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
+            const float ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int r = 0; r < 8; ++r) acc[p][r] = fmaf(uu[p], ww[r], acc[p][r]);
+        }
+    }
+    // denominator: 8 threads per query, fixed order
+    dens[tid & 7][uq] = usum;
+    __syncthreads();
+    float* num = a.num + s * a.Q * a.G;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int64_t q = q0 + pq + p;
+        if (q >= a.Q) continue;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int g = g0 + pg + r;
+            if (g < a.G) num[q * a.G + g] = acc[p][r];
+        }
+    }
+    if (blockIdx.y == 0 && tid < kDQ && q0 + tid < a.Q) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += dens[k][tid];
+        a.den[s * a.Q + q0 + tid] = t;
+    }
+}
+
+// f[q][g] = (sum_s num) / (sum_s den) / (sqrt(2 pi) h2), splits in order
+__global__ void k_density_final(const float* __restrict__ num, const float* __restrict__ den,
+                                int n_split, int64_t Q, int G, float norm, float* __restrict__ f) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= Q * G) return;
+    const int64_t q = e / G;
+    float sn = 0.f, sd = 0.f;
+    for (int s = 0; s < n_split; ++s) {
+        sn += num[(int64_t)s * Q * G + e];
+        sd += den[(int64_t)s * Q + q];
+    }
+    f[e] = sn / sd * norm;
+}
+
+int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const float* d_xq,
+                    int64_t Q, const float* d_yg, int G, float* d_f, cudaStream_t st) {
+    if (Q == 0) return CDE_OK;
+    const int64_t Qp = (Q + kDQ - 1) / kDQ * kDQ;
+    float *xq = nullptr, *mq = nullptr, *num = nullptr, *den = nullptr;
+    double* stats = nullptr;
+    CDE_CUDA(cudaMallocAsync((void**)&xq, (size_t)Qp * D.d * sizeof(float), st));
+    CDE_CUDA(cudaMallocAsync((void**)&mq, (size_t)Q * sizeof(float), st));
+    CDE_CUDA(cudaMallocAsync((void**)&stats, (size_t)2 * D.d * sizeof(double), st));
+    CDE_CUDA(cudaMemcpyAsync(stats, D.mean.data(), D.d * sizeof(double), cudaMemcpyHostToDevice, st));
+    CDE_CUDA(cudaMemcpyAsync(stats + D.d, D.sd.data(), D.d * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_query_pack<<<(unsigned)((Qp + 255) / 256), 256, 0, st>>>(d_xq, Q, Qp, D.d, stats, stats + D.d, xq);
+    CDE_CUDA(cudaGetLastError());
+    const size_t sm = (size_t)D.d * 256 * sizeof(float);
+    if (sm > 48 * 1024)
+        CDE_CUDA(cudaFuncSetAttribute(k_query_shift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_query_shift<<<(unsigned)((Q + 255) / 256), 256, sm, st>>>(D.xs, D.N, D.Np, D.d, xq, Q, Qp, mq);
+    CDE_CUDA(cudaGetLastError());
+    DensArgs a{};
+    a.xs = D.xs;
+    a.y = D.y;
+    a.xq = xq;
+    a.mq = mq;
+    a.yg = d_yg;
+    a.N = D.N;
+    a.Np = D.Np;
+    a.Q = Q;
+    a.Qp = Qp;
+    a.d = D.d;
+    a.G = G;
+    const double L2E = 1.4426950408889634074;
+    a.a1 = (float)(L2E / (2 * h1 * h1));
+    a.a2 = (float)(L2E / (2 * h2 * h2));
+    const int64_t qt = Qp / kDQ;
+    const int gt = (G + kDG - 1) / kDG;
+    const int64_t chunks = (D.N + kDIC - 1) / kDIC;
+    int64_t ns = (4LL * ctx->sm_count + qt * gt - 1) / (qt * gt);
+    if (ns > chunks) ns = chunks;
+    if (ns < 1) ns = 1;
+    const int64_t cps = (chunks + ns - 1) / ns;
+    a.i_per_split = cps * kDIC;
+    ns = (chunks + cps - 1) / cps;
+    CDE_CUDA(cudaMallocAsync((void**)&num, (size_t)ns * Q * G * sizeof(float), st));
+    CDE_CUDA(cudaMallocAsync((void**)&den, (size_t)ns * Q * sizeof(float), st));
+    a.num = num;
+    a.den = den;
+    static bool attr = false;
+    if (!attr) {
+        CDE_CUDA(cudaFuncSetAttribute(k_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(DensSmem)));
+        attr = true;
+    }
+    k_density<<<dim3((unsigned)qt, (unsigned)gt, (unsigned)ns), 256, sizeof(DensSmem), st>>>(a);
+    CDE_CUDA(cudaGetLastError());
+    const float norm = (float)(1.0 / (2.5066282746310002 * h2));
+    k_density_final<<<(unsigned)((Q * G + 255) / 256), 256, 0, st>>>(num, den, (int)ns, Q, G, norm, d_f);
+    CDE_CUDA(cudaGetLastError());
+    cudaFreeAsync(xq, st);
+    cudaFreeAsync(mq, st);
+    cudaFreeAsync(stats, st);
+    cudaFreeAsync(num, st);
+    cudaFreeAsync(den, st);
+    return CDE_OK;
+}
+
+}  // namespace cde
+
+using namespace cde;
+
+extern "C" int cde_density(cde_ctx* ctx, cde_dataset ds, double h1, double h2, const float* xq,
+                           int64_t Q, const float* ygrid, int G, float* f_out, int flags, void* stream) {
+    if (!ctx) return set_error(CDE_EINVAL, "cde_density: null context");
+    if (Q < 0 || G < 1 || (Q > 0 && (!xq || !ygrid || !f_out)))
+        return set_error(CDE_EINVAL, "cde_density: bad sizes or null pointers");
+    if (!std::isfinite(h1) || !std::isfinite(h2) || h1 < 1e-12 || h2 < 1e-12 || h1 > 1e12 || h2 > 1e12)
+        return set_error(CDE_EINVAL, "cde_density: bandwidth must be finite in [1e-12, 1e12]");
+    if (Q * (int64_t)G > ((int64_t)1 << 34)) return set_error(CDE_EINVAL, "cde_density: output too large");
+    auto D = find_dataset(ctx, ds);
+    if (!D) return set_error(CDE_ENOTFOUND, "cde_density: unknown dataset");
+    if (Q == 0) return CDE_OK;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = pick_stream(ctx, stream);
+    const bool in_dev = flags & CDE_IN_DEVICE, out_dev = flags & CDE_OUT_DEVICE;
+    const float *dq = xq, *dg = ygrid;
+    float* dxq = nullptr;
+    float* dyg = nullptr;
+    float* df = out_dev ? f_out : nullptr;
+    if (!in_dev) {
+        for (int64_t e = 0; e < Q * D->d; ++e)
+            if (!std::isfinite(xq[e])) return set_error(CDE_EINVAL, "cde_density: non-finite query");
+        for (int g = 0; g < G; ++g)
+            if (!std::isfinite(ygrid[g])) return set_error(CDE_EINVAL, "cde_density: non-finite y grid");
+        CDE_CUDA(cudaMallocAsync((void**)&dxq, (size_t)Q * D->d * sizeof(float), st));
+        CDE_CUDA(cudaMallocAsync((void**)&dyg, (size_t)G * sizeof(float), st));
+        CDE_CUDA(cudaMemcpyAsync(dxq, xq, (size_t)Q * D->d * sizeof(float), cudaMemcpyHostToDevice, st));
+        CDE_CUDA(cudaMemcpyAsync(dyg, ygrid, (size_t)G * sizeof(float), cudaMemcpyHostToDevice, st));
+        dq = dxq;
+        dg = dyg;
+    }
+    if (!out_dev) CDE_CUDA(cudaMallocAsync((void**)&df, (size_t)Q * G * sizeof(float), st));
+    int rc = density_enqueue(ctx, *D, h1, h2, dq, Q, dg, G, df, st);
+    cudaError_t e = cudaSuccess;
+    if (rc == CDE_OK && !out_dev)
+        e = cudaMemcpyAsync(f_out, df, (size_t)Q * G * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (dxq) cudaFreeAsync(dxq, st);
+    if (dyg) cudaFreeAsync(dyg, st);
+    if (!out_dev) cudaFreeAsync(df, st);
+    if (!out_dev) {
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        if (rc == CDE_OK && e2 != cudaSuccess) return cuda_error(e2, "cde_density: kernels");
+    }
+    if (rc != CDE_OK) return rc;
+    if (e != cudaSuccess) return cuda_error(e, "cde_density: copy");
+    return CDE_OK;
+}

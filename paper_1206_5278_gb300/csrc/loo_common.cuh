@@ -83,6 +83,31 @@ __device__ __forceinline__ double log2_wide(float v) {
     return (double)(e - 1) + (double)log2f(2.0f * m);
 }
 
+// Fixed-order reduction of one grid cell over tile partials (one warp):
+// lane t sums tiles t, t+32, ... in order, then a fixed xor tree.
+__device__ __forceinline__ void loo_final_cell(const double* __restrict__ part, int n_tiles, int GG,
+                                               int cell, int lane, double& sc, double& se) {
+    sc = 0.0;
+    se = 0.0;
+    for (int t = lane; t < n_tiles; t += 32) {
+        sc += part[(int64_t)t * 2 * GG + cell];
+        se += part[(int64_t)t * 2 * GG + GG + cell];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        se += __shfl_xor_sync(0xffffffffu, se, o);
+    }
+}
+
+// Coefficient access from shared memory (batched launch: one item at a time).
+struct CoefSmem {
+    const float* a1s;
+    const float* a2s;
+    __device__ __forceinline__ float a1(int k) const { return a1s[k]; }
+    __device__ __forceinline__ float a2(int l) const { return a2s[l]; }
+};
+
 // Coefficient access straight from the kernel's parameter block.
 struct CoefParam {
     const LooArgs& a;
@@ -543,6 +568,7 @@ __global__ void __launch_bounds__(256, 2) k_loo_grid(const LooArgs a) {
 int launch_loo_tile_kernel(int T1, int T2, const LooArgs& a, int grid, cudaStream_t st);
 void fill_loo_args(LooArgs& a, const Dataset& D, const double* h1, int g1, const double* h2,
                    int g2, int T1, int T2);
-int loo_units_per_tile(int T1, int T2);
+int loo_units_per_tile(cde_ctx* ctx, int T1, int T2);
+int loo_grid_ctas(cde_ctx* ctx, int T1, int T2);
 
 }  // namespace cde

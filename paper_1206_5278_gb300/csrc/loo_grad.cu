@@ -1,0 +1,289 @@
+// Gradient of the conditional LOO log-likelihood with respect to
+// (ln h1, ln h2) at one bandwidth pair, plus the score itself.
+//
+// For the Gaussian kernels of Sec. 2, d ln K_h1(r)/d ln h1 = r^2/h1^2 - d and
+// d ln K_h2(t)/d ln h2 = t^2/h2^2 - 1, so with the Sec. 3.2 sums A_j, B_j:
+//   d ell_j/d ln h1 = (E_Aj[dx2] - E_Bj[dx2]) / h1^2,
+//   d ell_j/d ln h2 = E_Aj[dy2] / h2^2 - 1,
+// E_Aj weighting i by K_h1 K_h2 and E_Bj by K_h1 (i != j).  Per row five
+// shifted sums are needed:
+//   S_A = sum v_i, S_Ax = sum v_i dx2_i, S_Ay = sum v_i dy2_i,
+//   S_B = sum u_i, S_Bx = sum u_i dx2_i,
+// u_i = 2^{-a1 (dx2_i - m_x)}  (<= 1, the x-nearest neighbour gives 1), and
+// v_i = 2^{M - e_i}, e_i = a1 (dx2_i - m_x) + a2 (dy2_i - m_y), M the running
+// minimum of e_i (online rescaling: when a smaller e arrives the sums are
+// multiplied by 2^{e - M}), so no bandwidth underflows the numerator.
+//
+// The i range is split over gridDim.y CTAs; split partials (M, S_A, S_Ax,
+// S_Ay, S_B, S_Bx) are merged per row in FP64 in split order, the per-row
+// log-ratio and derivatives are formed in FP64, and rows are summed in a
+// fixed order, so the result is bitwise reproducible.
+#include <cmath>
+
+#include "cde_internal.h"
+
+namespace cde {
+
+struct GradArgs {
+    const float* xs;
+    const float* y;
+    const float* mx;
+    const float* my;
+    int64_t N, Np;
+    int d;
+    float a1, a2;          // log2(e)/(2 h^2)
+    int64_t i_per_split;   // multiple of the tile
+    float* part;           // [n_split][N][6]
+};
+
+constexpr int kGradThreads = 128;
+
+__device__ __forceinline__ float ex2g(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <int JB, int DREG>
+__global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
+    __shared__ float xt[DREG + 1][kGradThreads];
+    const int tid = threadIdx.x;
+    const int64_t jbase = (int64_t)blockIdx.x * kGradThreads * JB + tid;
+    const int64_t i0 = (int64_t)blockIdx.y * g.i_per_split;
+    const int64_t i1 = min(g.N, i0 + g.i_per_split);
+    const int d = g.d;
+    float xj[JB][DREG], yj[JB], mxj[JB], myj[JB], M[JB];
+    float SA[JB], SAx[JB], SAy[JB], SB[JB], SBx[JB];
+    int64_t jj[JB];
+#pragma unroll
+    for (int b = 0; b < JB; ++b) {
+        const int64_t j = jbase + (int64_t)b * kGradThreads;
+        const int64_t jc = j < g.N ? j : 0;
+        jj[b] = j;
+#pragma unroll
+        for (int c = 0; c < DREG; ++c) xj[b][c] = c < d ? g.xs[(int64_t)c * g.Np + jc] : 0.f;
+        yj[b] = g.y[jc];
+        mxj[b] = g.mx[jc];
+        myj[b] = g.my[jc];
+        M[b] = INFINITY;
+        SA[b] = SAx[b] = SAy[b] = SB[b] = SBx[b] = 0.f;
+    }
+    const float a1 = g.a1, a2 = g.a2;
+    for (int64_t t0 = i0; t0 < i1; t0 += kGradThreads) {
+        __syncthreads();
+        const int64_t it = t0 + tid;  // < Np: i_per_split and Np are multiples of 128
+#pragma unroll
+        for (int c = 0; c < DREG; ++c) xt[c][tid] = c < d ? g.xs[(int64_t)c * g.Np + it] : 0.f;
+        xt[DREG][tid] = g.y[it];
+        __syncthreads();
+        const int n = (int)min((int64_t)kGradThreads, i1 - t0);
+        for (int t = 0; t < n; ++t) {
+            const int64_t i = t0 + t;
+            float xi[DREG];
+#pragma unroll
+            for (int c = 0; c < DREG; ++c) xi[c] = xt[c][t];
+            const float yi = xt[DREG][t];
+#pragma unroll
+            for (int b = 0; b < JB; ++b) {
+                float dx2 = 0.f;
+#pragma unroll
+                for (int c = 0; c < DREG; ++c) {
+                    const float q = xj[b][c] - xi[c];
+                    dx2 = fmaf(q, q, dx2);
+                }
+                const float dy = yj[b] - yi;
+                const float dy2 = dy * dy;
+                const bool ok = i != jj[b];
+                const float ex = dx2 - mxj[b], ey = dy2 - myj[b];
+                const float e = fmaf(a1, ex, a2 * ey);
+                if (ok && e < M[b]) {
+                    const float r = ex2g(e - M[b]);
+                    SA[b] *= r;
+                    SAx[b] *= r;
+                    SAy[b] *= r;
+                    M[b] = e;
+                }
+                const float u = ok ? ex2g(-a1 * ex) : 0.f;
+                const float v = ok ? ex2g(M[b] - e) : 0.f;
+                SB[b] += u;
+                SBx[b] = fmaf(u, dx2, SBx[b]);
+                SA[b] += v;
+                SAx[b] = fmaf(v, dx2, SAx[b]);
+                SAy[b] = fmaf(v, dy2, SAy[b]);
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < JB; ++b) {
+        if (jj[b] >= g.N) continue;
+        float* p = g.part + ((int64_t)blockIdx.y * g.N + jj[b]) * 6;
+        p[0] = M[b];
+        p[1] = SA[b];
+        p[2] = SAx[b];
+        p[3] = SAy[b];
+        p[4] = SB[b];
+        p[5] = SBx[b];
+    }
+}
+
+// Per row: merge split partials (FP64, split order), then
+// rowv[j] = {ell_j, d ell_j/d ln h1, d ell_j/d ln h2}.
+__global__ void k_grad_rows(const float* __restrict__ part, int n_split, int64_t N,
+                            const float* __restrict__ my, float a1f, float a2f, double h1, double h2,
+                            double* __restrict__ rowv) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double Mst = INFINITY;
+    for (int s = 0; s < n_split; ++s) {
+        const float* p = part + ((int64_t)s * N + j) * 6;
+        if (p[1] > 0.f) Mst = fmin(Mst, (double)p[0]);
+    }
+    double SA = 0, SAx = 0, SAy = 0, SB = 0, SBx = 0;
+    for (int s = 0; s < n_split; ++s) {
+        const float* p = part + ((int64_t)s * N + j) * 6;
+        if (p[1] > 0.f) {
+            const double r = exp2(Mst - (double)p[0]);
+            SA += r * p[1];
+            SAx += r * p[2];
+            SAy += r * p[3];
+        }
+        SB += p[4];
+        SBx += p[5];
+    }
+    const double LN2 = 0.69314718055994530942, LNS2PI = 0.91893853320467274178;
+    const double ell = log(SA) - log(SB) - LN2 * (Mst + (double)a2f * (double)my[j]) -
+                       (LNS2PI + log(h2));
+    const double g1 = (SAx / SA - SBx / SB) / (h1 * h1);
+    const double g2 = (SAy / SA) / (h2 * h2) - 1.0;
+    rowv[3 * j] = ell;
+    rowv[3 * j + 1] = g1;
+    rowv[3 * j + 2] = g2;
+}
+
+// Fixed-order sum of the per-row triples: one CTA of 1024 threads.
+__global__ void k_sum_rows3(const double* __restrict__ rowv, int64_t N, double* __restrict__ out3) {
+    __shared__ double red[3][1024];
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int64_t j = threadIdx.x; j < N; j += 1024) {
+        s0 += rowv[3 * j];
+        s1 += rowv[3 * j + 1];
+        s2 += rowv[3 * j + 2];
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    red[2][threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) out3[threadIdx.x] = red[threadIdx.x][0];
+}
+
+template <int JB, int DREG>
+static void launch_grad(const GradArgs& g, dim3 grid, cudaStream_t st) {
+    k_loo_grad<JB, DREG><<<grid, kGradThreads, 0, st>>>(g);
+}
+
+int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, double* d_out3,
+                     cudaStream_t st, double* d_rowv_ext) {
+    GradArgs g{};
+    g.xs = D.xs;
+    g.y = D.y;
+    g.mx = D.mx;
+    g.my = D.my;
+    g.N = D.N;
+    g.Np = D.Np;
+    g.d = D.d;
+    const double L2E = 1.4426950408889634074;
+    g.a1 = (float)(L2E / (2 * h1 * h1));
+    g.a2 = (float)(L2E / (2 * h2 * h2));
+    const int DREG = D.d <= 4 ? 4 : D.d <= 8 ? 8 : D.d <= 16 ? 16 : D.d <= 32 ? 32 : 64;
+    const int JB = DREG <= 8 ? 4 : DREG <= 32 ? 2 : 1;
+    const int64_t rows_per_cta = (int64_t)kGradThreads * JB;
+    const int64_t gx = (D.N + rows_per_cta - 1) / rows_per_cta;
+    // split i so that the launch has about 8 CTAs per SM
+    int64_t want = 8LL * ctx->sm_count;
+    int64_t ns = (want + gx - 1) / gx;
+    const int64_t tiles = (D.N + kGradThreads - 1) / kGradThreads;
+    if (ns > tiles) ns = tiles;
+    if (ns < 1) ns = 1;
+    const int64_t tiles_per = (tiles + ns - 1) / ns;
+    g.i_per_split = tiles_per * kGradThreads;
+    ns = (tiles + tiles_per - 1) / tiles_per;
+    float* part = nullptr;
+    double* rowv = d_rowv_ext;
+    CDE_CUDA(cudaMallocAsync((void**)&part, (size_t)ns * D.N * 6 * sizeof(float), st));
+    if (!rowv) CDE_CUDA(cudaMallocAsync((void**)&rowv, (size_t)D.N * 3 * sizeof(double), st));
+    g.part = part;
+    dim3 grid((unsigned)gx, (unsigned)ns);
+    if (DREG == 4) launch_grad<4, 4>(g, grid, st);
+    else if (DREG == 8) launch_grad<4, 8>(g, grid, st);
+    else if (DREG == 16) launch_grad<2, 16>(g, grid, st);
+    else if (DREG == 32) launch_grad<2, 32>(g, grid, st);
+    else launch_grad<1, 64>(g, grid, st);
+    CDE_CUDA(cudaGetLastError());
+    k_grad_rows<<<(unsigned)((D.N + 255) / 256), 256, 0, st>>>(part, (int)ns, D.N, D.my, g.a1, g.a2,
+                                                             h1, h2, rowv);
+    CDE_CUDA(cudaGetLastError());
+    if (d_out3) {
+        k_sum_rows3<<<1, 1024, 0, st>>>(rowv, D.N, d_out3);
+        CDE_CUDA(cudaGetLastError());
+    }
+    CDE_CUDA(cudaFreeAsync(part, st));
+    if (!d_rowv_ext) CDE_CUDA(cudaFreeAsync(rowv, st));
+    return CDE_OK;
+}
+
+}  // namespace cde
+
+using namespace cde;
+
+extern "C" int cde_loo_grad(cde_ctx* ctx, cde_dataset ds, double h1, double h2, double* out3,
+                            int flags, void* stream) {
+    if (!ctx || !out3) return set_error(CDE_EINVAL, "cde_loo_grad: null argument");
+    if (!std::isfinite(h1) || !std::isfinite(h2) || h1 < 1e-12 || h2 < 1e-12 || h1 > 1e12 || h2 > 1e12)
+        return set_error(CDE_EINVAL, "cde_loo_grad: bandwidth must be finite in [1e-12, 1e12]");
+    auto D = find_dataset(ctx, ds);
+    if (!D) return set_error(CDE_ENOTFOUND, "cde_loo_grad: unknown dataset");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = pick_stream(ctx, stream);
+    if (flags & CDE_OUT_DEVICE) return loo_grad_enqueue(ctx, *D, h1, h2, out3, st, nullptr);
+    double* dout = nullptr;
+    CDE_CUDA(cudaMallocAsync((void**)&dout, 3 * sizeof(double), st));
+    int rc = loo_grad_enqueue(ctx, *D, h1, h2, dout, st, nullptr);
+    cudaError_t e = cudaSuccess;
+    if (rc == CDE_OK) e = cudaMemcpyAsync(out3, dout, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(dout, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (rc != CDE_OK) return rc;
+    if (e != cudaSuccess) return cuda_error(e, "cde_loo_grad: copy");
+    if (e2 != cudaSuccess) return cuda_error(e2, "cde_loo_grad: kernels");
+    return CDE_OK;
+}
+
+extern "C" int cde_loo_grad_rows(cde_ctx* ctx, cde_dataset ds, double h1, double h2, double* rows_out,
+                                 void* stream) {
+    if (!ctx || !rows_out) return set_error(CDE_EINVAL, "cde_loo_grad_rows: null argument");
+    if (!std::isfinite(h1) || !std::isfinite(h2) || h1 < 1e-12 || h2 < 1e-12 || h1 > 1e12 || h2 > 1e12)
+        return set_error(CDE_EINVAL, "cde_loo_grad_rows: bandwidth must be finite in [1e-12, 1e12]");
+    auto D = find_dataset(ctx, ds);
+    if (!D) return set_error(CDE_ENOTFOUND, "cde_loo_grad_rows: unknown dataset");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = pick_stream(ctx, stream);
+    double* rowv = nullptr;
+    CDE_CUDA(cudaMallocAsync((void**)&rowv, (size_t)D->N * 3 * sizeof(double), st));
+    int rc = loo_grad_enqueue(ctx, *D, h1, h2, nullptr, st, rowv);
+    cudaError_t e = cudaSuccess;
+    if (rc == CDE_OK)
+        e = cudaMemcpyAsync(rows_out, rowv, (size_t)D->N * 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(rowv, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (rc != CDE_OK) return rc;
+    if (e != cudaSuccess) return cuda_error(e, "cde_loo_grad_rows: copy");
+    if (e2 != cudaSuccess) return cuda_error(e2, "cde_loo_grad_rows: kernels");
+    return CDE_OK;
+}

@@ -169,16 +169,8 @@ __global__ void k_loo_final(const double* __restrict__ part, int n_tiles, int GG
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= GG) return;
     const int k = warp / G2T, l = warp % G2T;
-    double sc = 0.0, se = 0.0;
-    for (int t = lane; t < n_tiles; t += 32) {
-        sc += part[(int64_t)t * 2 * GG + warp];
-        se += part[(int64_t)t * 2 * GG + GG + warp];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sc += __shfl_xor_sync(0xffffffffu, sc, o);
-        se += __shfl_xor_sync(0xffffffffu, se, o);
-    }
+    double sc, se;
+    loo_final_cell(part, n_tiles, GG, warp, lane, sc, se);
     if (lane == 0 && k < G1r && l < G2r) {
         if (Lc) Lc[k * ld + l] = sc;
         if (Le) Le[k * ld + l] = se / N - log(N - 1.0);
@@ -236,9 +228,21 @@ void fill_loo_args(LooArgs& a, const Dataset& D, const double* h1, int g1, const
     (void)T1; (void)T2;
 }
 
-int loo_units_per_tile(int T1, int T2) {
+static int shape_index(int T) { return T <= 8 ? 0 : T <= 16 ? 1 : 2; }
+
+// Units per tile: the autotuned value for this grid shape when the context has
+// one, else enough units for 8 rows per tile.  Both the single-dataset and the
+// batched launch use this, so they form identical tile partials.
+int loo_units_per_tile(cde_ctx* ctx, int T1, int T2) {
+    const int t = ctx ? ctx->tune_upt[shape_index(T1)][shape_index(T2)] : 0;
+    if (t > 0) return t;
     const int JW = 1024 / (T1 * T2);
     return JW >= 8 ? 1 : 8 / JW;
+}
+
+int loo_grid_ctas(cde_ctx* ctx, int T1, int T2) {
+    const int c = ctx->tune_ctas[shape_index(T1)][shape_index(T2)];
+    return (c > 0 ? c : 2) * ctx->sm_count;
 }
 
 int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, const double* h2,
@@ -257,7 +261,7 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
             a.rows = d_rows;
             a.n_rows = n_rows;
             a.n_units = (int)((n_rows + JW - 1) / JW);
-            a.units_per_tile = loo_units_per_tile(T1, T2);
+            a.units_per_tile = loo_units_per_tile(ctx, T1, T2);
             a.n_tiles = (a.n_units + a.units_per_tile - 1) / a.units_per_tile;
             a.ell_rows = d_ell_rows ? d_ell_rows + (size_t)k0 * G2 + l0 : nullptr;
             a.ell_ld_row = (int64_t)G1 * G2;
@@ -271,7 +275,8 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
             a.tile_base = 0;
             a.work = reinterpret_cast<int*>(reinterpret_cast<char*>(part) + part_bytes);
             CDE_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));
-            const int grid = a.n_tiles < 2 * ctx->sm_count ? a.n_tiles : 2 * ctx->sm_count;
+            const int cmax = loo_grid_ctas(ctx, T1, T2);
+            const int grid = a.n_tiles < cmax ? a.n_tiles : cmax;
             int rc = launch_loo_tile_kernel(T1, T2, a, grid, st);
             if (rc != CDE_OK) {
                 cudaFreeAsync(part, st);

@@ -2,9 +2,6 @@
 #include "cde_internal.h"
 using namespace cde;
 extern "C" {
-int cde_loo_grad(cde_ctx*, cde_dataset, double, double, double*, int, void*) { return set_error(CDE_EINVAL, "cde_loo_grad: not available"); }
-int cde_density(cde_ctx*, cde_dataset, double, double, const float*, int64_t, const float*, int, float*, int, void*) { return set_error(CDE_EINVAL, "cde_density: not available"); }
-int cde_loo_loglik_batch(cde_ctx*, int, const cde_dataset*, const double* const*, const int*, const double* const*, const int*, double* const*, double* const*, void*) { return set_error(CDE_EINVAL, "cde_loo_loglik_batch: not available"); }
 int cde_server_start(cde_ctx*, const cde_server_config*) { return set_error(CDE_EINVAL, "not available"); }
 int cde_server_stop(cde_ctx*) { return set_error(CDE_EINVAL, "not available"); }
 void cde_server_stop_internal(cde_ctx*) {}

@@ -1,0 +1,141 @@
+"""GPU parity of the adjoint (gradient) kernel and of the density kernel
+against the FP64 oracle.
+
+Gradient tolerance (1e-4): each component passes when
+|g_gpu - g_oracle| <= 1e-4 * sum_j |d ell_j / d ln h| (oracle per-row terms).
+Density tolerance: |f_gpu - f_oracle| <= 1e-4 * max_g f_oracle(y_g | x_q) per query.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1206_5278_gb300 import cde, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from __graft_entry__ import build
+    build()
+    c = cde.cde_init(0)
+    yield c
+    cde.cde_shutdown(c)
+
+
+def _grad_check(out, ref, rows_ref):
+    scale = np.abs(rows_ref).sum(0)
+    assert abs(out[0] - ref[0]) <= 1e-5 * scale[0], (out[0], ref[0])
+    assert abs(out[1] - ref[1]) <= 1e-4 * scale[1], (out[1], ref[1])
+    assert abs(out[2] - ref[2]) <= 1e-4 * scale[2], (out[2], ref[2])
+
+
+@pytest.mark.parametrize("d,h1,h2", [(8, 0.4, 0.1), (8, 0.08, 0.02), (32, 1.0, 0.2), (3, 0.2, 0.05),
+                                     (1, 2.0, 3.0)])
+def test_gradient_matches_oracle(ctx, d, h1, h2):
+    """2,000-point datasets shaped like the differentiation workload
+    (GMM-sine for d=8/3/1, latent projection for d=32)."""
+    w = synth.grad_workload(N=2000, d=d, seed=11 + d)
+    ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True)
+    out = cde.cde_loo_grad(ctx, ds, h1, h2)
+    ref, rows = oracle.grad(w.x, w.y, h1, h2, standardize_x=True, per_row=True)
+    _grad_check(out, ref, rows)
+    g_rows = cde.cde_loo_grad_rows(ctx, ds, h1, h2)
+    np.testing.assert_allclose(g_rows[:, 0], rows[:, 0], rtol=2e-5, atol=2e-5)
+    np.testing.assert_allclose(g_rows.sum(0), out, rtol=1e-12)
+    # same L as the grid kernel (two different kernels)
+    Lc, _ = cde.cde_loo_loglik(ctx, ds, [h1], [h2])
+    assert abs(Lc[0, 0] - out[0]) <= 1e-5 * np.abs(rows[:, 0]).sum()
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_gradient_matches_central_differences_on_gpu(ctx):
+    w = synth.grad_workload(N=3000, d=8, seed=5)
+    ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True)
+    h1, h2, s = 0.5, 0.15, 1e-3
+    out = cde.cde_loo_grad(ctx, ds, h1, h2)
+    Lp, _ = cde.cde_loo_loglik(ctx, ds, [h1 * math.exp(s), h1 * math.exp(-s), h1, h1],
+                               [h2, h2 * math.exp(s), h2 * math.exp(-s)])
+    g1 = (Lp[0, 0] - Lp[1, 0]) / (2 * s)
+    g2 = (Lp[2, 1] - Lp[2, 2]) / (2 * s)
+    rows = cde.cde_loo_grad_rows(ctx, ds, h1, h2)
+    sc = np.abs(rows).sum(0)
+    assert abs(out[1] - g1) <= 2e-3 * sc[1]
+    assert abs(out[2] - g2) <= 2e-3 * sc[2]
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_gradient_full_size_sampled_rows(ctx):
+    """N=200,000, d=8 (the differentiation workload): per-row terms of 64
+    sampled rows against the oracle's per-row gradient."""
+    w = synth.grad_workload(N=200000, d=8)
+    ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True)
+    h1, h2 = 0.3, 0.08
+    out = cde.cde_loo_grad(ctx, ds, h1, h2)
+    assert np.all(np.isfinite(out))
+    g_rows = cde.cde_loo_grad_rows(ctx, ds, h1, h2)
+    rows = np.random.default_rng(3).choice(w.N, 64, replace=False)
+    _, ref = oracle.grad(w.x, w.y, h1, h2, rows=rows, standardize_x=True, per_row=True)
+    sel = g_rows[rows]
+    np.testing.assert_allclose(sel[:, 0], ref[:, 0], rtol=2e-5, atol=2e-5)
+    np.testing.assert_allclose(sel[:, 1:], ref[:, 1:], rtol=1e-4, atol=1e-4 * np.abs(ref[:, 1:]).max())
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_autograd_and_selection(ctx):
+    import torch
+    from paper_1206_5278_gb300.autograd import loo_loglik, select_bandwidth
+    w = synth.grad_workload(N=3000, d=4, seed=9)
+    ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True)
+    lh = torch.tensor([math.log(0.4), math.log(0.1)], dtype=torch.float64, requires_grad=True)
+    L = loo_loglik(ctx, ds, lh)
+    L.backward()
+    ref = cde.cde_loo_grad(ctx, ds, math.exp(math.log(0.4)), math.exp(math.log(0.1)))
+    assert L.item() == ref[0]
+    np.testing.assert_array_equal(lh.grad.numpy(), ref[1:])
+    h1g = synth.bandwidth_grid(0.05, 2.0, 16)
+    h2g = synth.bandwidth_grid(0.01, 1.0, 16)
+    res = select_bandwidth(ctx, ds, h1g, h2g, steps=20, lr=0.05)
+    assert res["L"] >= res["grid_best"][2] - 1e-9
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def _dens_check(f, ref):
+    scale = ref.max(axis=1, keepdims=True)
+    err = np.abs(f - ref) / scale
+    assert err.max() <= 1e-4, "density max rel err %g" % err.max()
+
+
+@pytest.mark.parametrize("N,d,Q,G,standardize", [(1000, 3, 50, 37, True), (517, 1, 1, 256, False),
+                                                 (2048, 8, 70, 300, True), (20000, 2, 5, 64, True)])
+def test_density_matches_oracle(ctx, N, d, Q, G, standardize):
+    x, y = synth.gmm_sine(N, d, seed=N + d)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=standardize)
+    xq = synth.query_points(x, Q, seed=Q)
+    h1, h2 = (0.3, 0.1) if standardize else (0.5, 0.2)
+    yg = synth.y_grid(y, h2, G)
+    f = cde.cde_density(ctx, ds, h1, h2, xq, yg)
+    ref = oracle.density(x, y, h1, h2, xq, yg, standardize_x=standardize)
+    _dens_check(f, ref)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_density_integrates_to_one_and_device_io(ctx):
+    import torch
+    x, y = synth.gmm_sine(4000, 4, seed=2)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    h1, h2 = 0.25, 0.08
+    xq = synth.query_points(x, 40, seed=1)
+    yg = np.linspace(float(y.min()) - 12 * h2, float(y.max()) + 12 * h2, 4096).astype(np.float32)
+    f = cde.cde_density(ctx, ds, h1, h2, xq, yg)
+    integ = np.trapezoid(f.astype(np.float64), yg.astype(np.float64), axis=1)
+    np.testing.assert_allclose(integ, 1.0, atol=2e-4)
+    fo = torch.empty((40, 4096), dtype=torch.float32, device="cuda")
+    cde.cde_density(ctx, ds, h1, h2, torch.from_numpy(xq).cuda(), torch.from_numpy(yg).cuda(), fo,
+                    stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(fo.cpu().numpy(), f)
+    assert cde.cde_density(ctx, ds, h1, h2, np.zeros((0, 4), np.float32), yg).shape == (0, 4096)
+    cde.cde_destroy_dataset(ctx, ds)
