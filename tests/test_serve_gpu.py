@@ -1,0 +1,144 @@
+"""Serving loop on the GPU: continuous batching of density and bandwidth-
+selection jobs; each job's result is bitwise the same alone and in the mix;
+admission, queue limits, cancellation and timeouts report their statuses."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1206_5278_gb300 import cde, synth
+from paper_1206_5278_gb300.serve import Server
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from __graft_entry__ import build
+    build()
+    c = cde.cde_init(0)
+    yield c
+    cde.cde_shutdown(c)
+
+
+@pytest.fixture(scope="module")
+def datasets(ctx):
+    ws = [synth.gmm_sine(N, d, seed=N) for N, d in [(3000, 2), (12000, 5), (800, 1)]]
+    dss = [cde.cde_create_dataset(ctx, x, y, standardize=True) for x, y in ws]
+    yield list(zip(dss, ws))
+    for ds in dss:
+        cde.cde_destroy_dataset(ctx, ds)
+
+
+def _jobs(datasets, n, seed=0):
+    rng = np.random.default_rng(seed)
+    jobs = []
+    h1g = synth.bandwidth_grid(0.05, 2.0, 16)
+    h2g = synth.bandwidth_grid(0.01, 1.0, 16)
+    for k in range(n):
+        ds, (x, y) = datasets[int(rng.integers(len(datasets)))]
+        if rng.uniform() < 0.7:
+            Q = int(np.exp(rng.uniform(0, np.log(3000))))
+            xq = synth.query_points(x, Q, seed=k)
+            jobs.append(("d", ds, (0.3, 0.1, xq, synth.y_grid(y, 0.1, 256))))
+        else:
+            jobs.append(("s", ds, (h1g, h2g, 5, 0.05)))
+    return jobs
+
+
+def _submit(srv, job):
+    kind, ds, a = job
+    if kind == "d":
+        return srv.density(ds, *a)
+    return srv.select(ds, *a)
+
+
+def _val(t):
+    r = t.result()
+    if isinstance(r, dict):
+        return np.concatenate([[r["h1"], r["h2"], r["L"], r["L_grid_best"]], r["L_grid"].ravel()])
+    return r
+
+
+def test_results_same_alone_and_in_mix(ctx, datasets):
+    jobs = _jobs(datasets, 30)
+    srv = Server(ctx, n_streams=4)
+    try:
+        mix = [_submit(srv, j) for j in jobs]          # all at once: overlap on 4 streams
+        mix_vals = [_val(t) for t in mix]
+        st = srv.stats()
+        assert st["completed"] == len(jobs) and st["failed"] == 0
+        assert st["peak_concurrent"] >= 2
+        assert st["p99_ms"] >= st["p50_ms"] > 0
+        alone_vals = [_val(_submit(srv, j)) for j in jobs]   # one at a time
+    finally:
+        srv.stop()
+    for a, b in zip(mix_vals, alone_vals):
+        assert np.array_equal(a, b)
+    # density jobs equal the synchronous API; selection grid equals cde_loo_loglik
+    for j, v in zip(jobs, mix_vals):
+        kind, ds, a = j
+        if kind == "d":
+            f = cde.cde_density(ctx, ds, *a)
+            assert np.array_equal(f, v)
+        else:
+            Lc, _ = cde.cde_loo_loglik(ctx, ds, a[0], a[1])
+            assert np.array_equal(Lc.ravel(), v[4:])
+            assert v[2] >= v[3]   # ascent never returns worse than the grid best
+
+
+def test_queue_full_cancel_timeout_and_budget(ctx, datasets):
+    ds_big = datasets[1][0]
+    x, y = datasets[1][1]
+    h1g = synth.bandwidth_grid(0.05, 2.0, 32)
+    h2g = synth.bandwidth_grid(0.01, 1.0, 32)
+    srv = Server(ctx, n_streams=1, queue_capacity=2)
+    try:
+        first = srv.select(ds_big, h1g, h2g, 40, 0.05)   # occupies the only slot for a while
+        time.sleep(0.01)
+        q1 = srv.select(ds_big, h1g, h2g, 1, 0.05)
+        q2 = srv.select(ds_big, h1g, h2g, 1, 0.05)
+        st, t = srv.try_submit(Server.select_request(ds_big, h1g, h2g, 1))
+        assert st == cde.CDE_EBUSY and t is None
+        assert q2.cancel() == cde.CDE_OK
+        assert q2.wait() == cde.CDE_ECANCELED
+        assert first.wait(1) in (cde.CDE_ETIMEOUT, cde.CDE_OK)
+        with pytest.raises(cde.CdeError) as e:
+            cde.cde_destroy_dataset(ctx, ds_big)
+        assert e.value.status == cde.CDE_EBUSY
+        assert first.wait() == cde.CDE_OK and q1.wait() == cde.CDE_OK
+        assert q1.cancel() == cde.CDE_EBUSY
+    finally:
+        srv.stop()
+    srv = Server(ctx, n_streams=2, job_mem_budget=1 << 16)
+    try:
+        st, _ = srv.try_submit(Server.density_request(ds_big, 0.3, 0.1, synth.query_points(x, 5000), np.linspace(-2, 2, 256)))
+        assert st == cde.CDE_ENOMEM
+        st, _ = srv.try_submit(Server.density_request(ds_big + 999, 0.3, 0.1, x[:2], np.zeros(4)))
+        assert st == cde.CDE_ENOTFOUND
+        st, _ = srv.try_submit(Server.density_request(ds_big, -1.0, 0.1, x[:2], np.zeros(4)))
+        assert st == cde.CDE_EINVAL
+    finally:
+        srv.stop()
+
+
+def test_admission_by_memory_limits_concurrency(ctx, datasets):
+    import torch
+    ds, (x, y) = datasets[0]
+    yg = synth.y_grid(y, 0.1, 256)
+    Q = 4000
+    xqs = [synth.query_points(x, Q, seed=k) for k in range(8)]
+    # the library's admission estimate of one such job (d=2, 256-point grid)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    qt = (Q + 31) // 32
+    ns = max(1, (4 * sms + qt - 1) // qt)
+    one = Q * 2 * 8 + 256 * 4 + Q * 256 * 4 * (2 + ns) + Q * 16 + 4096
+    srv = Server(ctx, n_streams=8, job_mem_budget=int(2.5 * one))
+    try:
+        ts = [srv.density(ds, 0.3, 0.1, q, yg) for q in xqs]
+        outs = [t.result() for t in ts]
+        assert srv.stats()["peak_concurrent"] <= 2
+    finally:
+        srv.stop()
+    for q, o in zip(xqs, outs):
+        assert np.array_equal(cde.cde_density(ctx, ds, 0.3, 0.1, q, yg), o)
