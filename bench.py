@@ -257,6 +257,199 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def _timed(fn, reps):
+    import torch
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    return np.array(ts)
+
+
+def _line(**kw):
+    base = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    base.update(kw)
+    print(json.dumps(base), flush=True)
+
+
+def run_tiny(args):
+    """N=2000 d=1 8x8 grid: per-call latency (host-timed, synchronous C-ABI call)."""
+    import torch
+    from paper_1206_5278_gb300 import cde, synth
+    w = synth.tiny_workload()
+    ctx = cde.cde_init(0)
+    ds = cde.cde_create_dataset(ctx, w.x, w.y)
+    for _ in range(max(3, args.warmup)):
+        cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
+    t = _timed(lambda: cde.cde_loo_loglik(ctx, ds, w.h1, w.h2), max(200, args.steps))
+    pe = w.N * w.N * 64
+    _line(workload=w.name, value=pe / float(np.median(t)), steps=len(t), warmup=args.warmup,
+          ms_per_step=1e3 * float(np.median(t)),
+          latency_ms={"p50": 1e3 * float(np.percentile(t, 50)), "p99": 1e3 * float(np.percentile(t, 99))},
+          config={"workload": w.name, "N": w.N, "d_x": 1, "G1": 8, "G2": 8,
+                  "timing": "host wall clock around the synchronous call (host outputs)"})
+    cde.cde_shutdown(ctx)
+
+
+def run_batch(args):
+    """256 datasets (N log-uniform [500, 20000], d in {1,2,4,8}, 16x16 grids):
+    one graph-captured persistent launch vs one launch per dataset."""
+    from paper_1206_5278_gb300 import cde, synth
+    ws = synth.batch_workloads(n_datasets=args.n_datasets)
+    ctx = cde.cde_init(0)
+    dss = [cde.cde_create_dataset(ctx, w.x, w.y, standardize=w.standardize) for w in ws]
+    h1s, h2s = [w.h1 for w in ws], [w.h2 for w in ws]
+    tune = None
+    if args.autotune:
+        big = int(np.argmax([w.N for w in ws]))
+        tune = cde.cde_autotune(ctx, dss[big], ws[big].h1, ws[big].h2)
+    for _ in range(max(1, args.warmup)):
+        cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s)
+    tb = _timed(lambda: cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s), args.steps)
+
+    def loop():
+        for ds, w in zip(dss, ws):
+            cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
+    loop()
+    tl = _timed(loop, max(2, args.steps // 2))
+    # bitwise check of the batch against the single launches
+    Lc, _ = cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s)
+    same = all(np.array_equal(Lc[b], cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)[0])
+               for b, (ds, w) in enumerate(zip(dss, ws)))
+    pe = sum(w.N * w.N * w.h1.size * w.h2.size for w in ws)
+    _line(workload="batch_%d_datasets_16x16" % len(ws), value=pe / float(np.median(tb)),
+          steps=len(tb), warmup=args.warmup, ms_per_step=1e3 * float(np.median(tb)),
+          latency_ms={"p50": 1e3 * float(np.percentile(tb, 50)), "p99": 1e3 * float(np.percentile(tb, 99))},
+          per_dataset_loop={"value": pe / float(np.median(tl)), "ms_per_step": 1e3 * float(np.median(tl))},
+          speedup_vs_loop=float(np.median(tl) / np.median(tb)), bitwise_equal_to_single=bool(same),
+          autotune=tune, gpu_launches=2,
+          config={"workload": "batch", "datasets": len(ws), "pair_evals": pe,
+                  "N_range": [min(w.N for w in ws), max(w.N for w in ws)],
+                  "timing": "host wall clock around the synchronous batched call (graph replay)"})
+    cde.cde_shutdown(ctx)
+
+
+def run_grad(args):
+    """N=200,000, d in {8, 32}: adjoint evaluations (pairs/s) and gradient
+    ascent vs the exhaustive 32x32 grid."""
+    from paper_1206_5278_gb300 import cde, synth
+    from paper_1206_5278_gb300.autograd import select_bandwidth
+    for d in (8, 32):
+        w = synth.grad_workload(N=args.N_grad, d=d)
+        ctx = cde.cde_init(0)
+        ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True)
+        h1, h2 = 0.5, 0.1
+        for _ in range(max(1, args.warmup)):
+            cde.cde_loo_grad(ctx, ds, h1, h2)
+        tg = _timed(lambda: cde.cde_loo_grad(ctx, ds, h1, h2), args.steps)
+        tgrid = _timed(lambda: cde.cde_loo_loglik(ctx, ds, w.h1, w.h2), 1)
+        Lgrid, _ = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
+        t0 = time.perf_counter()
+        res = select_bandwidth(ctx, ds, synth.bandwidth_grid(0.05, 2.0, 4), synth.bandwidth_grid(0.01, 1.0, 4),
+                               steps=args.ascent_steps, lr=0.1)
+        ta = time.perf_counter() - t0
+        pairs = w.N * w.N
+        _line(workload=w.name, metric="LOO-CV gradient pair-evals/s (N^2 per (h1,h2)) at 1e-4 rel err",
+              value=pairs / float(np.median(tg)), steps=len(tg), warmup=args.warmup,
+              ms_per_step=1e3 * float(np.median(tg)),
+              ascent={"steps": args.ascent_steps, "seconds": ta, "h1": res["h1"], "h2": res["h2"], "L": res["L"],
+                      "start": "best of a 4x4 grid"},
+              grid32={"seconds": float(tgrid[0]), "L_best": float(Lgrid.max()),
+                      "h1": float(w.h1[np.unravel_index(Lgrid.argmax(), Lgrid.shape)[0]]),
+                      "h2": float(w.h2[np.unravel_index(Lgrid.argmax(), Lgrid.shape)[1]])},
+              config={"workload": w.name, "N": w.N, "d_x": d, "h1": h1, "h2": h2})
+        cde.cde_shutdown(ctx)
+
+
+def run_serve(args):
+    """Poisson stream, 70% density jobs (Q log-uniform [1, Q_max] x 256-point y
+    grid), 30% selection jobs (16x16 grid + 20 Adam steps) over resident
+    datasets; capacity from sequential synchronous calls, then the stream at
+    50/80/95% of it through the request loop."""
+    from paper_1206_5278_gb300 import cde, synth
+    from paper_1206_5278_gb300.serve import Server
+    ws = synth.serving_datasets(n=args.serve_datasets, N_max=args.serve_N_max)
+    ctx = cde.cde_init(0)
+    dss = [cde.cde_create_dataset(ctx, w.x, w.y, standardize=True) for w in ws]
+    reqs = synth.poisson_requests(args.serve_jobs, 1.0, len(ws), Q_max=args.serve_Q_max)
+    h1g = synth.bandwidth_grid(0.05, 2.0, 16)
+    h2g = synth.bandwidth_grid(0.01, 1.0, 16)
+    payload = []
+    for r in reqs:
+        w = ws[r.dataset]
+        if r.kind == 0:
+            payload.append((0, dss[r.dataset], synth.query_points(w.x, r.Q, seed=r.seed), synth.y_grid(w.y, 0.1)))
+        else:
+            payload.append((1, dss[r.dataset], None, None))
+    # sequential plain launches (synchronous API, one job at a time)
+    from paper_1206_5278_gb300.autograd import select_bandwidth
+
+    def run_seq(p):
+        if p[0] == 0:
+            cde.cde_density(ctx, p[1], 0.3, 0.1, p[2], p[3])
+        else:
+            select_bandwidth(ctx, p[1], h1g, h2g, steps=20, lr=0.05)
+    run_seq(payload[0])
+    t0 = time.perf_counter()
+    seq_lat = []
+    for p in payload:
+        t1 = time.perf_counter()
+        run_seq(p)
+        seq_lat.append(time.perf_counter() - t1)
+    seq_s = time.perf_counter() - t0
+    cap = len(payload) / seq_s
+    loads = {}
+    srv = Server(ctx, n_streams=args.serve_streams)
+    try:
+        for frac in (0.5, 0.8, 0.95):
+            rate = frac * cap
+            gaps = np.random.default_rng(int(frac * 100)).exponential(1.0 / rate, len(payload))
+            srv.reset_stats()
+            tickets = []
+            t0 = time.perf_counter()
+            tnext = t0
+            for p, g in zip(payload, gaps):
+                tnext += g
+                while time.perf_counter() < tnext:
+                    time.sleep(min(0.0005, max(0.0, tnext - time.perf_counter())))
+                if p[0] == 0:
+                    tickets.append(srv.density(p[1], 0.3, 0.1, p[2], p[3]))
+                else:
+                    tickets.append(srv.select(p[1], h1g, h2g, 20, 0.05))
+            for t in tickets:
+                t.result()
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+            loads["%d%%" % int(frac * 100)] = {
+                "offered_jobs_per_s": rate, "jobs_per_s": len(payload) / wall,
+                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                "p50_density_ms": st["p50_density_ms"], "p99_density_ms": st["p99_density_ms"],
+                "p50_select_ms": st["p50_select_ms"], "p99_select_ms": st["p99_select_ms"],
+                "peak_concurrent": st["peak_concurrent"]}
+        # saturation: everything submitted at once
+        srv.reset_stats()
+        t0 = time.perf_counter()
+        tickets = [srv.density(p[1], 0.3, 0.1, p[2], p[3]) if p[0] == 0 else srv.select(p[1], h1g, h2g, 20, 0.05)
+                   for p in payload]
+        for t in tickets:
+            t.result()
+        sat = len(payload) / (time.perf_counter() - t0)
+    finally:
+        srv.stop()
+    _line(workload="serve", metric="serving jobs/s with p50/p99 latency (density 70% / selection 30%)",
+          unit="jobs/s", value=sat, steps=len(payload), warmup=1, ms_per_step=1e3 / sat,
+          sequential={"jobs_per_s": cap, "p50_ms": 1e3 * float(np.percentile(seq_lat, 50)),
+                      "p99_ms": 1e3 * float(np.percentile(seq_lat, 99))},
+          speedup_vs_sequential=sat / cap, loads=loads,
+          config={"workload": "serve", "datasets": [w.N for w in ws], "d": [w.d for w in ws],
+                  "jobs": len(payload), "Q_max": args.serve_Q_max, "streams": args.serve_streams})
+    cde.cde_shutdown(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,9 +460,25 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--N", type=int, default=50000, help="dataset size (profiling runs use less)")
+    ap.add_argument("--workload", default="scale", choices=["scale", "tiny", "batch", "grad", "serve"])
+    ap.add_argument("--n-datasets", type=int, default=256)
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--N-grad", type=int, default=200000)
+    ap.add_argument("--ascent-steps", type=int, default=30)
+    ap.add_argument("--serve-datasets", type=int, default=6)
+    ap.add_argument("--serve-N-max", type=int, default=100000)
+    ap.add_argument("--serve-Q-max", type=int, default=100000)
+    ap.add_argument("--serve-jobs", type=int, default=60)
+    ap.add_argument("--serve-streams", type=int, default=4)
     args = ap.parse_args()
     from paper_1206_5278_gb300 import synth
     rank, _, _ = _env_rank()
+    if args.workload != "scale":
+        if not os.path.exists(os.path.join(ROOT, "paper_1206_5278_gb300", "libcde.so")):
+            from __graft_entry__ import build
+            build()
+        {"tiny": run_tiny, "batch": run_batch, "grad": run_grad, "serve": run_serve}[args.workload](args)
+        return
     w = synth.scale_workload(N=args.N, seed=1 + 1000 * rank)
     if args.impl == "reference":
         run_reference(args, w)
