@@ -133,9 +133,11 @@ def test_density_integrates_to_one_and_device_io(ctx):
     integ = np.trapezoid(f.astype(np.float64), yg.astype(np.float64), axis=1)
     np.testing.assert_allclose(integ, 1.0, atol=2e-4)
     fo = torch.empty((40, 4096), dtype=torch.float32, device="cuda")
-    cde.cde_density(ctx, ds, h1, h2, torch.from_numpy(xq).cuda(), torch.from_numpy(yg).cuda(), fo,
-                    stream=torch.cuda.current_stream())
-    torch.cuda.synchronize()
+    xqd, ygd = torch.from_numpy(xq).cuda(), torch.from_numpy(yg).cuda()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    cde.cde_density(ctx, ds, h1, h2, xqd, ygd, fo, stream=s)
+    s.synchronize()
     np.testing.assert_array_equal(fo.cpu().numpy(), f)
     assert cde.cde_density(ctx, ds, h1, h2, np.zeros((0, 4), np.float32), yg).shape == (0, 4096)
     cde.cde_destroy_dataset(ctx, ds)

@@ -142,7 +142,8 @@ def test_deterministic_and_device_io(ctx):
     assert np.array_equal(a, c) and np.array_equal(b, e)
     Lc = torch.empty(64, dtype=torch.float64, device="cuda")
     Le = torch.empty(64, dtype=torch.float64, device="cuda")
-    s = torch.cuda.current_stream()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
     cde.cde_loo_loglik(ctx, ds, w.h1, w.h2, Lc, Le, stream=s)
     s.synchronize()
     assert np.array_equal(Lc.cpu().numpy().reshape(8, 8), a)
