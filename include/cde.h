@@ -107,6 +107,33 @@ int cde_loo_loglik(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const
                    int G2, double *L_cond_out, double *L_eq3_out, int flags, void *stream);
 
 /*
+ * cde_loo_loglik without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory --
+ * a process whose device memory is owned by another allocator (for example a
+ * framework's caching allocator that has reserved most of HBM, so a
+ * cudaMalloc here could fail or fragment its pool), a latency-bound service
+ * loop in which cudaMalloc/cudaFree may synchronise the device and stall other
+ * work, or a host that forbids allocation calls to the plugins it loads.
+ *   Same scores as cde_loo_loglik (up to the order of FP64 additions) for one
+ *   grid of at most 32 x 32 bandwidths; larger grids give CDE_EINVAL.
+ *   d_L_cond, d_L_eq3: caller-owned DEVICE arrays of G1 x G2 doubles (either
+ *   may be NULL); the call only enqueues work on `stream` (NULL: the context's
+ *   stream) and returns.
+ *   Scratch: the tile partials and the tile counter live in one fixed 16 MiB
+ *   array in the library's device memory, held on every GPU that loads the
+ *   library until the process exits; tiles are enlarged so that any N fits.
+ *   The first call on a device looks up that array's address (set-up); make
+ *   it before any stream capture.  Every call uses the same array and it keeps
+ *   the last call's contents (the counter is cleared by each call), so calls
+ *   whose work overlaps on the GPU -- on different streams or contexts, or
+ *   from different host threads -- race and give wrong results: order them.
+ *   Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+int cde_loo_loglik_noalloc(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1,
+                           const double *h2, int G2, double *d_L_cond, double *d_L_eq3,
+                           void *stream);
+
+/*
  * Per-row terms ell_j(k,l) = ln(A_j/B_j) for a list of rows (Eq. 1 at the
  * left-out point), for checking full-size runs row by row.
  *   rows[n_rows]: host int64 row indices in [0, N); ell_out: n_rows x G1 x G2

@@ -34,6 +34,7 @@ EXPORTED = [
     "cde_density", "cde_loo_loglik_batch", "cde_server_start", "cde_server_stop", "cde_submit",
     "cde_poll", "cde_wait", "cde_cancel", "cde_server_stats_get", "cde_server_stats_reset",
     "cde_measure_peaks", "cde_autotune", "cde_tuning_get", "cde_tuning_set",
+    "cde_loo_loglik_noalloc",
 ]
 
 
@@ -120,6 +121,8 @@ def lib():
                             ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cde_tuning_set": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
                            ctypes.c_int),
+        "cde_loo_loglik_noalloc": ([_vp, _i64, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp],
+                                   ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -229,6 +232,16 @@ def cde_loo_loglik(ctx, ds: int, h1, h2, L_cond_out=None, L_eq3_out=None, stream
     _check(lib().cde_loo_loglik(ctx, int(ds), _ptr(h1), G1, _ptr(h2), G2, _ptr(Lc), _ptr(Le), 0,
                                 _stream(stream)))
     return Lc, Le
+
+
+def cde_loo_loglik_noalloc(ctx, ds: int, h1, h2, L_cond_out, L_eq3_out, stream=None):
+    """Enqueue the LOO scores into caller-owned CUDA float64 tensors (G1*G2
+    elements each, either may be None) without any device allocation."""
+    h1 = _f64(h1).reshape(-1)
+    h2 = _f64(h2).reshape(-1)
+    _check(lib().cde_loo_loglik_noalloc(ctx, int(ds), _ptr(h1), h1.size, _ptr(h2), h2.size,
+                                        _ptr(L_cond_out), _ptr(L_eq3_out), _stream(stream)))
+    return L_cond_out, L_eq3_out
 
 
 def cde_loo_rows(ctx, ds: int, h1, h2, rows, stream=None) -> np.ndarray:
