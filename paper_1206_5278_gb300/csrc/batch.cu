@@ -23,6 +23,7 @@
 
 #include "cde_internal.h"
 #include "loo_common.cuh"
+#include "loo_mma.cuh"
 
 namespace cde {
 
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(256, 2) k_loo_batch(const LooArgs* __restrict_
             __syncthreads();
         }
         const CoefSmem cf{A.a1, A.a2};
-        loo_tile<G1, G2>(A, cf, work[w].y, reinterpret_cast<float*>(sm4));
+        loo_tile_mma<G1, G2>(A, cf, work[w].y, reinterpret_cast<float*>(sm4));
     }
 }
 
@@ -88,7 +89,7 @@ __global__ void k_loo_final_batch(const LooArgs* __restrict__ items, const int* 
 template <int G1, int G2>
 static int launch_batch_shape(const LooArgs* d_items, const int2* d_work, int n_work, int* counter,
                               int grid, cudaStream_t st, int dmax) {
-    using C = LooCfg<G1, G2>;
+    using C = MmaCfg<G1, G2>;
     static bool attr_set = false;
     if (!attr_set) {
         CDE_CUDA(cudaFuncSetAttribute(k_loo_batch<G1, G2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -104,14 +105,13 @@ static int launch_batch(int T1, int T2, const LooArgs* d_items, const int2* d_wo
                         int* counter, int grid, cudaStream_t st, int dmax) {
 #define CDE_BSHAPE(A, B) \
     if (T1 == A && T2 == B) return launch_batch_shape<A, B>(d_items, d_work, n_work, counter, grid, st, dmax);
-    CDE_BSHAPE(8, 8) CDE_BSHAPE(8, 16) CDE_BSHAPE(8, 32)
     CDE_BSHAPE(16, 8) CDE_BSHAPE(16, 16) CDE_BSHAPE(16, 32)
     CDE_BSHAPE(32, 8) CDE_BSHAPE(32, 16) CDE_BSHAPE(32, 32)
 #undef CDE_BSHAPE
     return set_error(CDE_EINVAL, "batch: unsupported grid shape");
 }
 
-static int pad_shape(int g) { return g <= 8 ? 8 : (g <= 16 ? 16 : 32); }
+
 
 // A captured batched launch and the device memory it references.
 struct BatchPlan {
@@ -156,7 +156,7 @@ static int build_plan(cde_ctx* ctx, const std::vector<BatchItem>& items, BatchPl
     int dmax = 1;
     for (int b = 0; b < n; ++b) {
         const BatchItem& it = items[b];
-        const int T1 = pad_shape(it.G1), T2 = pad_shape(it.G2);
+        const int T1 = loo_pad1(it.G1), T2 = loo_pad2(it.G2);
         shape[b] = T1 * 64 + T2;
         LooArgs& a = args[b];
         memset(&a, 0, sizeof(a));
@@ -342,7 +342,7 @@ void batch_plan_free(cde_ctx* ctx) {
 // ---------------------------------------------------------------------------
 int autotune_shape(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, const double* h2, int G2,
                    int* best_upt, int* best_ctas, double* best_ms) {
-    const int T1 = pad_shape(G1), T2 = pad_shape(G2);
+    const int T1 = loo_pad1(G1), T2 = loo_pad2(G2);
     const int a = T1 <= 8 ? 0 : T1 <= 16 ? 1 : 2, b = T2 <= 8 ? 0 : T2 <= 16 ? 1 : 2;
     const int JW = 1024 / (T1 * T2);
     std::vector<int> upts;
@@ -441,7 +441,7 @@ extern "C" int cde_autotune(cde_ctx* ctx, cde_dataset ds, const double* h1, int 
 
 extern "C" int cde_tuning_get(cde_ctx* ctx, int G1, int G2, int* units_per_tile, int* ctas_per_sm) {
     if (!ctx || G1 < 1 || G1 > 32 || G2 < 1 || G2 > 32) return set_error(CDE_EINVAL, "cde_tuning_get: bad arguments");
-    const int T1 = pad_shape(G1), T2 = pad_shape(G2);
+    const int T1 = loo_pad1(G1), T2 = loo_pad2(G2);
     if (units_per_tile) *units_per_tile = loo_units_per_tile(ctx, T1, T2);
     if (ctas_per_sm) *ctas_per_sm = loo_grid_ctas(ctx, T1, T2) / ctx->sm_count;
     return CDE_OK;

@@ -34,6 +34,7 @@ struct LooArgs {
 template <int G1, int G2>
 struct LooCfg {
     static constexpr int kThreads = 256, kWarps = 8;
+    static constexpr int G1v = G1, G2v = G2;
     static constexpr int GG = G1 * G2;
     static constexpr int JW = 1024 / GG;               // rows per unit
     static constexpr int IC = (32 / JW) > 8 ? 32 / JW : 8;  // i per warp chunk
@@ -56,6 +57,7 @@ struct LooCfg {
     __host__ __device__ static int dpad(int d) { return (d * JW + 3) & ~3; }
     // float offsets of the per-unit area
     __host__ __device__ static int off_xj() { return BIG; }
+    __host__ __device__ static int off_xj(int) { return BIG; }
     __host__ __device__ static int off_yj(int d) { return BIG + dpad(d); }
     __host__ __device__ static int off_mx(int d) { return off_yj(d) + 16; }
     __host__ __device__ static int off_my(int d) { return off_yj(d) + 32; }
@@ -121,14 +123,13 @@ struct CoefParam {
 // so the dominant term is exactly 1 and log2 At = -e_* + log2 S.  Cells are
 // sorted, grouped by row and processed FB at a time, each pass visiting every
 // point once for the whole group.
-template <int G1, int G2, class Coef>
+template <class C, class Coef>
 __device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, float* sm, int nfl) {
-    using C = LooCfg<G1, G2>;
-    constexpr int GG = C::GG, FB = C::FB;
+    constexpr int GG = C::GG, FB = C::FB, G2 = C::G2v;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int d = a.d;
     const int64_t N = a.N, Np = a.Np;
-    float* xj_s = sm + C::off_xj();
+    float* xj_s = sm + C::off_xj(d);
     float* yj_s = sm + C::off_yj(d);
     float* mx_s = sm + C::off_mx(d);
     float* my_s = sm + C::off_my(d);
@@ -279,6 +280,85 @@ __device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, f
         __syncthreads();
         q0 += nb;
     }
+}
+
+// Per-unit epilogue shared by the tile bodies.  On entry At[m] holds the
+// warp-combined shifted numerator of cell tid + 256 m and btl_s the FP64 log2
+// of the shifted denominators; `big` (the first BIG floats of shared memory)
+// is free.  Flags cells below the threshold, recomputes them exactly, and adds
+// the FP64 log-ratios of the unit's rows into the tile partial (thread-owned
+// cells, rows in order).
+template <class C, class Coef>
+__device__ __forceinline__ void loo_unit_epilogue(const LooArgs& a, const Coef& cf, float* sm, int u,
+                                                  int u_begin, int tile, const float (&At)[4]) {
+    constexpr int JW = C::JW, GG = C::GG, G1 = C::G1v, G2 = C::G2v;
+    constexpr double LN2 = 0.69314718055994530942;
+    const int tid = threadIdx.x;
+    const int d = a.d;
+    float* big = sm;
+    float* mx_s = sm + C::off_mx(d);
+    float* my_s = sm + C::off_my(d);
+    int* vr_s = reinterpret_cast<int*>(sm + C::off_vr(d));
+    double* btl_s = reinterpret_cast<double*>(sm + C::off_btl(d));
+    int* flag_s = reinterpret_cast<int*>(sm + C::off_flag(d));
+    int* nflag_s = reinterpret_cast<int*>(sm + C::off_nflag(d));
+        // ---- shifted log numerators; flag cells that lost range ----
+        double* la2 = reinterpret_cast<double*>(big);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int c = tid + 256 * m;
+            const int jl = c / GG;
+            if (!vr_s[jl]) continue;
+            const float v = At[m];
+            if (v >= a.thresh) {
+                la2[c] = log2_wide(v);
+            } else {
+                const int q = atomicAdd(nflag_s, 1);
+                flag_s[q] = c;
+            }
+        }
+        __syncthreads();
+        const int nfl = *nflag_s;
+        if (nfl > 0) loo_fallback<C>(a, cf, sm, nfl);
+        __syncthreads();
+
+        // ---- FP64 log-ratio; each thread owns whole grid cells (all rows of
+        //      the unit, in row order) and adds them to the tile partial ----
+        {
+            const bool first = (u == u_begin);
+            double* part = a.part + (int64_t)tile * 2 * GG;
+            constexpr int NOWN = GG >= 256 ? GG / 256 : 1;
+#pragma unroll
+            for (int s = 0; s < NOWN; ++s) {
+                const int kl = tid + 256 * s;
+                if (kl >= GG) continue;
+                const int k = kl / G2, l = kl - k * G2;
+                const double a1k = (double)cf.a1(k), a2l = (double)cf.a2(l);
+                const double lam = a.lam1[k], kap = a.kap2[l];
+                double sc = 0.0, se = 0.0;
+                for (int jl = 0; jl < JW; ++jl) {
+                    if (!vr_s[jl]) continue;
+                    const int c = jl * GG + kl;
+                    const double shy = a2l * (double)my_s[jl];
+                    const double lA = la2[c];
+                    const double ell = LN2 * (lA - btl_s[jl * G1 + k] - shy) - kap;
+                    const double lnA = LN2 * (lA - a1k * (double)mx_s[jl] - shy) - lam - kap;
+                    sc += ell;
+                    se += lnA;
+                    if (a.ell_rows && k < a.G1r && l < a.G2r) {
+                        const int64_t r = (int64_t)u * JW + jl;
+                        a.ell_rows[r * a.ell_ld_row + (int64_t)k * a.ell_ld_k + l] = ell;
+                    }
+                }
+                if (first) {
+                    part[kl] = sc;
+                    part[GG + kl] = se;
+                } else {
+                    part[kl] += sc;
+                    part[GG + kl] += se;
+                }
+            }
+        }
 }
 
 // One tile of units: units [tile*UPT, min(n_units, (tile+1)*UPT)).
@@ -488,63 +568,7 @@ __device__ __forceinline__ void loo_tile(const LooArgs& a, const Coef& cf, int t
         }
         __syncthreads();
 
-        // ---- shifted log numerators; flag cells that lost range ----
-        double* la2 = reinterpret_cast<double*>(big);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int c = tid + 256 * m;
-            const int jl = c / GG;
-            if (!vr_s[jl]) continue;
-            const float v = At[m];
-            if (v >= a.thresh) {
-                la2[c] = log2_wide(v);
-            } else {
-                const int q = atomicAdd(nflag_s, 1);
-                flag_s[q] = c;
-            }
-        }
-        __syncthreads();
-        const int nfl = *nflag_s;
-        if (nfl > 0) loo_fallback<G1, G2>(a, cf, sm, nfl);
-        __syncthreads();
-
-        // ---- FP64 log-ratio; each thread owns whole grid cells (all rows of
-        //      the unit, in row order) and adds them to the tile partial ----
-        {
-            const bool first = (u == u_begin);
-            double* part = a.part + (int64_t)tile * 2 * GG;
-            constexpr int NOWN = GG >= 256 ? GG / 256 : 1;
-#pragma unroll
-            for (int s = 0; s < NOWN; ++s) {
-                const int kl = tid + 256 * s;
-                if (kl >= GG) continue;
-                const int k = kl / G2, l = kl - k * G2;
-                const double a1k = (double)cf.a1(k), a2l = (double)cf.a2(l);
-                const double lam = a.lam1[k], kap = a.kap2[l];
-                double sc = 0.0, se = 0.0;
-                for (int jl = 0; jl < JW; ++jl) {
-                    if (!vr_s[jl]) continue;
-                    const int c = jl * GG + kl;
-                    const double shy = a2l * (double)my_s[jl];
-                    const double lA = la2[c];
-                    const double ell = LN2 * (lA - btl_s[jl * G1 + k] - shy) - kap;
-                    const double lnA = LN2 * (lA - a1k * (double)mx_s[jl] - shy) - lam - kap;
-                    sc += ell;
-                    se += lnA;
-                    if (a.ell_rows && k < a.G1r && l < a.G2r) {
-                        const int64_t r = (int64_t)u * JW + jl;
-                        a.ell_rows[r * a.ell_ld_row + (int64_t)k * a.ell_ld_k + l] = ell;
-                    }
-                }
-                if (first) {
-                    part[kl] = sc;
-                    part[GG + kl] = se;
-                } else {
-                    part[kl] += sc;
-                    part[GG + kl] += se;
-                }
-            }
-        }
+        loo_unit_epilogue<C>(a, cf, sm, u, u_begin, tile, At);
     }
 }
 
@@ -564,6 +588,11 @@ __global__ void __launch_bounds__(256, 2) k_loo_grid(const LooArgs a) {
         loo_tile<G1, G2>(a, cf, t, reinterpret_cast<float*>(sm4));
     }
 }
+
+// Grid shapes of the tile kernels: k (h1) padded to an M-tile multiple of 16,
+// l (h2) to 8, 16 or 32.
+inline int loo_pad1(int g) { return g <= 16 ? 16 : 32; }
+inline int loo_pad2(int g) { return g <= 8 ? 8 : (g <= 16 ? 16 : 32); }
 
 int launch_loo_tile_kernel(int T1, int T2, const LooArgs& a, int grid, cudaStream_t st);
 void fill_loo_args(LooArgs& a, const Dataset& D, const double* h1, int g1, const double* h2,

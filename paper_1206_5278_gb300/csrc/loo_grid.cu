@@ -32,6 +32,7 @@
 
 #include "cde_internal.h"
 #include "loo_common.cuh"
+#include "loo_mma.cuh"
 
 namespace cde {
 
@@ -182,26 +183,24 @@ __global__ void k_loo_final(const double* __restrict__ part, int n_tiles, int GG
 // --------------------------------------------------------------------------
 template <int G1, int G2>
 static int launch_shape(const LooArgs& a, int grid, cudaStream_t st) {
-    using C = LooCfg<G1, G2>;
+    using C = MmaCfg<G1, G2>;
     const size_t smem = C::smem_bytes(a.d);
     static bool attr_set = false;  // per instantiation; guarded by the ctx lock
     if (!attr_set) {
-        CDE_CUDA(cudaFuncSetAttribute(k_loo_grid<G1, G2>,
+        CDE_CUDA(cudaFuncSetAttribute(k_loo_mma<G1, G2>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)C::smem_bytes(kMaxD)));
         attr_set = true;
     }
-    k_loo_grid<G1, G2><<<grid, C::kThreads, smem, st>>>(a);
+    k_loo_mma<G1, G2><<<grid, C::kThreads, smem, st>>>(a);
     CDE_CUDA(cudaGetLastError());
     return CDE_OK;
 }
 
-static int pad_g(int g) { return g <= 8 ? 8 : (g <= 16 ? 16 : 32); }
 
 int launch_loo_tile_kernel(int T1, int T2, const LooArgs& a, int grid, cudaStream_t st) {
 #define CDE_SHAPE(A, B) \
     if (T1 == A && T2 == B) return launch_shape<A, B>(a, grid, st);
-    CDE_SHAPE(8, 8) CDE_SHAPE(8, 16) CDE_SHAPE(8, 32)
     CDE_SHAPE(16, 8) CDE_SHAPE(16, 16) CDE_SHAPE(16, 32)
     CDE_SHAPE(32, 8) CDE_SHAPE(32, 16) CDE_SHAPE(32, 32)
 #undef CDE_SHAPE
@@ -251,10 +250,10 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
     if (!d_rows) n_rows = D.N;
     for (int k0 = 0; k0 < G1; k0 += 32) {
         const int g1 = G1 - k0 < 32 ? G1 - k0 : 32;
-        const int T1 = pad_g(g1);
+        const int T1 = loo_pad1(g1);
         for (int l0 = 0; l0 < G2; l0 += 32) {
             const int g2 = G2 - l0 < 32 ? G2 - l0 : 32;
-            const int T2 = pad_g(g2);
+            const int T2 = loo_pad2(g2);
             LooArgs a{};
             fill_loo_args(a, D, h1 + k0, g1, h2 + l0, g2, T1, T2);
             const int JW = 1024 / (T1 * T2);

@@ -1,0 +1,313 @@
+// Tensor-core tile body of the leave-one-out grid kernel.
+//
+// Same sums as the FP32 tile body in loo_common.cuh (At_j(k,l) = sum_i
+// u_i(k) w_i(l), Bt_j(k) = sum_i u_i(k)), with the outer-product accumulation
+// issued as m16n8k8 TF32 tensor-core MMAs whose operands never touch shared
+// memory: for row j the GEMM is D[k][l] += sum_i U[k][i] W[i][l] (M = k,
+// N = l, K = i), and every lane produces exactly the fragment elements it
+// owns -- A: (k = 16 mt + g [+8], i = t [+4]), B: (i = t [+4], l = 8 nt + g),
+// g = lane/4, t = lane%4 -- with its own exp2 on the SFU (G1 + G2 per pair,
+// no duplication across lanes).
+//
+// Precision: each factor v is split v = hi + lo, hi = v truncated to TF32,
+// lo = v - hi (exact in FP32, |lo| < 2^-10 |v|, truncated to TF32 by the
+// MMA), and the three products hi*hi + hi*lo + lo*hi are accumulated: the
+// dropped lo*lo and the truncation of lo leave about 2^-19 relative per term.  The tensor core's FP32 accumulation is kept short: each chunk of 32
+// points (12 MMAs per accumulator) starts from zero and is then added to an
+// FP32 running total with a rounded add.
+#pragma once
+
+#include <cstdint>
+
+#include "loo_common.cuh"
+
+namespace cde {
+
+template <int G1, int G2>
+struct MmaCfg {
+    static_assert(G1 == 16 || G1 == 32, "M tiles of 16");
+    static_assert(G2 == 8 || G2 == 16 || G2 == 32, "N tiles of 8");
+    static constexpr int kThreads = 256, kWarps = 8;
+    static constexpr int G1v = G1, G2v = G2;
+    static constexpr int GG = G1 * G2;
+    static constexpr int JW = 1024 / GG;     // rows per unit (all handled by every warp)
+    static constexpr int MT = G1 / 16, NT = G2 / 8;
+    static constexpr int IC = 32;            // points per warp chunk (4 MMA k-steps)
+    static constexpr int FB = 8;
+    static constexpr int COMB = kWarps * 1024 + kWarps * JW * G1;
+    // per warp: (t1, t2) for JW rows x IC points
+    __host__ __device__ static int stage(int) { return kWarps * JW * IC * 2; }
+    __host__ __device__ static int big(int d) {
+        const int s = stage(d);
+        const int b = s > COMB ? s : COMB;
+        return b > 2048 ? b : 2048;
+    }
+    __host__ __device__ static int dpad(int d) { return (d * JW + 3) & ~3; }
+    __host__ __device__ static int off_xj(int d) { return big(d); }
+    __host__ __device__ static int off_yj(int d) { return big(d) + dpad(d); }
+    __host__ __device__ static int off_mx(int d) { return off_yj(d) + 16; }
+    __host__ __device__ static int off_my(int d) { return off_yj(d) + 32; }
+    __host__ __device__ static int off_ji(int d) { return off_yj(d) + 48; }
+    __host__ __device__ static int off_vr(int d) { return off_yj(d) + 80; }
+    __host__ __device__ static int off_btl(int d) { return off_yj(d) + 96; }
+    __host__ __device__ static int off_flag(int d) { return off_btl(d) + 2 * JW * G1; }
+    __host__ __device__ static int off_nflag(int d) { return off_flag(d) + 1024; }
+    __host__ __device__ static int off_red(int d) { return off_nflag(d) + 4; }
+    __host__ __device__ static int off_fb(int d) { return off_red(d) + 2 * kWarps * FB; }
+    static size_t smem_bytes(int d) { return (size_t)(off_fb(d) + 2 * FB + 8) * sizeof(float); }
+};
+
+__device__ __forceinline__ uint32_t tf32_rna(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
+}
+
+// split v into hi (v with the 13 low mantissa bits cleared: a TF32 value) and
+// lo = v - hi (exact in FP32; the MMA reads its leading 10 mantissa bits)
+__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
+    hi = __float_as_uint(v) & 0xffffe000u;
+    lo = __float_as_uint(v - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int G1, int G2, class Coef>
+__device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, int tile, float* sm) {
+    using C = MmaCfg<G1, G2>;
+    constexpr int JW = C::JW, MT = C::MT, NT = C::NT, GG = C::GG, IC = C::IC;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int d = a.d;
+    float* big = sm;
+    float* xj_s = sm + C::off_xj(d);
+    float* yj_s = sm + C::off_yj(d);
+    float* mx_s = sm + C::off_mx(d);
+    float* my_s = sm + C::off_my(d);
+    long long* ji_s = reinterpret_cast<long long*>(sm + C::off_ji(d));
+    int* vr_s = reinterpret_cast<int*>(sm + C::off_vr(d));
+    double* btl_s = reinterpret_cast<double*>(sm + C::off_btl(d));
+    int* nflag_s = reinterpret_cast<int*>(sm + C::off_nflag(d));
+    float2* tt = reinterpret_cast<float2*>(big) + warp * JW * IC;  // [JW][32] (t1, t2) of this warp's chunk
+
+    // this lane's coefficients: k = 16 mt + g (+8), l = 8 nt + g
+    float ca1[MT][2], ca2[NT];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+        ca1[mt][0] = cf.a1(16 * mt + g);
+        ca1[mt][1] = cf.a1(16 * mt + g + 8);
+    }
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) ca2[nt] = cf.a2(8 * nt + g);
+
+    const int u_begin = tile * a.units_per_tile;
+    const int u_end = min(a.n_units, u_begin + a.units_per_tile);
+    const int64_t N = a.N, Np = a.Np;
+    const int64_t n_chunks = (N + IC - 1) / IC;
+
+    for (int u = u_begin; u < u_end; ++u) {
+        __syncthreads();
+        if (tid < JW) {
+            const int64_t r = (int64_t)u * JW + tid;
+            const bool v = r < a.n_rows;
+            const int64_t r0 = v ? r : 0;
+            const int64_t j = a.rows ? a.rows[r0] : r0;
+            ji_s[tid] = j;
+            vr_s[tid] = v;
+            yj_s[tid] = a.y[j];
+            mx_s[tid] = a.mx[j];
+            my_s[tid] = a.my[j];
+        }
+        if (tid == 0) *nflag_s = 0;
+        __syncthreads();
+        for (int e = tid; e < JW * d; e += C::kThreads) {
+            const int jl = e / d, c = e - jl * d;
+            xj_s[e] = a.xs[(int64_t)c * Np + ji_s[jl]];
+        }
+        __syncthreads();
+
+        float Dt[JW][MT][NT][4];
+        float bt[JW][MT][2];
+#pragma unroll
+        for (int r = 0; r < JW; ++r)
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                bt[r][mt][0] = bt[r][mt][1] = 0.f;
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) Dt[r][mt][nt][q] = 0.f;
+            }
+
+        // point coordinates of the first chunk (lane = point), prefetched one chunk ahead
+        float xin[8], yin = 0.f;
+        int64_t ch = warp;
+        if (ch < n_chunks) {
+            const int64_t i = ch * IC + lane;  // < Np
+#pragma unroll
+            for (int c = 0; c < 8; ++c) xin[c] = c < d ? a.xs[(int64_t)c * Np + i] : 0.f;
+            yin = a.y[i];
+        }
+        for (; ch < n_chunks; ch += C::kWarps) {
+            const int64_t i = ch * IC + lane;
+            // ---- distance pass: lane = point; masked pairs get t1 = -inf ----
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < JW; ++r) {
+                const float* xjr = xj_s + r * d;
+                float dx2 = 0.f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c < d) {
+                        const float q = xjr[c] - xin[c];
+                        dx2 = fmaf(q, q, dx2);
+                    }
+                for (int c = 8; c < d; ++c) {
+                    const float q = xjr[c] - a.xs[(int64_t)c * Np + i];
+                    dx2 = fmaf(q, q, dx2);
+                }
+                const float dy = yj_s[r] - yin;
+                const bool ok = i < N && i != ji_s[r];
+                tt[r * IC + lane] = make_float2(ok ? mx_s[r] - dx2 : -INFINITY, my_s[r] - dy * dy);
+            }
+            if (ch + C::kWarps < n_chunks) {
+                const int64_t i2 = (ch + C::kWarps) * IC + lane;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) xin[c] = c < d ? a.xs[(int64_t)c * Np + i2] : 0.f;
+                yin = a.y[i2];
+            }
+            __syncwarp();
+            // ---- MMA pass: 4 k-steps of 8 points ----
+            float D[JW][MT][NT][4];
+#pragma unroll
+            for (int r = 0; r < JW; ++r)
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) D[r][mt][nt][q] = 0.f;
+#pragma unroll
+            for (int s = 0; s < IC / 8; ++s) {
+#pragma unroll
+                for (int r = 0; r < JW; ++r) {
+                    const float2 pa = tt[r * IC + 8 * s + t];
+                    const float2 pb = tt[r * IC + 8 * s + t + 4];
+                    uint32_t bh[NT][2], bl[NT][2];
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) {
+                        split_tf32(ex2_approx(ca2[nt] * pa.y), bh[nt][0], bl[nt][0]);
+                        split_tf32(ex2_approx(ca2[nt] * pb.y), bh[nt][1], bl[nt][1]);
+                    }
+                    uint32_t ah[MT][4], al[MT][4];
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt) {
+                        const float u0 = ex2_approx(ca1[mt][0] * pa.x);  // (k0, ia)
+                        const float u1 = ex2_approx(ca1[mt][1] * pa.x);  // (k0+8, ia)
+                        const float u2 = ex2_approx(ca1[mt][0] * pb.x);  // (k0, ib)
+                        const float u3 = ex2_approx(ca1[mt][1] * pb.x);  // (k0+8, ib)
+                        {
+                            const float2 s2 = __fadd2_rn(make_float2(bt[r][mt][0], bt[r][mt][1]),
+                                                         __fadd2_rn(make_float2(u0, u1), make_float2(u2, u3)));
+                            bt[r][mt][0] = s2.x;
+                            bt[r][mt][1] = s2.y;
+                        }
+                        split_tf32(u0, ah[mt][0], al[mt][0]);
+                        split_tf32(u1, ah[mt][1], al[mt][1]);
+                        split_tf32(u2, ah[mt][2], al[mt][2]);
+                        split_tf32(u3, ah[mt][3], al[mt][3]);
+                    }
+                    // consecutive MMAs go to different accumulators
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt) mma_tf32(D[r][mt][nt], ah[mt], bh[nt][0], bh[nt][1]);
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt) mma_tf32(D[r][mt][nt], ah[mt], bl[nt][0], bl[nt][1]);
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt) mma_tf32(D[r][mt][nt], al[mt], bh[nt][0], bh[nt][1]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < JW; ++r)
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                        for (int q = 0; q < 4; q += 2) {
+                            const float2 s2 = __fadd2_rn(make_float2(Dt[r][mt][nt][q], Dt[r][mt][nt][q + 1]),
+                                                         make_float2(D[r][mt][nt][q], D[r][mt][nt][q + 1]));
+                            Dt[r][mt][nt][q] = s2.x;
+                            Dt[r][mt][nt][q + 1] = s2.y;
+                        }
+        }
+
+        // ---- combine the 8 warps in fixed order ----
+        __syncthreads();
+        float* accS = big;
+        float* btS = big + C::kWarps * 1024;
+#pragma unroll
+        for (int r = 0; r < JW; ++r)
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = 16 * mt + g + 8 * (q >> 1), l = 8 * nt + 2 * t + (q & 1);
+                        accS[warp * 1024 + r * GG + k * G2 + l] = Dt[r][mt][nt][q];
+                    }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float v = bt[r][mt][h];
+                    v += __shfl_xor_sync(0xffffffffu, v, 1);
+                    v += __shfl_xor_sync(0xffffffffu, v, 2);
+                    if (t == 0) btS[warp * JW * G1 + r * G1 + 16 * mt + g + 8 * h] = v;
+                }
+            }
+        __syncthreads();
+        float At[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int c = tid + 256 * m;
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < C::kWarps; ++w) s += accS[w * 1024 + c];
+            At[m] = s;
+        }
+        for (int e = tid; e < JW * G1; e += C::kThreads) {
+            float s = 0.f;
+            for (int w = 0; w < C::kWarps; ++w) s += btS[w * JW * G1 + e];
+            btl_s[e] = log2_wide(s);
+        }
+        __syncthreads();
+        loo_unit_epilogue<C>(a, cf, sm, u, u_begin, tile, At);
+    }
+}
+
+template <int G1, int G2>
+__global__ void __launch_bounds__(256, 2) k_loo_mma(const LooArgs a) {
+    extern __shared__ float4 sm4[];
+    __shared__ int next_tile;
+    const CoefParam cf{a};
+    for (int t0 = blockIdx.x;; t0 += gridDim.x) {
+        if (threadIdx.x == 0) next_tile = a.work ? atomicAdd(a.work, 1) : t0;
+        __syncthreads();
+        const int t = next_tile;
+        if (t >= a.n_tiles) break;
+        loo_tile_mma<G1, G2>(a, cf, t, reinterpret_cast<float*>(sm4));
+    }
+}
+
+}  // namespace cde

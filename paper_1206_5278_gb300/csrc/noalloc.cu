@@ -43,7 +43,6 @@ static int noalloc_scratch(int device, void** out) {
     return CDE_OK;
 }
 
-static int pad_shape_na(int g) { return g <= 8 ? 8 : (g <= 16 ? 16 : 32); }
 
 }  // namespace cde
 
@@ -72,7 +71,7 @@ extern "C" int cde_loo_loglik_noalloc(cde_ctx* ctx, cde_dataset ds, const double
     if (rc != CDE_OK) return rc;
     cudaStream_t st = pick_stream(ctx, stream);
 
-    const int T1 = pad_shape_na(G1), T2 = pad_shape_na(G2);
+    const int T1 = loo_pad1(G1), T2 = loo_pad2(G2);
     LooArgs a{};
     fill_loo_args(a, *D, h1, G1, h2, G2, T1, T2);
     const int JW = 1024 / (T1 * T2);
