@@ -1,6 +1,9 @@
-// The leave-one-out pair kernel, shared by the single-dataset launch
-// (loo_grid.cu) and the persistent batched launch (batch.cu).
-// See loo_grid.cu for the method; this file holds the tile body.
+// Pieces of the leave-one-out grid kernel shared by the single-dataset launch
+// (loo_grid.cu), the persistent batched launch (batch.cu) and the
+// allocation-free launch (noalloc.cu): the argument block, coefficient access,
+// the exact joint-shift fallback and the FP64 per-unit epilogue.  The tile
+// body (tensor-core outer product) is in loo_mma.cuh; loo_grid.cu describes
+// the method.
 #pragma once
 
 #include <cstdint>
@@ -29,46 +32,6 @@ struct LooArgs {
     float a1[32], a2[32];   // log2(e)/(2 h^2), padded by repeating the last bandwidth
     double lam1[32];        // d ln(sqrt(2 pi) h1_k)
     double kap2[32];        // ln(sqrt(2 pi) h2_l)
-};
-
-template <int G1, int G2>
-struct LooCfg {
-    static constexpr int kThreads = 256, kWarps = 8;
-    static constexpr int G1v = G1, G2v = G2;
-    static constexpr int GG = G1 * G2;
-    static constexpr int JW = 1024 / GG;               // rows per unit
-    static constexpr int IC = (32 / JW) > 8 ? 32 / JW : 8;  // i per warp chunk
-    static constexpr int PPL = IC * JW / 32;           // phase-1 pairs per lane
-    static constexpr int NKQ = G1 / 4, NLQ = G2 / 8;   // phase-2 lane tile: 4 k x 8 l
-    static constexpr int LPJ = NKQ * NLQ;              // lanes per row in phase 2
-    static constexpr int UCH = JW * G1 / 4;            // 16-B chunks of a u row
-    static constexpr int WCH = JW * G2 / 4;            // 16-B chunks of a w row
-    static constexpr int UROW = UCH * 4 + 4;           // floats per u row (+16 B pad: no bank conflicts)
-    static constexpr int WROW = WCH * 4 + 4;
-    static constexpr int STAGE = IC * (UROW + WROW);   // floats per warp
-    static constexpr int COMB = kWarps * 1024 + kWarps * 32 * 4;
-    static constexpr int BIG0 = kWarps * STAGE > COMB ? kWarps * STAGE : COMB;
-    static constexpr int BIG = BIG0 > 2048 ? BIG0 : 2048;  // also holds 1024 doubles
-    static constexpr int NKL = GG >= 256 ? GG / 256 : 1;
-    static_assert(LPJ * JW == 32, "lane tiling");
-    static_assert(UCH >= 8 && WCH >= 8, "row chunks");
-    static constexpr int FB = 8;                       // flagged cells per fallback pass
-
-    __host__ __device__ static int dpad(int d) { return (d * JW + 3) & ~3; }
-    // float offsets of the per-unit area
-    __host__ __device__ static int off_xj() { return BIG; }
-    __host__ __device__ static int off_xj(int) { return BIG; }
-    __host__ __device__ static int off_yj(int d) { return BIG + dpad(d); }
-    __host__ __device__ static int off_mx(int d) { return off_yj(d) + 16; }
-    __host__ __device__ static int off_my(int d) { return off_yj(d) + 32; }
-    __host__ __device__ static int off_ji(int d) { return off_yj(d) + 48; }    // 16 int64
-    __host__ __device__ static int off_vr(int d) { return off_yj(d) + 80; }    // 16 int
-    __host__ __device__ static int off_btl(int d) { return off_yj(d) + 96; }   // JW*G1 doubles
-    __host__ __device__ static int off_flag(int d) { return off_btl(d) + 2 * JW * G1; }  // 1024 int
-    __host__ __device__ static int off_nflag(int d) { return off_flag(d) + 1024; }
-    __host__ __device__ static int off_red(int d) { return off_nflag(d) + 4; }   // 8 warps x FB x 2 words
-    __host__ __device__ static int off_fb(int d) { return off_red(d) + 2 * kWarps * FB; }  // FB x 2 words
-    static size_t smem_bytes(int d) { return (size_t)(off_fb(d) + 2 * FB + 8) * sizeof(float); }
 };
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -359,234 +322,6 @@ __device__ __forceinline__ void loo_unit_epilogue(const LooArgs& a, const Coef& 
                 }
             }
         }
-}
-
-// One tile of units: units [tile*UPT, min(n_units, (tile+1)*UPT)).
-template <int G1, int G2, class Coef>
-__device__ __forceinline__ void loo_tile(const LooArgs& a, const Coef& cf, int tile, float* sm) {
-    using C = LooCfg<G1, G2>;
-    constexpr int JW = C::JW, IC = C::IC, PPL = C::PPL, NKQ = C::NKQ, NLQ = C::NLQ;
-    constexpr int LPJ = C::LPJ, GG = C::GG, UROW = C::UROW, WROW = C::WROW;
-    constexpr int WH = C::WCH / 2;
-    constexpr double LN2 = 0.69314718055994530942;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int d = a.d;
-    float* big = sm;
-    float* xj_s = sm + C::off_xj();
-    float* yj_s = sm + C::off_yj(d);
-    float* mx_s = sm + C::off_mx(d);
-    float* my_s = sm + C::off_my(d);
-    long long* ji_s = reinterpret_cast<long long*>(sm + C::off_ji(d));
-    int* vr_s = reinterpret_cast<int*>(sm + C::off_vr(d));
-    double* btl_s = reinterpret_cast<double*>(sm + C::off_btl(d));
-    int* flag_s = reinterpret_cast<int*>(sm + C::off_flag(d));
-    int* nflag_s = reinterpret_cast<int*>(sm + C::off_nflag(d));
-    const int u_begin = tile * a.units_per_tile;
-    const int u_end = min(a.n_units, u_begin + a.units_per_tile);
-    const int64_t N = a.N, Np = a.Np;
-    const int64_t n_chunks = (N + IC - 1) / IC;
-
-    // phase-2 lane tile
-    const int jl2 = lane / LPJ, rr = lane % LPJ, kq2 = rr / NLQ, lq2 = rr % NLQ;
-    float* ust = big + warp * C::STAGE;
-    float* wst = ust + IC * UROW;
-    const float* urd = ust + 4 * (jl2 * NKQ + kq2);
-    const float* wrd = wst + 4 * (jl2 * NLQ + lq2);
-    const int il = lane % IC;
-
-    for (int u = u_begin; u < u_end; ++u) {
-        // ---- unit set-up ----
-        __syncthreads();
-        if (tid < JW) {
-            const int64_t r = (int64_t)u * JW + tid;
-            const bool v = r < a.n_rows;
-            const int64_t r0 = v ? r : 0;
-            const int64_t j = a.rows ? a.rows[r0] : r0;
-            ji_s[tid] = j;
-            vr_s[tid] = v;
-            yj_s[tid] = a.y[j];
-            mx_s[tid] = a.mx[j];
-            my_s[tid] = a.my[j];
-        }
-        if (tid == 0) *nflag_s = 0;
-        __syncthreads();
-        for (int e = tid; e < JW * d; e += C::kThreads) {
-            const int jl = e / d, c = e - jl * d;
-            xj_s[e] = a.xs[(int64_t)c * Np + ji_s[jl]];
-        }
-        __syncthreads();
-
-        float2 acc[4][4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[p][q] = make_float2(0.f, 0.f);
-        // B partial sums: lane (jl2, kq2, lq2) owns k = 4 kq2 + lq2 * NBT + q, q < NBT
-        constexpr int NBT = 4 / NLQ;
-        float bt[NBT];
-#pragma unroll
-        for (int q = 0; q < NBT; ++q) bt[q] = 0.f;
-
-        // per-pair row constants (fixed for the unit)
-        float pmx[PPL], pmy[PPL], pyj[PPL];
-        long long pj[PPL];
-        int pjl[PPL];
-#pragma unroll
-        for (int r = 0; r < PPL; ++r) {
-            const int jl = (lane + 32 * r) / IC;
-            pjl[r] = jl;
-            pmx[r] = mx_s[jl];
-            pmy[r] = my_s[jl];
-            pyj[r] = yj_s[jl];
-            pj[r] = ji_s[jl];
-        }
-
-        float xin[8], yin = 0.f;
-        int64_t ch = warp;
-        if (ch < n_chunks) {
-            const int64_t i = ch * IC + il;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) xin[c] = c < d ? a.xs[(int64_t)c * Np + i] : 0.f;
-            yin = a.y[i];
-        }
-        for (; ch < n_chunks; ch += C::kWarps) {
-            const int64_t i = ch * IC + il;
-            float xi[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) xi[c] = xin[c];
-            const float yi = yin;
-            // ---- phase 1: distances and exp2 factors for this lane's pairs ----
-#pragma unroll
-            for (int r = 0; r < PPL; ++r) {
-                const int jl = pjl[r];
-                const float* xjr = xj_s + jl * d;
-                float dx2 = 0.f;
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    if (c < d) {
-                        const float t = xjr[c] - xi[c];
-                        dx2 = fmaf(t, t, dx2);
-                    }
-                for (int c = 8; c < d; ++c) {
-                    const float t = xjr[c] - a.xs[(int64_t)c * Np + i];
-                    dx2 = fmaf(t, t, dx2);
-                }
-                const float dy = pyj[r] - yi;
-                const float dy2 = dy * dy;
-                const bool ok = (i < N) && (i != pj[r]);
-                const float t1 = ok ? pmx[r] - dx2 : -INFINITY;
-                const float t2 = pmy[r] - dy2;
-                float* ub = ust + il * UROW + 4 * jl * NKQ;
-#pragma unroll
-                for (int kq = 0; kq < NKQ; ++kq) {
-                    const float u0 = ex2_approx(cf.a1(4 * kq + 0) * t1);
-                    const float u1 = ex2_approx(cf.a1(4 * kq + 1) * t1);
-                    const float u2 = ex2_approx(cf.a1(4 * kq + 2) * t1);
-                    const float u3 = ex2_approx(cf.a1(4 * kq + 3) * t1);
-                    *reinterpret_cast<float4*>(ub + 4 * kq) = make_float4(u0, u1, u2, u3);
-                }
-                float* wb = wst + il * WROW + 4 * jl * NLQ;
-#pragma unroll
-                for (int lq = 0; lq < NLQ; ++lq) {
-                    float w[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) w[q] = ex2_approx(cf.a2(8 * lq + q) * t2);
-                    *reinterpret_cast<float4*>(wb + 4 * lq) = make_float4(w[0], w[1], w[2], w[3]);
-                    *reinterpret_cast<float4*>(wb + 4 * (WH + lq)) =
-                        make_float4(w[4], w[5], w[6], w[7]);
-                }
-            }
-            // prefetch the next chunk's point
-            if (ch + C::kWarps < n_chunks) {
-                const int64_t i2 = (ch + C::kWarps) * IC + il;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) xin[c] = c < d ? a.xs[(int64_t)c * Np + i2] : 0.f;
-                yin = a.y[i2];
-            }
-            __syncwarp();
-            // ---- phase 2: outer-product accumulation, 4 k x 8 l per lane ----
-#pragma unroll
-            for (int ii = 0; ii < IC; ++ii) {
-                const float4 ua = *reinterpret_cast<const float4*>(urd + ii * UROW);
-                const float4 wa = *reinterpret_cast<const float4*>(wrd + ii * WROW);
-                const float4 wb = *reinterpret_cast<const float4*>(wrd + ii * WROW + 4 * WH);
-                const float2 U[4] = {make_float2(ua.x, ua.x), make_float2(ua.y, ua.y),
-                                     make_float2(ua.z, ua.z), make_float2(ua.w, ua.w)};
-                const float2 W[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w),
-                                     make_float2(wb.x, wb.y), make_float2(wb.z, wb.w)};
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[p][q] = __ffma2_rn(U[p], W[q], acc[p][q]);
-                if constexpr (NLQ == 1) {
-                    bt[0] += ua.x;
-                    bt[1] += ua.y;
-                    bt[2] += ua.z;
-                    bt[3] += ua.w;
-                } else if constexpr (NLQ == 2) {
-                    bt[0] += lq2 ? ua.z : ua.x;
-                    bt[1] += lq2 ? ua.w : ua.y;
-                } else {
-                    const float lo = (lq2 & 1) ? ua.y : ua.x;
-                    const float hi = (lq2 & 1) ? ua.w : ua.z;
-                    bt[0] += (lq2 & 2) ? hi : lo;
-                }
-            }
-            __syncwarp();
-        }
-
-        // ---- combine the 8 warps' partial sums in fixed order ----
-        __syncthreads();
-        float* accS = big;
-        float* bpS = big + C::kWarps * 1024;
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                *reinterpret_cast<float2*>(accS + warp * 1024 + jl2 * GG + (4 * kq2 + p) * G2 +
-                                           8 * lq2 + 2 * q) = acc[p][q];
-#pragma unroll
-        for (int q = 0; q < NBT; ++q) bpS[(warp * 32 + lane) * 4 + q] = bt[q];
-        __syncthreads();
-        float At[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int c = tid + 256 * m;
-            float s = 0.f;
-#pragma unroll
-            for (int w = 0; w < C::kWarps; ++w) s += accS[w * 1024 + c];
-            At[m] = s;
-        }
-        for (int e = tid; e < JW * G1; e += C::kThreads) {
-            // owner lane of (jl, k): kq = k/4, lq = (k%4)/NBT, q = (k%4)%NBT
-            const int jl = e / G1, k = e - jl * G1;
-            const int kq = k >> 2, lq = (k & 3) / NBT, q = (k & 3) % NBT;
-            const int ln = jl * LPJ + kq * NLQ + lq;
-            float s = 0.f;
-            for (int w = 0; w < C::kWarps; ++w) s += bpS[(w * 32 + ln) * 4 + q];
-            btl_s[e] = log2_wide(s);
-        }
-        __syncthreads();
-
-        loo_unit_epilogue<C>(a, cf, sm, u, u_begin, tile, At);
-    }
-}
-
-// Tiles are taken from a counter (a.work, zeroed before the launch) so that
-// units needing the exact fallback do not leave other SMs idle; each tile's
-// partial has its own slot, so the schedule does not change the result.
-template <int G1, int G2>
-__global__ void __launch_bounds__(256, 2) k_loo_grid(const LooArgs a) {
-    extern __shared__ float4 sm4[];
-    __shared__ int next_tile;
-    const CoefParam cf{a};
-    for (int t0 = blockIdx.x;; t0 += gridDim.x) {
-        if (threadIdx.x == 0) next_tile = a.work ? atomicAdd(a.work, 1) : t0;
-        __syncthreads();
-        const int t = next_tile;
-        if (t >= a.n_tiles) break;
-        loo_tile<G1, G2>(a, cf, t, reinterpret_cast<float*>(sm4));
-    }
 }
 
 // Grid shapes of the tile kernels: k (h1) padded to an M-tile multiple of 16,

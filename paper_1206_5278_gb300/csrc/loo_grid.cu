@@ -13,7 +13,8 @@
 // where m_x,j / m_y,j are row j's nearest squared distances in x and in y (so
 // the largest u and the largest w are exactly 1: no overflow, and B never
 // underflows).  The Gaussian factors are separable, so one squared distance
-// per pair feeds G1 + G2 exp2 (MUFU) and G1*G2 multiply-adds.  The epilogue
+// per pair feeds G1 + G2 exp2 (MUFU), and the G1 x G2 outer-product sums run on
+// the tensor cores as per-row TF32 GEMMs with split operands (loo_mma.cuh).  The epilogue
 // removes the shifts and the kernel constants in FP64:
 //   ell_j = ln2 (log2 At - log2 Bt - a2_l m_y,j) - ln(sqrt(2 pi) h2_l)
 //   ln A_j = ln2 (log2 At - a1_k m_x,j - a2_l m_y,j) - d ln(sqrt(2pi) h1_k) - ln(sqrt(2pi) h2_l)
@@ -22,8 +23,9 @@
 // exactly with a joint shift anchored at argmin_i [a1 (dx2-m_x) + a2 (dy2-m_y)].
 //
 // Work decomposition: a CTA of 8 warps owns a "unit" of JW = 1024/(G1 G2)
-// rows; the 8 warps split the i range in interleaved chunks of IC points and
-// their FP32 partial sums are combined in fixed warp order.  Units are grouped
+// rows (G1 padded to 16 or 32, G2 to 8, 16 or 32); the 8 warps split the i
+// range in interleaved chunks of 32 points and their FP32 partial sums are
+// combined in fixed warp order.  Units are grouped
 // into tiles; each tile's FP64 partial scores go to their own slot and a final
 // kernel sums the slots in tile order, so results are bitwise reproducible and
 // independent of how tiles are scheduled.
