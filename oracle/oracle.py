@@ -20,8 +20,11 @@ from typing import Optional, Tuple
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# ORACLE_SRC may name another copy of oracle.c (the mutation tests compile
+# deliberately broken copies to check that the pins catch them).
+_SRC = os.environ.get("ORACLE_SRC") or os.path.join(_HERE, "oracle.c")
+_LIB = (os.path.join(os.path.dirname(os.path.abspath(_SRC)), "liboracle_variant.so")
+        if os.environ.get("ORACLE_SRC") else os.path.join(_HERE, "liboracle.so"))
 _lib = None
 
 _dp = ctypes.POINTER(ctypes.c_double)

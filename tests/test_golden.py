@@ -1,0 +1,54 @@
+"""Stored oracle values (tests/golden/loo_small.json, written by
+tests/golden/make_golden.py from oracle/ only): the oracle still reproduces
+them on CPU, and the library matches them on the GPU within the LOO and
+gradient tolerances."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1206_5278_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+G = json.load(open(os.path.join(HERE, "golden", "loo_small.json")))
+
+
+def _inputs(name):
+    if name == "tanh_mixture_N300_d1":
+        w = synth.tiny_workload(N=300)
+        return w.x, w.y
+    return synth.gmm_sine(400, 3, seed=12)
+
+
+@pytest.mark.parametrize("case", G["cases"], ids=[c["name"] for c in G["cases"]])
+def test_oracle_reproduces_golden(case):
+    x, y = _inputs(case["name"])
+    Lc, Le = oracle.loo_grid(x, y, case["h1"], case["h2"], standardize_x=case["standardize"], n_threads=1)
+    np.testing.assert_allclose(Lc, case["L_cond"], rtol=1e-12)
+    np.testing.assert_allclose(Le, case["L_eq3"], rtol=1e-12)
+    g = oracle.grad(x, y, *case["grad_at"], standardize_x=case["standardize"], n_threads=1)
+    np.testing.assert_allclose(g, case["grad"], rtol=1e-11)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", G["cases"], ids=[c["name"] for c in G["cases"]])
+def test_library_matches_golden(case):
+    from __graft_entry__ import build
+    build()
+    from paper_1206_5278_gb300 import cde
+    x, y = _inputs(case["name"])
+    ctx = cde.cde_init(0)
+    try:
+        ds = cde.cde_create_dataset(ctx, x, y, standardize=case["standardize"])
+        Lc, Le = cde.cde_loo_loglik(ctx, ds, case["h1"], case["h2"])
+        ref = np.array(case["L_cond"])
+        assert np.all(np.abs(Lc - ref) <= 1e-5 * np.abs(ref))
+        assert np.all(np.abs(Le - np.array(case["L_eq3"])) <= 1e-5 * np.abs(np.array(case["L_eq3"])))
+        g = cde.cde_loo_grad(ctx, ds, *case["grad_at"])
+        gr = np.array(case["grad"])
+        assert abs(g[0] - gr[0]) <= 1e-5 * abs(gr[0])
+        assert np.all(np.abs(g[1:] - gr[1:]) <= 1e-4 * np.abs(gr[1:]) + 1e-4)
+    finally:
+        cde.cde_shutdown(ctx)
