@@ -44,6 +44,29 @@ __device__ __forceinline__ float ex2g(float x) {
     return r;
 }
 
+// One pair's contribution with the online joint shift, without branches: when
+// e does not lower the running minimum the rescale factor is exactly 2^0 = 1.
+__device__ __forceinline__ void grad_accumulate(bool ok, float dx2, float dy2, float mx, float my,
+                                                float a1, float a2, float& M, float& SA, float& SAx,
+                                                float& SAy, float& SB, float& SBx) {
+    const float ex = dx2 - mx, ey = dy2 - my;
+    const float e = fmaf(a1, ex, a2 * ey);
+    const bool lower = ok && e < M;
+    const float Mn = lower ? e : M;
+    const float r = lower ? ex2g(e - M) : 1.f;  // M = +inf at the start: r = 0, the sums are 0
+    SA *= r;
+    SAx *= r;
+    SAy *= r;
+    M = Mn;
+    const float u = ok ? ex2g(-a1 * ex) : 0.f;
+    const float v = ok ? ex2g(M - e) : 0.f;
+    SB += u;
+    SBx = fmaf(u, dx2, SBx);
+    SA += v;
+    SAx = fmaf(v, dx2, SAx);
+    SAy = fmaf(v, dy2, SAy);
+}
+
 template <int JB, int DREG>
 __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
     __shared__ float xt[DREG + 1][kGradThreads];
@@ -93,23 +116,8 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
                 }
                 const float dy = yj[b] - yi;
                 const float dy2 = dy * dy;
-                const bool ok = i != jj[b];
-                const float ex = dx2 - mxj[b], ey = dy2 - myj[b];
-                const float e = fmaf(a1, ex, a2 * ey);
-                if (ok && e < M[b]) {
-                    const float r = ex2g(e - M[b]);
-                    SA[b] *= r;
-                    SAx[b] *= r;
-                    SAy[b] *= r;
-                    M[b] = e;
-                }
-                const float u = ok ? ex2g(-a1 * ex) : 0.f;
-                const float v = ok ? ex2g(M[b] - e) : 0.f;
-                SB[b] += u;
-                SBx[b] = fmaf(u, dx2, SBx[b]);
-                SA[b] += v;
-                SAx[b] = fmaf(v, dx2, SAx[b]);
-                SAy[b] = fmaf(v, dy2, SAy[b]);
+                grad_accumulate(i != jj[b], dx2, dy2, mxj[b], myj[b], a1, a2, M[b], SA[b], SAx[b],
+                                SAy[b], SB[b], SBx[b]);
             }
         }
     }
@@ -123,6 +131,143 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
         p[3] = SAy[b];
         p[4] = SB[b];
         p[5] = SBx[b];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// d >= 16: the x cross-term on the tensor cores.  |x_j - x_i|^2 =
+// n_j + n_i - 2 x_j.x_i with the dot products of a 16-row x 8-point tile from
+// m16n8k8 TF32 MMAs on split operands (x = hi + lo, products hi*hi + hi*lo +
+// lo*hi, FP32 accumulation), norms n in FP32, the result clamped at 0.  Each
+// warp owns 16 rows (their split fragments stay in registers); the CTA stages
+// 64 points at a time, already split, in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kGMWarps = 4, kGMTile = 64;
+
+__device__ __forceinline__ void split_tf32_g(float v, uint32_t& hi, uint32_t& lo) {
+    hi = __float_as_uint(v) & 0xffffe000u;
+    lo = __float_as_uint(v - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32_g(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int DK>
+__global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g) {
+    constexpr int KK = DK / 8, RS = DK + 4;  // padded smem row (bank spread)
+    __shared__ uint32_t xh[kGMTile * RS], xl[kGMTile * RS];
+    __shared__ float ni_s[kGMTile], yi_s[kGMTile];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gq = lane >> 2, t = lane & 3;
+    const int d = g.d;
+    const int64_t N = g.N, Np = g.Np;
+    const int64_t i0 = (int64_t)blockIdx.y * g.i_per_split;
+    const int64_t i1 = min(N, i0 + g.i_per_split);
+    int64_t jr[2];
+    float nj[2], yj[2], mxj[2], myj[2];
+    uint32_t ah[KK][4], al[KK][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t j = (int64_t)blockIdx.x * (kGMWarps * 16) + warp * 16 + gq + 8 * h;
+        jr[h] = j;
+        const int64_t jc = j < N ? j : 0;
+        float n = 0.f;
+        for (int c = 0; c < d; ++c) {
+            const float v = g.xs[(int64_t)c * Np + jc];
+            n = fmaf(v, v, n);
+        }
+        nj[h] = n;
+        yj[h] = g.y[jc];
+        mxj[h] = g.mx[jc];
+        myj[h] = g.my[jc];
+#pragma unroll
+        for (int kk = 0; kk < KK; ++kk) {
+            const int c0 = 8 * kk + t, c1 = c0 + 4;
+            const float v0 = c0 < d ? g.xs[(int64_t)c0 * Np + jc] : 0.f;
+            const float v1 = c1 < d ? g.xs[(int64_t)c1 * Np + jc] : 0.f;
+            split_tf32_g(v0, ah[kk][h], al[kk][h]);        // a0 / a1: (row g [+8], k t)
+            split_tf32_g(v1, ah[kk][2 + h], al[kk][2 + h]); // a2 / a3: (row g [+8], k t+4)
+        }
+    }
+    const float a1 = g.a1, a2 = g.a2;
+    float M[2] = {INFINITY, INFINITY}, SA[2] = {0, 0}, SAx[2] = {0, 0}, SAy[2] = {0, 0}, SB[2] = {0, 0},
+          SBx[2] = {0, 0};
+    for (int64_t t0 = i0; t0 < i1; t0 += kGMTile) {
+        __syncthreads();
+        for (int e = tid; e < DK * kGMTile; e += kGMWarps * 32) {
+            const int c = e / kGMTile, p = e - c * kGMTile;
+            const float v = c < d ? g.xs[(int64_t)c * Np + t0 + p] : 0.f;  // t0 + p < Np
+            uint32_t hv, lv;
+            split_tf32_g(v, hv, lv);
+            xh[p * RS + c] = hv;
+            xl[p * RS + c] = lv;
+        }
+        if (tid < kGMTile) {
+            float n = 0.f;
+            for (int c = 0; c < d; ++c) {
+                const float v = g.xs[(int64_t)c * Np + t0 + tid];
+                n = fmaf(v, v, n);
+            }
+            ni_s[tid] = n;
+            yi_s[tid] = g.y[t0 + tid];
+        }
+        __syncthreads();
+        // 4 n-tiles (32 points) at a time: independent accumulators hide the MMA latency
+#pragma unroll 1
+        for (int n4 = 0; n4 < kGMTile / 32; ++n4) {
+            float D[4][4];
+#pragma unroll
+            for (int n = 0; n < 4; ++n) D[n][0] = D[n][1] = D[n][2] = D[n][3] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < KK; ++kk) {
+#pragma unroll
+                for (int n = 0; n < 4; ++n) {
+                    const int pr = (32 * n4 + 8 * n + gq) * RS + 8 * kk + t;
+                    const uint32_t bh0 = xh[pr], bh1 = xh[pr + 4], bl0 = xl[pr], bl1 = xl[pr + 4];
+                    mma_tf32_g(D[n], ah[kk], bh0, bh1);
+                    mma_tf32_g(D[n], ah[kk], bl0, bl1);
+                    mma_tf32_g(D[n], al[kk], bh0, bh1);
+                }
+            }
+#pragma unroll
+            for (int n = 0; n < 4; ++n)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int h = q >> 1, p = 32 * n4 + 8 * n + 2 * t + (q & 1);
+                    const int64_t i = t0 + p;
+                    const float dx2 = fmaxf(nj[h] + ni_s[p] - 2.f * D[n][q], 0.f);
+                    const float dy = yj[h] - yi_s[p];
+                    grad_accumulate(i < i1 && i != jr[h], dx2, dy * dy, mxj[h], myj[h], a1, a2, M[h], SA[h],
+                                    SAx[h], SAy[h], SB[h], SBx[h]);
+                }
+        }
+    }
+    // combine the 4 lanes that share a row (t = 0..3): common shift, fixed xor order
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float Mm = M[h];
+        Mm = fminf(Mm, __shfl_xor_sync(0xffffffffu, Mm, 1));
+        Mm = fminf(Mm, __shfl_xor_sync(0xffffffffu, Mm, 2));
+        const float r = (SA[h] > 0.f) ? ex2g(Mm - M[h]) : 0.f;
+        float v[5] = {SA[h] * r, SAx[h] * r, SAy[h] * r, SB[h], SBx[h]};
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            v[q] += __shfl_xor_sync(0xffffffffu, v[q], 1);
+            v[q] += __shfl_xor_sync(0xffffffffu, v[q], 2);
+        }
+        if (t == 0 && jr[h] < N) {
+            float* pp = g.part + ((int64_t)blockIdx.y * N + jr[h]) * 6;
+            pp[0] = Mm;
+            pp[1] = v[0];
+            pp[2] = v[1];
+            pp[3] = v[2];
+            pp[4] = v[3];
+            pp[5] = v[4];
+        }
     }
 }
 
@@ -199,18 +344,20 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     const double L2E = 1.4426950408889634074;
     g.a1 = (float)(L2E / (2 * h1 * h1));
     g.a2 = (float)(L2E / (2 * h2 * h2));
+    const bool tc = D.d >= 16;   // tensor-core cross term
     const int DREG = D.d <= 4 ? 4 : D.d <= 8 ? 8 : D.d <= 16 ? 16 : D.d <= 32 ? 32 : 64;
     const int JB = DREG <= 8 ? 4 : DREG <= 32 ? 2 : 1;
-    const int64_t rows_per_cta = (int64_t)kGradThreads * JB;
+    const int64_t rows_per_cta = tc ? (int64_t)kGMWarps * 16 : (int64_t)kGradThreads * JB;
+    const int tile = tc ? kGMTile : kGradThreads;
     const int64_t gx = (D.N + rows_per_cta - 1) / rows_per_cta;
     // split i so that the launch has about 8 CTAs per SM
-    int64_t want = 8LL * ctx->sm_count;
+    int64_t want = (tc ? 16LL : 8LL) * ctx->sm_count;
     int64_t ns = (want + gx - 1) / gx;
-    const int64_t tiles = (D.N + kGradThreads - 1) / kGradThreads;
+    const int64_t tiles = (D.N + tile - 1) / tile;
     if (ns > tiles) ns = tiles;
     if (ns < 1) ns = 1;
     const int64_t tiles_per = (tiles + ns - 1) / ns;
-    g.i_per_split = tiles_per * kGradThreads;
+    g.i_per_split = tiles_per * tile;
     ns = (tiles + tiles_per - 1) / tiles_per;
     float* part = nullptr;
     double* rowv = d_rowv_ext;
@@ -218,11 +365,13 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     if (!rowv) CDE_CUDA(cudaMallocAsync((void**)&rowv, (size_t)D.N * 3 * sizeof(double), st));
     g.part = part;
     dim3 grid((unsigned)gx, (unsigned)ns);
-    if (DREG == 4) launch_grad<4, 4>(g, grid, st);
+    if (tc) {
+        if (D.d <= 16) k_loo_grad_mma<16><<<grid, kGMWarps * 32, 0, st>>>(g);
+        else if (D.d <= 32) k_loo_grad_mma<32><<<grid, kGMWarps * 32, 0, st>>>(g);
+        else k_loo_grad_mma<64><<<grid, kGMWarps * 32, 0, st>>>(g);
+    } else if (DREG == 4) launch_grad<4, 4>(g, grid, st);
     else if (DREG == 8) launch_grad<4, 8>(g, grid, st);
-    else if (DREG == 16) launch_grad<2, 16>(g, grid, st);
-    else if (DREG == 32) launch_grad<2, 32>(g, grid, st);
-    else launch_grad<1, 64>(g, grid, st);
+    else launch_grad<2, 16>(g, grid, st);
     CDE_CUDA(cudaGetLastError());
     k_grad_rows<<<(unsigned)((D.N + 255) / 256), 256, 0, st>>>(part, (int)ns, D.N, D.my, g.a1, g.a2,
                                                              h1, h2, rowv);
