@@ -367,6 +367,38 @@ def run_grad(args):
         cde.cde_shutdown(ctx)
 
 
+def run_density(args):
+    """Density queries: Q query points x 256-point y grid against N data points
+    (one cde_density call with device inputs/outputs, CUDA-event timed)."""
+    import torch
+    from paper_1206_5278_gb300 import cde, synth
+    x, y = synth.gmm_sine(args.dens_N, args.dens_d, seed=8)
+    ctx = cde.cde_init(0)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    xq = torch.from_numpy(synth.query_points(x, args.dens_Q, seed=9)).cuda()
+    yg = torch.from_numpy(synth.y_grid(y, 0.1, 256)).cuda()
+    f = torch.empty((args.dens_Q, 256), dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    for _ in range(max(2, args.warmup)):
+        cde.cde_density(ctx, ds, 0.3, 0.1, xq, yg, f, stream=st)
+    st.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        a.record(st)
+        cde.cde_density(ctx, ds, 0.3, 0.1, xq, yg, f, stream=st)
+        b.record(st)
+    st.synchronize()
+    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    pairs = args.dens_Q * args.dens_N
+    _line(workload="density_Q%d_N%d_d%d_G256" % (args.dens_Q, args.dens_N, args.dens_d),
+          metric="density (query, data point) pairs/s x 256-point y grid", unit="pairs/s",
+          value=pairs / (ms * 1e-3), steps=args.steps, warmup=args.warmup, ms_per_step=ms,
+          flops_per_pair=2 * 256 * 1 + 3 * args.dens_d, tflops=pairs * 512 / (ms * 1e-3) / 1e12,
+          config={"workload": "density", "Q": args.dens_Q, "N": args.dens_N, "d_x": args.dens_d, "G_y": 256})
+    cde.cde_shutdown(ctx)
+
+
 def run_serve(args):
     """Poisson stream, 70% density jobs (Q log-uniform [1, Q_max] x 256-point y
     grid), 30% selection jobs (16x16 grid + 20 Adam steps) over resident
@@ -462,7 +494,10 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--N", type=int, default=50000, help="dataset size (profiling runs use less)")
-    ap.add_argument("--workload", default="scale", choices=["scale", "tiny", "batch", "grad", "serve"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "tiny", "batch", "grad", "serve", "density"])
+    ap.add_argument("--dens-Q", type=int, default=10000)
+    ap.add_argument("--dens-N", type=int, default=100000)
+    ap.add_argument("--dens-d", type=int, default=4)
     ap.add_argument("--n-datasets", type=int, default=256)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--N-grad", type=int, default=200000)
@@ -479,7 +514,8 @@ def main():
         if not os.path.exists(os.path.join(ROOT, "paper_1206_5278_gb300", "libcde.so")):
             from __graft_entry__ import build
             build()
-        {"tiny": run_tiny, "batch": run_batch, "grad": run_grad, "serve": run_serve}[args.workload](args)
+        {"tiny": run_tiny, "batch": run_batch, "grad": run_grad, "serve": run_serve,
+         "density": run_density}[args.workload](args)
         return
     w = synth.scale_workload(N=args.N, seed=1 + 1000 * rank)
     if args.impl == "reference":

@@ -7,12 +7,13 @@
 //
 // m_q the query's nearest squared distance (so max_i u_qi = 1 and neither sum
 // underflows), a = log2(e)/(2 h^2).  The numerator is a (Q x N) x (N x G)
-// product whose left factor is generated on the fly; each CTA owns 32 queries
-// x 256 grid points, computes the 32 x IC block of u and the IC x 256 block of
-// w for each chunk of IC data points into shared memory, and accumulates a
-// 4 x 8 register tile per thread.  Small Q splits the data range across CTAs;
-// split partials are summed in split order.
+// product whose factors are generated on the fly; each CTA owns 32 queries x
+// 256 grid points and runs the product on the tensor cores (k_density).  Small
+// Q splits the data range across CTAs; split partials are summed in split
+// order.
 #include <cmath>
+
+#include <cstdint>
 
 #include "cde_internal.h"
 
@@ -51,50 +52,77 @@ __global__ void k_query_pack(const float* __restrict__ xq, int64_t Q, int64_t Qp
         out[(int64_t)c * Qp + q] = q < Q ? (float)(((double)xq[q * d + c] - mean[c]) / sd[c]) : 0.f;
 }
 
-// per-query nearest squared distance to the data (same FP32 formula as the main kernel)
+// per-query nearest squared distance to the data (same FP32 formula as the
+// main kernel).  The data range is split over gridDim.y; split minima are
+// merged with an integer atomicMin on the float bits (exact and order-free:
+// squared distances are non-negative, so their bit patterns order like ints).
 __global__ void __launch_bounds__(256) k_query_shift(const float* __restrict__ xs, int64_t N,
                                                      int64_t Np, int d, const float* __restrict__ xq,
-                                                     int64_t Q, int64_t Qp, float* __restrict__ mq) {
+                                                     int64_t Q, int64_t Qp, int64_t i_per_split,
+                                                     unsigned int* __restrict__ mq_bits) {
     extern __shared__ float sm[];  // [d][256]
     const int64_t q = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int64_t ib = (int64_t)blockIdx.y * i_per_split;
+    const int64_t ie = min(N, ib + i_per_split);
+    float xqr[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) xqr[c] = (q < Qp && c < d) ? xq[(int64_t)c * Qp + q] : 0.f;
     float best = INFINITY;
-    for (int64_t i0 = 0; i0 < N; i0 += 256) {
+    for (int64_t i0 = ib; i0 < ie; i0 += 256) {
         __syncthreads();
         for (int c = 0; c < d; ++c) sm[c * 256 + threadIdx.x] = xs[(int64_t)c * Np + i0 + threadIdx.x];
         __syncthreads();
-        const int n = (int)min((int64_t)256, N - i0);
+        const int n = (int)min((int64_t)256, ie - i0);
         if (q < Q)
-            for (int t = 0; t < n; ++t) {
+            for (int tt = 0; tt < n; ++tt) {
                 float dx2 = 0.f;
-                for (int c = 0; c < d; ++c) {
-                    const float u = xq[(int64_t)c * Qp + q] - sm[c * 256 + t];
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c < d) {
+                        const float u = xqr[c] - sm[c * 256 + tt];
+                        dx2 = fmaf(u, u, dx2);
+                    }
+                for (int c = 8; c < d; ++c) {
+                    const float u = xq[(int64_t)c * Qp + q] - sm[c * 256 + tt];
                     dx2 = fmaf(u, u, dx2);
                 }
                 best = fminf(best, dx2);
             }
     }
-    if (q < Q) mq[q] = best;
+    if (q < Q) atomicMin(mq_bits + q, __float_as_uint(best));
 }
 
 struct DensSmem {
-    float Us[kDIC][kDQ + 4];    // u[i][q]
-    float Ws[kDIC][kDG + 4];    // w[i][g]
+    float T[kDQ][kDIC + 4];     // exp2 argument a1 (m_q - |x_q - x_i|^2), -inf when masked
+    float yis[kDIC];
     float xqs[kMaxD][kDQ];
     float xis[kMaxD][kDIC];
-    float yis[kDIC];
-    float dens[8][kDQ];
+    float dens[kDQ];
 };
 
+__device__ __forceinline__ void split_tf32_d(float v, uint32_t& hi, uint32_t& lo) {
+    hi = __float_as_uint(v) & 0xffffe000u;
+    lo = __float_as_uint(v - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32_d(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Numerator tile F[32 queries][256 grid points] += U[32 x IC] W[IC x 256] on
+// the tensor cores: m16n8k8 TF32 with split operands (hi*hi + hi*lo + lo*hi),
+// A (u, M = queries) and B (w, N = grid points) fragments made in-lane with
+// exp2; warp w owns grid points [32 w, 32 w + 32).  The 32 x IC exponent
+// arguments of u are computed once per chunk into shared memory.  Each
+// 32-point chunk accumulates from zero and is added to an FP32 running total.
 __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
     extern __shared__ float4 dsm4[];
     DensSmem& S = *reinterpret_cast<DensSmem*>(dsm4);
-    auto& Us = S.Us;
-    auto& Ws = S.Ws;
-    auto& xqs = S.xqs;
-    auto& xis = S.xis;
-    auto& yis = S.yis;
-    auto& dens = S.dens;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t = lane & 3;
     const int64_t q0 = (int64_t)blockIdx.x * kDQ;
     const int g0 = blockIdx.y * kDG;
     const int64_t s = blockIdx.z;
@@ -103,82 +131,117 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
     const int d = a.d;
     for (int e = tid; e < d * kDQ; e += 256) {
         const int c = e / kDQ, qq = e % kDQ;
-        xqs[c][qq] = (q0 + qq < a.Qp) ? a.xq[(int64_t)c * a.Qp + q0 + qq] : 0.f;
+        S.xqs[c][qq] = (q0 + qq < a.Qp) ? a.xq[(int64_t)c * a.Qp + q0 + qq] : 0.f;
     }
-    // phase-1 roles: u for (q = tid / 8, 4 data points), w for grid point g = tid
-    const int uq = tid >> 3, ui = (tid & 7) * 4;
-    const float mqv = (q0 + uq < a.Q) ? a.mq[q0 + uq] : 0.f;
-    const int gg = g0 + tid < a.G ? g0 + tid : a.G - 1;
-    const float ygv = a.yg[gg];
-    // phase-2 tile: 4 queries x 8 grid points
-    const int pq = (tid >> 5) * 4, pg = (tid & 31) * 8;
-    float acc[4][8];
+    // distance-pass role: query dq, points dp..dp+3
+    const int dq = tid >> 3, dp = (tid & 7) * 4;
+    const float mqv = (q0 + dq < a.Q) ? a.mq[q0 + dq] : 0.f;
+    float ygv[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int nt = 0; nt < 4; ++nt) {
+        const int gg = g0 + 32 * warp + 8 * nt + g;
+        ygv[nt] = a.yg[gg < a.G ? gg : a.G - 1];
+    }
+    float Dt[2][4][4];
+    float bt[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
-        for (int r = 0; r < 8; ++r) acc[p][r] = 0.f;
-    float usum = 0.f;
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) Dt[mt][nt][0] = Dt[mt][nt][1] = Dt[mt][nt][2] = Dt[mt][nt][3] = 0.f;
     const float a1 = a.a1, a2 = a.a2;
     for (int64_t c0 = i_begin; c0 < i_end; c0 += kDIC) {
         __syncthreads();
         for (int e = tid; e < (d + 1) * kDIC; e += 256) {
             const int c = e / kDIC, ii = e % kDIC;
             const int64_t i = c0 + ii;  // < Np
-            if (c < d) xis[c][ii] = a.xs[(int64_t)c * a.Np + i];
-            else yis[ii] = a.y[i];
+            if (c < d) S.xis[c][ii] = a.xs[(int64_t)c * a.Np + i];
+            else S.yis[ii] = a.y[i];
         }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            const int ii = ui + r;
+            const int ii = dp + r;
             float dx2 = 0.f;
             for (int c = 0; c < d; ++c) {
-                const float t = xqs[c][uq] - xis[c][ii];
-                dx2 = fmaf(t, t, dx2);
+                const float u = S.xqs[c][dq] - S.xis[c][ii];
+                dx2 = fmaf(u, u, dx2);
             }
-            const bool ok = c0 + ii < i_end;
-            const float u = ok ? ex2d(a1 * (mqv - dx2)) : 0.f;
-            usum += u;
-            Us[ii][uq] = u;
-        }
-#pragma unroll 8
-        for (int ii = 0; ii < kDIC; ++ii) {
-            const float t = ygv - yis[ii];
-            Ws[ii][tid] = ex2d(-a2 * (t * t));
+            S.T[dq][ii] = (c0 + ii < i_end) ? a1 * (mqv - dx2) : -INFINITY;
         }
         __syncthreads();
-#pragma unroll 8
-        for (int ii = 0; ii < kDIC; ++ii) {
-            const float4 u4 = *reinterpret_cast<const float4*>(&Us[ii][pq]);
-            const float4 wa = *reinterpret_cast<const float4*>(&Ws[ii][pg]);
-            const float4 wb = *reinterpret_cast<const float4*>(&Ws[ii][pg + 4]);
-            const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
-            const float ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+        float D[2][4][4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
+        for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-                for (int r = 0; r < 8; ++r) acc[p][r] = fmaf(uu[p], ww[r], acc[p][r]);
+            for (int nt = 0; nt < 4; ++nt) D[mt][nt][0] = D[mt][nt][1] = D[mt][nt][2] = D[mt][nt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < kDIC / 8; ++ks) {
+            const int pa = 8 * ks + t, pb = pa + 4;
+            uint32_t ah[2][4], al[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const float u0 = ex2d(S.T[16 * mt + g][pa]);       // (q, pa)
+                const float u1 = ex2d(S.T[16 * mt + g + 8][pa]);   // (q + 8, pa)
+                const float u2 = ex2d(S.T[16 * mt + g][pb]);       // (q, pb)
+                const float u3 = ex2d(S.T[16 * mt + g + 8][pb]);   // (q + 8, pb)
+                bt[mt][0] += u0 + u2;
+                bt[mt][1] += u1 + u3;
+                split_tf32_d(u0, ah[mt][0], al[mt][0]);
+                split_tf32_d(u1, ah[mt][1], al[mt][1]);
+                split_tf32_d(u2, ah[mt][2], al[mt][2]);
+                split_tf32_d(u3, ah[mt][3], al[mt][3]);
+            }
+            const float ya = S.yis[pa], yb = S.yis[pb];
+            uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const float ta = ygv[nt] - ya, tb = ygv[nt] - yb;
+                split_tf32_d(ex2d(-a2 * (ta * ta)), bh[nt][0], bl[nt][0]);
+                split_tf32_d(ex2d(-a2 * (tb * tb)), bh[nt][1], bl[nt][1]);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_tf32_d(D[mt][nt], ah[mt], bh[nt][0], bh[nt][1]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_tf32_d(D[mt][nt], ah[mt], bl[nt][0], bl[nt][1]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_tf32_d(D[mt][nt], al[mt], bh[nt][0], bh[nt][1]);
         }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) Dt[mt][nt][q] += D[mt][nt][q];
     }
-    // denominator: 8 threads per query, fixed order
-    dens[tid & 7][uq] = usum;
+    // denominators: every warp holds the same u sums; warp 0 reduces over t
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v = bt[mt][h];
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            if (warp == 0 && t == 0) S.dens[16 * mt + g + 8 * h] = v;
+        }
     __syncthreads();
     float* num = a.num + s * a.Q * a.G;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const int64_t q = q0 + pq + p;
-        if (q >= a.Q) continue;
+    for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int g = g0 + pg + r;
-            if (g < a.G) num[q * a.G + g] = acc[p][r];
-        }
-    }
-    if (blockIdx.y == 0 && tid < kDQ && q0 + tid < a.Q) {
-        float t = 0.f;
-        for (int k = 0; k < 8; ++k) t += dens[k][tid];
-        a.den[s * a.Q + q0 + tid] = t;
-    }
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t qq = q0 + 16 * mt + g + 8 * (q >> 1);
+                const int gg = g0 + 32 * warp + 8 * nt + 2 * t + (q & 1);
+                if (qq < a.Q && gg < a.G) num[qq * a.G + gg] = Dt[mt][nt][q];
+            }
+    if (blockIdx.y == 0 && tid < kDQ && q0 + tid < a.Q) a.den[s * a.Q + q0 + tid] = S.dens[tid];
 }
 
 // f[q][g] = (sum_s num) / (sum_s den) / (sqrt(2 pi) h2), splits in order
@@ -211,8 +274,19 @@ int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const 
     const size_t sm = (size_t)D.d * 256 * sizeof(float);
     if (sm > 48 * 1024)
         CDE_CUDA(cudaFuncSetAttribute(k_query_shift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_query_shift<<<(unsigned)((Q + 255) / 256), 256, sm, st>>>(D.xs, D.N, D.Np, D.d, xq, Q, Qp, mq);
-    CDE_CUDA(cudaGetLastError());
+    {
+        const int64_t qb = (Q + 255) / 256;
+        const int64_t tiles = (D.N + 255) / 256;
+        int64_t sy = (4LL * ctx->sm_count + qb - 1) / qb;
+        if (sy > tiles) sy = tiles;
+        if (sy < 1) sy = 1;
+        const int64_t tps = (tiles + sy - 1) / sy;
+        sy = (tiles + tps - 1) / tps;
+        CDE_CUDA(cudaMemsetAsync(mq, 0x7f, (size_t)Q * sizeof(float), st));  // 3.4e38: above any distance
+        k_query_shift<<<dim3((unsigned)qb, (unsigned)sy), 256, sm, st>>>(
+            D.xs, D.N, D.Np, D.d, xq, Q, Qp, tps * 256, reinterpret_cast<unsigned int*>(mq));
+        CDE_CUDA(cudaGetLastError());
+    }
     DensArgs a{};
     a.xs = D.xs;
     a.y = D.y;
