@@ -9,13 +9,21 @@
 // g = lane/4, t = lane%4 -- with its own exp2 on the SFU (G1 + G2 per pair,
 // no duplication across lanes).
 //
-// Precision: each factor v is split v = hi + lo, hi = v truncated to TF32,
-// lo = v - hi (exact in FP32, |lo| < 2^-10 |v|, truncated to TF32 by the
-// MMA), and the three products hi*hi + hi*lo + lo*hi are accumulated: the
-// dropped lo*lo and the truncation of lo leave about 2^-19 relative per term.  The tensor core's FP32 accumulation is kept short: each chunk of 32
-// points (12 MMAs per accumulator) starts from zero and is then added to an
-// FP32 running total with a rounded add.
+// Precision: each factor v is split v = hi + lo, hi = v truncated to TF32
+// (11 significant bits), lo = v - hi (exact in FP32, |lo| < 2^-10 |v|).  The
+// product u w is formed as hi_u hi_w (TF32 m16n8k8) plus the two cross terms
+// hi_u lo_w + lo_u hi_w, which carry at most 2^-9 of the product and so need
+// only BF16 precision: both go through ONE BF16 m16n8k16 MMA whose k axis
+// stacks [hi_u | lo_u] against [lo_w ; hi_w] (twice the MAC rate of TF32).
+// Dropped lo*lo and the BF16 rounding of the cross terms leave about 2^-17
+// relative per term (the sums over i average these errors).  Each lane takes
+// the points (2t, 2t+1) of a k-step so the TF32 and BF16 fragment layouts hold
+// the same points.  The tensor core's FP32 accumulation is kept short: each
+// chunk of 32 points (8 MMAs per accumulator) starts from zero and is then
+// added to an FP32 running total with a rounded add.
 #pragma once
+
+#include <cuda_bf16.h>
 
 #include <cstdint>
 
@@ -73,6 +81,20 @@ __device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
                                          uint32_t b1) {
     asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// two floats to one register of BF16 (x in the low half: the lower k index)
+__device__ __forceinline__ uint32_t pack_bf16x2(float x, float y) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(x, y);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
         "{%8,%9}, {%0,%1,%2,%3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
@@ -197,33 +219,43 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
             for (int s = 0; s < IC / 8; ++s) {
 #pragma unroll
                 for (int r = 0; r < JW; ++r) {
-                    const float2 pa = tt[r * IC + 8 * s + t];
-                    const float2 pb = tt[r * IC + 8 * s + t + 4];
-                    uint32_t bh[NT][2], bl[NT][2];
+                    // this lane's two points of the k-step: p0 = 8s + 2t, p1 = p0 + 1
+                    const float4 pp = *reinterpret_cast<const float4*>(&tt[r * IC + 8 * s + 2 * t]);
+                    uint32_t bh[NT][2], bx[NT][2];
 #pragma unroll
                     for (int nt = 0; nt < NT; ++nt) {
-                        split_tf32(ex2_approx(ca2[nt] * pa.y), bh[nt][0], bl[nt][0]);
-                        split_tf32(ex2_approx(ca2[nt] * pb.y), bh[nt][1], bl[nt][1]);
+                        uint32_t l0, l1;
+                        const float w0 = ex2_approx(ca2[nt] * pp.y), w1 = ex2_approx(ca2[nt] * pp.w);
+                        split_tf32(w0, bh[nt][0], l0);
+                        split_tf32(w1, bh[nt][1], l1);
+                        bx[nt][0] = pack_bf16x2(__uint_as_float(l0), __uint_as_float(l1));             // rows 2t, 2t+1: lo w
+                        bx[nt][1] = pack_bf16x2(__uint_as_float(bh[nt][0]), __uint_as_float(bh[nt][1]));  // rows 2t+8, +9: hi w
                     }
-                    uint32_t ah[MT][4], al[MT][4];
+                    uint32_t ah[MT][4], ax[MT][4];
 #pragma unroll
                     for (int mt = 0; mt < MT; ++mt) {
-                        const float u0 = ex2_approx(ca1[mt][0] * pa.x);  // (k0, ia)
-                        const float u1 = ex2_approx(ca1[mt][1] * pa.x);  // (k0+8, ia)
-                        const float u2 = ex2_approx(ca1[mt][0] * pb.x);  // (k0, ib)
-                        const float u3 = ex2_approx(ca1[mt][1] * pb.x);  // (k0+8, ib)
+                        const float u0 = ex2_approx(ca1[mt][0] * pp.x);  // (k0, p0)
+                        const float u1 = ex2_approx(ca1[mt][1] * pp.x);  // (k0+8, p0)
+                        const float u2 = ex2_approx(ca1[mt][0] * pp.z);  // (k0, p1)
+                        const float u3 = ex2_approx(ca1[mt][1] * pp.z);  // (k0+8, p1)
                         {
                             const float2 s2 = __fadd2_rn(make_float2(bt[r][mt][0], bt[r][mt][1]),
                                                          __fadd2_rn(make_float2(u0, u1), make_float2(u2, u3)));
                             bt[r][mt][0] = s2.x;
                             bt[r][mt][1] = s2.y;
                         }
-                        split_tf32(u0, ah[mt][0], al[mt][0]);
-                        split_tf32(u1, ah[mt][1], al[mt][1]);
-                        split_tf32(u2, ah[mt][2], al[mt][2]);
-                        split_tf32(u3, ah[mt][3], al[mt][3]);
+                        uint32_t l0, l1, l2, l3;
+                        split_tf32(u0, ah[mt][0], l0);
+                        split_tf32(u1, ah[mt][1], l1);
+                        split_tf32(u2, ah[mt][2], l2);
+                        split_tf32(u3, ah[mt][3], l3);
+                        // BF16 cross-term fragment: columns 2t, 2t+1 hold hi u, 2t+8, 2t+9 lo u
+                        ax[mt][0] = pack_bf16x2(__uint_as_float(ah[mt][0]), __uint_as_float(ah[mt][2]));
+                        ax[mt][1] = pack_bf16x2(__uint_as_float(ah[mt][1]), __uint_as_float(ah[mt][3]));
+                        ax[mt][2] = pack_bf16x2(__uint_as_float(l0), __uint_as_float(l2));
+                        ax[mt][3] = pack_bf16x2(__uint_as_float(l1), __uint_as_float(l3));
                     }
-                    // consecutive MMAs go to different accumulators
+                    // hi*hi on TF32; hi*lo + lo*hi together on one BF16 k16 MMA
 #pragma unroll
                     for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
@@ -231,11 +263,7 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
 #pragma unroll
                     for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-                        for (int nt = 0; nt < NT; ++nt) mma_tf32(D[r][mt][nt], ah[mt], bl[nt][0], bl[nt][1]);
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < NT; ++nt) mma_tf32(D[r][mt][nt], al[mt], bh[nt][0], bh[nt][1]);
+                        for (int nt = 0; nt < NT; ++nt) mma_bf16(D[r][mt][nt], ax[mt], bx[nt][0], bx[nt][1]);
                 }
             }
 #pragma unroll
