@@ -13,6 +13,8 @@
 // order.
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "cde_internal.h"
@@ -105,6 +107,18 @@ __device__ __forceinline__ void split_tf32_d(float v, uint32_t& hi, uint32_t& lo
     lo = __float_as_uint(v - __uint_as_float(hi));
 }
 
+__device__ __forceinline__ uint32_t pack_bf16x2_d(float x, float y) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(x, y);  // x in the low half
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_d(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 __device__ __forceinline__ void mma_tf32_d(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
         "{%8,%9}, {%0,%1,%2,%3};"
@@ -113,7 +127,8 @@ __device__ __forceinline__ void mma_tf32_d(float (&d)[4], const uint32_t (&a)[4]
 }
 
 // Numerator tile F[32 queries][256 grid points] += U[32 x IC] W[IC x 256] on
-// the tensor cores: m16n8k8 TF32 with split operands (hi*hi + hi*lo + lo*hi),
+// the tensor cores with split operands v = hi + lo: hi*hi as TF32 m16n8k8, the
+// two cross terms together as one BF16 m16n8k16 (about 2^-17 per term),
 // A (u, M = queries) and B (w, N = grid points) fragments made in-lane with
 // exp2; warp w owns grid points [32 w, 32 w + 32).  The 32 x IC exponent
 // arguments of u are computed once per chunk into shared memory.  Each
@@ -176,29 +191,39 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
             for (int nt = 0; nt < 4; ++nt) D[mt][nt][0] = D[mt][nt][1] = D[mt][nt][2] = D[mt][nt][3] = 0.f;
 #pragma unroll
         for (int ks = 0; ks < kDIC / 8; ++ks) {
-            const int pa = 8 * ks + t, pb = pa + 4;
-            uint32_t ah[2][4], al[2][4];
+            // this lane's two points of the k-step: p0 = 8 ks + 2t, p1 = p0 + 1
+            const int pa = 8 * ks + 2 * t, pb = pa + 1;
+            uint32_t ah[2][4], ax[2][4];
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
-                const float u0 = ex2d(S.T[16 * mt + g][pa]);       // (q, pa)
-                const float u1 = ex2d(S.T[16 * mt + g + 8][pa]);   // (q + 8, pa)
-                const float u2 = ex2d(S.T[16 * mt + g][pb]);       // (q, pb)
-                const float u3 = ex2d(S.T[16 * mt + g + 8][pb]);   // (q + 8, pb)
+                const float u0 = ex2d(S.T[16 * mt + g][pa]);       // (q, p0)
+                const float u1 = ex2d(S.T[16 * mt + g + 8][pa]);   // (q + 8, p0)
+                const float u2 = ex2d(S.T[16 * mt + g][pb]);       // (q, p1)
+                const float u3 = ex2d(S.T[16 * mt + g + 8][pb]);   // (q + 8, p1)
                 bt[mt][0] += u0 + u2;
                 bt[mt][1] += u1 + u3;
-                split_tf32_d(u0, ah[mt][0], al[mt][0]);
-                split_tf32_d(u1, ah[mt][1], al[mt][1]);
-                split_tf32_d(u2, ah[mt][2], al[mt][2]);
-                split_tf32_d(u3, ah[mt][3], al[mt][3]);
+                uint32_t l0, l1, l2, l3;
+                split_tf32_d(u0, ah[mt][0], l0);
+                split_tf32_d(u1, ah[mt][1], l1);
+                split_tf32_d(u2, ah[mt][2], l2);
+                split_tf32_d(u3, ah[mt][3], l3);
+                ax[mt][0] = pack_bf16x2_d(__uint_as_float(ah[mt][0]), __uint_as_float(ah[mt][2]));
+                ax[mt][1] = pack_bf16x2_d(__uint_as_float(ah[mt][1]), __uint_as_float(ah[mt][3]));
+                ax[mt][2] = pack_bf16x2_d(__uint_as_float(l0), __uint_as_float(l2));
+                ax[mt][3] = pack_bf16x2_d(__uint_as_float(l1), __uint_as_float(l3));
             }
             const float ya = S.yis[pa], yb = S.yis[pb];
-            uint32_t bh[4][2], bl[4][2];
+            uint32_t bh[4][2], bx[4][2];
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
                 const float ta = ygv[nt] - ya, tb = ygv[nt] - yb;
-                split_tf32_d(ex2d(-a2 * (ta * ta)), bh[nt][0], bl[nt][0]);
-                split_tf32_d(ex2d(-a2 * (tb * tb)), bh[nt][1], bl[nt][1]);
+                uint32_t l0, l1;
+                split_tf32_d(ex2d(-a2 * (ta * ta)), bh[nt][0], l0);
+                split_tf32_d(ex2d(-a2 * (tb * tb)), bh[nt][1], l1);
+                bx[nt][0] = pack_bf16x2_d(__uint_as_float(l0), __uint_as_float(l1));
+                bx[nt][1] = pack_bf16x2_d(__uint_as_float(bh[nt][0]), __uint_as_float(bh[nt][1]));
             }
+            // hi*hi on TF32; both cross terms in one BF16 k16 MMA
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -206,11 +231,7 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma_tf32_d(D[mt][nt], ah[mt], bl[nt][0], bl[nt][1]);
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma_tf32_d(D[mt][nt], al[mt], bh[nt][0], bh[nt][1]);
+                for (int nt = 0; nt < 4; ++nt) mma_bf16_d(D[mt][nt], ax[mt], bx[nt][0], bx[nt][1]);
         }
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
