@@ -43,8 +43,8 @@ struct MmaCfg {
     static constexpr int IC = 32;            // points per warp chunk (4 MMA k-steps)
     static constexpr int FB = 8;
     static constexpr int COMB = kWarps * 1024 + kWarps * JW * G1;
-    // per warp: (t1, t2) for JW rows x IC points
-    __host__ __device__ static int stage(int) { return kWarps * JW * IC * 2; }
+    // per warp: (t1, t1) and t2 for JW rows x IC points
+    __host__ __device__ static int stage(int) { return kWarps * JW * IC * 3; }
     __host__ __device__ static int big(int d) {
         const int s = stage(d);
         const int b = s > COMB ? s : COMB;
@@ -116,17 +116,17 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
     int* vr_s = reinterpret_cast<int*>(sm + C::off_vr(d));
     double* btl_s = reinterpret_cast<double*>(sm + C::off_btl(d));
     int* nflag_s = reinterpret_cast<int*>(sm + C::off_nflag(d));
-    float2* tt = reinterpret_cast<float2*>(big) + warp * JW * IC;  // [JW][32] (t1, t2) of this warp's chunk
+    // per warp and row: t1 of each point twice ([32] float2), then t2 ([32] float):
+    // the packed FP32x2 multiplies pair two x coefficients on one point, and one
+    // y coefficient on two points
+    float* tt = big + warp * JW * IC * 3;
 
-    // this lane's coefficients: k = 16 mt + g (+8), l = 8 nt + g
-    float ca1[MT][2], ca2[NT];
+    // this lane's coefficients: (k = 16 mt + g, k + 8) as a pair; l = 8 nt + g twice
+    float2 ca1[MT], ca2[NT];
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt) {
-        ca1[mt][0] = cf.a1(16 * mt + g);
-        ca1[mt][1] = cf.a1(16 * mt + g + 8);
-    }
+    for (int mt = 0; mt < MT; ++mt) ca1[mt] = make_float2(cf.a1(16 * mt + g), cf.a1(16 * mt + g + 8));
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) ca2[nt] = cf.a2(8 * nt + g);
+    for (int nt = 0; nt < NT; ++nt) ca2[nt] = make_float2(cf.a2(8 * nt + g), cf.a2(8 * nt + g));
 
     const int u_begin = tile * a.units_per_tile;
     const int u_end = min(a.n_units, u_begin + a.units_per_tile);
@@ -155,12 +155,12 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
         __syncthreads();
 
         float Dt[JW][MT][NT][4];
-        float bt[JW][MT][2];
+        float2 bt[JW][MT];  // denominator partials of k = 16 mt + g and k + 8
 #pragma unroll
         for (int r = 0; r < JW; ++r)
 #pragma unroll
             for (int mt = 0; mt < MT; ++mt) {
-                bt[r][mt][0] = bt[r][mt][1] = 0.f;
+                bt[r][mt] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
@@ -196,7 +196,9 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                 }
                 const float dy = yj_s[r] - yin;
                 const bool ok = i < N && i != ji_s[r];
-                tt[r * IC + lane] = make_float2(ok ? mx_s[r] - dx2 : -INFINITY, my_s[r] - dy * dy);
+                const float t1 = ok ? mx_s[r] - dx2 : -INFINITY, t2 = my_s[r] - dy * dy;
+                reinterpret_cast<float2*>(tt + r * 3 * IC)[lane] = make_float2(t1, t1);
+                tt[r * 3 * IC + 2 * IC + lane] = t2;
             }
             if (ch + C::kWarps < n_chunks) {
                 const int64_t i2 = (ch + C::kWarps) * IC + lane;
@@ -220,40 +222,47 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
 #pragma unroll
                 for (int r = 0; r < JW; ++r) {
                     // this lane's two points of the k-step: p0 = 8s + 2t, p1 = p0 + 1
-                    const float4 pp = *reinterpret_cast<const float4*>(&tt[r * IC + 8 * s + 2 * t]);
+                    const float4 q1 = *reinterpret_cast<const float4*>(tt + r * 3 * IC + 2 * (8 * s + 2 * t));
+                    const float2 t1p0 = make_float2(q1.x, q1.y), t1p1 = make_float2(q1.z, q1.w);
+                    const float2 t2p = *reinterpret_cast<const float2*>(tt + r * 3 * IC + 2 * IC + 8 * s + 2 * t);
+                    // B fragments: w(l, p0) in register 0, w(l, p1) in register 1 (TF32);
+                    // BF16: register 0 = lo w at (p0, p1), register 1 = hi w at (p0, p1)
                     uint32_t bh[NT][2], bx[NT][2];
 #pragma unroll
                     for (int nt = 0; nt < NT; ++nt) {
-                        uint32_t l0, l1;
-                        const float w0 = ex2_approx(ca2[nt] * pp.y), w1 = ex2_approx(ca2[nt] * pp.w);
-                        split_tf32(w0, bh[nt][0], l0);
-                        split_tf32(w1, bh[nt][1], l1);
-                        bx[nt][0] = pack_bf16x2(__uint_as_float(l0), __uint_as_float(l1));             // rows 2t, 2t+1: lo w
-                        bx[nt][1] = pack_bf16x2(__uint_as_float(bh[nt][0]), __uint_as_float(bh[nt][1]));  // rows 2t+8, +9: hi w
+                        const float2 aw = __fmul2_rn(ca2[nt], t2p);
+                        const float2 w = make_float2(ex2_approx(aw.x), ex2_approx(aw.y));
+                        const float2 h = make_float2(__uint_as_float(__float_as_uint(w.x) & 0xffffe000u),
+                                                     __uint_as_float(__float_as_uint(w.y) & 0xffffe000u));
+                        const float2 l = __ffma2_rn(h, make_float2(-1.f, -1.f), w);  // w - hi, exact
+                        bh[nt][0] = __float_as_uint(h.x);
+                        bh[nt][1] = __float_as_uint(h.y);
+                        bx[nt][0] = pack_bf16x2(l.x, l.y);
+                        bx[nt][1] = pack_bf16x2(h.x, h.y);
                     }
+                    // A fragments: TF32 (k, p0), (k+8, p0), (k, p1), (k+8, p1);
+                    // BF16 columns 2t, 2t+1 hold hi u at (p0, p1), columns 2t+8, 2t+9 lo u
                     uint32_t ah[MT][4], ax[MT][4];
 #pragma unroll
                     for (int mt = 0; mt < MT; ++mt) {
-                        const float u0 = ex2_approx(ca1[mt][0] * pp.x);  // (k0, p0)
-                        const float u1 = ex2_approx(ca1[mt][1] * pp.x);  // (k0+8, p0)
-                        const float u2 = ex2_approx(ca1[mt][0] * pp.z);  // (k0, p1)
-                        const float u3 = ex2_approx(ca1[mt][1] * pp.z);  // (k0+8, p1)
-                        {
-                            const float2 s2 = __fadd2_rn(make_float2(bt[r][mt][0], bt[r][mt][1]),
-                                                         __fadd2_rn(make_float2(u0, u1), make_float2(u2, u3)));
-                            bt[r][mt][0] = s2.x;
-                            bt[r][mt][1] = s2.y;
-                        }
-                        uint32_t l0, l1, l2, l3;
-                        split_tf32(u0, ah[mt][0], l0);
-                        split_tf32(u1, ah[mt][1], l1);
-                        split_tf32(u2, ah[mt][2], l2);
-                        split_tf32(u3, ah[mt][3], l3);
-                        // BF16 cross-term fragment: columns 2t, 2t+1 hold hi u, 2t+8, 2t+9 lo u
-                        ax[mt][0] = pack_bf16x2(__uint_as_float(ah[mt][0]), __uint_as_float(ah[mt][2]));
-                        ax[mt][1] = pack_bf16x2(__uint_as_float(ah[mt][1]), __uint_as_float(ah[mt][3]));
-                        ax[mt][2] = pack_bf16x2(__uint_as_float(l0), __uint_as_float(l2));
-                        ax[mt][3] = pack_bf16x2(__uint_as_float(l1), __uint_as_float(l3));
+                        const float2 a0 = __fmul2_rn(ca1[mt], t1p0), a1 = __fmul2_rn(ca1[mt], t1p1);
+                        const float2 u0 = make_float2(ex2_approx(a0.x), ex2_approx(a0.y));  // (k, p0), (k+8, p0)
+                        const float2 u1 = make_float2(ex2_approx(a1.x), ex2_approx(a1.y));  // (k, p1), (k+8, p1)
+                        bt[r][mt] = __fadd2_rn(bt[r][mt], __fadd2_rn(u0, u1));
+                        const float2 h0 = make_float2(__uint_as_float(__float_as_uint(u0.x) & 0xffffe000u),
+                                                      __uint_as_float(__float_as_uint(u0.y) & 0xffffe000u));
+                        const float2 h1 = make_float2(__uint_as_float(__float_as_uint(u1.x) & 0xffffe000u),
+                                                      __uint_as_float(__float_as_uint(u1.y) & 0xffffe000u));
+                        const float2 l0 = __ffma2_rn(h0, make_float2(-1.f, -1.f), u0);
+                        const float2 l1 = __ffma2_rn(h1, make_float2(-1.f, -1.f), u1);
+                        ah[mt][0] = __float_as_uint(h0.x);
+                        ah[mt][1] = __float_as_uint(h0.y);
+                        ah[mt][2] = __float_as_uint(h1.x);
+                        ah[mt][3] = __float_as_uint(h1.y);
+                        ax[mt][0] = pack_bf16x2(h0.x, h1.x);
+                        ax[mt][1] = pack_bf16x2(h0.y, h1.y);
+                        ax[mt][2] = pack_bf16x2(l0.x, l1.x);
+                        ax[mt][3] = pack_bf16x2(l0.y, l1.y);
                     }
                     // hi*hi on TF32; hi*lo + lo*hi together on one BF16 k16 MMA
 #pragma unroll
@@ -298,7 +307,7 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                     }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    float v = bt[r][mt][h];
+                    float v = h ? bt[r][mt].y : bt[r][mt].x;
                     v += __shfl_xor_sync(0xffffffffu, v, 1);
                     v += __shfl_xor_sync(0xffffffffu, v, 2);
                     if (t == 0) btS[warp * JW * G1 + r * G1 + 16 * mt + g + 8 * h] = v;
