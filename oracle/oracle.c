@@ -16,12 +16,21 @@
  *   L_cond     = sum_j ell_j                (conditional LOO log-likelihood)
  *   L_eq3      = (1/n) sum_j ln(fhat^{-j}(y_j|x_j) fhat^{-j}(x_j))   (Eq. 3)
  *              = (1/n) sum_j ln A_j - ln(n-1)                       (Sec. 3.2)
- * Every sum over i is evaluated with a log-sum-exp (max, then sum of shifted
- * exponentials) so that no bandwidth underflows; every loop is a straight loop
- * over all i != j (exclusion by index).  Rows j are split across threads;
+ * Second kernel family (kernel = 1): the radial Epanechnikov kernel that the
+ * paper uses in all its experiments (Sec. 4),
+ *   K(t) = c_d (1 - |t|^2) for |t| < 1, 0 otherwise,  c_d = (d + 2) / (2 V_d),
+ *   V_d = pi^{d/2} / Gamma(d/2 + 1) (volume of the unit d-ball),
+ * with the same h^{-d} scaling.  Its sums are plain sums of bounded terms.
+ * Compact support makes exact zeros possible: A_j = 0 gives ell_j = -inf
+ * (the paper's divergence at small bandwidths, Sec. 4.1), and so does an
+ * empty x-neighbourhood (B_j = 0, where Eq. 1 is 0/0).
+ * Every Gaussian sum over i is evaluated with a log-sum-exp (max, then sum of
+ * shifted exponentials) so that no bandwidth underflows; every loop is a
+ * straight loop over all i != j (exclusion by index).  Rows j are split across threads;
  * sums over j are Neumaier-compensated in a fixed block order, so results do
  * not depend on the thread count.
  */
+#define _GNU_SOURCE
 #include <math.h>
 #include <pthread.h>
 #include <stdint.h>
@@ -34,6 +43,10 @@
 typedef struct { double s, c; } neumaier_t;
 
 static void nm_add(neumaier_t *a, double v) {
+    if (isinf(v) || isinf(a->s)) {  /* -inf terms (Epanechnikov): no compensation */
+        a->s += v;
+        return;
+    }
     double t = a->s + v;
     if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
     else a->c += (v - t) + a->s;
@@ -71,6 +84,17 @@ static double sqdist(const double *a, const double *b, int d) {
     return s;
 }
 
+/* ln c_d of the radial Epanechnikov kernel in d dimensions. */
+static double epan_log_cd(int d) {
+    return log(d + 2.0) - log(2.0) - 0.5 * d * log(M_PI) + lgamma(0.5 * d + 1.0);
+}
+
+/* Epanechnikov profile (1 - t2/h^2)_+ (no normalisation). */
+static double epan_prof(double t2, double h) {
+    const double v = 1.0 - t2 / (h * h);
+    return v > 0.0 ? v : 0.0;
+}
+
 /* ln sum_{i != j} exp(e_i), by max then shifted sum. */
 static double lse_excl(const double *e, int64_t N, int64_t j) {
     double m = -INFINITY;
@@ -97,9 +121,33 @@ typedef struct {
     neumaier_t *blk_cond;     /* optional: n_blocks x G1 x G2 */
     neumaier_t *blk_lnA;      /* optional: n_blocks x G1 x G2 */
     int64_t block;            /* rows per work item (fixed: sums do not depend on threads) */
+    int kernel;               /* 0 Gaussian, 1 Epanechnikov */
     int64_t next_block;
     pthread_mutex_t mu;
 } rows_job_t;
+
+/* Epanechnikov row terms: plain sums of K_h1 K_h2 and of K_h1 over i != j. */
+static void row_terms_epan(const rows_job_t *J, int64_t j, const double *dx2, const double *dy2,
+                           double *ell_out, double *lnA_out) {
+    const int d = J->d;
+    const double lcd = epan_log_cd(d), lc1 = epan_log_cd(1);
+    for (int k = 0; k < J->G1; ++k) {
+        const double h1 = J->h1[k];
+        double B = 0.0;
+        for (int64_t i = 0; i < J->N; ++i)
+            if (i != j) B += epan_prof(dx2[i], h1);
+        const double lnB = log(B) + lcd - d * log(h1);
+        for (int l = 0; l < J->G2; ++l) {
+            const double h2 = J->h2[l];
+            double A = 0.0;
+            for (int64_t i = 0; i < J->N; ++i)
+                if (i != j) A += epan_prof(dx2[i], h1) * epan_prof(dy2[i], h2);
+            const double lnA = log(A) + lcd - d * log(h1) + lc1 - log(h2);
+            ell_out[k * J->G2 + l] = B > 0.0 ? lnA - lnB : -INFINITY;
+            lnA_out[k * J->G2 + l] = lnA;
+        }
+    }
+}
 
 static void row_terms(const rows_job_t *J, int64_t j, double *dx2, double *dy2, double *e,
                       double *ell_out, double *lnA_out) {
@@ -108,6 +156,10 @@ static void row_terms(const rows_job_t *J, int64_t j, double *dx2, double *dy2, 
         dx2[i] = sqdist(J->x + j * d, J->x + i * d, d);
         double t = J->y[j] - J->y[i];
         dy2[i] = t * t;
+    }
+    if (J->kernel == 1) {
+        row_terms_epan(J, j, dx2, dy2, ell_out, lnA_out);
+        return;
     }
     for (int k = 0; k < J->G1; ++k) {
         const double h1 = J->h1[k];
@@ -173,9 +225,10 @@ static void run_rows(rows_job_t *J, int n_threads) {
 void oracle_loo_rows(const double *x, const double *y, int64_t N, int d,
                      const double *h1, int G1, const double *h2, int G2,
                      const int64_t *rows, int64_t n_rows, double *ell, double *lnA,
-                     int n_threads) {
+                     int n_threads, int kernel) {
     rows_job_t J;
     memset(&J, 0, sizeof(J));
+    J.kernel = kernel;
     J.x = x; J.y = y; J.h1 = h1; J.h2 = h2; J.N = N; J.d = d; J.G1 = G1; J.G2 = G2;
     J.rows = rows; J.n_rows = n_rows; J.ell = ell; J.lnA = lnA;
     J.block = 1;
@@ -185,11 +238,12 @@ void oracle_loo_rows(const double *x, const double *y, int64_t N, int d,
 /* Whole-grid scores: L_cond[k][l] = sum_j ell_j, L_eq3[k][l] = (1/N) sum_j ln A_j - ln(N-1). */
 void oracle_loo_grid(const double *x, const double *y, int64_t N, int d,
                      const double *h1, int G1, const double *h2, int G2,
-                     double *L_cond, double *L_eq3, int n_threads) {
+                     double *L_cond, double *L_eq3, int n_threads, int kernel) {
     const int64_t G = (int64_t)G1 * G2;
     const int64_t n_blocks = (N + ROW_BLOCK - 1) / ROW_BLOCK;
     rows_job_t J;
     memset(&J, 0, sizeof(J));
+    J.kernel = kernel;
     J.x = x; J.y = y; J.h1 = h1; J.h2 = h2; J.N = N; J.d = d; J.G1 = G1; J.G2 = G2;
     J.rows = NULL; J.n_rows = N;
     J.block = ROW_BLOCK;
@@ -226,14 +280,51 @@ typedef struct {
     int64_t n_rows;
     double *row_out;          /* optional n_rows x 3: ell, d/dlnh1, d/dlnh2 */
     neumaier_t *blk;          /* n_blocks x 3 */
+    int kernel;               /* 0 Gaussian, 1 Epanechnikov */
     int64_t next_block;
     pthread_mutex_t mu;
 } grad_job_t;
+
+/* Epanechnikov: with u = (1 - dx2/h1^2)_+ and w = (1 - dy2/h2^2)_+,
+ *   d K_h1/d ln h1 = c_d h1^{-d} (2 dx2/h1^2 [dx2 < h1^2] - d u),
+ *   d K_h2/d ln h2 = c_1 h2^{-1} (2 dy2/h2^2 [dy2 < h2^2] - w),
+ * so, with v = 2 dx2/h1^2 [dx2 < h1^2] and z = 2 dy2/h2^2 [dy2 < h2^2],
+ *   d ell_j/d ln h1 = sum v w / sum u w - sum v / sum u,
+ *   d ell_j/d ln h2 = sum u z / sum u w - 1.
+ * A row with A_j = 0 has ell_j = -inf and contributes 0 to both derivatives. */
+static void grad_row_epan(const grad_job_t *J, int64_t j, const double *dx2, const double *dy2,
+                          double out[3]) {
+    const int d = J->d;
+    const double h1 = J->h1, h2 = J->h2;
+    double sA = 0, sAv = 0, sAz = 0, sB = 0, sBv = 0;
+    for (int64_t i = 0; i < J->N; ++i) {
+        if (i == j) continue;
+        const double u = epan_prof(dx2[i], h1), w = epan_prof(dy2[i], h2);
+        const double v = dx2[i] < h1 * h1 ? 2.0 * dx2[i] / (h1 * h1) : 0.0;
+        const double z = dy2[i] < h2 * h2 ? 2.0 * dy2[i] / (h2 * h2) : 0.0;
+        sA += u * w; sAv += v * w; sAz += u * z;
+        sB += u; sBv += v;
+    }
+    const double lnA = log(sA) + epan_log_cd(d) - d * log(h1) + epan_log_cd(1) - log(h2);
+    const double lnB = log(sB) + epan_log_cd(d) - d * log(h1);
+    out[0] = sB > 0.0 ? lnA - lnB : -INFINITY;
+    out[1] = sA > 0.0 ? sAv / sA - sBv / sB : 0.0;
+    out[2] = sA > 0.0 ? sAz / sA - 1.0 : 0.0;
+}
 
 static void grad_row(const grad_job_t *J, int64_t j, double *dx2, double *dy2, double out[3]) {
     const int d = J->d;
     const double a1 = 1.0 / (2.0 * J->h1 * J->h1), a2 = 1.0 / (2.0 * J->h2 * J->h2);
     double mA = -INFINITY, mB = -INFINITY;
+    if (J->kernel == 1) {
+        for (int64_t i = 0; i < J->N; ++i) {
+            dx2[i] = sqdist(J->x + j * d, J->x + i * d, d);
+            double t = J->y[j] - J->y[i];
+            dy2[i] = t * t;
+        }
+        grad_row_epan(J, j, dx2, dy2, out);
+        return;
+    }
     for (int64_t i = 0; i < J->N; ++i) {
         dx2[i] = sqdist(J->x + j * d, J->x + i * d, d);
         double t = J->y[j] - J->y[i];
@@ -284,9 +375,10 @@ static void *grad_worker(void *arg) {
  * (rows == NULL: all N rows).  out3 = {L, dL/dlnh1, dL/dlnh2}. */
 void oracle_grad(const double *x, const double *y, int64_t N, int d, double h1, double h2,
                  const int64_t *rows, int64_t n_rows, double *row_out, double *out3,
-                 int n_threads) {
+                 int n_threads, int kernel) {
     grad_job_t J;
     memset(&J, 0, sizeof(J));
+    J.kernel = kernel;
     J.x = x; J.y = y; J.N = N; J.d = d; J.h1 = h1; J.h2 = h2;
     J.rows = rows; J.n_rows = n_rows; J.row_out = row_out;
     const int64_t n_blocks = (n_rows + ROW_BLOCK - 1) / ROW_BLOCK;
@@ -315,9 +407,29 @@ typedef struct {
     int d, G;
     double h1, h2;
     double *f;
+    int kernel;               /* 0 Gaussian, 1 Epanechnikov */
     int64_t next;
     pthread_mutex_t mu;
 } dens_job_t;
+
+/* Epanechnikov: plain sums; a query with no x-neighbour inside h1 (Eq. 1 is
+ * 0/0 there) gets f = 0 on the whole y grid. */
+static void dens_query_epan(const dens_job_t *J, int64_t q, double *ex) {
+    const double lc1 = epan_log_cd(1);
+    double B = 0.0;
+    for (int64_t i = 0; i < J->N; ++i) {
+        ex[i] = epan_prof(sqdist(J->xq + q * J->d, J->x + i * J->d, J->d), J->h1);
+        B += ex[i];
+    }
+    for (int g = 0; g < J->G; ++g) {
+        double A = 0.0;
+        for (int64_t i = 0; i < J->N; ++i) {
+            const double t = J->yg[g] - J->y[i];
+            A += ex[i] * epan_prof(t * t, J->h2);
+        }
+        J->f[q * J->G + g] = B > 0.0 ? A / B * exp(lc1 - log(J->h2)) : 0.0;
+    }
+}
 
 static void *dens_worker(void *arg) {
     dens_job_t *J = (dens_job_t *)arg;
@@ -329,6 +441,10 @@ static void *dens_worker(void *arg) {
         int64_t q = J->next++;
         pthread_mutex_unlock(&J->mu);
         if (q >= J->Q) break;
+        if (J->kernel == 1) {
+            dens_query_epan(J, q, ex);
+            continue;
+        }
         double mB = -INFINITY;
         for (int64_t i = 0; i < J->N; ++i) {
             ex[i] = -a1 * sqdist(J->xq + q * J->d, J->x + i * J->d, J->d);
@@ -354,12 +470,14 @@ static void *dens_worker(void *arg) {
     return NULL;
 }
 
-/* f[q][g] = fhat(yg[g] | xq[q]) of Eq. 1 with Gaussian kernels, all N points. */
+/* f[q][g] = fhat(yg[g] | xq[q]) of Eq. 1 over all N points (kernel 0 Gaussian,
+ * 1 Epanechnikov). */
 void oracle_density(const double *x, const double *y, int64_t N, int d, double h1, double h2,
                     const double *xq, int64_t Q, const double *yg, int G, double *f,
-                    int n_threads) {
+                    int n_threads, int kernel) {
     dens_job_t J;
     memset(&J, 0, sizeof(J));
+    J.kernel = kernel;
     J.x = x; J.y = y; J.xq = xq; J.yg = yg; J.N = N; J.Q = Q; J.d = d; J.G = G;
     J.h1 = h1; J.h2 = h2; J.f = f;
     pthread_mutex_init(&J.mu, NULL);

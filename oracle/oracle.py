@@ -9,6 +9,8 @@ Every function follows the definitions of Holmes, Gray & Isbell:
 Eq. 1 (double-kernel conditional density), Eq. 3 and its expansion in
 Sec. 3.2 (leave-one-out log-likelihood, A_j and B_j sums), Sec. 4 (per-
 dimension standardisation).  Bandwidth roles: h1 on x, h2 on y.
+``kernel`` selects the kernel family: "gauss" (standard normal) or "epan"
+(the radial Epanechnikov kernel of the paper's experiments, Sec. 4).
 """
 from __future__ import annotations
 
@@ -49,16 +51,26 @@ def _load():
         lib.oracle_standardize.restype = ctypes.c_int
         lib.oracle_loo_rows.argtypes = [_dp, _dp, ctypes.c_int64, ctypes.c_int, _dp, ctypes.c_int,
                                         _dp, ctypes.c_int, _i64p, ctypes.c_int64, _dp, _dp,
-                                        ctypes.c_int]
+                                        ctypes.c_int, ctypes.c_int]
         lib.oracle_loo_grid.argtypes = [_dp, _dp, ctypes.c_int64, ctypes.c_int, _dp, ctypes.c_int,
-                                        _dp, ctypes.c_int, _dp, _dp, ctypes.c_int]
+                                        _dp, ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int]
         lib.oracle_grad.argtypes = [_dp, _dp, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
-                                    ctypes.c_double, _i64p, ctypes.c_int64, _dp, _dp, ctypes.c_int]
+                                    ctypes.c_double, _i64p, ctypes.c_int64, _dp, _dp, ctypes.c_int,
+                                    ctypes.c_int]
         lib.oracle_density.argtypes = [_dp, _dp, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, _dp, ctypes.c_int64, _dp, ctypes.c_int,
-                                       _dp, ctypes.c_int]
+                                       _dp, ctypes.c_int, ctypes.c_int]
         _lib = lib
     return _lib
+
+
+KERNELS = {"gauss": 0, "epan": 1}
+
+
+def _kern(kernel: str) -> int:
+    if kernel not in KERNELS:
+        raise ValueError("kernel must be one of %s" % sorted(KERNELS))
+    return KERNELS[kernel]
 
 
 def _f64(a) -> np.ndarray:
@@ -97,7 +109,7 @@ def _prep(x, y, standardize_x: bool):
 
 
 def loo_grid(x, y, h1, h2, standardize_x: bool = False,
-             n_threads: Optional[int] = None) -> Tuple[np.ndarray, np.ndarray]:
+             n_threads: Optional[int] = None, kernel: str = "gauss") -> Tuple[np.ndarray, np.ndarray]:
     """(L_cond, L_eq3), each G1 x G2 (h1 major)."""
     x, y = _prep(x, y, standardize_x)
     h1, h2 = _f64(h1), _f64(h2)
@@ -105,12 +117,12 @@ def loo_grid(x, y, h1, h2, standardize_x: bool = False,
     Lc = np.empty((G1, G2))
     Le = np.empty((G1, G2))
     _load().oracle_loo_grid(_ptr(x), _ptr(y), x.shape[0], x.shape[1], _ptr(h1), G1, _ptr(h2), G2,
-                            _ptr(Lc), _ptr(Le), n_threads or default_threads())
+                            _ptr(Lc), _ptr(Le), n_threads or default_threads(), _kern(kernel))
     return Lc, Le
 
 
 def loo_rows(x, y, h1, h2, rows=None, standardize_x: bool = False,
-             n_threads: Optional[int] = None) -> Tuple[np.ndarray, np.ndarray]:
+             n_threads: Optional[int] = None, kernel: str = "gauss") -> Tuple[np.ndarray, np.ndarray]:
     """(ell, lnA) for the chosen rows, each n_rows x G1 x G2."""
     x, y = _prep(x, y, standardize_x)
     h1, h2 = _f64(h1), _f64(h2)
@@ -120,12 +132,13 @@ def loo_rows(x, y, h1, h2, rows=None, standardize_x: bool = False,
     ell = np.empty((n, h1.size, h2.size))
     lnA = np.empty((n, h1.size, h2.size))
     _load().oracle_loo_rows(_ptr(x), _ptr(y), N, x.shape[1], _ptr(h1), h1.size, _ptr(h2), h2.size,
-                            _ptr(r), n, _ptr(ell), _ptr(lnA), n_threads or default_threads())
+                            _ptr(r), n, _ptr(ell), _ptr(lnA), n_threads or default_threads(),
+                            _kern(kernel))
     return ell, lnA
 
 
 def grad(x, y, h1: float, h2: float, rows=None, standardize_x: bool = False,
-         n_threads: Optional[int] = None, per_row: bool = False):
+         n_threads: Optional[int] = None, per_row: bool = False, kernel: str = "gauss"):
     """(L, dL/dln h1, dL/dln h2) summed over the rows; per_row also returns
     an n_rows x 3 array of (ell_j, d ell_j/dln h1, d ell_j/dln h2)."""
     x, y = _prep(x, y, standardize_x)
@@ -135,12 +148,12 @@ def grad(x, y, h1: float, h2: float, rows=None, standardize_x: bool = False,
     out = np.empty(3)
     row_out = np.empty((n, 3)) if per_row else None
     _load().oracle_grad(_ptr(x), _ptr(y), N, x.shape[1], float(h1), float(h2), _ptr(r), n,
-                        _ptr(row_out), _ptr(out), n_threads or default_threads())
+                        _ptr(row_out), _ptr(out), n_threads or default_threads(), _kern(kernel))
     return (out, row_out) if per_row else out
 
 
 def density(x, y, h1: float, h2: float, xq, ygrid, standardize_x: bool = False,
-            n_threads: Optional[int] = None) -> np.ndarray:
+            n_threads: Optional[int] = None, kernel: str = "gauss") -> np.ndarray:
     """f[q, g] = fhat(ygrid[g] | xq[q]) (Eq. 1).  With standardize_x the
     queries are mapped by the data's mean and sd, like the data."""
     xr = _f64(x)
@@ -163,5 +176,5 @@ def density(x, y, h1: float, h2: float, xq, ygrid, standardize_x: bool = False,
     f = np.empty((q.shape[0], g.size))
     _load().oracle_density(_ptr(xs), _ptr(yv), xs.shape[0], xs.shape[1], float(h1), float(h2),
                            _ptr(q), q.shape[0], _ptr(g), g.size, _ptr(f),
-                           n_threads or default_threads())
+                           n_threads or default_threads(), _kern(kernel))
     return f

@@ -27,6 +27,20 @@ MUTATIONS = {
                         "double sd = sqrt(nm_val(&v) / (double)N);"),
     "eq3_wrong_count": ("L_eq3[c] = nm_val(&b) / (double)N - log((double)(N - 1));",
                         "L_eq3[c] = nm_val(&b) / (double)N - log((double)N);"),
+    # Epanechnikov kernel
+    "epan_support_not_truncated": ("return v > 0.0 ? v : 0.0;", "return v;"),
+    "epan_constant_halved": ("return log(d + 2.0) - log(2.0) - 0.5 * d * log(M_PI) + lgamma(0.5 * d + 1.0);",
+                             "return log(d + 2.0) - 0.5 * d * log(M_PI) + lgamma(0.5 * d + 1.0);"),
+    "epan_ball_volume_power": ("return log(d + 2.0) - log(2.0) - 0.5 * d * log(M_PI) + lgamma(0.5 * d + 1.0);",
+                               "return log(d + 2.0) - log(2.0) - d * log(M_PI) + lgamma(0.5 * d + 1.0);"),
+    "epan_leave_one_out_dropped": ("if (i != j) A += epan_prof(dx2[i], h1) * epan_prof(dy2[i], h2);",
+                                   "A += epan_prof(dx2[i], h1) * epan_prof(dy2[i], h2);"),
+    "epan_gradient_indicator_dropped": ("const double v = dx2[i] < h1 * h1 ? 2.0 * dx2[i] / (h1 * h1) : 0.0;",
+                                        "const double v = 2.0 * dx2[i] / (h1 * h1);"),
+    "epan_gradient_h2_sign": ("out[2] = sA > 0.0 ? sAz / sA - 1.0 : 0.0;",
+                              "out[2] = sA > 0.0 ? sAz / sA + 1.0 : 0.0;"),
+    "epan_density_missing_h2": ("J->f[q * J->G + g] = B > 0.0 ? A / B * exp(lc1 - log(J->h2)) : 0.0;",
+                                "J->f[q * J->G + g] = B > 0.0 ? A / B * exp(lc1) : 0.0;"),
 }
 
 

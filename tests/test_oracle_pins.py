@@ -200,3 +200,147 @@ def test_bandwidth_grid_inclusive_log_spaced():
     assert g[0] == 0.05 and abs(g[-1] - 2.0) < 1e-15
     r = g[1:] / g[:-1]
     np.testing.assert_allclose(r, r[0], rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Radial Epanechnikov kernel (Sec. 4): K(t) = c_d (1 - |t|^2)_+ with the
+# textbook normalising constants c_1 = 3/4, c_2 = 2/pi, c_3 = 15/(8 pi).
+# ---------------------------------------------------------------------------
+EPAN_CD = {1: 0.75, 2: 2.0 / math.pi, 3: 15.0 / (8.0 * math.pi)}
+
+
+def _epan_np(t2, h, d):
+    r2 = np.asarray(t2, dtype=np.float64) / (h * h)
+    return np.where(r2 < 1.0, EPAN_CD[d] * (1.0 - r2) / h ** d, 0.0)
+
+
+@pytest.mark.parametrize("N,d,seed", [(6, 1, 30), (9, 2, 31), (12, 3, 32)])
+def test_epan_oracle_matches_brute_force(N, d, seed):
+    """Eq. 1 / Eq. 3 with the Epanechnikov kernel, evaluated directly; the
+    bandwidths are chosen so that some cells have empty supports (-inf)."""
+    x, y = _small(N, d, seed)
+    h1 = np.array([0.05, 0.9, 2.5])
+    h2 = np.array([0.02, 0.6, 3.0])
+    Lc, Le = oracle.loo_grid(x, y, h1, h2, n_threads=2, kernel="epan")
+    ell, lnA = oracle.loo_rows(x, y, h1, h2, kernel="epan")
+    xl, yl = x.astype(np.float64).tolist(), y.astype(np.float64).tolist()
+    n_inf = 0
+    for k in range(h1.size):
+        for l in range(h2.size):
+            bc = brute.L_cond(xl, yl, h1[k], h2[l], "epan")
+            be = brute.L_eq3(xl, yl, h1[k], h2[l], "epan")
+            for got, want in ((Lc[k, l], bc), (Le[k, l], be)):
+                if math.isinf(want):
+                    n_inf += 1
+                    assert got == want
+                else:
+                    assert abs(got - want) <= 1e-11 * max(1.0, abs(want))
+    assert n_inf > 0 and np.isfinite(Lc).any()
+    with np.errstate(invalid="ignore"):
+        np.testing.assert_allclose(ell.sum(0), Lc, rtol=1e-12)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_epan_two_points_closed_form(d):
+    """N = 2: A_1 = A_2 = K_h1(x1-x2) K_h2(y1-y2), B_j = K_h1(x1-x2), so
+    L_cond = 2 ln K_h2(dy) and L_eq3 = ln K_h1(dx) + ln K_h2(dy) inside the
+    supports; an x distance outside h1 or a y distance outside h2 gives -inf."""
+    x, y = _small(2, d, 33)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    dx2 = float(((xd[0] - xd[1]) ** 2).sum())
+    dy2 = float((yd[0] - yd[1]) ** 2)
+    h1 = np.array([0.5 * math.sqrt(dx2), 1.3 * math.sqrt(dx2), 7.0])
+    h2 = np.array([0.5 * math.sqrt(dy2), 1.2 * math.sqrt(dy2), 4.0])
+    Lc, Le = oracle.loo_grid(x, y, h1, h2, kernel="epan")
+    for k, a in enumerate(h1):
+        for l, b in enumerate(h2):
+            kx, ky = float(_epan_np(dx2, a, d)), float(_epan_np(dy2, b, 1))
+            if kx == 0.0 or ky == 0.0:
+                assert Lc[k, l] == -math.inf and Le[k, l] == -math.inf
+            else:
+                assert abs(Lc[k, l] - 2 * math.log(ky)) <= 1e-12 * max(1, abs(Lc[k, l]))
+                assert abs(Le[k, l] - (math.log(kx) + math.log(ky))) <= 1e-12 * max(1, abs(Le[k, l]))
+
+
+def test_epan_h1_infinite_limit_is_loo_kde_of_y():
+    """h1 -> inf: the x weights become equal, so L_cond is the LOO
+    Epanechnikov KDE log-likelihood of y alone."""
+    x, y = _small(40, 2, 34)
+    yd = y.astype(np.float64)
+    h2 = 0.9
+    Lc, _ = oracle.loo_grid(x, y, np.array([1e7]), np.array([h2]), kernel="epan")
+    K = _epan_np((yd[:, None] - yd[None, :]) ** 2, h2, 1)
+    np.fill_diagonal(K, 0.0)
+    want = np.log(K.sum(1) / (yd.size - 1)).sum()
+    assert abs(Lc[0, 0] - want) <= 1e-9 * abs(want)
+
+
+def test_epan_invariances():
+    x, y = _small(30, 2, 35)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    h1, h2 = np.array([1.5, 2.4]), np.array([1.8, 2.6])
+    L0, _ = oracle.loo_grid(xd, yd, h1, h2, kernel="epan")
+    assert np.isfinite(L0).all()
+    perm = np.random.default_rng(1).permutation(30)
+    Lp, _ = oracle.loo_grid(xd[perm], yd[perm], h1, h2, kernel="epan")
+    np.testing.assert_allclose(Lp, L0, rtol=1e-12)
+    c = 2.0  # a power of two keeps every scaled distance exact
+    Lx, _ = oracle.loo_grid(c * xd, yd, c * h1, h2, kernel="epan")
+    np.testing.assert_allclose(Lx, L0, rtol=1e-12)
+    Ly, _ = oracle.loo_grid(xd, c * yd, h1, c * h2, kernel="epan")
+    np.testing.assert_allclose(Ly, L0 - 30 * math.log(c), rtol=1e-12)
+
+
+def test_epan_kernel_sums_with_pair_distances():
+    """sum_j A_j and sum_j B_j are twice the sums over unordered pairs
+    (scipy pdist), with the textbook constants c_3 and c_1."""
+    N, d = 50, 3
+    x, y = _small(N, d, 36)
+    h1, h2 = 2.6, 8.0  # every row keeps an x-neighbour, and A_j > 0 whenever B_j > 0
+    ell, lnA = oracle.loo_rows(x, y, np.array([h1]), np.array([h2]), kernel="epan")
+    lnB = lnA - ell
+    kx = _epan_np(pdist(x.astype(np.float64), "sqeuclidean"), h1, d)
+    ky = _epan_np(pdist(y.astype(np.float64)[:, None], "sqeuclidean"), h2, 1)
+    assert (kx > 0).any() and (kx * ky > 0).any()
+    np.testing.assert_allclose(np.exp(lnB[:, 0, 0]).sum(), 2 * kx.sum(), rtol=1e-12)
+    np.testing.assert_allclose(np.exp(lnA[:, 0, 0]).sum(), 2 * (kx * ky).sum(), rtol=1e-12)
+
+
+def test_epan_gradient_matches_finite_differences():
+    x, y = _small(60, 2, 37)
+    h1, h2 = 1.9, 2.2
+    out, rows = oracle.grad(x, y, h1, h2, per_row=True, kernel="epan")
+    Lc, _ = oracle.loo_grid(x, y, np.array([h1]), np.array([h2]), kernel="epan")
+    assert np.isfinite(Lc).all() and abs(out[0] - Lc[0, 0]) < 1e-10 * abs(Lc[0, 0])
+    np.testing.assert_allclose(rows.sum(0), out, rtol=1e-12)
+    s = 1e-5
+    e = math.exp
+    f = lambda a, b: oracle.loo_grid(x, y, np.array([a]), np.array([b]), kernel="epan")[0][0, 0]
+    g1 = (f(h1 * e(s), h2) - f(h1 * e(-s), h2)) / (2 * s)
+    g2 = (f(h1, h2 * e(s)) - f(h1, h2 * e(-s))) / (2 * s)
+    assert abs(out[1] - g1) <= 1e-5 * (abs(g1) + 1)
+    assert abs(out[2] - g2) <= 1e-5 * (abs(g2) + 1)
+    xl, yl = x.astype(np.float64).tolist(), y.astype(np.float64).tolist()
+    b1, b2 = brute.grad_fd(xl, yl, h1, h2, step=1e-5, kernel="epan")
+    assert abs(out[1] - b1) <= 1e-5 * (abs(b1) + 1) and abs(out[2] - b2) <= 1e-5 * (abs(b2) + 1)
+
+
+def test_epan_density_matches_brute_and_integrates_to_one():
+    x, y = _small(40, 2, 38)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    h1, h2 = 0.9, 0.5
+    xq = np.vstack([xd[:3] + 0.1, [[50.0, 50.0]]])  # the last query has no x-neighbour
+    grid = np.linspace(yd.min() - 1.2 * h2, yd.max() + 1.2 * h2, 40001)
+    f = oracle.density(xd, yd, h1, h2, xq, grid, kernel="epan")
+    assert (f[3] == 0.0).all()
+    np.testing.assert_allclose(np.trapezoid(f[:3], grid, axis=1), 1.0, atol=1e-7)
+    # mean of fhat(.|x) = sum_i u_i y_i / sum_i u_i (the kernel is symmetric)
+    for q in range(3):
+        u = _epan_np(((xd - xq[q]) ** 2).sum(1), h1, 2)
+        np.testing.assert_allclose(np.trapezoid(grid * f[q], grid), (u * yd).sum() / u.sum(),
+                                   rtol=1e-6, atol=1e-7)
+    xl, yl = xd.tolist(), yd.tolist()
+    for q in range(4):
+        for g in range(0, grid.size, 5000):
+            want = brute.density(xl, yl, xq[q].tolist(), grid[g], h1, h2, "epan")
+            assert abs(f[q, g] - want) <= 1e-12 * want + 1e-300
