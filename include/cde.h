@@ -4,14 +4,24 @@
  * Conditional Density Estimation".
  *
  * Notation (the paper's h1/h2 roles are swapped here; this library uses):
- *   h1 = bandwidth of the x kernel (d_x dimensions, isotropic Gaussian),
- *   h2 = bandwidth of the y kernel (scalar y, Gaussian).
- *   K_h(t) = h^{-d} K(t/h), K the standard normal density (Sec. 2).
+ *   h1 = bandwidth of the x kernel (d_x dimensions, isotropic),
+ *   h2 = bandwidth of the y kernel (scalar y).
+ *   K_h(t) = h^{-d} K(t/h) (Sec. 2), K one of two radial kernel families,
+ *   chosen per dataset at creation:
+ *     Gaussian (default): K the standard normal density;
+ *     Epanechnikov (CDE_KERNEL_EPANECHNIKOV, the kernel of all the paper's
+ *     experiments, Sec. 4): K(t) = c_d (1 - |t|^2) for |t| < 1, else 0,
+ *     c_d = (d + 2) / (2 V_d), V_d = pi^{d/2} / Gamma(d/2 + 1).
  *   fhat(y|x) = sum_i K_h1(|x-x_i|) K_h2(y-y_i) / sum_i K_h1(|x-x_i|)   (Eq. 1)
  *   A_j = sum_{i!=j} K_h1(|x_j-x_i|) K_h2(y_j-y_i),
  *   B_j = sum_{i!=j} K_h1(|x_j-x_i|)                          (Sec. 3.2)
  *   L_cond(h1,h2) = sum_j ln(A_j / B_j)      (conditional LOO log-likelihood)
  *   L_eq3(h1,h2)  = (1/N) sum_j ln A_j - ln(N-1)   (Eq. 3 and its expansion)
+ *   With the Epanechnikov kernel sums can be exactly zero: A_j = 0 (and the
+ *   0/0 case B_j = 0) give ln(A_j/B_j) = -inf, so a score is -inf at
+ *   bandwidths where some left-out point has no neighbour inside the supports
+ *   (the divergence at small bandwidths of Sec. 4.1); a density query with no
+ *   x-neighbour inside h1 gets fhat = 0.
  *
  * Conventions for every entry point:
  *   - Returns a cde_status; never aborts the process.  On failure the
@@ -53,7 +63,10 @@ typedef enum {
 } cde_status;
 
 enum { CDE_OUT_DEVICE = 1,    /* output pointers are device memory; call is async */
-       CDE_IN_DEVICE = 2 };   /* input arrays (x, y, queries, grids) are device memory */
+       CDE_IN_DEVICE = 2,     /* input arrays (x, y, queries, grids) are device memory */
+       CDE_KERNEL_EPANECHNIKOV = 4 };  /* cde_create_dataset: Epanechnikov kernels (Sec. 4) */
+
+enum { CDE_KERNEL_GAUSS = 0, CDE_KERNEL_EPAN = 1 };  /* values reported by cde_dataset_kernel */
 
 /* Library version string (static storage). */
 const char *cde_version(void);
@@ -77,8 +90,11 @@ void cde_shutdown(cde_ctx *ctx);
  *   divides it by its sample standard deviation (ddof = 1), in FP64 (Sec. 4);
  *   y is never scaled.  Requires N >= 2, d_x >= 1, finite values, and a
  *   non-zero spread in every dimension when standardising.
- *   Also computes, once, each row's nearest squared distance to any other row
- *   in x and in y (the per-row shifts used to keep exp2 in range).
+ *   CDE_KERNEL_EPANECHNIKOV in `flags` makes every score, gradient and
+ *   density on this dataset use Epanechnikov kernels on x and y (default:
+ *   Gaussian).  For Gaussian datasets the call also computes, once, each row's
+ *   nearest squared distance to any other row in x and in y (the per-row
+ *   shifts used to keep exp2 in range); Epanechnikov sums need no shift.
  *   *out receives the handle.  Memory: about (d_x + 3) * 4 * N bytes.
  */
 int cde_create_dataset(cde_ctx *ctx, const float *x, const float *y, int64_t N, int d_x,
@@ -92,6 +108,9 @@ int cde_destroy_dataset(cde_ctx *ctx, cde_dataset ds);
 int cde_dataset_info(cde_ctx *ctx, cde_dataset ds, int64_t *N, int *d_x, double *mean,
                      double *sd);
 
+/* Kernel family of a dataset: *kernel = CDE_KERNEL_GAUSS or CDE_KERNEL_EPAN. */
+int cde_dataset_kernel(cde_ctx *ctx, cde_dataset ds, int *kernel);
+
 /*
  * Exact LOO log-likelihood over a bandwidth grid (Eq. 3 and Sec. 3.2),
  * every pair (j, i != j) evaluated once for all G1 x G2 bandwidth pairs.
@@ -101,7 +120,9 @@ int cde_dataset_info(cde_ctx *ctx, cde_dataset ds, int64_t *N, int *d_x, double 
  * Numerics: pair sums in FP32 with per-row shifts (exp2 on the SFU),
  * exact joint-shift recomputation of any cell whose shifted numerator falls
  * below 2^-40, log-ratio and the sum over j in FP64 in a fixed order (the
- * result is bitwise reproducible).
+ * result is bitwise reproducible).  Epanechnikov datasets: the kernel
+ * profile (1 - t^2/h^2)_+ by one saturating FP32 FMA per factor, no shifts,
+ * and -inf scores where a sum is zero (see the notation above).
  */
 int cde_loo_loglik(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const double *h2,
                    int G2, double *L_cond_out, double *L_eq3_out, int flags, void *stream);
@@ -193,6 +214,43 @@ int cde_autotune(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const d
 /* Read / set the tile parameters for the shape of a G1 x G2 grid (0 = default). */
 int cde_tuning_get(cde_ctx *ctx, int G1, int G2, int *units_per_tile, int *ctas_per_sm);
 int cde_tuning_set(cde_ctx *ctx, int G1, int G2, int units_per_tile, int ctas_per_sm);
+
+/* ------------------------------------------------------------------ */
+/* Bandwidth selection as in the paper (Sec. 3.5, Sec. 4)              */
+/* ------------------------------------------------------------------ */
+enum { CDE_L_COND = 0, CDE_L_EQ3 = 1 };   /* which score a selector maximises */
+
+/*
+ * Random-search selection (Sec. 3.5; bandwidths sampled from [0, h_max],
+ * Sec. 4).  Each of `rounds` rounds draws G1 values of h1 uniformly from
+ * (0, h1_max] and G2 values of h2 from (0, h2_max], scores all G1 x G2 pairs
+ * exactly (one grid evaluation, as cde_loo_loglik) and keeps the pair with the
+ * largest score `objective` (CDE_L_EQ3: the paper's Eq. 3; CDE_L_COND: the
+ * conditional score).  Draws: value k of the SplitMix64 stream of `seed`
+ * (Steele, Lea & Flood 2014; counter form z = seed + (k+1) 0x9E3779B97F4A7C15,
+ * then the published mixing steps) gives u = (z >> 11) 2^-53 and
+ * h = h_max (1 - u), raised to at least 1e-6 h_max; round r uses k = r (G1 + G2)
+ * + 0 .. G1-1 for h1, then the next G2 values for h2.
+ *   best[4] (host) = {h1, h2, L_cond, L_eq3} of the first strict maximum in
+ *   (round, k, l) order; scores of -inf never win (all -inf: best h = NaN).
+ *   Optional host outputs (NULL to skip): h1_out[rounds x G1],
+ *   h2_out[rounds x G2], Lc_out / Le_out[rounds x G1 x G2].
+ *   1 <= G1, G2 <= 32; h_max in [1e-6, 1e6].  Synchronous.
+ */
+int cde_select_random(cde_ctx *ctx, cde_dataset ds, double h1_max, double h2_max, int rounds,
+                      int G1, int G2, uint64_t seed, int objective, double *best,
+                      double *h1_out, double *h2_out, double *Lc_out, double *Le_out);
+
+/*
+ * Reference-rule bandwidths (the paper's baseline, Sec. 4.2, after Silverman):
+ * each kernel gets the AMISE-optimal bandwidth of an unconditional KDE of a
+ * normal density with the data's spread, h = A(K, d) sigma n^{-1/(d+4)}, with
+ * A^{d+4} = 4/(d+2) for the Gaussian and 8 (d+4) (2 sqrt(pi))^d / V_d for the
+ * Epanechnikov kernel (V_d the unit-ball volume).  h1: the dataset's d_x
+ * dimensions as stored (standardised if it was created so), sigma^2 their mean
+ * sample variance; h2: d = 1, sigma the sample sd of y.  Synchronous.
+ */
+int cde_reference_rule(cde_ctx *ctx, cde_dataset ds, double *h1, double *h2);
 
 /* ------------------------------------------------------------------ */
 /* Request queue (continuous batching of density and selection jobs)   */

@@ -18,8 +18,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcde.so")
 
 CDE_OK, CDE_EINVAL, CDE_ENOMEM, CDE_ECUDA, CDE_EBUSY, CDE_ETIMEOUT, CDE_ENOTFOUND, CDE_ECANCELED = range(8)
-CDE_OUT_DEVICE, CDE_IN_DEVICE = 1, 2
+CDE_OUT_DEVICE, CDE_IN_DEVICE, CDE_KERNEL_EPANECHNIKOV = 1, 2, 4
+CDE_KERNEL_GAUSS, CDE_KERNEL_EPAN = 0, 1
+KERNELS = {"gauss": CDE_KERNEL_GAUSS, "epan": CDE_KERNEL_EPAN}
 CDE_REQ_DENSITY, CDE_REQ_SELECT = 0, 1
+CDE_L_COND, CDE_L_EQ3 = 0, 1
 STATUS_NAMES = {0: "CDE_OK", 1: "CDE_EINVAL", 2: "CDE_ENOMEM", 3: "CDE_ECUDA", 4: "CDE_EBUSY",
                 5: "CDE_ETIMEOUT", 6: "CDE_ENOTFOUND", 7: "CDE_ECANCELED"}
 
@@ -34,7 +37,7 @@ EXPORTED = [
     "cde_density", "cde_loo_loglik_batch", "cde_server_start", "cde_server_stop", "cde_submit",
     "cde_poll", "cde_wait", "cde_cancel", "cde_server_stats_get", "cde_server_stats_reset",
     "cde_measure_peaks", "cde_autotune", "cde_tuning_get", "cde_tuning_set",
-    "cde_loo_loglik_noalloc",
+    "cde_loo_loglik_noalloc", "cde_dataset_kernel", "cde_select_random", "cde_reference_rule",
 ]
 
 
@@ -123,6 +126,12 @@ def lib():
                            ctypes.c_int),
         "cde_loo_loglik_noalloc": ([_vp, _i64, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp],
                                    ctypes.c_int),
+        "cde_dataset_kernel": ([_vp, _i64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cde_select_random": ([_vp, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, ctypes.c_uint64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
+                              ctypes.c_int),
+        "cde_reference_rule": ([_vp, _i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                               ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -179,8 +188,12 @@ def cde_shutdown(ctx) -> None:
     lib().cde_shutdown(ctx)
 
 
-def cde_create_dataset(ctx, x, y, standardize: bool = False) -> int:
-    """x: (N, d_x) float32, y: (N,) float32 -- numpy (host) or CUDA tensors."""
+def cde_create_dataset(ctx, x, y, standardize: bool = False, kernel: str = "gauss") -> int:
+    """x: (N, d_x) float32, y: (N,) float32 -- numpy (host) or CUDA tensors.
+    kernel: "gauss" or "epan" (radial Epanechnikov, Sec. 4) for every call on
+    the dataset."""
+    if kernel not in KERNELS:
+        raise ValueError("kernel must be one of %s" % sorted(KERNELS))
     dev = _is_cuda(x)
     if dev:
         if not _is_cuda(y):
@@ -197,9 +210,44 @@ def cde_create_dataset(ctx, x, y, standardize: bool = False) -> int:
     if ys.shape[0] != N:
         raise ValueError("x and y have different lengths")
     h = _i64()
+    flags = (CDE_IN_DEVICE if dev else 0) | (CDE_KERNEL_EPANECHNIKOV if kernel == "epan" else 0)
     _check(lib().cde_create_dataset(ctx, _ptr(xs), _ptr(ys), N, d, int(bool(standardize)),
-                                    CDE_IN_DEVICE if dev else 0, ctypes.byref(h)))
+                                    flags, ctypes.byref(h)))
     return h.value
+
+
+def cde_select_random(ctx, ds: int, h1_max: float, h2_max: float, rounds: int, G1: int = 32,
+                      G2: int = 32, seed: int = 0, objective: str = "eq3", samples: bool = False):
+    """Random-search selection; returns dict(h1, h2, L_cond, L_eq3) and, with
+    samples=True, the drawn bandwidths and every score."""
+    obj = {"cond": CDE_L_COND, "eq3": CDE_L_EQ3}[objective]
+    best = np.empty(4)
+    h1o = np.empty(rounds * G1) if samples else None
+    h2o = np.empty(rounds * G2) if samples else None
+    Lco = np.empty(rounds * G1 * G2) if samples else None
+    Leo = np.empty(rounds * G1 * G2) if samples else None
+    _check(lib().cde_select_random(ctx, int(ds), float(h1_max), float(h2_max), int(rounds), int(G1),
+                                   int(G2), int(seed) & ((1 << 64) - 1), obj, _ptr(best), _ptr(h1o),
+                                   _ptr(h2o), _ptr(Lco), _ptr(Leo)))
+    out = {"h1": best[0], "h2": best[1], "L_cond": best[2], "L_eq3": best[3]}
+    if samples:
+        out.update(h1s=h1o.reshape(rounds, G1), h2s=h2o.reshape(rounds, G2),
+                   Lc=Lco.reshape(rounds, G1, G2), Le=Leo.reshape(rounds, G1, G2))
+    return out
+
+
+def cde_reference_rule(ctx, ds: int):
+    """(h1, h2) of the normal-reference rule for the dataset's kernel family."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().cde_reference_rule(ctx, int(ds), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def cde_dataset_kernel(ctx, ds: int) -> str:
+    """"gauss" or "epan"."""
+    k = ctypes.c_int()
+    _check(lib().cde_dataset_kernel(ctx, int(ds), ctypes.byref(k)))
+    return {v: n for n, v in KERNELS.items()}[k.value]
 
 
 def cde_destroy_dataset(ctx, ds: int) -> None:

@@ -27,7 +27,7 @@
 
 namespace cde {
 
-template <int G1, int G2>
+template <int G1, int G2, int KERN>
 __global__ void __launch_bounds__(256, 2) k_loo_batch(const LooArgs* __restrict__ items,
                                                       const int2* __restrict__ work, int n_work,
                                                       int* counter) {
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256, 2) k_loo_batch(const LooArgs* __restrict_
             __syncthreads();
         }
         const CoefSmem cf{A.a1, A.a2};
-        loo_tile_mma<G1, G2>(A, cf, work[w].y, reinterpret_cast<float*>(sm4));
+        loo_tile_mma<G1, G2, KERN>(A, cf, work[w].y, reinterpret_cast<float*>(sm4));
     }
 }
 
@@ -86,25 +86,38 @@ __global__ void k_loo_final_batch(const LooArgs* __restrict__ items, const int* 
     }
 }
 
-template <int G1, int G2>
-static int launch_batch_shape(const LooArgs* d_items, const int2* d_work, int n_work, int* counter,
-                              int grid, cudaStream_t st, int dmax) {
+template <int G1, int G2, int KERN>
+static int launch_batch_shape_k(const LooArgs* d_items, const int2* d_work, int n_work, int* counter,
+                                int grid, cudaStream_t st, int dmax) {
     using C = MmaCfg<G1, G2>;
     static bool attr_set = false;
     if (!attr_set) {
-        CDE_CUDA(cudaFuncSetAttribute(k_loo_batch<G1, G2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CDE_CUDA(cudaFuncSetAttribute(k_loo_batch<G1, G2, KERN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)C::smem_bytes(kMaxD)));
         attr_set = true;
     }
-    k_loo_batch<G1, G2><<<grid, C::kThreads, C::smem_bytes(dmax), st>>>(d_items, d_work, n_work, counter);
+    k_loo_batch<G1, G2, KERN><<<grid, C::kThreads, C::smem_bytes(dmax), st>>>(d_items, d_work, n_work, counter);
     CDE_CUDA(cudaGetLastError());
     return CDE_OK;
 }
 
-static int launch_batch(int T1, int T2, const LooArgs* d_items, const int2* d_work, int n_work,
+template <int G1, int G2>
+static int launch_batch_shape(int kern, const LooArgs* d_items, const int2* d_work, int n_work,
+                              int* counter, int grid, cudaStream_t st, int dmax) {
+    return kern == CDE_KERNEL_EPAN
+               ? launch_batch_shape_k<G1, G2, 1>(d_items, d_work, n_work, counter, grid, st, dmax)
+               : launch_batch_shape_k<G1, G2, 0>(d_items, d_work, n_work, counter, grid, st, dmax);
+}
+
+// work groups are keyed by kern * 4096 + T1 * 64 + T2
+static int shape_t1(int key) { return (key % 4096) / 64; }
+static int shape_t2(int key) { return key % 64; }
+static int shape_kern(int key) { return key / 4096; }
+
+static int launch_batch(int T1, int T2, int kern, const LooArgs* d_items, const int2* d_work, int n_work,
                         int* counter, int grid, cudaStream_t st, int dmax) {
 #define CDE_BSHAPE(A, B) \
-    if (T1 == A && T2 == B) return launch_batch_shape<A, B>(d_items, d_work, n_work, counter, grid, st, dmax);
+    if (T1 == A && T2 == B) return launch_batch_shape<A, B>(kern, d_items, d_work, n_work, counter, grid, st, dmax);
     CDE_BSHAPE(16, 8) CDE_BSHAPE(16, 16) CDE_BSHAPE(16, 32)
     CDE_BSHAPE(32, 8) CDE_BSHAPE(32, 16) CDE_BSHAPE(32, 32)
 #undef CDE_BSHAPE
@@ -157,7 +170,7 @@ static int build_plan(cde_ctx* ctx, const std::vector<BatchItem>& items, BatchPl
     for (int b = 0; b < n; ++b) {
         const BatchItem& it = items[b];
         const int T1 = loo_pad1(it.G1), T2 = loo_pad2(it.G2);
-        shape[b] = T1 * 64 + T2;
+        shape[b] = it.D->kernel * 4096 + T1 * 64 + T2;
         LooArgs& a = args[b];
         memset(&a, 0, sizeof(a));
         fill_loo_args(a, *it.D, it.h1, it.G1, it.h2, it.G2, T1, T2);
@@ -209,7 +222,7 @@ static int build_plan(cde_ctx* ctx, const std::vector<BatchItem>& items, BatchPl
     size_t po = 0;
     for (int b = 0; b < n; ++b) {
         args[b].part = dpart + po;
-        const int GG = (shape[b] / 64) * (shape[b] % 64);
+        const int GG = shape_t1(shape[b]) * shape_t2(shape[b]);
         po += (size_t)args[b].n_tiles * 2 * GG;
     }
     CDE_CUDA(cudaMallocHost((void**)&P.hout, sizeof(double) * std::max<size_t>(out, 1)));
@@ -235,7 +248,7 @@ static int build_plan(cde_ctx* ctx, const std::vector<BatchItem>& items, BatchPl
     // per shape: a LooArgs sub-array view in member order for the final kernel
     std::vector<std::vector<int>> cell0(shapes.size());
     for (size_t s = 0; s < shapes.size(); ++s) {
-        const int T1 = shapes[s] / 64, T2 = shapes[s] % 64;
+        const int T1 = shape_t1(shapes[s]), T2 = shape_t2(shapes[s]);
         cell0[s].resize(n + 1, 0);
         // item-major cell numbering over all n items; items of other shapes get 0 cells
         int acc = 0;
@@ -253,11 +266,12 @@ static int build_plan(cde_ctx* ctx, const std::vector<BatchItem>& items, BatchPl
     int rc = CDE_OK;
     cudaError_t e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * 2 * shapes.size(), st);
     for (size_t s = 0; s < shapes.size() && rc == CDE_OK && e == cudaSuccess; ++s) {
-        const int T1 = shapes[s] / 64, T2 = shapes[s] % 64;
+        const int T1 = shape_t1(shapes[s]), T2 = shape_t2(shapes[s]);
         const int n_work = (int)work[s].size();
         const int cmax = loo_grid_ctas(ctx, T1, T2);
         const int grid = std::max(1, std::min(n_work, cmax));
-        rc = launch_batch(T1, T2, d_items, d_work + woff[s], n_work, d_cnt + s, grid, st, dmax);
+        rc = launch_batch(T1, T2, shape_kern(shapes[s]), d_items, d_work + woff[s], n_work, d_cnt + s,
+                          grid, st, dmax);
         if (rc != CDE_OK) break;
         const int GG = T1 * T2;
         const int cells = cell0[s][n];

@@ -136,6 +136,7 @@ int cde_create_dataset(cde_ctx* ctx, const float* x, const float* y, int64_t N, 
     D->d = d;
     D->Np = (N + kPadRows - 1) / kPadRows * kPadRows;
     D->standardized = standardize ? 1 : 0;
+    D->kernel = (flags & CDE_KERNEL_EPANECHNIKOV) ? CDE_KERNEL_EPAN : CDE_KERNEL_GAUSS;
     D->bytes = (size_t)D->Np * (d + 1) * 4 + (size_t)N * 8;
     if (ctx->used.load() + D->bytes > ctx->budget)
         return set_error(CDE_ENOMEM, "cde_create_dataset: memory budget exceeded");
@@ -191,8 +192,14 @@ int cde_create_dataset(cde_ctx* ctx, const float* x, const float* y, int64_t N, 
             if (!(stats[2 * c + 1] > 0.0))
                 return fail(set_error(CDE_EINVAL, "cde_create_dataset: zero spread in a dimension"));
     }
-    rc = nn_shift_enqueue(*D, st);
-    if (rc != CDE_OK) return fail(rc);
+    if (D->kernel == CDE_KERNEL_GAUSS) {
+        rc = nn_shift_enqueue(*D, st);
+        if (rc != CDE_OK) return fail(rc);
+    } else {
+        e = cudaMemsetAsync(D->mx, 0, (size_t)N * 4, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(D->my, 0, (size_t)N * 4, st);
+        if (e != cudaSuccess) return fail(cuda_error(e, "cde_create_dataset: shifts"));
+    }
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(cuda_error(e, "cde_create_dataset: kernels"));
     if (!in_dev) {
@@ -246,6 +253,14 @@ int cde_dataset_info(cde_ctx* ctx, cde_dataset ds, int64_t* N, int* d, double* m
         if (mean) mean[c] = D->mean[c];
         if (sd) sd[c] = D->sd[c];
     }
+    return CDE_OK;
+}
+
+int cde_dataset_kernel(cde_ctx* ctx, cde_dataset ds, int* kernel) {
+    if (!ctx || !kernel) return set_error(CDE_EINVAL, "cde_dataset_kernel: null argument");
+    auto D = find_dataset(ctx, ds);
+    if (!D) return set_error(CDE_ENOTFOUND, "cde_dataset_kernel: unknown dataset");
+    *kernel = D->kernel;
     return CDE_OK;
 }
 

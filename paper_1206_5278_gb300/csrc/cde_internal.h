@@ -32,10 +32,12 @@ struct Dataset {
     int64_t N = 0, Np = 0;
     int d = 0;
     int standardized = 0;
+    int kernel = 0;        // CDE_KERNEL_GAUSS or CDE_KERNEL_EPAN
     float* xs = nullptr;   // [d][Np]
     float* y = nullptr;    // [Np]
-    float* mx = nullptr;   // [N] min_{i!=j} |x_j - x_i|^2 (FP32, same formula as the kernels)
-    float* my = nullptr;   // [N] min_{i!=j} (y_j - y_i)^2
+    float* mx = nullptr;   // [N] min_{i!=j} |x_j - x_i|^2 (FP32, same formula as the kernels);
+                           //     zeros for Epanechnikov datasets (no shift)
+    float* my = nullptr;   // [N] min_{i!=j} (y_j - y_i)^2 (zeros for Epanechnikov)
     std::vector<double> mean, sd;  // per-dimension (identity when not standardised)
     size_t bytes = 0;
     std::atomic<int> users{0};     // jobs currently reading it (serving)
@@ -68,6 +70,9 @@ struct cde_ctx {
 namespace cde {
 
 std::shared_ptr<Dataset> find_dataset(cde_ctx* ctx, cde_dataset ds);
+
+// ln c_d of the radial Epanechnikov kernel in d dimensions (loo_grid.cu)
+double epan_log_norm(int d);
 cudaStream_t pick_stream(cde_ctx* ctx, void* s);
 
 // ---- LOO grid (loo_grid.cu) ----

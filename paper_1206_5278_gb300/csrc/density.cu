@@ -6,7 +6,10 @@
 //   u_qi = 2^{a1 (m_q - |x_q - x_i|^2)},  w_ig = 2^{-a2 (y_g - y_i)^2},
 //
 // m_q the query's nearest squared distance (so max_i u_qi = 1 and neither sum
-// underflows), a = log2(e)/(2 h^2).  The numerator is a (Q x N) x (N x G)
+// underflows), a = log2(e)/(2 h^2).  Epanechnikov datasets use the profiles
+// u_qi = (1 - |x_q - x_i|^2/h1^2)_+ and w_ig = (1 - (y_g - y_i)^2/h2^2)_+ (no
+// shift; a = 1/h^2) and the constant c_1/h2 = 3/(4 h2); a query with no
+// x-neighbour inside h1 (0/0) gets f = 0.  The numerator is a (Q x N) x (N x G)
 // product whose factors are generated on the fly; each CTA owns 32 queries x
 // 256 grid points and runs the product on the tensor cores (k_density).  Small
 // Q splits the data range across CTAs; split partials are summed in split
@@ -43,6 +46,28 @@ __device__ __forceinline__ float ex2d(float x) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// a * b + c clamped to [0, 1] (the Epanechnikov profile in one instruction)
+__device__ __forceinline__ float fma_sat_d(float a, float b, float c) {
+    float r;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// x factor from its shared-memory argument: Gaussian 2^T (T = a1 (m_q - dx2),
+// -inf masked), Epanechnikov (1 - a1 T)_+ (T = dx2, +inf masked)
+template <int KERN>
+__device__ __forceinline__ float dens_ufac(float T, float a1) {
+    if constexpr (KERN == 0) return ex2d(T);
+    else return fma_sat_d(-a1, T, 1.f);
+}
+
+// y factor at squared distance t2
+template <int KERN>
+__device__ __forceinline__ float dens_wfac(float t2, float a2) {
+    if constexpr (KERN == 0) return ex2d(-a2 * t2);
+    else return fma_sat_d(-a2, t2, 1.f);
 }
 
 __global__ void k_query_pack(const float* __restrict__ xq, int64_t Q, int64_t Qp, int d,
@@ -95,7 +120,7 @@ __global__ void __launch_bounds__(256) k_query_shift(const float* __restrict__ x
 }
 
 struct DensSmem {
-    float T[kDQ][kDIC + 4];     // exp2 argument a1 (m_q - |x_q - x_i|^2), -inf when masked
+    float T[kDQ][kDIC + 4];     // x factor argument (dens_ufac), masked points give 0
     float yis[kDIC];
     float xqs[kMaxD][kDQ];
     float xis[kMaxD][kDIC];
@@ -133,6 +158,7 @@ __device__ __forceinline__ void mma_tf32_d(float (&d)[4], const uint32_t (&a)[4]
 // exp2; warp w owns grid points [32 w, 32 w + 32).  The 32 x IC exponent
 // arguments of u are computed once per chunk into shared memory.  Each
 // 32-point chunk accumulates from zero and is added to an FP32 running total.
+template <int KERN>
 __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
     extern __shared__ float4 dsm4[];
     DensSmem& S = *reinterpret_cast<DensSmem*>(dsm4);
@@ -150,7 +176,7 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
     }
     // distance-pass role: query dq, points dp..dp+3
     const int dq = tid >> 3, dp = (tid & 7) * 4;
-    const float mqv = (q0 + dq < a.Q) ? a.mq[q0 + dq] : 0.f;
+    const float mqv = (KERN == 0 && q0 + dq < a.Q) ? a.mq[q0 + dq] : 0.f;
     float ygv[4];
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
@@ -181,7 +207,8 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
                 const float u = S.xqs[c][dq] - S.xis[c][ii];
                 dx2 = fmaf(u, u, dx2);
             }
-            S.T[dq][ii] = (c0 + ii < i_end) ? a1 * (mqv - dx2) : -INFINITY;
+            if constexpr (KERN == 0) S.T[dq][ii] = (c0 + ii < i_end) ? a1 * (mqv - dx2) : -INFINITY;
+            else S.T[dq][ii] = (c0 + ii < i_end) ? dx2 : INFINITY;
         }
         __syncthreads();
         float D[2][4][4];
@@ -196,10 +223,10 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
             uint32_t ah[2][4], ax[2][4];
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
-                const float u0 = ex2d(S.T[16 * mt + g][pa]);       // (q, p0)
-                const float u1 = ex2d(S.T[16 * mt + g + 8][pa]);   // (q + 8, p0)
-                const float u2 = ex2d(S.T[16 * mt + g][pb]);       // (q, p1)
-                const float u3 = ex2d(S.T[16 * mt + g + 8][pb]);   // (q + 8, p1)
+                const float u0 = dens_ufac<KERN>(S.T[16 * mt + g][pa], a1);       // (q, p0)
+                const float u1 = dens_ufac<KERN>(S.T[16 * mt + g + 8][pa], a1);   // (q + 8, p0)
+                const float u2 = dens_ufac<KERN>(S.T[16 * mt + g][pb], a1);       // (q, p1)
+                const float u3 = dens_ufac<KERN>(S.T[16 * mt + g + 8][pb], a1);   // (q + 8, p1)
                 bt[mt][0] += u0 + u2;
                 bt[mt][1] += u1 + u3;
                 uint32_t l0, l1, l2, l3;
@@ -218,8 +245,8 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
             for (int nt = 0; nt < 4; ++nt) {
                 const float ta = ygv[nt] - ya, tb = ygv[nt] - yb;
                 uint32_t l0, l1;
-                split_tf32_d(ex2d(-a2 * (ta * ta)), bh[nt][0], l0);
-                split_tf32_d(ex2d(-a2 * (tb * tb)), bh[nt][1], l1);
+                split_tf32_d(dens_wfac<KERN>(ta * ta, a2), bh[nt][0], l0);
+                split_tf32_d(dens_wfac<KERN>(tb * tb, a2), bh[nt][1], l1);
                 bx[nt][0] = pack_bf16x2_d(__uint_as_float(l0), __uint_as_float(l1));
                 bx[nt][1] = pack_bf16x2_d(__uint_as_float(bh[nt][0]), __uint_as_float(bh[nt][1]));
             }
@@ -265,7 +292,8 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
     if (blockIdx.y == 0 && tid < kDQ && q0 + tid < a.Q) a.den[s * a.Q + q0 + tid] = S.dens[tid];
 }
 
-// f[q][g] = (sum_s num) / (sum_s den) / (sqrt(2 pi) h2), splits in order
+// f[q][g] = (sum_s num) / (sum_s den) * norm, splits in order (norm the y
+// kernel's constant; a zero denominator -- no x-neighbour -- gives 0)
 __global__ void k_density_final(const float* __restrict__ num, const float* __restrict__ den,
                                 int n_split, int64_t Q, int G, float norm, float* __restrict__ f) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -276,7 +304,7 @@ __global__ void k_density_final(const float* __restrict__ num, const float* __re
         sn += num[(int64_t)s * Q * G + e];
         sd += den[(int64_t)s * Q + q];
     }
-    f[e] = sn / sd * norm;
+    f[e] = sd > 0.f ? sn / sd * norm : 0.f;
 }
 
 int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const float* d_xq,
@@ -295,7 +323,8 @@ int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const 
     const size_t sm = (size_t)D.d * 256 * sizeof(float);
     if (sm > 48 * 1024)
         CDE_CUDA(cudaFuncSetAttribute(k_query_shift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    {
+    const bool epan = D.kernel == CDE_KERNEL_EPAN;
+    if (!epan) {
         const int64_t qb = (Q + 255) / 256;
         const int64_t tiles = (D.N + 255) / 256;
         int64_t sy = (4LL * ctx->sm_count + qb - 1) / qb;
@@ -321,8 +350,8 @@ int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const 
     a.d = D.d;
     a.G = G;
     const double L2E = 1.4426950408889634074;
-    a.a1 = (float)(L2E / (2 * h1 * h1));
-    a.a2 = (float)(L2E / (2 * h2 * h2));
+    a.a1 = (float)(epan ? 1.0 / (h1 * h1) : L2E / (2 * h1 * h1));
+    a.a2 = (float)(epan ? 1.0 / (h2 * h2) : L2E / (2 * h2 * h2));
     const int64_t qt = Qp / kDQ;
     const int gt = (G + kDG - 1) / kDG;
     const int64_t chunks = (D.N + kDIC - 1) / kDIC;
@@ -338,13 +367,17 @@ int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const 
     a.den = den;
     static bool attr = false;
     if (!attr) {
-        CDE_CUDA(cudaFuncSetAttribute(k_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CDE_CUDA(cudaFuncSetAttribute(k_density<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(DensSmem)));
+        CDE_CUDA(cudaFuncSetAttribute(k_density<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sizeof(DensSmem)));
         attr = true;
     }
-    k_density<<<dim3((unsigned)qt, (unsigned)gt, (unsigned)ns), 256, sizeof(DensSmem), st>>>(a);
+    const dim3 dgrid((unsigned)qt, (unsigned)gt, (unsigned)ns);
+    if (epan) k_density<1><<<dgrid, 256, sizeof(DensSmem), st>>>(a);
+    else k_density<0><<<dgrid, 256, sizeof(DensSmem), st>>>(a);
     CDE_CUDA(cudaGetLastError());
-    const float norm = (float)(1.0 / (2.5066282746310002 * h2));
+    const float norm = (float)(epan ? std::exp(epan_log_norm(1)) / h2 : 1.0 / (2.5066282746310002 * h2));
     k_density_final<<<(unsigned)((Q * G + 255) / 256), 256, 0, st>>>(num, den, (int)ns, Q, G, norm, d_f);
     CDE_CUDA(cudaGetLastError());
     cudaFreeAsync(xq, st);

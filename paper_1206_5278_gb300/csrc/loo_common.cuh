@@ -28,16 +28,41 @@ struct LooArgs {
     int n_units, units_per_tile, n_tiles;
     int tile_base;          // batched launch: first global tile of this item
     int* work;              // batched launch: queue counter
+    int kern;               // CDE_KERNEL_GAUSS or CDE_KERNEL_EPAN
     float thresh;           // cells with shifted numerator below this are recomputed
-    float a1[32], a2[32];   // log2(e)/(2 h^2), padded by repeating the last bandwidth
-    double lam1[32];        // d ln(sqrt(2 pi) h1_k)
-    double kap2[32];        // ln(sqrt(2 pi) h2_l)
+    // per-bandwidth coefficients, padded by repeating the last bandwidth:
+    //   Gaussian:     a = log2(e)/(2 h^2), lam1 = d ln(sqrt(2 pi) h1), kap2 = ln(sqrt(2 pi) h2)
+    //   Epanechnikov: a = 1/h^2,           lam1 = d ln h1 - ln c_d,     kap2 = ln h2 - ln c_1
+    float a1[32], a2[32];
+    double lam1[32];
+    double kap2[32];
 };
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// a * b + c clamped to [0, 1] in the same instruction (NaN -> 0)
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {
+    float r;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Kernel factors of two values that share nothing but the family.
+//   Gaussian (KERN 0):     t = shifted negative squared distance, factor 2^{c t}
+//   Epanechnikov (KERN 1): t = squared distance, factor (1 - c t)_+ (c = 1/h^2;
+//                          t = +inf gives exactly 0)
+template <int KERN>
+__device__ __forceinline__ float2 kernel_factor2(float2 c, float2 t) {
+    if constexpr (KERN == 0) {
+        const float2 a = __fmul2_rn(c, t);
+        return make_float2(ex2_approx(a.x), ex2_approx(a.y));
+    } else {
+        return make_float2(fma_sat(-c.x, t.x, 1.f), fma_sat(-c.y, t.y, 1.f));
+    }
 }
 
 // log2 of a positive normal float, returned in FP64: exact exponent plus the
@@ -251,7 +276,7 @@ __device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, f
 // is free.  Flags cells below the threshold, recomputes them exactly, and adds
 // the FP64 log-ratios of the unit's rows into the tile partial (thread-owned
 // cells, rows in order).
-template <class C, class Coef>
+template <class C, int KERN, class Coef>
 __device__ __forceinline__ void loo_unit_epilogue(const LooArgs& a, const Coef& cf, float* sm, int u,
                                                   int u_begin, int tile, const float (&At)[4]) {
     constexpr int JW = C::JW, GG = C::GG, G1 = C::G1v, G2 = C::G2v;
@@ -281,8 +306,11 @@ __device__ __forceinline__ void loo_unit_epilogue(const LooArgs& a, const Coef& 
             }
         }
         __syncthreads();
-        const int nfl = *nflag_s;
-        if (nfl > 0) loo_fallback<C>(a, cf, sm, nfl);
+        if constexpr (KERN == 0) {
+            // (Epanechnikov sums need no shift: their threshold is 0, nothing is flagged)
+            const int nfl = *nflag_s;
+            if (nfl > 0) loo_fallback<C>(a, cf, sm, nfl);
+        }
         __syncthreads();
 
         // ---- FP64 log-ratio; each thread owns whole grid cells (all rows of
@@ -304,7 +332,9 @@ __device__ __forceinline__ void loo_unit_epilogue(const LooArgs& a, const Coef& 
                     const int c = jl * GG + kl;
                     const double shy = a2l * (double)my_s[jl];
                     const double lA = la2[c];
-                    const double ell = LN2 * (lA - btl_s[jl * G1 + k] - shy) - kap;
+                    // a zero numerator (Epanechnikov: empty support, also when
+                    // the denominator is zero) is ell = -inf, never NaN
+                    const double ell = lA == -INFINITY ? -INFINITY : LN2 * (lA - btl_s[jl * G1 + k] - shy) - kap;
                     const double lnA = LN2 * (lA - a1k * (double)mx_s[jl] - shy) - lam - kap;
                     sc += ell;
                     se += lnA;

@@ -14,6 +14,15 @@
 // minimum of e_i (online rescaling: when a smaller e arrives the sums are
 // multiplied by 2^{e - M}), so no bandwidth underflows the numerator.
 //
+// Epanechnikov datasets (profiles u = (1 - dx2/h1^2)_+, w = (1 - dy2/h2^2)_+):
+// d K_h1/d ln h1 = c_d h1^{-d} (v - d u) with v = 2 dx2/h1^2 inside the support,
+// d K_h2/d ln h2 = c_1 h2^{-1} (z - w) with z = 2 dy2/h2^2 inside, so
+//   d ell_j/d ln h1 = sum v w / sum u w - sum v / sum u,
+//   d ell_j/d ln h2 = sum u z / sum u w - 1,
+// and the same five slots hold sum u w, sum v w, sum u z, sum u, sum v (no
+// shift: M = 0).  A row with sum u w = 0 has ell_j = -inf and adds 0 to both
+// derivatives.
+//
 // The i range is split over gridDim.y CTAs; split partials (M, S_A, S_Ax,
 // S_Ay, S_B, S_Bx) are merged per row in FP64 in split order, the per-row
 // log-ratio and derivatives are formed in FP64, and rows are summed in a
@@ -31,7 +40,7 @@ struct GradArgs {
     const float* my;
     int64_t N, Np;
     int d;
-    float a1, a2;          // log2(e)/(2 h^2)
+    float a1, a2;          // Gaussian log2(e)/(2 h^2); Epanechnikov 1/h^2
     int64_t i_per_split;   // multiple of the tile
     float* part;           // [n_split][N][6]
 };
@@ -44,11 +53,36 @@ __device__ __forceinline__ float ex2g(float x) {
     return r;
 }
 
-// One pair's contribution with the online joint shift, without branches: when
-// e does not lower the running minimum the rescale factor is exactly 2^0 = 1.
+__device__ __forceinline__ float fma_sat_g(float a, float b, float c) {
+    float r;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Initial running shift: +inf (Gaussian, lowered by the first pair), 0 (Epanechnikov, unused)
+template <int KERN>
+__device__ __forceinline__ float grad_m0() { return KERN == 0 ? INFINITY : 0.f; }
+
+// One pair's contribution.  Gaussian: online joint shift, without branches --
+// when e does not lower the running minimum the rescale factor is exactly
+// 2^0 = 1.  Epanechnikov: plain sums of the profiles and their log-derivative
+// weights (the support test is the profile itself being positive).
+template <int KERN>
 __device__ __forceinline__ void grad_accumulate(bool ok, float dx2, float dy2, float mx, float my,
                                                 float a1, float a2, float& M, float& SA, float& SAx,
                                                 float& SAy, float& SB, float& SBx) {
+    if constexpr (KERN == 1) {
+        const float u = ok ? fma_sat_g(-a1, dx2, 1.f) : 0.f;
+        const float w = fma_sat_g(-a2, dy2, 1.f);
+        const float v = u > 0.f ? 2.f * a1 * dx2 : 0.f;
+        const float z = w > 0.f ? 2.f * a2 * dy2 : 0.f;
+        SA = fmaf(u, w, SA);
+        SAx = fmaf(v, w, SAx);
+        SAy = fmaf(u, z, SAy);
+        SB += u;
+        SBx += v;
+        return;
+    }
     const float ex = dx2 - mx, ey = dy2 - my;
     const float e = fmaf(a1, ex, a2 * ey);
     const bool lower = ok && e < M;
@@ -67,7 +101,7 @@ __device__ __forceinline__ void grad_accumulate(bool ok, float dx2, float dy2, f
     SAy = fmaf(v, dy2, SAy);
 }
 
-template <int JB, int DREG>
+template <int JB, int DREG, int KERN>
 __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
     __shared__ float xt[DREG + 1][kGradThreads];
     const int tid = threadIdx.x;
@@ -88,7 +122,7 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
         yj[b] = g.y[jc];
         mxj[b] = g.mx[jc];
         myj[b] = g.my[jc];
-        M[b] = INFINITY;
+        M[b] = grad_m0<KERN>();
         SA[b] = SAx[b] = SAy[b] = SB[b] = SBx[b] = 0.f;
     }
     const float a1 = g.a1, a2 = g.a2;
@@ -116,8 +150,8 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
                 }
                 const float dy = yj[b] - yi;
                 const float dy2 = dy * dy;
-                grad_accumulate(i != jj[b], dx2, dy2, mxj[b], myj[b], a1, a2, M[b], SA[b], SAx[b],
-                                SAy[b], SB[b], SBx[b]);
+                grad_accumulate<KERN>(i != jj[b], dx2, dy2, mxj[b], myj[b], a1, a2, M[b], SA[b], SAx[b],
+                                      SAy[b], SB[b], SBx[b]);
             }
         }
     }
@@ -156,7 +190,7 @@ __device__ __forceinline__ void mma_tf32_g(float (&d)[4], const uint32_t (&a)[4]
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-template <int DK>
+template <int DK, int KERN>
 __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g) {
     constexpr int KK = DK / 8, RS = DK + 4;  // padded smem row (bank spread)
     __shared__ uint32_t xh[kGMTile * RS], xl[kGMTile * RS];
@@ -194,7 +228,7 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
         }
     }
     const float a1 = g.a1, a2 = g.a2;
-    float M[2] = {INFINITY, INFINITY}, SA[2] = {0, 0}, SAx[2] = {0, 0}, SAy[2] = {0, 0}, SB[2] = {0, 0},
+    float M[2] = {grad_m0<KERN>(), grad_m0<KERN>()}, SA[2] = {0, 0}, SAx[2] = {0, 0}, SAy[2] = {0, 0}, SB[2] = {0, 0},
           SBx[2] = {0, 0};
     for (int64_t t0 = i0; t0 < i1; t0 += kGMTile) {
         __syncthreads();
@@ -241,8 +275,8 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
                     const int64_t i = t0 + p;
                     const float dx2 = fmaxf(nj[h] + ni_s[p] - 2.f * D[n][q], 0.f);
                     const float dy = yj[h] - yi_s[p];
-                    grad_accumulate(i < i1 && i != jr[h], dx2, dy * dy, mxj[h], myj[h], a1, a2, M[h], SA[h],
-                                    SAx[h], SAy[h], SB[h], SBx[h]);
+                    grad_accumulate<KERN>(i < i1 && i != jr[h], dx2, dy * dy, mxj[h], myj[h], a1, a2, M[h],
+                                          SA[h], SAx[h], SAy[h], SB[h], SBx[h]);
                 }
         }
     }
@@ -275,7 +309,7 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
 // rowv[j] = {ell_j, d ell_j/d ln h1, d ell_j/d ln h2}.
 __global__ void k_grad_rows(const float* __restrict__ part, int n_split, int64_t N,
                             const float* __restrict__ my, float a1f, float a2f, double h1, double h2,
-                            double* __restrict__ rowv) {
+                            int epan, double lnc1, double* __restrict__ rowv) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     double Mst = INFINITY;
@@ -296,10 +330,18 @@ __global__ void k_grad_rows(const float* __restrict__ part, int n_split, int64_t
         SBx += p[5];
     }
     const double LN2 = 0.69314718055994530942, LNS2PI = 0.91893853320467274178;
-    const double ell = log(SA) - log(SB) - LN2 * (Mst + (double)a2f * (double)my[j]) -
-                       (LNS2PI + log(h2));
-    const double g1 = (SAx / SA - SBx / SB) / (h1 * h1);
-    const double g2 = (SAy / SA) / (h2 * h2) - 1.0;
+    double ell, g1, g2;
+    if (epan) {
+        // slots: sum u w, sum v w, sum u z, sum u, sum v
+        const bool live = SA > 0.0;
+        ell = live ? log(SA) - log(SB) - (log(h2) - lnc1) : -INFINITY;
+        g1 = live ? SAx / SA - SBx / SB : 0.0;
+        g2 = live ? SAy / SA - 1.0 : 0.0;
+    } else {
+        ell = log(SA) - log(SB) - LN2 * (Mst + (double)a2f * (double)my[j]) - (LNS2PI + log(h2));
+        g1 = (SAx / SA - SBx / SB) / (h1 * h1);
+        g2 = (SAy / SA) / (h2 * h2) - 1.0;
+    }
     rowv[3 * j] = ell;
     rowv[3 * j + 1] = g1;
     rowv[3 * j + 2] = g2;
@@ -327,8 +369,15 @@ __global__ void k_sum_rows3(const double* __restrict__ rowv, int64_t N, double* 
 }
 
 template <int JB, int DREG>
-static void launch_grad(const GradArgs& g, dim3 grid, cudaStream_t st) {
-    k_loo_grad<JB, DREG><<<grid, kGradThreads, 0, st>>>(g);
+static void launch_grad(const GradArgs& g, dim3 grid, cudaStream_t st, bool epan) {
+    if (epan) k_loo_grad<JB, DREG, 1><<<grid, kGradThreads, 0, st>>>(g);
+    else k_loo_grad<JB, DREG, 0><<<grid, kGradThreads, 0, st>>>(g);
+}
+
+template <int DK>
+static void launch_grad_mma(const GradArgs& g, dim3 grid, cudaStream_t st, bool epan) {
+    if (epan) k_loo_grad_mma<DK, 1><<<grid, kGMWarps * 32, 0, st>>>(g);
+    else k_loo_grad_mma<DK, 0><<<grid, kGMWarps * 32, 0, st>>>(g);
 }
 
 int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, double* d_out3,
@@ -342,8 +391,9 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     g.Np = D.Np;
     g.d = D.d;
     const double L2E = 1.4426950408889634074;
-    g.a1 = (float)(L2E / (2 * h1 * h1));
-    g.a2 = (float)(L2E / (2 * h2 * h2));
+    const bool epan = D.kernel == CDE_KERNEL_EPAN;
+    g.a1 = (float)(epan ? 1.0 / (h1 * h1) : L2E / (2 * h1 * h1));
+    g.a2 = (float)(epan ? 1.0 / (h2 * h2) : L2E / (2 * h2 * h2));
     const bool tc = D.d >= 16;   // tensor-core cross term
     const int DREG = D.d <= 4 ? 4 : D.d <= 8 ? 8 : D.d <= 16 ? 16 : D.d <= 32 ? 32 : 64;
     const int JB = DREG <= 8 ? 4 : DREG <= 32 ? 2 : 1;
@@ -366,15 +416,15 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     g.part = part;
     dim3 grid((unsigned)gx, (unsigned)ns);
     if (tc) {
-        if (D.d <= 16) k_loo_grad_mma<16><<<grid, kGMWarps * 32, 0, st>>>(g);
-        else if (D.d <= 32) k_loo_grad_mma<32><<<grid, kGMWarps * 32, 0, st>>>(g);
-        else k_loo_grad_mma<64><<<grid, kGMWarps * 32, 0, st>>>(g);
-    } else if (DREG == 4) launch_grad<4, 4>(g, grid, st);
-    else if (DREG == 8) launch_grad<4, 8>(g, grid, st);
-    else launch_grad<2, 16>(g, grid, st);
+        if (D.d <= 16) launch_grad_mma<16>(g, grid, st, epan);
+        else if (D.d <= 32) launch_grad_mma<32>(g, grid, st, epan);
+        else launch_grad_mma<64>(g, grid, st, epan);
+    } else if (DREG == 4) launch_grad<4, 4>(g, grid, st, epan);
+    else if (DREG == 8) launch_grad<4, 8>(g, grid, st, epan);
+    else launch_grad<2, 16>(g, grid, st, epan);
     CDE_CUDA(cudaGetLastError());
     k_grad_rows<<<(unsigned)((D.N + 255) / 256), 256, 0, st>>>(part, (int)ns, D.N, D.my, g.a1, g.a2,
-                                                             h1, h2, rowv);
+                                                             h1, h2, epan ? 1 : 0, epan_log_norm(1), rowv);
     CDE_CUDA(cudaGetLastError());
     if (d_out3) {
         k_sum_rows3<<<1, 1024, 0, st>>>(rowv, D.N, d_out3);

@@ -183,20 +183,26 @@ __global__ void k_loo_final(const double* __restrict__ part, int n_tiles, int GG
 // --------------------------------------------------------------------------
 // Host side
 // --------------------------------------------------------------------------
-template <int G1, int G2>
-static int launch_shape(const LooArgs& a, int grid, cudaStream_t st) {
+template <int G1, int G2, int KERN>
+static int launch_shape_k(const LooArgs& a, int grid, cudaStream_t st) {
     using C = MmaCfg<G1, G2>;
     const size_t smem = C::smem_bytes(a.d);
     static bool attr_set = false;  // per instantiation; guarded by the ctx lock
     if (!attr_set) {
-        CDE_CUDA(cudaFuncSetAttribute(k_loo_mma<G1, G2>,
+        CDE_CUDA(cudaFuncSetAttribute(k_loo_mma<G1, G2, KERN>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)C::smem_bytes(kMaxD)));
         attr_set = true;
     }
-    k_loo_mma<G1, G2><<<grid, C::kThreads, smem, st>>>(a);
+    k_loo_mma<G1, G2, KERN><<<grid, C::kThreads, smem, st>>>(a);
     CDE_CUDA(cudaGetLastError());
     return CDE_OK;
+}
+
+template <int G1, int G2>
+static int launch_shape(const LooArgs& a, int grid, cudaStream_t st) {
+    return a.kern == CDE_KERNEL_EPAN ? launch_shape_k<G1, G2, 1>(a, grid, st)
+                                     : launch_shape_k<G1, G2, 0>(a, grid, st);
 }
 
 
@@ -209,10 +215,36 @@ int launch_loo_tile_kernel(int T1, int T2, const LooArgs& a, int grid, cudaStrea
     return set_error(CDE_EINVAL, "unsupported grid block shape");
 }
 
+// ln c_d of the radial Epanechnikov kernel, c_d = (d + 2) / (2 V_d), with the
+// unit-ball volume from V_0 = 1, V_1 = 2, V_k = (2 pi / k) V_{k-2}.
+double epan_log_norm(int d) {
+    double lv = (d % 2) ? std::log(2.0) : 0.0;
+    for (int k = 2 + d % 2; k <= d; k += 2) lv += std::log(2.0 * M_PI / k);
+    return std::log(d + 2.0) - std::log(2.0) - lv;
+}
+
 void fill_loo_args(LooArgs& a, const Dataset& D, const double* h1, int g1, const double* h2,
                    int g2, int T1, int T2) {
     a.xs = D.xs; a.y = D.y; a.mx = D.mx; a.my = D.my;
     a.N = D.N; a.Np = D.Np; a.d = D.d;
+    a.kern = D.kernel;
+    if (D.kernel == CDE_KERNEL_EPAN) {
+        // profiles (1 - t/h^2)_+; ln K_h = ln(profile) - (d ln h - ln c_d); no shifts
+        a.thresh = 0.f;
+        const double lcd = epan_log_norm(D.d), lc1 = epan_log_norm(1);
+        for (int k = 0; k < 32; ++k) {
+            const double h = h1[k < g1 ? k : g1 - 1];
+            a.a1[k] = (float)(1.0 / (h * h));
+            a.lam1[k] = D.d * log(h) - lcd;
+        }
+        for (int l = 0; l < 32; ++l) {
+            const double h = h2[l < g2 ? l : g2 - 1];
+            a.a2[l] = (float)(1.0 / (h * h));
+            a.kap2[l] = log(h) - lc1;
+        }
+        (void)T1; (void)T2;
+        return;
+    }
     a.thresh = 0x1p-40f;
     const double L2E = 1.4426950408889634074;      // log2(e)
     const double LNS2PI = 0.91893853320467274178;  // ln sqrt(2 pi)

@@ -100,7 +100,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-template <int G1, int G2, class Coef>
+template <int G1, int G2, int KERN, class Coef>
 __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, int tile, float* sm) {
     using C = MmaCfg<G1, G2>;
     constexpr int JW = C::JW, MT = C::MT, NT = C::NT, GG = C::GG, IC = C::IC;
@@ -196,7 +196,10 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                 }
                 const float dy = yj_s[r] - yin;
                 const bool ok = i < N && i != ji_s[r];
-                const float t1 = ok ? mx_s[r] - dx2 : -INFINITY, t2 = my_s[r] - dy * dy;
+                // Gaussian: shifted exponents (masked pairs -inf); Epanechnikov:
+                // squared distances (masked pairs +inf)
+                const float t1 = KERN == 0 ? (ok ? mx_s[r] - dx2 : -INFINITY) : (ok ? dx2 : INFINITY);
+                const float t2 = KERN == 0 ? my_s[r] - dy * dy : dy * dy;
                 reinterpret_cast<float2*>(tt + r * 3 * IC)[lane] = make_float2(t1, t1);
                 tt[r * 3 * IC + 2 * IC + lane] = t2;
             }
@@ -230,8 +233,7 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                     uint32_t bh[NT][2], bx[NT][2];
 #pragma unroll
                     for (int nt = 0; nt < NT; ++nt) {
-                        const float2 aw = __fmul2_rn(ca2[nt], t2p);
-                        const float2 w = make_float2(ex2_approx(aw.x), ex2_approx(aw.y));
+                        const float2 w = kernel_factor2<KERN>(ca2[nt], t2p);
                         const float2 h = make_float2(__uint_as_float(__float_as_uint(w.x) & 0xffffe000u),
                                                      __uint_as_float(__float_as_uint(w.y) & 0xffffe000u));
                         const float2 l = __ffma2_rn(h, make_float2(-1.f, -1.f), w);  // w - hi, exact
@@ -245,9 +247,8 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                     uint32_t ah[MT][4], ax[MT][4];
 #pragma unroll
                     for (int mt = 0; mt < MT; ++mt) {
-                        const float2 a0 = __fmul2_rn(ca1[mt], t1p0), a1 = __fmul2_rn(ca1[mt], t1p1);
-                        const float2 u0 = make_float2(ex2_approx(a0.x), ex2_approx(a0.y));  // (k, p0), (k+8, p0)
-                        const float2 u1 = make_float2(ex2_approx(a1.x), ex2_approx(a1.y));  // (k, p1), (k+8, p1)
+                        const float2 u0 = kernel_factor2<KERN>(ca1[mt], t1p0);  // (k, p0), (k+8, p0)
+                        const float2 u1 = kernel_factor2<KERN>(ca1[mt], t1p1);  // (k, p1), (k+8, p1)
                         bt[r][mt] = __fadd2_rn(bt[r][mt], __fadd2_rn(u0, u1));
                         const float2 h0 = make_float2(__uint_as_float(__float_as_uint(u0.x) & 0xffffe000u),
                                                       __uint_as_float(__float_as_uint(u0.y) & 0xffffe000u));
@@ -329,11 +330,11 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
             btl_s[e] = log2_wide(s);
         }
         __syncthreads();
-        loo_unit_epilogue<C>(a, cf, sm, u, u_begin, tile, At);
+        loo_unit_epilogue<C, KERN>(a, cf, sm, u, u_begin, tile, At);
     }
 }
 
-template <int G1, int G2>
+template <int G1, int G2, int KERN>
 __global__ void __launch_bounds__(256, 2) k_loo_mma(const LooArgs a) {
     extern __shared__ float4 sm4[];
     __shared__ int next_tile;
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(256, 2) k_loo_mma(const LooArgs a) {
         __syncthreads();
         const int t = next_tile;
         if (t >= a.n_tiles) break;
-        loo_tile_mma<G1, G2>(a, cf, t, reinterpret_cast<float*>(sm4));
+        loo_tile_mma<G1, G2, KERN>(a, cf, t, reinterpret_cast<float*>(sm4));
     }
 }
 

@@ -129,6 +129,15 @@ def scale_workload(N: int = 50000, d: int = 5, G1: int = 32, G2: int = 32, seed:
                     bandwidth_grid(0.05, 2.0, G1), bandwidth_grid(0.01, 1.0, G2), True)
 
 
+def epan_scale_workload(N: int = 50000, d: int = 5, G1: int = 32, G2: int = 32,
+                        seed: int = 1) -> Workload:
+    """The scale workload's data with a grid for Epanechnikov kernels, whose
+    support radius is h: h1 in [0.2, 4] (standardised x), h2 in [0.02, 2]."""
+    x, y = gmm_sine(N, d, seed=seed)
+    return Workload("gmm_sine_N%d_d%d_%dx%d_epan" % (N, d, G1, G2), x, y,
+                    bandwidth_grid(0.2, 4.0, G1), bandwidth_grid(0.02, 2.0, G2), True)
+
+
 def batch_workloads(n_datasets: int = 256, N_min: int = 500, N_max: int = 20000,
                     G: int = 16, seed: int = 2, dims=(1, 2, 4, 8)) -> List[Workload]:
     """Many independent datasets: N log-uniform in [N_min, N_max], d drawn
