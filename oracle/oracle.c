@@ -488,3 +488,99 @@ void oracle_density(const double *x, const double *y, int64_t N, int d, double h
     free(th);
     pthread_mutex_destroy(&J.mu);
 }
+
+/* ------------------------------------------------------------------ */
+/* Products of the conditional density at query points (Sec. 4.2)     */
+/* ------------------------------------------------------------------ */
+/* With x weights K_h1(x_q - x_i) (Eq. 1), at each query q:
+ *   mean[q] = E[y | x_q] = sum_i K_h1 y_i / sum_i K_h1 (the y kernel is symmetric),
+ *   fat[q]  = fhat(yq[q] | x_q),
+ *   F[q][g] = P(y <= yg[g] | x_q) = sum_i K_h1 G((yg[g] - y_i)/h2) / sum_i K_h1,
+ * G the y kernel's CDF: Phi for the Gaussian, (2 + 3t - t^3)/4 on [-1, 1] for
+ * the Epanechnikov kernel.  Gaussian x weights are exp(e_i - max e) (FP64).
+ * An Epanechnikov query with no x-neighbour inside h1 gets mean = NaN (0/0),
+ * fat = 0 and F = NaN. */
+typedef struct {
+    const double *x, *y, *xq, *yq, *yg;
+    int64_t N, Q;
+    int d, G, kernel;
+    double h1, h2;
+    double *mean, *fat, *F;
+    int64_t next;
+    pthread_mutex_t mu;
+} prod_job_t;
+
+static double kernel_cdf(int kernel, double t) {
+    if (kernel == 1) {
+        if (t <= -1.0) return 0.0;
+        if (t >= 1.0) return 1.0;
+        return (2.0 + 3.0 * t - t * t * t) / 4.0;
+    }
+    return 0.5 * erfc(-t / sqrt(2.0));
+}
+
+static double kernel_pdf_y(int kernel, double t, double h2) {
+    if (kernel == 1) return 0.75 * epan_prof(t * t, 1.0) / h2;
+    return exp(-0.5 * t * t - LN_SQRT_2PI) / h2;
+}
+
+static void *prod_worker(void *arg) {
+    prod_job_t *J = (prod_job_t *)arg;
+    double *wx = malloc(sizeof(double) * J->N);
+    for (;;) {
+        pthread_mutex_lock(&J->mu);
+        int64_t q = J->next++;
+        pthread_mutex_unlock(&J->mu);
+        if (q >= J->Q) break;
+        double m = -INFINITY;
+        for (int64_t i = 0; i < J->N; ++i) {
+            const double r2 = sqdist(J->xq + q * J->d, J->x + i * J->d, J->d);
+            if (J->kernel == 1) {
+                wx[i] = epan_prof(r2, J->h1);
+            } else {
+                wx[i] = -r2 / (2.0 * J->h1 * J->h1);
+                if (wx[i] > m) m = wx[i];
+            }
+        }
+        if (J->kernel != 1)
+            for (int64_t i = 0; i < J->N; ++i) wx[i] = exp(wx[i] - m);
+        double B = 0.0, S1 = 0.0;
+        for (int64_t i = 0; i < J->N; ++i) {
+            B += wx[i];
+            S1 += wx[i] * J->y[i];
+        }
+        if (J->mean) J->mean[q] = S1 / B;
+        if (J->fat) {
+            double A = 0.0;
+            for (int64_t i = 0; i < J->N; ++i)
+                A += wx[i] * kernel_pdf_y(J->kernel, (J->yq[q] - J->y[i]) / J->h2, J->h2);
+            J->fat[q] = B > 0.0 ? A / B : 0.0;
+        }
+        if (J->F)
+            for (int g = 0; g < J->G; ++g) {
+                double A = 0.0;
+                for (int64_t i = 0; i < J->N; ++i)
+                    A += wx[i] * kernel_cdf(J->kernel, (J->yg[g] - J->y[i]) / J->h2);
+                J->F[q * J->G + g] = A / B;
+            }
+    }
+    free(wx);
+    return NULL;
+}
+
+/* mean[Q], fat[Q] (needs yq) and F[Q][G] (needs yg); any output may be NULL. */
+void oracle_cond_products(const double *x, const double *y, int64_t N, int d, double h1, double h2,
+                          const double *xq, const double *yq, int64_t Q, const double *yg, int G,
+                          double *mean, double *fat, double *F, int n_threads, int kernel) {
+    prod_job_t J;
+    memset(&J, 0, sizeof(J));
+    J.x = x; J.y = y; J.xq = xq; J.yq = yq; J.yg = yg; J.N = N; J.Q = Q; J.d = d; J.G = G;
+    J.kernel = kernel; J.h1 = h1; J.h2 = h2; J.mean = mean; J.fat = fat; J.F = F;
+    pthread_mutex_init(&J.mu, NULL);
+    if (n_threads < 1) n_threads = 1;
+    pthread_t *th = malloc(sizeof(pthread_t) * n_threads);
+    for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, prod_worker, &J);
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&J.mu);
+}

@@ -60,6 +60,9 @@ def _load():
         lib.oracle_density.argtypes = [_dp, _dp, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, _dp, ctypes.c_int64, _dp, ctypes.c_int,
                                        _dp, ctypes.c_int, ctypes.c_int]
+        lib.oracle_cond_products.argtypes = [_dp, _dp, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, _dp, _dp, ctypes.c_int64, _dp, ctypes.c_int,
+                                             _dp, _dp, _dp, ctypes.c_int, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -150,6 +153,55 @@ def grad(x, y, h1: float, h2: float, rows=None, standardize_x: bool = False,
     _load().oracle_grad(_ptr(x), _ptr(y), N, x.shape[1], float(h1), float(h2), _ptr(r), n,
                         _ptr(row_out), _ptr(out), n_threads or default_threads(), _kern(kernel))
     return (out, row_out) if per_row else out
+
+
+def _queries(x, xq, standardize_x: bool):
+    """(data, queries) in FP64, both standardised by the data's mean/sd if asked."""
+    xr = _f64(x)
+    if xr.ndim == 1:
+        xr = xr[:, None]
+    q = _f64(xq)
+    if q.ndim == 1:
+        q = q[:, None]
+    if standardize_x:
+        q = (q - xr.mean(axis=0)) / xr.std(axis=0, ddof=1)
+        xr = standardize(xr)
+    return np.ascontiguousarray(xr), np.ascontiguousarray(q)
+
+
+def cond_products(x, y, h1: float, h2: float, xq, yq=None, ygrid=None, standardize_x: bool = False,
+                  n_threads: Optional[int] = None, kernel: str = "gauss"):
+    """Sec. 4.2 products of fhat(.|x_q): E[y|x_q] ('mean'), fhat(yq|x_q)
+    ('fat', when yq is given) and the conditional CDF on ygrid ('F')."""
+    xs, q = _queries(x, xq, standardize_x)
+    yv = _f64(y)
+    Q = q.shape[0]
+    yqv = None if yq is None else _f64(yq).reshape(-1)
+    yg = None if ygrid is None else _f64(ygrid).reshape(-1)
+    mean = np.empty(Q)
+    fat = np.empty(Q) if yqv is not None else None
+    F = np.empty((Q, yg.size)) if yg is not None else None
+    _load().oracle_cond_products(_ptr(xs), _ptr(yv), xs.shape[0], xs.shape[1], float(h1), float(h2),
+                                 _ptr(q), _ptr(yqv), Q, _ptr(yg), 0 if yg is None else yg.size,
+                                 _ptr(mean), _ptr(fat), _ptr(F), n_threads or default_threads(),
+                                 _kern(kernel))
+    return {"mean": mean, "fat": fat, "F": F}
+
+
+def narrowest_interval(ygrid, F, alpha: float):
+    """Narrowest [lo, hi] of grid points with F(hi) - F(lo) >= 1 - alpha, per
+    row of F (Sec. 4: the narrowest set of quantiles with the coverage)."""
+    g = _f64(ygrid).reshape(-1)
+    F = np.atleast_2d(_f64(F))
+    out = np.empty((F.shape[0], 2))
+    for r in range(F.shape[0]):
+        hi_idx = np.searchsorted(F[r], F[r] + (1.0 - alpha), side="left")
+        ok = hi_idx < g.size
+        lo = np.nonzero(ok)[0]
+        w = g[hi_idx[ok]] - g[lo]
+        k = int(np.argmin(w))
+        out[r] = (g[lo[k]], g[hi_idx[ok][k]])
+    return out
 
 
 def density(x, y, h1: float, h2: float, xq, ygrid, standardize_x: bool = False,

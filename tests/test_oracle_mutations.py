@@ -39,6 +39,10 @@ MUTATIONS = {
                                         "const double v = 2.0 * dx2[i] / (h1 * h1);"),
     "epan_gradient_h2_sign": ("out[2] = sA > 0.0 ? sAz / sA - 1.0 : 0.0;",
                               "out[2] = sA > 0.0 ? sAz / sA + 1.0 : 0.0;"),
+    # products of fhat(.|x) (Sec. 4.2)
+    "cdf_wrong_tail": ("return 0.5 * erfc(-t / sqrt(2.0));", "return 0.5 * erfc(t / sqrt(2.0));"),
+    "epan_cdf_cubic_sign": ("return (2.0 + 3.0 * t - t * t * t) / 4.0;", "return (2.0 + 3.0 * t + t * t * t) / 4.0;"),
+    "cond_mean_unweighted": ("S1 += wx[i] * J->y[i];", "S1 += J->y[i];"),
     "epan_density_missing_h2": ("J->f[q * J->G + g] = B > 0.0 ? A / B * exp(lc1 - log(J->h2)) : 0.0;",
                                 "J->f[q * J->G + g] = B > 0.0 ? A / B * exp(lc1) : 0.0;"),
 }

@@ -344,3 +344,69 @@ def test_epan_density_matches_brute_and_integrates_to_one():
         for g in range(0, grid.size, 5000):
             want = brute.density(xl, yl, xq[q].tolist(), grid[g], h1, h2, "epan")
             assert abs(f[q, g] - want) <= 1e-12 * want + 1e-300
+
+
+# ---------------------------------------------------------------------------
+# Products of fhat(.|x) used by the paper's evaluation (Sec. 4.2): the
+# conditional mean, the density at a point, the conditional CDF and the
+# narrowest interval of given coverage.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kernel", ["gauss", "epan"])
+def test_products_limits_and_consistency(kernel):
+    x, y = _small(60, 2, 50)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    xq = xd[:5] + 0.05
+    # h1 -> inf: the conditional mean is the mean of y
+    p = oracle.cond_products(xd, yd, 1e7, 0.5, xq, kernel=kernel)
+    np.testing.assert_allclose(p["mean"], yd.mean(), rtol=1e-9)
+    # the density at a point equals the pinned grid density there
+    h1, h2 = 1.5, 0.4
+    p = oracle.cond_products(xd, yd, h1, h2, xq, yq=yd[:5] + 0.1, kernel=kernel)
+    f = oracle.density(xd, yd, h1, h2, xq, yd[:5] + 0.1, kernel=kernel)
+    np.testing.assert_allclose(p["fat"], np.diag(f), rtol=1e-12)
+    # the mean against the weights written out
+    r2 = ((xd[None, :, :] - xq[:, None, :]) ** 2).sum(-1)
+    u = np.exp(-r2 / (2 * h1 * h1)) if kernel == "gauss" else np.clip(1 - r2 / (h1 * h1), 0, None)
+    np.testing.assert_allclose(p["mean"], (u * yd).sum(1) / u.sum(1), rtol=1e-12)
+
+
+def test_conditional_mean_h1_zero_is_nearest_neighbour():
+    x, y = _small(40, 2, 51)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    xq = xd[:6] + 0.01
+    p = oracle.cond_products(xd, yd, 1e-3, 0.3, xq)
+    nn = ((xd[None, :, :] - xq[:, None, :]) ** 2).sum(-1).argmin(1)
+    np.testing.assert_allclose(p["mean"], yd[nn], rtol=1e-9)
+
+
+@pytest.mark.parametrize("kernel", ["gauss", "epan"])
+def test_cdf_is_the_integral_of_the_density(kernel):
+    x, y = _small(50, 1, 52)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    h1, h2 = 0.7, 0.35
+    g = np.linspace(yd.min() - 8 * h2, yd.max() + 8 * h2, 40001)
+    xq = xd[:3]
+    F = oracle.cond_products(xd, yd, h1, h2, xq, ygrid=g, kernel=kernel)["F"]
+    f = oracle.density(xd, yd, h1, h2, xq, g, kernel=kernel)
+    integ = np.concatenate([np.zeros((3, 1)), np.cumsum(0.5 * (f[:, 1:] + f[:, :-1]) * np.diff(g), 1)], 1)
+    np.testing.assert_allclose(F, integ, atol=2e-7)
+    assert np.all(np.diff(F, axis=1) >= -1e-15) and np.allclose(F[:, -1], 1.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("kernel,t", [("gauss", 1.959963984540054),
+                                      ("epan", 2 * math.sin(math.asin(0.95) / 3))])
+def test_narrowest_interval_of_one_component(kernel, t):
+    """h1 -> 0 leaves one data point's y kernel: the narrowest 95% interval is
+    symmetric, +-1.96 h2 (normal) or +-t h2 with (3t - t^3)/2 = 0.95."""
+    x, y = _small(30, 2, 53)
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    xq = xd[:1] + 1e-4
+    h2 = 0.5
+    nn = int(((xd - xq) ** 2).sum(1).argmin())
+    g = np.linspace(yd[nn] - 3, yd[nn] + 3, 60001)
+    F = oracle.cond_products(xd, yd, 1e-3, h2, xq, ygrid=g, kernel=kernel)["F"]
+    lo, hi = oracle.narrowest_interval(g, F, 0.05)[0]
+    # the width is well conditioned; the location of the narrowest window is
+    # not (the width is flat to second order in it)
+    assert abs((hi - lo) - 2 * t * h2) < 3e-4
+    assert abs(0.5 * (lo + hi) - yd[nn]) < 0.01
