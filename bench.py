@@ -414,6 +414,45 @@ def run_density(args):
     cde.cde_shutdown(ctx)
 
 
+def run_select(args):
+    """The paper's selection protocol (Sec. 3.5, Sec. 4): random search over
+    (0, h_max] on standardised data with the Epanechnikov kernel, every
+    candidate scored exactly (Eq. 3), against the normal-reference rule
+    (Sec. 4.2).  N = 10,000 with d = 9 and d = 3 (the largest sizes and the
+    dimensions of the paper's time trials, Sec. 4.1); host-timed selections
+    (synchronous C-ABI call)."""
+    from paper_1206_5278_gb300 import cde, synth
+    ctx = cde.cde_init(0)
+    out = {}
+    R, G = args.select_rounds, 32
+    for d in (9, 3):
+        x, y = synth.gmm_sine(args.select_N, d, seed=40 + d)
+        ds = cde.cde_create_dataset(ctx, x, y, standardize=True, kernel="epan")
+        h2_max = 10.0 * float(np.std(y.astype(np.float64), ddof=1))
+        cde.cde_select_random(ctx, ds, 10.0, h2_max, 1, G, G, seed=99)  # warm-up
+        times = []
+        for s in range(max(1, args.steps)):
+            t0 = time.perf_counter()
+            best = cde.cde_select_random(ctx, ds, 10.0, h2_max, R, G, G, seed=s)
+            times.append(time.perf_counter() - t0)
+        h1r, h2r = cde.cde_reference_rule(ctx, ds)
+        Lr_c, Lr_e = cde.cde_loo_loglik(ctx, ds, [h1r], [h2r])
+        sec = float(np.median(times))
+        out["d%d" % d] = {"seconds_per_selection": sec, "candidates": R * G * G,
+                          "pair_evals_per_s": R * G * G * args.select_N ** 2 / sec,
+                          "best": {k: float(best[k]) for k in ("h1", "h2", "L_eq3", "L_cond")},
+                          "reference_rule": {"h1": h1r, "h2": h2r, "L_eq3": float(Lr_e[0, 0]),
+                                             "L_cond": float(Lr_c[0, 0])}}
+        cde.cde_destroy_dataset(ctx, ds)
+    v = out["d9"]["pair_evals_per_s"]
+    _line(workload="select_N%d_epan" % args.select_N, value=v, steps=args.steps, warmup=1,
+          ms_per_step=1e3 * out["d9"]["seconds_per_selection"], selections=out,
+          config={"workload": "select", "N": args.select_N, "d_x": [9, 3], "kernel": "epan",
+                  "rounds": R, "G1": G, "G2": G, "h1_max": 10.0, "h2_max": "10 sd(y)",
+                  "objective": "L_eq3", "timing": "host wall clock around the synchronous call"})
+    cde.cde_shutdown(ctx)
+
+
 def run_serve(args):
     """Poisson stream, 70% density jobs (Q log-uniform [1, Q_max] x 256-point y
     grid), 30% selection jobs (16x16 grid + 20 Adam steps) over resident
@@ -509,7 +548,10 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--N", type=int, default=50000, help="dataset size (profiling runs use less)")
-    ap.add_argument("--workload", default="scale", choices=["scale", "tiny", "batch", "grad", "serve", "density"])
+    ap.add_argument("--workload", default="scale",
+                    choices=["scale", "tiny", "batch", "grad", "serve", "density", "select"])
+    ap.add_argument("--select-N", type=int, default=10000)
+    ap.add_argument("--select-rounds", type=int, default=8)
     ap.add_argument("--kernel", default="gauss", choices=["gauss", "epan"],
                     help="kernel family of the scale workload (epan: Epanechnikov, its own grid)")
     ap.add_argument("--dens-Q", type=int, default=10000)
@@ -532,7 +574,7 @@ def main():
             from __graft_entry__ import build
             build()
         {"tiny": run_tiny, "batch": run_batch, "grad": run_grad, "serve": run_serve,
-         "density": run_density}[args.workload](args)
+         "density": run_density, "select": run_select}[args.workload](args)
         return
     w = synth.scale_workload(N=args.N, seed=1 + 1000 * rank)
     if args.kernel == "epan":

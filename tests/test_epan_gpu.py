@@ -55,7 +55,7 @@ def _check_grid(Lc, Le, x, y, h1, h2, standardize=False, want_inf=None):
         assert err_c.max() <= TOL, "L_cond max rel err %g" % err_c.max()
     fe = np.isfinite(ref_e)
     if fe.any():
-        err_e = np.abs(Le[fe] - ref_e[fe]) / np.abs(lnA).mean(0)[fe]
+        err_e = np.abs(Le[fe] - ref_e[fe]) / np.abs(lnA - math.log(N - 1)).mean(0)[fe]
         assert err_e.max() <= TOL, "L_eq3 max rel err %g" % err_e.max()
     return fin.sum()
 

@@ -33,7 +33,7 @@ def _check_grid(Lc, Le, x, y, h1, h2, standardize=False):
     N = x.shape[0]
     ref_e = lnA.mean(0) - math.log(N - 1)
     scale_c = np.abs(ell).sum(0)
-    scale_e = np.abs(lnA).mean(0)
+    scale_e = np.abs(lnA - math.log(N - 1)).mean(0)  # L_eq3 = mean_j (ln A_j - ln(N-1))
     err_c = np.abs(Lc - ref_c) / scale_c
     err_e = np.abs(Le - ref_e) / scale_e
     assert np.all(np.isfinite(Lc)) and np.all(np.isfinite(Le))
