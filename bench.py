@@ -453,6 +453,118 @@ def run_select(args):
     cde.cde_shutdown(ctx)
 
 
+def run_products(args):
+    """Throughput of the Sec. 4.2 product kernels on device-resident inputs
+    (CUDA events on the launching stream): conditional mean + point density
+    for Q = 10,000 queries and 95% intervals from 1,000 draws for Q = 1,000
+    queries, against N = 100,000 points, d = 4, both kernel families."""
+    import torch
+    from paper_1206_5278_gb300 import cde, synth
+    ctx = cde.cde_init(0)
+    N, d = args.dens_N, args.dens_d
+    x, y = synth.gmm_sine(N, d, seed=8)
+    out = {}
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    for kern, h1 in (("gauss", 0.3), ("epan", 0.6)):
+        ds = cde.cde_create_dataset(ctx, x, y, standardize=True, kernel=kern)
+        Qs, Qi, S = 10000, 1000, 1000
+        xq = torch.from_numpy(synth.query_points(x, Qs, seed=9)).cuda()
+        yq = torch.from_numpy(np.resize(y, Qs)).cuda()
+        mean = torch.empty(Qs, dtype=torch.float64, device="cuda")
+        fat = torch.empty(Qs, dtype=torch.float64, device="cuda")
+        lo = torch.empty(Qi, dtype=torch.float32, device="cuda")
+        hi = torch.empty(Qi, dtype=torch.float32, device="cuda")
+        L = cde.lib()
+
+        def stats():
+            cde.cde_cond_stats(ctx, ds, h1, 0.1, xq, yq, mean, fat, stream=st)
+
+        def interval():
+            cde._check(L.cde_cond_interval(ctx, ds, h1, 0.1, cde._ptr(xq), Qi, S, 0.05, 7, cde._ptr(lo),
+                                           cde._ptr(hi), None, cde.CDE_IN_DEVICE | cde.CDE_OUT_DEVICE,
+                                           cde._stream(st)))
+        res = {}
+        for tag, fn, pairs in (("cond_stats", stats, Qs * N), ("interval", interval, Qi * N)):
+            for _ in range(max(2, args.warmup)):
+                fn()
+            st.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            for a, b in ev:
+                a.record(st)
+                fn()
+                b.record(st)
+            st.synchronize()
+            ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+            res[tag] = {"ms": ms, "query_point_pairs_per_s": pairs / (ms * 1e-3)}
+        res["interval"]["draws_per_s"] = Qi * S / (res["interval"]["ms"] * 1e-3)
+        out[kern] = res
+        cde.cde_destroy_dataset(ctx, ds)
+    _line(workload="products_N%d_d%d" % (N, d), metric="conditional mean + point density (query, point) pairs/s",
+          unit="pairs/s", value=out["gauss"]["cond_stats"]["query_point_pairs_per_s"], steps=args.steps,
+          warmup=args.warmup, ms_per_step=out["gauss"]["cond_stats"]["ms"], kernels=out,
+          config={"workload": "products", "N": N, "d_x": d, "Q_stats": 10000, "Q_interval": 1000,
+                  "draws": 1000, "alpha": 0.05})
+    cde.cde_shutdown(ctx)
+
+
+def run_evaluate(args):
+    """The evaluation of Sec. 4.2 on its three synthetic sets with known
+    f(y|x) (bimodal sine, 5-D uniform, decay series): K-fold cross-validation;
+    per fold, bandwidths from the likelihood (random search, Eq. 3,
+    Epanechnikov kernels, h_max = 10 on standardised data) and from the
+    reference rule; on the held-out fold ISE = mean (fhat(y|x) - f(y|x))^2,
+    MSE of E[y|x], coverage and half-width of 95% intervals (1,000 draws).
+    Every step runs through the C ABI; the line reports the wall time."""
+    from collections import defaultdict
+    from paper_1206_5278_gb300 import cde, synth
+    ctx = cde.cde_init(0)
+    # the sizes of the paper's Table 1 sets
+    gens = {"bimodal_sine": (synth.bimodal_sine, 10000), "uniform_5d": (synth.uniform_5d, 15000),
+            "decay_series": (synth.decay_series, 2000)}
+    K = args.eval_folds
+    table = {}
+    t0 = time.perf_counter()
+    for gi, (name, (gen, N)) in enumerate(gens.items()):
+        if args.eval_N:
+            N = args.eval_N
+        x, y = gen(N, seed=100 + gi)
+        folds = np.array_split(np.random.default_rng(gi).permutation(N), K)
+        acc = {"likelihood": defaultdict(list), "reference_rule": defaultdict(list)}
+        for f in range(K):
+            test = folds[f]
+            train = np.concatenate([folds[g] for g in range(K) if g != f])
+            ds = cde.cde_create_dataset(ctx, x[train], y[train], standardize=True, kernel="epan")
+            sdy = float(np.std(y[train].astype(np.float64), ddof=1))
+            sel = cde.cde_select_random(ctx, ds, 10.0, 10.0 * sdy, args.select_rounds, 32, 32, seed=f)
+            choices = {"likelihood": (sel["h1"], sel["h2"]), "reference_rule": cde.cde_reference_rule(ctx, ds)}
+            xt, yt = x[test], y[test]
+            ftrue = synth.true_cond_density(name, xt, yt)
+            for tag, (h1, h2) in choices.items():
+                mean, fat = cde.cde_cond_stats(ctx, ds, h1, h2, xt, yt)
+                lo, hi = cde.cde_cond_interval(ctx, ds, h1, h2, xt, S=1000, alpha=0.05, seed=f)
+                ok = np.isfinite(mean)
+                a = acc[tag]
+                a["h1"].append(h1)
+                a["h2"].append(h2)
+                a["ISE"].append(float(np.mean((fat - ftrue) ** 2)))
+                a["MSE"].append(float(np.mean((mean[ok] - yt[ok]) ** 2)) if ok.any() else float("nan"))
+                a["coverage"].append(float(np.mean((lo <= yt) & (yt <= hi))))
+                a["half_width"].append(float(np.mean(0.5 * (hi[ok] - lo[ok]))) if ok.any() else float("nan"))
+                a["empty_support_frac"].append(float(1.0 - ok.mean()))
+            cde.cde_destroy_dataset(ctx, ds)
+        table[name] = {tag: {k: float(np.mean(v)) for k, v in a.items()} for tag, a in acc.items()}
+    wall = time.perf_counter() - t0
+    _line(workload="evaluate_sec4_2", metric="Sec. 4.2 evaluation wall time (3 sets x %d folds)" % K,
+          unit="s", value=wall, higher_is_better=False, steps=1, warmup=0, ms_per_step=1e3 * wall,
+          table=table,
+          config={"workload": "evaluate", "N": {"bimodal_sine": 10000, "uniform_5d": 15000, "decay_series": 2000}
+                  if not args.eval_N else args.eval_N, "folds": K, "kernel": "epan", "objective": "L_eq3",
+                  "rounds": args.select_rounds, "G": 32, "interval_draws": 1000, "alpha": 0.05})
+    cde.cde_shutdown(ctx)
+
+
 def run_serve(args):
     """Poisson stream, 70% density jobs (Q log-uniform [1, Q_max] x 256-point y
     grid), 30% selection jobs (16x16 grid + 20 Adam steps) over resident
@@ -549,9 +661,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--N", type=int, default=50000, help="dataset size (profiling runs use less)")
     ap.add_argument("--workload", default="scale",
-                    choices=["scale", "tiny", "batch", "grad", "serve", "density", "select"])
+                    choices=["scale", "tiny", "batch", "grad", "serve", "density", "select", "evaluate",
+                             "products"])
     ap.add_argument("--select-N", type=int, default=10000)
     ap.add_argument("--select-rounds", type=int, default=8)
+    ap.add_argument("--eval-N", type=int, default=0, help="0: the sizes of the paper's Table 1 sets")
+    ap.add_argument("--eval-folds", type=int, default=10)
     ap.add_argument("--kernel", default="gauss", choices=["gauss", "epan"],
                     help="kernel family of the scale workload (epan: Epanechnikov, its own grid)")
     ap.add_argument("--dens-Q", type=int, default=10000)
@@ -574,7 +689,8 @@ def main():
             from __graft_entry__ import build
             build()
         {"tiny": run_tiny, "batch": run_batch, "grad": run_grad, "serve": run_serve,
-         "density": run_density, "select": run_select}[args.workload](args)
+         "density": run_density, "select": run_select, "evaluate": run_evaluate,
+         "products": run_products}[args.workload](args)
         return
     w = synth.scale_workload(N=args.N, seed=1 + 1000 * rank)
     if args.kernel == "epan":

@@ -253,6 +253,43 @@ int cde_select_random(cde_ctx *ctx, cde_dataset ds, double h1_max, double h2_max
 int cde_reference_rule(cde_ctx *ctx, cde_dataset ds, double *h1, double *h2);
 
 /* ------------------------------------------------------------------ */
+/* Products of fhat(.|x) used by the paper's evaluation (Sec. 4.2)     */
+/* ------------------------------------------------------------------ */
+/*
+ * Per query q (all N data points, no leave-one-out), with the x weights
+ * u_qi = K_h1(x_q - x_i) of Eq. 1:
+ *   mean_out[q] = E[y | x_q] = sum_i u_qi y_i / sum_i u_qi   (the y kernel is
+ *                 symmetric; NaN when the x-support is empty -- Epanechnikov);
+ *   fat_out[q]  = fhat(yq[q] | x_q), Eq. 1 at one point (0 when the x-support
+ *                 is empty; Gaussian values below about 2^-126 of the
+ *                 conditional peak flush to 0).
+ *   xq: Q x d_x row-major float32 in the dataset's original units; yq: Q
+ *   float32 (needed for fat_out only).  Either output may be NULL.  Outputs
+ *   are doubles, host unless CDE_OUT_DEVICE; CDE_IN_DEVICE: xq/yq on device.
+ * Sums in FP32 per data-range split, splits combined in FP64.
+ */
+int cde_cond_stats(cde_ctx *ctx, cde_dataset ds, double h1, double h2, const float *xq,
+                   const float *yq, int64_t Q, double *mean_out, double *fat_out, int flags,
+                   void *stream);
+
+/*
+ * Prediction intervals (Sec. 4): for each query, S draws from fhat(.|x_q)
+ * and the narrowest window [lo, hi] of ceil((1 - alpha) S) consecutive sorted
+ * draws.  A draw picks data index i with probability u_qi / sum u (inverse
+ * CDF over the cumulative weights in a fixed order) and adds h2 e, e drawn
+ * from the y kernel by inverse CDF (Gaussian: Phi^{-1}(V); Epanechnikov:
+ * 2 sin(asin(2V - 1)/3)).  Random numbers: value k of the SplitMix64 stream of
+ * `seed` (as in cde_select_random), k = 2 (q S + s) for draw s of query q and
+ * k + 1 for its kernel offset, u = ((z >> 40) + 1/2) 2^-24.
+ *   1 <= S <= 4096, 0 < alpha < 1.  lo_out, hi_out: Q floats; samples_out
+ *   (optional): Q x S sorted draws.  NaN for a query whose x-support is empty.
+ *   Host outputs unless CDE_OUT_DEVICE; CDE_IN_DEVICE: xq on device.
+ */
+int cde_cond_interval(cde_ctx *ctx, cde_dataset ds, double h1, double h2, const float *xq,
+                      int64_t Q, int S, double alpha, uint64_t seed, float *lo_out, float *hi_out,
+                      float *samples_out, int flags, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Request queue (continuous batching of density and selection jobs)   */
 /* ------------------------------------------------------------------ */
 enum { CDE_REQ_DENSITY = 0, CDE_REQ_SELECT = 1 };

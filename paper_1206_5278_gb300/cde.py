@@ -38,6 +38,7 @@ EXPORTED = [
     "cde_poll", "cde_wait", "cde_cancel", "cde_server_stats_get", "cde_server_stats_reset",
     "cde_measure_peaks", "cde_autotune", "cde_tuning_get", "cde_tuning_set",
     "cde_loo_loglik_noalloc", "cde_dataset_kernel", "cde_select_random", "cde_reference_rule",
+    "cde_cond_stats", "cde_cond_interval",
 ]
 
 
@@ -132,6 +133,11 @@ def lib():
                               ctypes.c_int),
         "cde_reference_rule": ([_vp, _i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                ctypes.c_int),
+        "cde_cond_stats": ([_vp, _i64, ctypes.c_double, ctypes.c_double, _vp, _vp, _i64, _vp, _vp,
+                            ctypes.c_int, _vp], ctypes.c_int),
+        "cde_cond_interval": ([_vp, _i64, ctypes.c_double, ctypes.c_double, _vp, _i64, ctypes.c_int,
+                               ctypes.c_double, ctypes.c_uint64, _vp, _vp, _vp, ctypes.c_int, _vp],
+                              ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -234,6 +240,46 @@ def cde_select_random(ctx, ds: int, h1_max: float, h2_max: float, rounds: int, G
         out.update(h1s=h1o.reshape(rounds, G1), h2s=h2o.reshape(rounds, G2),
                    Lc=Lco.reshape(rounds, G1, G2), Le=Leo.reshape(rounds, G1, G2))
     return out
+
+
+def cde_cond_stats(ctx, ds: int, h1: float, h2: float, xq, yq=None, mean_out=None, fat_out=None,
+                   stream=None):
+    """(E[y|x_q], fhat(yq|x_q)) per query; fhat only when yq is given.  Host
+    inputs return numpy arrays; CUDA tensors with outputs given run async."""
+    dev = _is_cuda(xq)
+    if dev:
+        q = xq.contiguous()
+        Q = int(q.shape[0])
+        _check(lib().cde_cond_stats(ctx, int(ds), float(h1), float(h2), _ptr(q), _ptr(yq), Q,
+                                    _ptr(mean_out), _ptr(fat_out), CDE_IN_DEVICE | CDE_OUT_DEVICE,
+                                    _stream(stream)))
+        return mean_out, fat_out
+    q = _f32(xq)
+    if q.ndim == 1:
+        q = q[:, None]
+    Q = q.shape[0]
+    yv = None if yq is None else _f32(yq).reshape(-1)
+    mean = np.empty(Q)
+    fat = np.empty(Q) if yv is not None else None
+    _check(lib().cde_cond_stats(ctx, int(ds), float(h1), float(h2), _ptr(q), _ptr(yv), Q, _ptr(mean),
+                                _ptr(fat), 0, _stream(stream)))
+    return mean, fat
+
+
+def cde_cond_interval(ctx, ds: int, h1: float, h2: float, xq, S: int = 1000, alpha: float = 0.05,
+                      seed: int = 0, samples: bool = False, stream=None):
+    """Narrowest (1 - alpha) windows of S draws from fhat(.|x_q): (lo, hi[, samples])."""
+    q = _f32(xq)
+    if q.ndim == 1:
+        q = q[:, None]
+    Q = q.shape[0]
+    lo = np.empty(Q, np.float32)
+    hi = np.empty(Q, np.float32)
+    sm = np.empty((Q, S), np.float32) if samples else None
+    _check(lib().cde_cond_interval(ctx, int(ds), float(h1), float(h2), _ptr(q), Q, int(S), float(alpha),
+                                   int(seed) & ((1 << 64) - 1), _ptr(lo), _ptr(hi), _ptr(sm), 0,
+                                   _stream(stream)))
+    return (lo, hi, sm) if samples else (lo, hi)
 
 
 def cde_reference_rule(ctx, ds: int):

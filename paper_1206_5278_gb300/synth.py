@@ -23,6 +23,16 @@ Recipes (all seeded, reproducible):
   mixture above, times a random 8x32 projection P (P_ij ~ N(0, 1/8)), plus
   N(0, 0.01) noise (variance 0.01).  y as in ``gmm_sine`` computed from the
   standardised 32-D x.
+* Sec. 4.2's synthetic sets with known f(y|x) (constants chosen here; the
+  paper gives only the shapes):
+  ``bimodal_sine``  -- x ~ U(0, 2 pi); y = s sin(x) + N(0, 0.2^2), s = -1 with
+  probability 0.2 (the sign flip), else +1;
+  ``uniform_5d``    -- five independent uniforms, dimension k = 1..5 of width
+  2^k on [0, 2^k]; x = dimensions 1..4, y = dimension 5 (f(y|x) = 1/32 on [0, 32]);
+  ``decay_series``  -- y_t = y_{t-k} + N(0, 1) with lag k in 1..7 drawn with
+  probability proportional to 2^-k; x_t = (y_{t-1}, ..., y_{t-7}); seven
+  N(0, 1) starting values.
+  ``true_cond_density`` evaluates f(y|x) of these generators.
 * ``bandwidth_grid`` -- log-spaced, both endpoints inclusive:
   h_k = h_min (h_max/h_min)^(k/(G-1)).
 """
@@ -136,6 +146,53 @@ def epan_scale_workload(N: int = 50000, d: int = 5, G1: int = 32, G2: int = 32,
     x, y = gmm_sine(N, d, seed=seed)
     return Workload("gmm_sine_N%d_d%d_%dx%d_epan" % (N, d, G1, G2), x, y,
                     bandwidth_grid(0.2, 4.0, G1), bandwidth_grid(0.02, 2.0, G2), True)
+
+
+def bimodal_sine(N: int, seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.0, 2.0 * math.pi, N)
+    sgn = np.where(rng.uniform(size=N) < 0.2, -1.0, 1.0)
+    y = sgn * np.sin(x) + 0.2 * rng.standard_normal(N)
+    return x[:, None].astype(np.float32), y.astype(np.float32)
+
+
+def uniform_5d(N: int, seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    rng = np.random.default_rng(seed)
+    z = rng.uniform(size=(N, 5)) * (2.0 ** np.arange(1, 6))
+    return z[:, :4].astype(np.float32), z[:, 4].astype(np.float32)
+
+
+DECAY_LAGS = 7
+DECAY_P = 2.0 ** -np.arange(1, DECAY_LAGS + 1) / (1.0 - 2.0 ** -DECAY_LAGS)
+
+
+def decay_series(N: int, seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    rng = np.random.default_rng(seed)
+    T = N + DECAY_LAGS
+    v = np.empty(T)
+    v[:DECAY_LAGS] = rng.standard_normal(DECAY_LAGS)
+    lags = rng.choice(np.arange(1, DECAY_LAGS + 1), size=T, p=DECAY_P)
+    eps = rng.standard_normal(T)
+    for t in range(DECAY_LAGS, T):
+        v[t] = v[t - lags[t]] + eps[t]
+    x = np.stack([v[DECAY_LAGS - k:T - k] for k in range(1, DECAY_LAGS + 1)], axis=1)
+    return x.astype(np.float32), v[DECAY_LAGS:].astype(np.float32)
+
+
+def true_cond_density(name: str, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """f(y|x) of the Sec. 4.2 generators above, at paired rows of x and y."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if name == "bimodal_sine":
+        s, sd = np.sin(x[:, 0]), 0.2
+        nrm = lambda m: np.exp(-0.5 * ((y - m) / sd) ** 2) / (sd * math.sqrt(2 * math.pi))
+        return 0.8 * nrm(s) + 0.2 * nrm(-s)
+    if name == "uniform_5d":
+        return np.where((y >= 0) & (y <= 32.0), 1.0 / 32.0, 0.0)
+    if name == "decay_series":
+        return sum(DECAY_P[k] * np.exp(-0.5 * (y - x[:, k]) ** 2) / math.sqrt(2 * math.pi)
+                   for k in range(DECAY_LAGS))
+    raise ValueError(name)
 
 
 def batch_workloads(n_datasets: int = 256, N_min: int = 500, N_max: int = 20000,
