@@ -57,6 +57,26 @@ __global__ void k_finite_check(const float* a, int64_t n, int* flag) {
 
 }  // namespace cde
 
+namespace cde {
+int workspace_reserve(cde_ctx* ctx, size_t dev, size_t host) {
+    if (dev > ctx->ws_bytes) {
+        if (ctx->ws) CDE_CUDA(cudaFree(ctx->ws));
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+        CDE_CUDA(cudaMalloc(&ctx->ws, dev));
+        ctx->ws_bytes = dev;
+    }
+    if (host > ctx->ws_host_bytes) {
+        if (ctx->ws_host) CDE_CUDA(cudaFreeHost(ctx->ws_host));
+        ctx->ws_host = nullptr;
+        ctx->ws_host_bytes = 0;
+        CDE_CUDA(cudaMallocHost(&ctx->ws_host, host));
+        ctx->ws_host_bytes = host;
+    }
+    return CDE_OK;
+}
+}  // namespace cde
+
 using namespace cde;
 
 extern "C" {
@@ -112,6 +132,8 @@ void cde_shutdown(cde_ctx* ctx) {
         ctx->datasets.clear();
     }
     cudaFree(ctx->d_err);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->ws_host) cudaFreeHost(ctx->ws_host);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -278,6 +300,24 @@ int cde_loo_loglik(cde_ctx* ctx, cde_dataset ds, const double* h1, int G1, const
     cudaStream_t st = pick_stream(ctx, stream);
     if (flags & CDE_OUT_DEVICE) return loo_grid_enqueue(ctx, *D, h1, G1, h2, G2, nullptr, 0, Lc, Le, nullptr, st);
     const size_t n = (size_t)G1 * G2;
+    // small calls: the context workspace (no per-call allocation, one copy into pinned memory)
+    const size_t out_bytes = (2 * n * sizeof(double) + 255) & ~(size_t)255;
+    const size_t scr = loo_grid_scratch_bytes(ctx, *D, G1, G2, D->N);
+    if (out_bytes + scr <= kWorkspaceMax && workspace_reserve(ctx, out_bytes + scr, 2 * n * sizeof(double)) == CDE_OK) {
+        double* dout = static_cast<double*>(ctx->ws);
+        rc = loo_grid_enqueue(ctx, *D, h1, G1, h2, G2, nullptr, 0, dout, dout + n, nullptr, st,
+                              static_cast<char*>(ctx->ws) + out_bytes, ctx->ws_bytes - out_bytes);
+        cudaError_t e = cudaSuccess;
+        if (rc == CDE_OK) e = cudaMemcpyAsync(ctx->ws_host, dout, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        if (rc != CDE_OK) return rc;
+        if (e != cudaSuccess) return cuda_error(e, "cde_loo_loglik: copy");
+        if (e2 != cudaSuccess) return cuda_error(e2, "cde_loo_loglik: kernels");
+        const double* hb = static_cast<const double*>(ctx->ws_host);
+        if (Lc) memcpy(Lc, hb, n * sizeof(double));
+        if (Le) memcpy(Le, hb + n, n * sizeof(double));
+        return CDE_OK;
+    }
     double* dbuf = nullptr;
     CDE_CUDA(cudaMallocAsync((void**)&dbuf, 2 * n * sizeof(double), st));
     rc = loo_grid_enqueue(ctx, *D, h1, G1, h2, G2, nullptr, 0, Lc ? dbuf : nullptr, Le ? dbuf + n : nullptr,

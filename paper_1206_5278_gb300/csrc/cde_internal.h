@@ -65,6 +65,13 @@ struct cde_ctx {
     int tune_upt[3][3] = {};  // autotuned units per tile by grid shape (8/16/32), 0 = default
     int tune_ctas[3][3] = {}; // autotuned resident CTAs per SM, 0 = default (2)
     void* batch_plan = nullptr;  // cached batched launch (graph), batch.cu
+    // workspace of the synchronous host-output calls (they hold `mu` until their
+    // stream has drained, so one call uses it at a time): device scratch and a
+    // pinned host buffer, grown on demand up to kWorkspaceMax, freed at shutdown
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    void* ws_host = nullptr;
+    size_t ws_host_bytes = 0;
 };
 
 namespace cde {
@@ -79,9 +86,19 @@ cudaStream_t pick_stream(cde_ctx* ctx, void* s);
 // Enqueue the LOO score for one dataset over a bandwidth grid (any G1, G2):
 // d_Lc / d_Le are device arrays G1 x G2 (either may be null); d_ell_rows
 // (n_rows x G1 x G2) is written when rows != null.
+// `scratch` (optional, stream-ordered exclusive use): device memory for the tile
+// partials and counters; when it is null or smaller than loo_grid_scratch_bytes
+// the call allocates from the stream-ordered pool instead.
 int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, const double* h2,
                      int G2, const int64_t* d_rows, int64_t n_rows, double* d_Lc, double* d_Le,
-                     double* d_ell_rows, cudaStream_t st);
+                     double* d_ell_rows, cudaStream_t st, void* scratch = nullptr,
+                     size_t scratch_bytes = 0);
+size_t loo_grid_scratch_bytes(cde_ctx* ctx, const Dataset& D, int G1, int G2, int64_t n_rows);
+
+constexpr size_t kWorkspaceMax = (size_t)64 << 20;
+// Make ctx->ws at least `dev` bytes and ctx->ws_host at least `host` bytes
+// (synchronous growth; callers hold ctx->mu and no work of theirs is in flight).
+int workspace_reserve(cde_ctx* ctx, size_t dev, size_t host);
 
 // Nearest squared distances per row (cached at dataset creation).
 int nn_shift_enqueue(const Dataset& D, cudaStream_t st);

@@ -278,9 +278,25 @@ int loo_grid_ctas(cde_ctx* ctx, int T1, int T2) {
     return (c > 0 ? c : 2) * ctx->sm_count;
 }
 
+size_t loo_grid_scratch_bytes(cde_ctx* ctx, const Dataset& D, int G1, int G2, int64_t n_rows) {
+    size_t mx = 0;
+    for (int k0 = 0; k0 < G1; k0 += 32) {
+        const int T1 = loo_pad1(G1 - k0 < 32 ? G1 - k0 : 32);
+        for (int l0 = 0; l0 < G2; l0 += 32) {
+            const int T2 = loo_pad2(G2 - l0 < 32 ? G2 - l0 : 32);
+            const int JW = 1024 / (T1 * T2);
+            const int64_t units = (n_rows + JW - 1) / JW;
+            const int upt = loo_units_per_tile(ctx, T1, T2);
+            const size_t b = (size_t)((units + upt - 1) / upt) * 2 * T1 * T2 * sizeof(double) + 256;
+            if (b > mx) mx = b;
+        }
+    }
+    return mx;
+}
+
 int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, const double* h2,
                      int G2, const int64_t* d_rows, int64_t n_rows, double* d_Lc, double* d_Le,
-                     double* d_ell_rows, cudaStream_t st) {
+                     double* d_ell_rows, cudaStream_t st, void* scratch, size_t scratch_bytes) {
     if (!d_rows) n_rows = D.N;
     for (int k0 = 0; k0 < G1; k0 += 32) {
         const int g1 = G1 - k0 < 32 ? G1 - k0 : 32;
@@ -303,7 +319,9 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
             a.G2r = g2;
             const size_t part_bytes = (size_t)a.n_tiles * 2 * T1 * T2 * sizeof(double);
             double* part = nullptr;
-            CDE_CUDA(cudaMallocAsync((void**)&part, part_bytes + 256, st));
+            const bool own = !(scratch && part_bytes + 256 <= scratch_bytes);
+            if (own) CDE_CUDA(cudaMallocAsync((void**)&part, part_bytes + 256, st));
+            else part = static_cast<double*>(scratch);
             a.part = part;
             a.tile_base = 0;
             a.work = reinterpret_cast<int*>(reinterpret_cast<char*>(part) + part_bytes);
@@ -312,7 +330,7 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
             const int grid = a.n_tiles < cmax ? a.n_tiles : cmax;
             int rc = launch_loo_tile_kernel(T1, T2, a, grid, st);
             if (rc != CDE_OK) {
-                cudaFreeAsync(part, st);
+                if (own) cudaFreeAsync(part, st);
                 return rc;
             }
             if (d_Lc || d_Le) {
@@ -323,7 +341,7 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
                     d_Le ? d_Le + (size_t)k0 * G2 + l0 : nullptr);
                 CDE_CUDA(cudaGetLastError());
             }
-            CDE_CUDA(cudaFreeAsync(part, st));
+            if (own) CDE_CUDA(cudaFreeAsync(part, st));
         }
     }
     return CDE_OK;
