@@ -9,10 +9,15 @@
 // shifted sums are needed:
 //   S_A = sum v_i, S_Ax = sum v_i dx2_i, S_Ay = sum v_i dy2_i,
 //   S_B = sum u_i, S_Bx = sum u_i dx2_i,
-// u_i = 2^{-a1 (dx2_i - m_x)}  (<= 1, the x-nearest neighbour gives 1), and
-// v_i = 2^{M - e_i}, e_i = a1 (dx2_i - m_x) + a2 (dy2_i - m_y), M the running
-// minimum of e_i (online rescaling: when a smaller e arrives the sums are
-// multiplied by 2^{e - M}), so no bandwidth underflows the numerator.
+// with the separable per-row shifts of the grid kernel:
+//   u_i = 2^{-a1 (dx2_i - m_x)}  (<= 1, the x-nearest neighbour gives 1),
+//   w_i = 2^{-a2 (dy2_i - m_y)},  v_i = u_i w_i,
+// two exp2 per pair.  S_B >= 1 never underflows; a row whose S_A falls below
+// 2^-40 (its x-near and y-near neighbours differ and both factors are small) is
+// recomputed exactly by k_grad_fallback with a joint shift: v_i = 2^{M - e_i},
+// e_i = a1 (dx2_i - m_x) + a2 (dy2_i - m_y), M the running minimum of e_i
+// (online rescaling: when a smaller e arrives the sums are multiplied by
+// 2^{e - M}).
 //
 // Epanechnikov datasets (profiles u = (1 - dx2/h1^2)_+, w = (1 - dy2/h2^2)_+):
 // d K_h1/d ln h1 = c_d h1^{-d} (v - d u) with v = 2 dx2/h1^2 inside the support,
@@ -59,35 +64,17 @@ __device__ __forceinline__ float fma_sat_g(float a, float b, float c) {
     return r;
 }
 
-// Initial running shift: +inf (Gaussian, lowered by the first pair), 0 (Epanechnikov, unused)
-template <int KERN>
-__device__ __forceinline__ float grad_m0() { return KERN == 0 ? INFINITY : 0.f; }
-
-// One pair's contribution.  Gaussian: online joint shift, without branches --
-// when e does not lower the running minimum the rescale factor is exactly
-// 2^0 = 1.  Epanechnikov: plain sums of the profiles and their log-derivative
-// weights (the support test is the profile itself being positive).
-template <int KERN>
-__device__ __forceinline__ void grad_accumulate(bool ok, float dx2, float dy2, float mx, float my,
-                                                float a1, float a2, float& M, float& SA, float& SAx,
-                                                float& SAy, float& SB, float& SBx) {
-    if constexpr (KERN == 1) {
-        const float u = ok ? fma_sat_g(-a1, dx2, 1.f) : 0.f;
-        const float w = fma_sat_g(-a2, dy2, 1.f);
-        const float v = u > 0.f ? 2.f * a1 * dx2 : 0.f;
-        const float z = w > 0.f ? 2.f * a2 * dy2 : 0.f;
-        SA = fmaf(u, w, SA);
-        SAx = fmaf(v, w, SAx);
-        SAy = fmaf(u, z, SAy);
-        SB += u;
-        SBx += v;
-        return;
-    }
+// One pair's contribution with the online joint shift, without branches: when
+// e does not lower the running minimum the rescale factor is exactly 2^0 = 1
+// (M = +inf at the start: r = 0, the sums are 0).  Gaussian fallback rows only.
+__device__ __forceinline__ void grad_accumulate_joint(bool ok, float dx2, float dy2, float mx, float my,
+                                                      float a1, float a2, float& M, float& SA, float& SAx,
+                                                      float& SAy, float& SB, float& SBx) {
     const float ex = dx2 - mx, ey = dy2 - my;
     const float e = fmaf(a1, ex, a2 * ey);
     const bool lower = ok && e < M;
     const float Mn = lower ? e : M;
-    const float r = lower ? ex2g(e - M) : 1.f;  // M = +inf at the start: r = 0, the sums are 0
+    const float r = lower ? ex2g(e - M) : 1.f;
     SA *= r;
     SAx *= r;
     SAy *= r;
@@ -101,15 +88,44 @@ __device__ __forceinline__ void grad_accumulate(bool ok, float dx2, float dy2, f
     SAy = fmaf(v, dy2, SAy);
 }
 
+// One pair's contribution.  Gaussian: the separable shifted factors u, w and
+// v = u w.  Epanechnikov: plain sums of the profiles and their log-derivative
+// weights (the support test is the profile itself being positive).
+template <int KERN>
+__device__ __forceinline__ void grad_accumulate(bool ok, float dx2, float dy2, float mx, float my,
+                                                float a1, float a2, float& SA, float& SAx,
+                                                float& SAy, float& SB, float& SBx) {
+    if constexpr (KERN == 1) {
+        const float u = ok ? fma_sat_g(-a1, dx2, 1.f) : 0.f;
+        const float w = fma_sat_g(-a2, dy2, 1.f);
+        const float v = u > 0.f ? 2.f * a1 * dx2 : 0.f;
+        const float z = w > 0.f ? 2.f * a2 * dy2 : 0.f;
+        SA = fmaf(u, w, SA);
+        SAx = fmaf(v, w, SAx);
+        SAy = fmaf(u, z, SAy);
+        SB += u;
+        SBx += v;
+        return;
+    }
+    const float u = ok ? ex2g(-a1 * (dx2 - mx)) : 0.f;
+    const float v = u * ex2g(-a2 * (dy2 - my));
+    SB += u;
+    SBx = fmaf(u, dx2, SBx);
+    SA += v;
+    SAx = fmaf(v, dx2, SAx);
+    SAy = fmaf(v, dy2, SAy);
+}
+
 template <int JB, int DREG, int KERN>
 __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
-    __shared__ float xt[DREG + 1][kGradThreads];
+    __shared__ __align__(16) float xt[kGradThreads][DREG];  // point-major: 128-bit broadcast loads
+    __shared__ float yt[kGradThreads];
     const int tid = threadIdx.x;
     const int64_t jbase = (int64_t)blockIdx.x * kGradThreads * JB + tid;
     const int64_t i0 = (int64_t)blockIdx.y * g.i_per_split;
     const int64_t i1 = min(g.N, i0 + g.i_per_split);
     const int d = g.d;
-    float xj[JB][DREG], yj[JB], mxj[JB], myj[JB], M[JB];
+    float xj[JB][DREG], yj[JB], mxj[JB], myj[JB];
     float SA[JB], SAx[JB], SAy[JB], SB[JB], SBx[JB];
     int64_t jj[JB];
 #pragma unroll
@@ -122,7 +138,6 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
         yj[b] = g.y[jc];
         mxj[b] = g.mx[jc];
         myj[b] = g.my[jc];
-        M[b] = grad_m0<KERN>();
         SA[b] = SAx[b] = SAy[b] = SB[b] = SBx[b] = 0.f;
     }
     const float a1 = g.a1, a2 = g.a2;
@@ -130,16 +145,22 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
         __syncthreads();
         const int64_t it = t0 + tid;  // < Np: i_per_split and Np are multiples of 128
 #pragma unroll
-        for (int c = 0; c < DREG; ++c) xt[c][tid] = c < d ? g.xs[(int64_t)c * g.Np + it] : 0.f;
-        xt[DREG][tid] = g.y[it];
+        for (int c = 0; c < DREG; ++c) xt[tid][c] = c < d ? g.xs[(int64_t)c * g.Np + it] : 0.f;
+        yt[tid] = g.y[it];
         __syncthreads();
         const int n = (int)min((int64_t)kGradThreads, i1 - t0);
         for (int t = 0; t < n; ++t) {
-            const int64_t i = t0 + t;
+            const int i32 = (int)(t0 + t);  // N < 2^31
             float xi[DREG];
 #pragma unroll
-            for (int c = 0; c < DREG; ++c) xi[c] = xt[c][t];
-            const float yi = xt[DREG][t];
+            for (int c = 0; c < DREG; c += 4) {
+                const float4 v4 = *reinterpret_cast<const float4*>(&xt[t][c]);
+                xi[c] = v4.x;
+                xi[c + 1] = v4.y;
+                xi[c + 2] = v4.z;
+                xi[c + 3] = v4.w;
+            }
+            const float yi = yt[t];
 #pragma unroll
             for (int b = 0; b < JB; ++b) {
                 float dx2 = 0.f;
@@ -150,7 +171,7 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
                 }
                 const float dy = yj[b] - yi;
                 const float dy2 = dy * dy;
-                grad_accumulate<KERN>(i != jj[b], dx2, dy2, mxj[b], myj[b], a1, a2, M[b], SA[b], SAx[b],
+                grad_accumulate<KERN>(i32 != (int)jj[b], dx2, dy2, mxj[b], myj[b], a1, a2, SA[b], SAx[b],
                                       SAy[b], SB[b], SBx[b]);
             }
         }
@@ -159,7 +180,7 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
     for (int b = 0; b < JB; ++b) {
         if (jj[b] >= g.N) continue;
         float* p = g.part + ((int64_t)blockIdx.y * g.N + jj[b]) * 6;
-        p[0] = M[b];
+        p[0] = 0.f;  // no running shift on this path
         p[1] = SA[b];
         p[2] = SAx[b];
         p[3] = SAy[b];
@@ -228,7 +249,7 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
         }
     }
     const float a1 = g.a1, a2 = g.a2;
-    float M[2] = {grad_m0<KERN>(), grad_m0<KERN>()}, SA[2] = {0, 0}, SAx[2] = {0, 0}, SAy[2] = {0, 0}, SB[2] = {0, 0},
+    float SA[2] = {0, 0}, SAx[2] = {0, 0}, SAy[2] = {0, 0}, SB[2] = {0, 0},
           SBx[2] = {0, 0};
     for (int64_t t0 = i0; t0 < i1; t0 += kGMTile) {
         __syncthreads();
@@ -275,19 +296,15 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
                     const int64_t i = t0 + p;
                     const float dx2 = fmaxf(nj[h] + ni_s[p] - 2.f * D[n][q], 0.f);
                     const float dy = yj[h] - yi_s[p];
-                    grad_accumulate<KERN>(i < i1 && i != jr[h], dx2, dy * dy, mxj[h], myj[h], a1, a2, M[h],
+                    grad_accumulate<KERN>(i < i1 && i != jr[h], dx2, dy * dy, mxj[h], myj[h], a1, a2,
                                           SA[h], SAx[h], SAy[h], SB[h], SBx[h]);
                 }
         }
     }
-    // combine the 4 lanes that share a row (t = 0..3): common shift, fixed xor order
+    // combine the 4 lanes that share a row (t = 0..3), fixed xor order
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        float Mm = M[h];
-        Mm = fminf(Mm, __shfl_xor_sync(0xffffffffu, Mm, 1));
-        Mm = fminf(Mm, __shfl_xor_sync(0xffffffffu, Mm, 2));
-        const float r = (SA[h] > 0.f) ? ex2g(Mm - M[h]) : 0.f;
-        float v[5] = {SA[h] * r, SAx[h] * r, SAy[h] * r, SB[h], SBx[h]};
+        float v[5] = {SA[h], SAx[h], SAy[h], SB[h], SBx[h]};
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             v[q] += __shfl_xor_sync(0xffffffffu, v[q], 1);
@@ -295,7 +312,7 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
         }
         if (t == 0 && jr[h] < N) {
             float* pp = g.part + ((int64_t)blockIdx.y * N + jr[h]) * 6;
-            pp[0] = Mm;
+            pp[0] = 0.f;
             pp[1] = v[0];
             pp[2] = v[1];
             pp[3] = v[2];
@@ -306,26 +323,20 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
 }
 
 // Per row: merge split partials (FP64, split order), then
-// rowv[j] = {ell_j, d ell_j/d ln h1, d ell_j/d ln h2}.
+// rowv[j] = {ell_j, d ell_j/d ln h1, d ell_j/d ln h2}.  Gaussian rows whose
+// numerator sum fell below 2^-40 are listed for k_grad_fallback instead.
 __global__ void k_grad_rows(const float* __restrict__ part, int n_split, int64_t N,
-                            const float* __restrict__ my, float a1f, float a2f, double h1, double h2,
-                            int epan, double lnc1, double* __restrict__ rowv) {
+                            const float* __restrict__ my, float a2f, double h1, double h2,
+                            int epan, double lnc1, double* __restrict__ rowv, int* __restrict__ fb_count,
+                            int* __restrict__ fb_rows) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
-    double Mst = INFINITY;
-    for (int s = 0; s < n_split; ++s) {
-        const float* p = part + ((int64_t)s * N + j) * 6;
-        if (p[1] > 0.f) Mst = fmin(Mst, (double)p[0]);
-    }
     double SA = 0, SAx = 0, SAy = 0, SB = 0, SBx = 0;
     for (int s = 0; s < n_split; ++s) {
         const float* p = part + ((int64_t)s * N + j) * 6;
-        if (p[1] > 0.f) {
-            const double r = exp2(Mst - (double)p[0]);
-            SA += r * p[1];
-            SAx += r * p[2];
-            SAy += r * p[3];
-        }
+        SA += p[1];
+        SAx += p[2];
+        SAy += p[3];
         SB += p[4];
         SBx += p[5];
     }
@@ -338,13 +349,86 @@ __global__ void k_grad_rows(const float* __restrict__ part, int n_split, int64_t
         g1 = live ? SAx / SA - SBx / SB : 0.0;
         g2 = live ? SAy / SA - 1.0 : 0.0;
     } else {
-        ell = log(SA) - log(SB) - LN2 * (Mst + (double)a2f * (double)my[j]) - (LNS2PI + log(h2));
+        if (!(SA >= 0x1p-40)) {
+            fb_rows[atomicAdd(fb_count, 1)] = (int)j;
+            return;
+        }
+        ell = log(SA) - log(SB) - LN2 * (double)a2f * (double)my[j] - (LNS2PI + log(h2));
         g1 = (SAx / SA - SBx / SB) / (h1 * h1);
         g2 = (SAy / SA) / (h2 * h2) - 1.0;
     }
     rowv[3 * j] = ell;
     rowv[3 * j + 1] = g1;
     rowv[3 * j + 2] = g2;
+}
+
+// Exact recomputation of the listed Gaussian rows (one CTA per row, rows
+// strided over the grid): every i with the online joint shift, thread partials
+// merged with a common shift in a fixed order.
+constexpr int kFbThreads = 256;
+
+__device__ __forceinline__ void merge_shifted(float& M, float (&S)[5], float Mo, const float (&So)[5]) {
+    const float Mm = fminf(M, Mo);
+    const float r = (M == Mm) ? 1.f : ex2g(Mm - M);    // the side at the minimum keeps its scale
+    const float ro = (Mo == Mm) ? 1.f : ex2g(Mm - Mo);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) S[q] = S[q] * r + So[q] * ro;
+    S[3] += So[3];  // the denominator sums carry no joint shift
+    S[4] += So[4];
+    M = Mm;
+}
+
+__global__ void __launch_bounds__(kFbThreads) k_grad_fallback(const GradArgs g, const int* __restrict__ fb_count,
+                                                               const int* __restrict__ fb_rows, double h1,
+                                                               double h2, double* __restrict__ rowv) {
+    __shared__ float xj_s[kMaxD];
+    __shared__ float redM[kFbThreads / 32], redS[kFbThreads / 32][5];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = *fb_count;
+    for (int r = blockIdx.x; r < n; r += gridDim.x) {
+        const int j = fb_rows[r];
+        __syncthreads();
+        for (int c = tid; c < g.d; c += kFbThreads) xj_s[c] = g.xs[(int64_t)c * g.Np + j];
+        __syncthreads();
+        const float yj = g.y[j], mx = g.mx[j], my = g.my[j];
+        float M = INFINITY, S[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int64_t i = tid; i < g.N; i += kFbThreads) {
+            float dx2 = 0.f;
+            for (int c = 0; c < g.d; ++c) {
+                const float q = xj_s[c] - g.xs[(int64_t)c * g.Np + i];
+                dx2 = fmaf(q, q, dx2);
+            }
+            const float dy = yj - g.y[i];
+            grad_accumulate_joint(i != j, dx2, dy * dy, mx, my, g.a1, g.a2, M, S[0], S[1], S[2], S[3], S[4]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float So[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) So[q] = __shfl_xor_sync(0xffffffffu, S[q], o);
+            merge_shifted(M, S, __shfl_xor_sync(0xffffffffu, M, o), So);
+        }
+        if (lane == 0) {
+            redM[warp] = M;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) redS[warp][q] = S[q];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < kFbThreads / 32; ++w) {
+                float So[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) So[q] = redS[w][q];
+                merge_shifted(M, S, redM[w], So);
+            }
+            const double LN2 = 0.69314718055994530942, LNS2PI = 0.91893853320467274178;
+            const double SA = S[0], SAx = S[1], SAy = S[2], SB = S[3], SBx = S[4];
+            rowv[3 * (int64_t)j] = log(SA) - log(SB) - LN2 * ((double)M + (double)g.a2 * (double)my) -
+                                   (LNS2PI + log(h2));
+            rowv[3 * (int64_t)j + 1] = (SAx / SA - SBx / SB) / (h1 * h1);
+            rowv[3 * (int64_t)j + 2] = (SAy / SA) / (h2 * h2) - 1.0;
+        }
+    }
 }
 
 // Fixed-order sum of the per-row triples: one CTA of 1024 threads.
@@ -411,7 +495,10 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     ns = (tiles + tiles_per - 1) / tiles_per;
     float* part = nullptr;
     double* rowv = d_rowv_ext;
+    int* fb = nullptr;  // [0] count, then the listed rows
     CDE_CUDA(cudaMallocAsync((void**)&part, (size_t)ns * D.N * 6 * sizeof(float), st));
+    CDE_CUDA(cudaMallocAsync((void**)&fb, (size_t)(D.N + 1) * sizeof(int), st));
+    CDE_CUDA(cudaMemsetAsync(fb, 0, sizeof(int), st));
     if (!rowv) CDE_CUDA(cudaMallocAsync((void**)&rowv, (size_t)D.N * 3 * sizeof(double), st));
     g.part = part;
     dim3 grid((unsigned)gx, (unsigned)ns);
@@ -423,14 +510,20 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     else if (DREG == 8) launch_grad<4, 8>(g, grid, st, epan);
     else launch_grad<2, 16>(g, grid, st, epan);
     CDE_CUDA(cudaGetLastError());
-    k_grad_rows<<<(unsigned)((D.N + 255) / 256), 256, 0, st>>>(part, (int)ns, D.N, D.my, g.a1, g.a2,
-                                                             h1, h2, epan ? 1 : 0, epan_log_norm(1), rowv);
+    k_grad_rows<<<(unsigned)((D.N + 255) / 256), 256, 0, st>>>(part, (int)ns, D.N, D.my, g.a2, h1, h2,
+                                                             epan ? 1 : 0, epan_log_norm(1), rowv, fb, fb + 1);
     CDE_CUDA(cudaGetLastError());
+    if (!epan) {
+        // listed rows only; exits at once when the list is empty
+        k_grad_fallback<<<2 * ctx->sm_count, kFbThreads, 0, st>>>(g, fb, fb + 1, h1, h2, rowv);
+        CDE_CUDA(cudaGetLastError());
+    }
     if (d_out3) {
         k_sum_rows3<<<1, 1024, 0, st>>>(rowv, D.N, d_out3);
         CDE_CUDA(cudaGetLastError());
     }
     CDE_CUDA(cudaFreeAsync(part, st));
+    CDE_CUDA(cudaFreeAsync(fb, st));
     if (!d_rowv_ext) CDE_CUDA(cudaFreeAsync(rowv, st));
     return CDE_OK;
 }

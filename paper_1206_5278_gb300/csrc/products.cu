@@ -9,8 +9,9 @@
 // u_qi are the x weights of Eq. 1 (Gaussian: 2^{a1 (m_q - |x_q - x_i|^2)} with
 // the query's nearest squared distance m_q; Epanechnikov: (1 - |x_q - x_i|^2/h1^2)_+).
 //
-// k_cond_stats: the three sums per query, queries in registers (two per
-// thread up to d = 16, else one), data points staged through shared memory, the data range split
+// k_cond_stats: the three sums per query, queries in registers (four per
+// thread up to d = 8, two up to 16, else one), data points staged through
+// shared memory point-major, the data range split
 // over gridDim.y; split partials are summed in FP64 in split order.
 //
 // k_cond_sample: one CTA per query.  A draw from fhat(.|x_q) is a mixture
@@ -95,7 +96,8 @@ struct StatArgs {
 
 template <int KERN, int DREG, int kCSJB>
 __global__ void __launch_bounds__(kCSThreads) k_cond_stats(const StatArgs a) {
-    __shared__ float xt[DREG + 1][kCSThreads];
+    __shared__ __align__(16) float xt[kCSThreads][DREG];  // point-major: 128-bit broadcast loads
+    __shared__ float yt[kCSThreads];
     const int tid = threadIdx.x;
     const int64_t qbase = (int64_t)blockIdx.x * kCSThreads * kCSJB + tid;
     const int64_t i0 = (int64_t)blockIdx.y * a.i_per_split;
@@ -117,18 +119,27 @@ __global__ void __launch_bounds__(kCSThreads) k_cond_stats(const StatArgs a) {
         __syncthreads();
         const int64_t it = t0 + tid;  // < Np: splits and Np are multiples of 128
 #pragma unroll
-        for (int c = 0; c < DREG; ++c) xt[c][tid] = c < d ? a.xs[(int64_t)c * a.Np + it] : 0.f;
-        xt[DREG][tid] = a.y[it];
+        for (int c = 0; c < DREG; ++c) xt[tid][c] = c < d ? a.xs[(int64_t)c * a.Np + it] : 0.f;
+        yt[tid] = a.y[it];
         __syncthreads();
         const int n = (int)min((int64_t)kCSThreads, i1 - t0);
         for (int t = 0; t < n; ++t) {
-            const float yi = xt[DREG][t];
+            const float yi = yt[t];
+            float xi[DREG];
+#pragma unroll
+            for (int c = 0; c < DREG; c += 4) {
+                const float4 v4 = *reinterpret_cast<const float4*>(&xt[t][c]);
+                xi[c] = v4.x;
+                xi[c + 1] = v4.y;
+                xi[c + 2] = v4.z;
+                xi[c + 3] = v4.w;
+            }
 #pragma unroll
             for (int b = 0; b < kCSJB; ++b) {
                 float dx2 = 0.f;
 #pragma unroll
                 for (int c = 0; c < DREG; ++c) {
-                    const float v = xq[b][c] - xt[c][t];
+                    const float v = xq[b][c] - xi[c];
                     dx2 = fmaf(v, v, dx2);
                 }
                 const float u = xweight<KERN>(dx2, a.a1, mq[b]);
@@ -419,13 +430,13 @@ static int prep_queries(cde_ctx* ctx, const Dataset& D, const float* d_xq, int64
     return CDE_OK;
 }
 
-// queries per thread: two while the coordinates fit in registers
-static int stats_jb(int d) { return d <= 16 ? 2 : 1; }
+// queries per thread: more while the coordinates fit in registers
+static int stats_jb(int d) { return d <= 8 ? 4 : d <= 16 ? 2 : 1; }
 
 template <int KERN>
 static void launch_stats_d(const StatArgs& a, dim3 grid, cudaStream_t st) {
-    if (a.d <= 4) k_cond_stats<KERN, 4, 2><<<grid, kCSThreads, 0, st>>>(a);
-    else if (a.d <= 8) k_cond_stats<KERN, 8, 2><<<grid, kCSThreads, 0, st>>>(a);
+    if (a.d <= 4) k_cond_stats<KERN, 4, 4><<<grid, kCSThreads, 0, st>>>(a);
+    else if (a.d <= 8) k_cond_stats<KERN, 8, 4><<<grid, kCSThreads, 0, st>>>(a);
     else if (a.d <= 16) k_cond_stats<KERN, 16, 2><<<grid, kCSThreads, 0, st>>>(a);
     else k_cond_stats<KERN, 64, 1><<<grid, kCSThreads, 0, st>>>(a);
 }

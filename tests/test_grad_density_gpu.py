@@ -51,6 +51,38 @@ def test_gradient_matches_oracle(ctx, d, h1, h2):
     cde.cde_destroy_dataset(ctx, ds)
 
 
+@pytest.mark.parametrize("d,h1,h2,d_mma", [(2, 0.08, 0.01, False), (3, 0.05, 0.005, False),
+                                            (20, 0.3, 0.005, True)])
+def test_gradient_rows_with_underflowing_numerators(ctx, d, h1, h2, d_mma):
+    """Bandwidths where, for some rows, the separably shifted numerator
+    sum_i 2^{-a1 (dx2 - m_x) - a2 (dy2 - m_y)} is below 2^-40 (checked here in
+    FP64): those rows take the exact joint-shift recomputation."""
+    w = synth.grad_workload(N=2000, d=d, seed=7)
+    xs = oracle.standardize(w.x)
+    yd = w.y.astype(np.float64)
+    D = ((xs[:, None, :] - xs[None, :, :]) ** 2).sum(-1)
+    Y = (yd[:, None] - yd[None, :]) ** 2
+    np.fill_diagonal(D, np.inf)
+    np.fill_diagonal(Y, np.inf)
+    l2e = math.log2(math.e)
+    e = l2e / (2 * h1 * h1) * (D - D.min(1)[:, None]) + l2e / (2 * h2 * h2) * (Y - Y.min(1)[:, None])
+    assert (np.exp2(-e).sum(1) < 2.0 ** -40).sum() >= 10
+    ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True)
+    out = cde.cde_loo_grad(ctx, ds, h1, h2)
+    ref, rows = oracle.grad(w.x, w.y, h1, h2, standardize_x=True, per_row=True)
+    _grad_check(out, ref, rows)
+    g_rows = cde.cde_loo_grad_rows(ctx, ds, h1, h2)
+    if d_mma:
+        # Gram-form distances n_j + n_i - 2 x_j.x_i (d >= 16): absolute error up
+        # to ~2^-19 (n_j + n_i), scaled by 1/(2 h1^2) in the row's log terms
+        n = (xs ** 2).sum(1)
+        tol = 2e-5 + (n + n.max()) * 2.0 ** -19 / (2 * h1 * h1)
+        assert np.all(np.abs(g_rows[:, 0] - rows[:, 0]) <= tol)
+    else:
+        np.testing.assert_allclose(g_rows[:, 0], rows[:, 0], rtol=2e-5, atol=2e-5)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
 def test_gradient_matches_central_differences_on_gpu(ctx):
     w = synth.grad_workload(N=3000, d=8, seed=5)
     ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True)
