@@ -384,32 +384,51 @@ def run_grad(args):
 
 def run_density(args):
     """Density queries: Q query points x 256-point y grid against N data points
-    (one cde_density call with device inputs/outputs, CUDA-event timed)."""
+    (one cde_density call with device inputs/outputs, CUDA-event timed), at
+    the configured Q x N and at a small-Q / large-N point (Q = 100 x N = 500,000).
+    Reports pairs/s, algorithmic TFLOP/s and the algorithmic HBM bytes of the
+    call (data read once, queries and grid read, density written) per second
+    against the measured copy bandwidth."""
     import torch
     from paper_1206_5278_gb300 import cde, synth
-    x, y = synth.gmm_sine(args.dens_N, args.dens_d, seed=8)
     ctx = cde.cde_init(0)
-    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
-    xq = torch.from_numpy(synth.query_points(x, args.dens_Q, seed=9)).cuda()
-    yg = torch.from_numpy(synth.y_grid(y, 0.1, 256)).cuda()
-    f = torch.empty((args.dens_Q, 256), dtype=torch.float32, device="cuda")
-    st = torch.cuda.Stream()
-    st.wait_stream(torch.cuda.current_stream())
-    for _ in range(max(2, args.warmup)):
-        cde.cde_density(ctx, ds, 0.3, 0.1, xq, yg, f, stream=st)
-    st.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for a, b in ev:
-        a.record(st)
-        cde.cde_density(ctx, ds, 0.3, 0.1, xq, yg, f, stream=st)
-        b.record(st)
-    st.synchronize()
-    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
-    pairs = args.dens_Q * args.dens_N
+    hbm_peak = 6688.8
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, ValueError, KeyError):
+        pass
+    runs = {}
+    for Q, N in ((args.dens_Q, args.dens_N), (100, 500000)):
+        x, y = synth.gmm_sine(N, args.dens_d, seed=8)
+        ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+        xq = torch.from_numpy(synth.query_points(x, Q, seed=9)).cuda()
+        yg = torch.from_numpy(synth.y_grid(y, 0.1, 256)).cuda()
+        f = torch.empty((Q, 256), dtype=torch.float32, device="cuda")
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        for _ in range(max(2, args.warmup)):
+            cde.cde_density(ctx, ds, 0.3, 0.1, xq, yg, f, stream=st)
+        st.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in ev:
+            a.record(st)
+            cde.cde_density(ctx, ds, 0.3, 0.1, xq, yg, f, stream=st)
+            b.record(st)
+        st.synchronize()
+        ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+        pairs = Q * N
+        nbytes = N * (args.dens_d + 1) * 4 + Q * args.dens_d * 4 + 256 * 4 + Q * 256 * 4
+        runs["Q%d_N%d" % (Q, N)] = {"ms": ms, "pairs_per_s": pairs / (ms * 1e-3),
+                                    "tflops": pairs * 512 / (ms * 1e-3) / 1e12,
+                                    "hbm": {"algorithmic_bytes": nbytes, "GB_s": nbytes / (ms * 1e-3) / 1e9,
+                                            "peak_GB_s": hbm_peak,
+                                            "frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}}
+        cde.cde_destroy_dataset(ctx, ds)
+    main = runs["Q%d_N%d" % (args.dens_Q, args.dens_N)]
     _line(workload="density_Q%d_N%d_d%d_G256" % (args.dens_Q, args.dens_N, args.dens_d),
           metric="density (query, data point) pairs/s x 256-point y grid", unit="pairs/s",
-          value=pairs / (ms * 1e-3), steps=args.steps, warmup=args.warmup, ms_per_step=ms,
-          flops_per_pair=2 * 256 * 1 + 3 * args.dens_d, tflops=pairs * 512 / (ms * 1e-3) / 1e12,
+          value=main["pairs_per_s"], steps=args.steps, warmup=args.warmup, ms_per_step=main["ms"],
+          flops_per_pair=2 * 256 * 1 + 3 * args.dens_d, tflops=main["tflops"], runs=runs,
           config={"workload": "density", "Q": args.dens_Q, "N": args.dens_N, "d_x": args.dens_d, "G_y": 256})
     cde.cde_shutdown(ctx)
 

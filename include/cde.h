@@ -57,7 +57,7 @@ typedef enum {
     CDE_ENOMEM = 2,     /* memory budget or device allocation refused */
     CDE_ECUDA = 3,      /* CUDA runtime error (message has the CUDA text) */
     CDE_EBUSY = 4,      /* request queue full */
-    CDE_ETIMEOUT = 5,   /* wait ran out, or a device-side bounded wait gave up */
+    CDE_ETIMEOUT = 5,   /* cde_wait ran out before the request finished */
     CDE_ENOTFOUND = 6,  /* unknown dataset handle or ticket */
     CDE_ECANCELED = 7   /* request cancelled before it ran */
 } cde_status;
@@ -214,6 +214,16 @@ int cde_autotune(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const d
 /* Read / set the tile parameters for the shape of a G1 x G2 grid (0 = default). */
 int cde_tuning_get(cde_ctx *ctx, int G1, int G2, int *units_per_tile, int *ctas_per_sm);
 int cde_tuning_set(cde_ctx *ctx, int G1, int G2, int units_per_tile, int ctas_per_sm);
+/*
+ * Tuning cache on disk: cde_tuning_save writes all shape classes' parameters
+ * with the device's name, compute capability and SM count (atomically, via a
+ * temporary file and rename); cde_tuning_load applies a file written for the
+ * same device (CDE_EINVAL for another device or a malformed file,
+ * CDE_ENOTFOUND when it cannot be read).  cde_init loads the file named by
+ * the environment variable CDE_TUNING_CACHE when it exists and matches.
+ */
+int cde_tuning_save(cde_ctx *ctx, const char *path);
+int cde_tuning_load(cde_ctx *ctx, const char *path);
 
 /* ------------------------------------------------------------------ */
 /* Bandwidth selection as in the paper (Sec. 3.5, Sec. 4)              */

@@ -38,7 +38,7 @@ EXPORTED = [
     "cde_poll", "cde_wait", "cde_cancel", "cde_server_stats_get", "cde_server_stats_reset",
     "cde_measure_peaks", "cde_autotune", "cde_tuning_get", "cde_tuning_set",
     "cde_loo_loglik_noalloc", "cde_dataset_kernel", "cde_select_random", "cde_reference_rule",
-    "cde_cond_stats", "cde_cond_interval",
+    "cde_cond_stats", "cde_cond_interval", "cde_tuning_save", "cde_tuning_load",
 ]
 
 
@@ -133,6 +133,8 @@ def lib():
                               ctypes.c_int),
         "cde_reference_rule": ([_vp, _i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                ctypes.c_int),
+        "cde_tuning_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
+        "cde_tuning_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
         "cde_cond_stats": ([_vp, _i64, ctypes.c_double, ctypes.c_double, _vp, _vp, _i64, _vp, _vp,
                             ctypes.c_int, _vp], ctypes.c_int),
         "cde_cond_interval": ([_vp, _i64, ctypes.c_double, ctypes.c_double, _vp, _i64, ctypes.c_int,
@@ -427,6 +429,14 @@ def cde_tuning_get(ctx, G1: int, G2: int):
     u, c = ctypes.c_int(), ctypes.c_int()
     _check(lib().cde_tuning_get(ctx, int(G1), int(G2), ctypes.byref(u), ctypes.byref(c)))
     return u.value, c.value
+
+
+def cde_tuning_save(ctx, path: str):
+    _check(lib().cde_tuning_save(ctx, os.fsencode(path)))
+
+
+def cde_tuning_load(ctx, path: str):
+    _check(lib().cde_tuning_load(ctx, os.fsencode(path)))
 
 
 def cde_tuning_set(ctx, G1: int, G2: int, units_per_tile: int = 0, ctas_per_sm: int = 0):

@@ -17,8 +17,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "cde_internal.h"
@@ -416,6 +418,7 @@ using namespace cde;
 extern "C" int cde_loo_loglik_batch(cde_ctx* ctx, int n, const cde_dataset* ds, const double* const* h1,
                                     const int* G1, const double* const* h2, const int* G2,
                                     double* const* L_cond_out, double* const* L_eq3_out, void* stream) {
+    CDE_NVTX("cde_loo_loglik_batch");
     if (!ctx || n < 0 || (n > 0 && (!ds || !h1 || !G1 || !h2 || !G2)))
         return set_error(CDE_EINVAL, "cde_loo_loglik_batch: bad arguments");
     if (n == 0) return CDE_OK;
@@ -444,6 +447,7 @@ extern "C" int cde_loo_loglik_batch(cde_ctx* ctx, int n, const cde_dataset* ds, 
 
 extern "C" int cde_autotune(cde_ctx* ctx, cde_dataset ds, const double* h1, int G1, const double* h2, int G2,
                             int* units_per_tile, int* ctas_per_sm, double* best_ms) {
+    CDE_NVTX("cde_autotune");
     if (!ctx || !h1 || !h2 || G1 < 1 || G1 > 32 || G2 < 1 || G2 > 32)
         return set_error(CDE_EINVAL, "cde_autotune: bad arguments (grids of 1..32 per axis)");
     auto D = find_dataset(ctx, ds);
@@ -461,11 +465,78 @@ extern "C" int cde_tuning_get(cde_ctx* ctx, int G1, int G2, int* units_per_tile,
     return CDE_OK;
 }
 
+// Tuning cache file: a header line with the device it was tuned on, then one
+// line "a b units_per_tile ctas_per_sm" per shape class (a, b in 0..2 for
+// padded sizes 8|16|32 of G1 and G2).
+static std::string tuning_device_key(cde_ctx* ctx) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, ctx->device) != cudaSuccess) return "unknown";
+    char buf[400];
+    snprintf(buf, sizeof(buf), "%s sm_%d%d sms=%d", p.name, p.major, p.minor, p.multiProcessorCount);
+    for (char* c = buf; *c; ++c)
+        if (*c == '\n') *c = ' ';
+    return buf;
+}
+
+extern "C" int cde_tuning_save(cde_ctx* ctx, const char* path) {
+    if (!ctx || !path) return set_error(CDE_EINVAL, "cde_tuning_save: null argument");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return set_error(CDE_EINVAL, std::string("cde_tuning_save: cannot write ") + path);
+    fprintf(f, "cde-tuning 1 %s\n", tuning_device_key(ctx).c_str());
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) fprintf(f, "%d %d %d %d\n", a, b, ctx->tune_upt[a][b], ctx->tune_ctas[a][b]);
+    const bool ok = fclose(f) == 0 && rename(tmp.c_str(), path) == 0;
+    if (!ok) return set_error(CDE_EINVAL, std::string("cde_tuning_save: cannot write ") + path);
+    return CDE_OK;
+}
+
+extern "C" int cde_tuning_load(cde_ctx* ctx, const char* path) {
+    if (!ctx || !path) return set_error(CDE_EINVAL, "cde_tuning_load: null argument");
+    FILE* f = fopen(path, "r");
+    if (!f) return set_error(CDE_ENOTFOUND, std::string("cde_tuning_load: cannot read ") + path);
+    char line[512];
+    int upt[3][3], ctas[3][3], seen = 0;
+    bool ok = fgets(line, sizeof(line), f) != nullptr;
+    if (ok) {
+        std::string h(line);
+        while (!h.empty() && (h.back() == '\n' || h.back() == '\r')) h.pop_back();
+        ok = h == "cde-tuning 1 " + tuning_device_key(ctx);
+        if (!ok) {
+            fclose(f);
+            return set_error(CDE_EINVAL, "cde_tuning_load: file was tuned on another device or version");
+        }
+    }
+    int a, b, u, c;
+    while (ok && fgets(line, sizeof(line), f)) {
+        if (sscanf(line, "%d %d %d %d", &a, &b, &u, &c) != 4 || a < 0 || a > 2 || b < 0 || b > 2 || u < 0 ||
+            u > 64 || c < 0 || c > 2 || (seen & (1 << (3 * a + b)))) {
+            ok = false;
+            break;
+        }
+        upt[a][b] = u;
+        ctas[a][b] = c;
+        seen |= 1 << (3 * a + b);
+    }
+    fclose(f);
+    if (!ok || seen != 0x1ff) return set_error(CDE_EINVAL, "cde_tuning_load: malformed file");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    for (a = 0; a < 3; ++a)
+        for (b = 0; b < 3; ++b) {
+            ctx->tune_upt[a][b] = upt[a][b];
+            ctx->tune_ctas[a][b] = ctas[a][b];
+        }
+    return CDE_OK;
+}
+
 extern "C" int cde_tuning_set(cde_ctx* ctx, int G1, int G2, int units_per_tile, int ctas_per_sm) {
     if (!ctx || G1 < 1 || G1 > 32 || G2 < 1 || G2 > 32 || units_per_tile < 0 || units_per_tile > 64 ||
         ctas_per_sm < 0 || ctas_per_sm > 2)
         return set_error(CDE_EINVAL, "cde_tuning_set: bad arguments");
-    const int a = G1 <= 8 ? 0 : G1 <= 16 ? 1 : 2, b = G2 <= 8 ? 0 : G2 <= 16 ? 1 : 2;
+    // the classes the kernels read: G1 padded to 16 | 32, G2 to 8 | 16 | 32
+    const int T1 = loo_pad1(G1), T2 = loo_pad2(G2);
+    const int a = T1 <= 8 ? 0 : T1 <= 16 ? 1 : 2, b = T2 <= 8 ? 0 : T2 <= 16 ? 1 : 2;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     ctx->tune_upt[a][b] = units_per_tile;
     ctx->tune_ctas[a][b] = ctas_per_sm;

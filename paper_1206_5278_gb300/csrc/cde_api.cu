@@ -1,6 +1,7 @@
 // C ABI: context, errors, datasets and the synchronous entry points.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -114,6 +115,10 @@ int cde_init(cde_ctx** out, int device, size_t budget) {
         delete ctx;
         return cuda_error(e, "cde_init");
     }
+    // a tuning cache named by the environment is applied when it matches this device
+    if (const char* tc = getenv("CDE_TUNING_CACHE")) {
+        if (cde_tuning_load(ctx, tc) != CDE_OK) set_error(CDE_OK, "");
+    }
     *out = ctx;
     return CDE_OK;
 }
@@ -140,6 +145,7 @@ void cde_shutdown(cde_ctx* ctx) {
 
 int cde_create_dataset(cde_ctx* ctx, const float* x, const float* y, int64_t N, int d, int standardize,
                        int flags, cde_dataset* out) {
+    CDE_NVTX("cde_create_dataset");
     if (!ctx || !x || !y || !out) return set_error(CDE_EINVAL, "cde_create_dataset: null argument");
     if (N < 2) return set_error(CDE_EINVAL, "cde_create_dataset: need N >= 2");
     if (N > (int64_t)1 << 30) return set_error(CDE_EINVAL, "cde_create_dataset: N too large");
@@ -288,6 +294,7 @@ int cde_dataset_kernel(cde_ctx* ctx, cde_dataset ds, int* kernel) {
 
 int cde_loo_loglik(cde_ctx* ctx, cde_dataset ds, const double* h1, int G1, const double* h2, int G2,
                    double* Lc, double* Le, int flags, void* stream) {
+    CDE_NVTX("cde_loo_loglik");
     if (!ctx) return set_error(CDE_EINVAL, "cde_loo_loglik: null context");
     int rc = check_grid(h1, G1, "h1");
     if (rc == CDE_OK) rc = check_grid(h2, G2, "h2");
@@ -336,6 +343,7 @@ int cde_loo_loglik(cde_ctx* ctx, cde_dataset ds, const double* h1, int G1, const
 
 int cde_loo_rows(cde_ctx* ctx, cde_dataset ds, const double* h1, int G1, const double* h2, int G2,
                  const int64_t* rows, int64_t n_rows, double* ell_out, void* stream) {
+    CDE_NVTX("cde_loo_rows");
     if (!ctx || !rows || !ell_out) return set_error(CDE_EINVAL, "cde_loo_rows: null argument");
     int rc = check_grid(h1, G1, "h1");
     if (rc == CDE_OK) rc = check_grid(h2, G2, "h2");

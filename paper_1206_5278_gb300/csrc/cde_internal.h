@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cstdint>
@@ -18,6 +19,16 @@ namespace cde {
 // Thread-local error text; set_error returns the status for `return set_error(...)`.
 int set_error(int status, const std::string& msg);
 int cuda_error(cudaError_t e, const char* where);
+
+// NVTX range over an entry point (visible to profilers that inject NVTX; a
+// few nanoseconds otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define CDE_NVTX(name) ::cde::NvtxRange cde_nvtx_range_(name)
 
 #define CDE_CUDA(call)                                         \
     do {                                                       \

@@ -394,6 +394,7 @@ using namespace cde;
 
 extern "C" int cde_density(cde_ctx* ctx, cde_dataset ds, double h1, double h2, const float* xq,
                            int64_t Q, const float* ygrid, int G, float* f_out, int flags, void* stream) {
+    CDE_NVTX("cde_density");
     if (!ctx) return set_error(CDE_EINVAL, "cde_density: null context");
     if (Q < 0 || G < 1 || (Q > 0 && (!xq || !ygrid || !f_out)))
         return set_error(CDE_EINVAL, "cde_density: bad sizes or null pointers");

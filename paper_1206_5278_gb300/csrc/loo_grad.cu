@@ -534,6 +534,7 @@ using namespace cde;
 
 extern "C" int cde_loo_grad(cde_ctx* ctx, cde_dataset ds, double h1, double h2, double* out3,
                             int flags, void* stream) {
+    CDE_NVTX("cde_loo_grad");
     if (!ctx || !out3) return set_error(CDE_EINVAL, "cde_loo_grad: null argument");
     if (!std::isfinite(h1) || !std::isfinite(h2) || h1 < 1e-12 || h2 < 1e-12 || h1 > 1e12 || h2 > 1e12)
         return set_error(CDE_EINVAL, "cde_loo_grad: bandwidth must be finite in [1e-12, 1e12]");
@@ -558,6 +559,7 @@ extern "C" int cde_loo_grad(cde_ctx* ctx, cde_dataset ds, double h1, double h2, 
 
 extern "C" int cde_loo_grad_rows(cde_ctx* ctx, cde_dataset ds, double h1, double h2, double* rows_out,
                                  void* stream) {
+    CDE_NVTX("cde_loo_grad_rows");
     if (!ctx || !rows_out) return set_error(CDE_EINVAL, "cde_loo_grad_rows: null argument");
     if (!std::isfinite(h1) || !std::isfinite(h2) || h1 < 1e-12 || h2 < 1e-12 || h1 > 1e12 || h2 > 1e12)
         return set_error(CDE_EINVAL, "cde_loo_grad_rows: bandwidth must be finite in [1e-12, 1e12]");

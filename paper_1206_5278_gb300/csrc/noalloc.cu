@@ -51,6 +51,7 @@ using namespace cde;
 extern "C" int cde_loo_loglik_noalloc(cde_ctx* ctx, cde_dataset ds, const double* h1, int G1,
                                       const double* h2, int G2, double* d_L_cond, double* d_L_eq3,
                                       void* stream) {
+    CDE_NVTX("cde_loo_loglik_noalloc");
     if (!ctx || !h1 || !h2) return set_error(CDE_EINVAL, "cde_loo_loglik_noalloc: null argument");
     if (G1 < 1 || G2 < 1 || G1 > 32 || G2 > 32)
         return set_error(CDE_EINVAL,

@@ -549,6 +549,7 @@ static int check_bw(double h1, double h2, const char* who) {
 extern "C" int cde_cond_stats(cde_ctx* ctx, cde_dataset ds, double h1, double h2, const float* xq,
                               const float* yq, int64_t Q, double* mean_out, double* fat_out, int flags,
                               void* stream) {
+    CDE_NVTX("cde_cond_stats");
     if (!ctx) return set_error(CDE_EINVAL, "cde_cond_stats: null context");
     int rc = check_bw(h1, h2, "cde_cond_stats");
     if (rc != CDE_OK) return rc;
@@ -604,6 +605,7 @@ extern "C" int cde_cond_stats(cde_ctx* ctx, cde_dataset ds, double h1, double h2
 extern "C" int cde_cond_interval(cde_ctx* ctx, cde_dataset ds, double h1, double h2, const float* xq,
                                  int64_t Q, int S, double alpha, uint64_t seed, float* lo_out, float* hi_out,
                                  float* samples_out, int flags, void* stream) {
+    CDE_NVTX("cde_cond_interval");
     if (!ctx) return set_error(CDE_EINVAL, "cde_cond_interval: null context");
     int rc = check_bw(h1, h2, "cde_cond_interval");
     if (rc != CDE_OK) return rc;

@@ -61,6 +61,7 @@ static double log_rule_constant(int kernel, int d) {
 using namespace cde;
 
 extern "C" int cde_reference_rule(cde_ctx* ctx, cde_dataset ds, double* h1, double* h2) {
+    CDE_NVTX("cde_reference_rule");
     if (!ctx || !h1 || !h2) return set_error(CDE_EINVAL, "cde_reference_rule: null argument");
     auto D = find_dataset(ctx, ds);
     if (!D) return set_error(CDE_ENOTFOUND, "cde_reference_rule: unknown dataset");
@@ -95,6 +96,7 @@ extern "C" int cde_reference_rule(cde_ctx* ctx, cde_dataset ds, double* h1, doub
 extern "C" int cde_select_random(cde_ctx* ctx, cde_dataset ds, double h1_max, double h2_max, int rounds,
                                  int G1, int G2, uint64_t seed, int objective, double* best,
                                  double* h1_out, double* h2_out, double* Lc_out, double* Le_out) {
+    CDE_NVTX("cde_select_random");
     if (!ctx || !best) return set_error(CDE_EINVAL, "cde_select_random: null argument");
     if (!std::isfinite(h1_max) || !std::isfinite(h2_max) || h1_max < 1e-6 || h2_max < 1e-6 ||
         h1_max > 1e6 || h2_max > 1e6)

@@ -84,3 +84,33 @@ def test_batch_rejects_bad_grids(ctx):
     with pytest.raises(cde.CdeError):
         cde.cde_loo_loglik_batch(ctx, [ds + 77], [np.ones(3)], [np.ones(4)])
     cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_tuning_cache_roundtrip(ctx, tmp_path):
+    """cde_tuning_save / cde_tuning_load: same values back, atomic file, and a
+    file written for another device (or malformed) is refused."""
+    saved = {(g1, g2): cde.cde_tuning_get(ctx, g1, g2) for g1 in (8, 16, 32) for g2 in (8, 16, 32)}
+    try:
+        cde.cde_tuning_set(ctx, 32, 32, 5, 1)
+        cde.cde_tuning_set(ctx, 8, 16, 3, 2)
+        path = str(tmp_path / "tune.txt")
+        cde.cde_tuning_save(ctx, path)
+        cde.cde_tuning_set(ctx, 32, 32, 0, 0)
+        cde.cde_tuning_set(ctx, 8, 16, 0, 0)
+        cde.cde_tuning_load(ctx, path)
+        assert tuple(cde.cde_tuning_get(ctx, 32, 32)) == (5, 1)
+        assert tuple(cde.cde_tuning_get(ctx, 8, 16)) == (3, 2)
+        lines = open(path).read().splitlines()
+        other = tmp_path / "other.txt"
+        other.write_text("\n".join(["cde-tuning 1 some other device sm_90 sms=132"] + lines[1:]) + "\n")
+        with pytest.raises(cde.CdeError):
+            cde.cde_tuning_load(ctx, str(other))
+        bad = tmp_path / "bad.txt"
+        bad.write_text("\n".join(lines[:-1]) + "\n")
+        with pytest.raises(cde.CdeError):
+            cde.cde_tuning_load(ctx, str(bad))
+        with pytest.raises(cde.CdeError):
+            cde.cde_tuning_load(ctx, str(tmp_path / "missing.txt"))
+    finally:
+        for (g1, g2), (u, c) in saved.items():
+            cde.cde_tuning_set(ctx, g1, g2, u, c)
