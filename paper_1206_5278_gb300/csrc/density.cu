@@ -121,6 +121,8 @@ __global__ void __launch_bounds__(256) k_query_shift(const float* __restrict__ x
 
 struct DensSmem {
     float T[kDQ][kDIC + 4];     // x factor argument (dens_ufac), masked points give 0
+    uint4 Af[kDIC / 8][2][32];  // per chunk, k-step, m-tile, lane: TF32 A fragment (hi u)
+    uint4 Ax[kDIC / 8][2][32];  //   and the BF16 cross-term A fragment [hi u | lo u]
     float yis[kDIC];
     float xqs[kMaxD][kDQ];
     float xis[kMaxD][kDIC];
@@ -154,10 +156,12 @@ __device__ __forceinline__ void mma_tf32_d(float (&d)[4], const uint32_t (&a)[4]
 // Numerator tile F[32 queries][256 grid points] += U[32 x IC] W[IC x 256] on
 // the tensor cores with split operands v = hi + lo: hi*hi as TF32 m16n8k8, the
 // two cross terms together as one BF16 m16n8k16 (about 2^-17 per term),
-// A (u, M = queries) and B (w, N = grid points) fragments made in-lane with
-// exp2; warp w owns grid points [32 w, 32 w + 32).  The 32 x IC exponent
-// arguments of u are computed once per chunk into shared memory.  Each
-// 32-point chunk accumulates from zero and is added to an FP32 running total.
+// A (u, M = queries) and B (w, N = grid points) operands; warp w owns grid
+// points [32 w, 32 w + 32) and makes its B fragments in-lane with exp2.  Per chunk the 32 x IC
+// arguments of u go to shared memory, then one thread per (k-step, m-tile,
+// lane) slot turns them into the split A fragments (TF32 hi, BF16 [hi | lo])
+// that every warp loads, so each u is evaluated once per CTA.  Each 32-point
+// chunk accumulates from zero and is added to an FP32 running total.
 template <int KERN>
 __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
     extern __shared__ float4 dsm4[];
@@ -184,7 +188,13 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
         ygv[nt] = a.yg[gg < a.G ? gg : a.G - 1];
     }
     float Dt[2][4][4];
-    float bt[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    // fragment-pass role (one thread per k-step, m-tile and lane slot): its two
+    // queries' denominator partials, summed over its points of every chunk
+    const int fks = tid >> 6, fmt = (tid >> 5) & 1;
+    float bq0 = 0.f, bq1 = 0.f;
+    float2 yg2[4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) yg2[nt] = make_float2(ygv[nt], ygv[nt]);
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -211,6 +221,28 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
             else S.T[dq][ii] = (c0 + ii < i_end) ? dx2 : INFINITY;
         }
         __syncthreads();
+        // fragment pass: every x factor of the chunk once (not once per warp),
+        // split hi + lo and packed into the A fragments the MMA pass loads
+        {
+            const int pa = 8 * fks + 2 * t, pb = pa + 1, r0 = 16 * fmt + g, r1 = r0 + 8;
+            const float u0 = dens_ufac<KERN>(S.T[r0][pa], a1);   // (q, p0)
+            const float u1 = dens_ufac<KERN>(S.T[r1][pa], a1);   // (q + 8, p0)
+            const float u2 = dens_ufac<KERN>(S.T[r0][pb], a1);   // (q, p1)
+            const float u3 = dens_ufac<KERN>(S.T[r1][pb], a1);   // (q + 8, p1)
+            bq0 += u0 + u2;
+            bq1 += u1 + u3;
+            uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
+            split_tf32_d(u0, h0, l0);
+            split_tf32_d(u1, h1, l1);
+            split_tf32_d(u2, h2, l2);
+            split_tf32_d(u3, h3, l3);
+            S.Af[fks][fmt][lane] = make_uint4(h0, h1, h2, h3);
+            S.Ax[fks][fmt][lane] = make_uint4(pack_bf16x2_d(__uint_as_float(h0), __uint_as_float(h2)),
+                                              pack_bf16x2_d(__uint_as_float(h1), __uint_as_float(h3)),
+                                              pack_bf16x2_d(__uint_as_float(l0), __uint_as_float(l2)),
+                                              pack_bf16x2_d(__uint_as_float(l1), __uint_as_float(l3)));
+        }
+        __syncthreads();
         float D[2][4][4];
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
@@ -219,36 +251,35 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
 #pragma unroll
         for (int ks = 0; ks < kDIC / 8; ++ks) {
             // this lane's two points of the k-step: p0 = 8 ks + 2t, p1 = p0 + 1
-            const int pa = 8 * ks + 2 * t, pb = pa + 1;
+            const int pa = 8 * ks + 2 * t;
             uint32_t ah[2][4], ax[2][4];
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
-                const float u0 = dens_ufac<KERN>(S.T[16 * mt + g][pa], a1);       // (q, p0)
-                const float u1 = dens_ufac<KERN>(S.T[16 * mt + g + 8][pa], a1);   // (q + 8, p0)
-                const float u2 = dens_ufac<KERN>(S.T[16 * mt + g][pb], a1);       // (q, p1)
-                const float u3 = dens_ufac<KERN>(S.T[16 * mt + g + 8][pb], a1);   // (q + 8, p1)
-                bt[mt][0] += u0 + u2;
-                bt[mt][1] += u1 + u3;
-                uint32_t l0, l1, l2, l3;
-                split_tf32_d(u0, ah[mt][0], l0);
-                split_tf32_d(u1, ah[mt][1], l1);
-                split_tf32_d(u2, ah[mt][2], l2);
-                split_tf32_d(u3, ah[mt][3], l3);
-                ax[mt][0] = pack_bf16x2_d(__uint_as_float(ah[mt][0]), __uint_as_float(ah[mt][2]));
-                ax[mt][1] = pack_bf16x2_d(__uint_as_float(ah[mt][1]), __uint_as_float(ah[mt][3]));
-                ax[mt][2] = pack_bf16x2_d(__uint_as_float(l0), __uint_as_float(l2));
-                ax[mt][3] = pack_bf16x2_d(__uint_as_float(l1), __uint_as_float(l3));
+                const uint4 f = S.Af[ks][mt][lane], x = S.Ax[ks][mt][lane];
+                ah[mt][0] = f.x;
+                ah[mt][1] = f.y;
+                ah[mt][2] = f.z;
+                ah[mt][3] = f.w;
+                ax[mt][0] = x.x;
+                ax[mt][1] = x.y;
+                ax[mt][2] = x.z;
+                ax[mt][3] = x.w;
             }
-            const float ya = S.yis[pa], yb = S.yis[pb];
+            const float2 yab = *reinterpret_cast<const float2*>(&S.yis[pa]);
+            const float2 nyab = make_float2(-yab.x, -yab.y);
             uint32_t bh[4][2], bx[4][2];
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
-                const float ta = ygv[nt] - ya, tb = ygv[nt] - yb;
-                uint32_t l0, l1;
-                split_tf32_d(dens_wfac<KERN>(ta * ta, a2), bh[nt][0], l0);
-                split_tf32_d(dens_wfac<KERN>(tb * tb, a2), bh[nt][1], l1);
-                bx[nt][0] = pack_bf16x2_d(__uint_as_float(l0), __uint_as_float(l1));
-                bx[nt][1] = pack_bf16x2_d(__uint_as_float(bh[nt][0]), __uint_as_float(bh[nt][1]));
+                const float2 tt = __fadd2_rn(yg2[nt], nyab);   // (y_g - y_p0, y_g - y_p1)
+                const float2 t2 = __fmul2_rn(tt, tt);
+                const float w0 = dens_wfac<KERN>(t2.x, a2), w1 = dens_wfac<KERN>(t2.y, a2);
+                const float2 h = make_float2(__uint_as_float(__float_as_uint(w0) & 0xffffe000u),
+                                             __uint_as_float(__float_as_uint(w1) & 0xffffe000u));
+                const float2 l = __ffma2_rn(h, make_float2(-1.f, -1.f), make_float2(w0, w1));  // exact
+                bh[nt][0] = __float_as_uint(h.x);
+                bh[nt][1] = __float_as_uint(h.y);
+                bx[nt][0] = pack_bf16x2_d(l.x, l.y);
+                bx[nt][1] = pack_bf16x2_d(h.x, h.y);
             }
             // hi*hi on TF32; both cross terms in one BF16 k16 MMA
 #pragma unroll
@@ -267,16 +298,20 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) Dt[mt][nt][q] += D[mt][nt][q];
     }
-    // denominators: every warp holds the same u sums; warp 0 reduces over t
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float v = bt[mt][h];
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            v += __shfl_xor_sync(0xffffffffu, v, 2);
-            if (warp == 0 && t == 0) S.dens[16 * mt + g + 8 * h] = v;
-        }
+    // denominators: a query's partials sit in the 4 lanes (t) of 4 warps (k-steps)
+    // of its m-tile; sum t by shuffles, then the k-steps in order
+    bq0 += __shfl_xor_sync(0xffffffffu, bq0, 1);
+    bq0 += __shfl_xor_sync(0xffffffffu, bq0, 2);
+    bq1 += __shfl_xor_sync(0xffffffffu, bq1, 1);
+    bq1 += __shfl_xor_sync(0xffffffffu, bq1, 2);
+    __syncthreads();                      // the last chunk's fragments are no longer read
+    float* red = reinterpret_cast<float*>(&S.Af[0][0][0]);   // [k-step][query]
+    if (t == 0) {
+        red[fks * kDQ + 16 * fmt + g] = bq0;
+        red[fks * kDQ + 16 * fmt + g + 8] = bq1;
+    }
+    __syncthreads();
+    if (tid < kDQ) S.dens[tid] = ((red[tid] + red[kDQ + tid]) + red[2 * kDQ + tid]) + red[3 * kDQ + tid];
     __syncthreads();
     float* num = a.num + s * a.Q * a.G;
 #pragma unroll
