@@ -114,3 +114,27 @@ def test_tuning_cache_roundtrip(ctx, tmp_path):
     finally:
         for (g1, g2), (u, c) in saved.items():
             cde.cde_tuning_set(ctx, g1, g2, u, c)
+
+
+def test_tuning_cache_applied_at_init(ctx, tmp_path):
+    """cde_init loads the file named by CDE_TUNING_CACHE (fresh process)."""
+    import os
+    import subprocess
+    import sys
+    saved = cde.cde_tuning_get(ctx, 32, 32)
+    path = str(tmp_path / "tune.txt")
+    try:
+        cde.cde_tuning_set(ctx, 32, 32, 6, 1)
+        cde.cde_tuning_save(ctx, path)
+    finally:
+        cde.cde_tuning_set(ctx, 32, 32, *saved)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1206_5278_gb300 import cde\n"
+            "c = cde.cde_init(0)\n"
+            "print(*cde.cde_tuning_get(c, 32, 32))\n"
+            "cde.cde_shutdown(c)\n") % root
+    env = dict(os.environ, CDE_TUNING_CACHE=path)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.split() == ["6", "1"]
