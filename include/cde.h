@@ -108,6 +108,16 @@ int cde_destroy_dataset(cde_ctx *ctx, cde_dataset ds);
 int cde_dataset_info(cde_ctx *ctx, cde_dataset ds, int64_t *N, int *d_x, double *mean,
                      double *sd);
 
+/*
+ * Device index checks of a checked build (libcde_checked.so, compiled with
+ * -DCDE_CHECKS; the closed sanitizers' stand-in): *enabled = 1 there, and
+ * *code receives the first failed check's code since the last call (0: none)
+ * and clears it -- a failed check redirects its access to index 0 instead of
+ * faulting.  In the normal library *enabled = 0 and *code = 0.  Waits for the
+ * device to be idle.  enabled may be NULL.
+ */
+int cde_check_status(cde_ctx *ctx, unsigned int *code, int *enabled);
+
 /* Kernel family of a dataset: *kernel = CDE_KERNEL_GAUSS or CDE_KERNEL_EPAN. */
 int cde_dataset_kernel(cde_ctx *ctx, cde_dataset ds, int *kernel);
 

@@ -17,6 +17,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcde.so")
+# checked build: device index checks (-DCDE_CHECKS), its own objects and library
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libcde_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -40,20 +43,24 @@ def _headers():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def build(verbose: bool = False, jobs: int = 0) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, jobs: int = 0, checks: bool = False) -> str:
+    """Compile and link libcde.so (checks=True: libcde_checked.so with the
+    device index checks of cde_check_status)."""
+    bdir, lib_out = (BUILD_CHECKED, LIB_CHECKED) if checks else (BUILD, LIB)
+    flags = NVCC_FLAGS + (["-DCDE_CHECKS"] if checks else [])
+    os.makedirs(bdir, exist_ok=True)
     srcs = _sources()
     hdr_t = max((os.path.getmtime(h) for h in _headers()), default=0.0)
     nvcc = _nvcc()
 
     def obj_of(s):
-        return os.path.join(BUILD, os.path.basename(s) + ".o")
+        return os.path.join(bdir, os.path.basename(s) + ".o")
 
     def compile_one(s):
         o = obj_of(s)
         if os.path.exists(o) and os.path.getmtime(o) >= max(os.path.getmtime(s), hdr_t):
             return o, ""
-        cmd = [nvcc] + NVCC_FLAGS + ["-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc] + flags + ["-c", s, "-o", o + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (s, r.stdout, r.stderr))
@@ -69,14 +76,14 @@ def build(verbose: bool = False, jobs: int = 0) -> str:
             if log:
                 sys.stderr.write(log)
     newest = max(os.path.getmtime(o) for o in objs)
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        tmp = LIB + ".tmp.%d" % os.getpid()
+    if not os.path.exists(lib_out) or os.path.getmtime(lib_out) < newest:
+        tmp = lib_out + ".tmp.%d" % os.getpid()
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_out)
+    return lib_out
 
 
 if __name__ == "__main__":

@@ -15,7 +15,10 @@ from typing import Optional, Sequence, Tuple
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libcde.so")
+# CDE_LIBRARY=checked selects the checked build (device index checks, see
+# cde_check_status); the default is the normal library
+LIB_PATH = os.path.join(HERE, "libcde_checked.so" if os.environ.get("CDE_LIBRARY") == "checked"
+                        else "libcde.so")
 
 CDE_OK, CDE_EINVAL, CDE_ENOMEM, CDE_ECUDA, CDE_EBUSY, CDE_ETIMEOUT, CDE_ENOTFOUND, CDE_ECANCELED = range(8)
 CDE_OUT_DEVICE, CDE_IN_DEVICE, CDE_KERNEL_EPANECHNIKOV = 1, 2, 4
@@ -38,7 +41,7 @@ EXPORTED = [
     "cde_poll", "cde_wait", "cde_cancel", "cde_server_stats_get", "cde_server_stats_reset",
     "cde_measure_peaks", "cde_autotune", "cde_tuning_get", "cde_tuning_set",
     "cde_loo_loglik_noalloc", "cde_dataset_kernel", "cde_select_random", "cde_reference_rule",
-    "cde_cond_stats", "cde_cond_interval", "cde_tuning_save", "cde_tuning_load",
+    "cde_cond_stats", "cde_cond_interval", "cde_tuning_save", "cde_tuning_load", "cde_check_status",
 ]
 
 
@@ -134,6 +137,7 @@ def lib():
         "cde_reference_rule": ([_vp, _i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                ctypes.c_int),
         "cde_tuning_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
+        "cde_check_status": ([_vp, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cde_tuning_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
         "cde_cond_stats": ([_vp, _i64, ctypes.c_double, ctypes.c_double, _vp, _vp, _i64, _vp, _vp,
                             ctypes.c_int, _vp], ctypes.c_int),
@@ -429,6 +433,14 @@ def cde_tuning_get(ctx, G1: int, G2: int):
     u, c = ctypes.c_int(), ctypes.c_int()
     _check(lib().cde_tuning_get(ctx, int(G1), int(G2), ctypes.byref(u), ctypes.byref(c)))
     return u.value, c.value
+
+
+def cde_check_status(ctx):
+    """(code, enabled): the first failed device index check since the last
+    call (0: none) in a checked build; enabled = False in the normal library."""
+    c, e = ctypes.c_uint(), ctypes.c_int()
+    _check(lib().cde_check_status(ctx, ctypes.byref(c), ctypes.byref(e)))
+    return c.value, bool(e.value)
 
 
 def cde_tuning_save(ctx, path: str):

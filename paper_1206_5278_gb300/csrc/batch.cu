@@ -411,6 +411,10 @@ int autotune_shape(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, con
     return CDE_OK;
 }
 
+#ifdef CDE_CHECKS
+CDE_CHECK_READER(check_status_batch)
+#endif
+
 }  // namespace cde
 
 using namespace cde;

@@ -78,6 +78,16 @@ int workspace_reserve(cde_ctx* ctx, size_t dev, size_t host) {
 }
 }  // namespace cde
 
+#ifdef CDE_CHECKS
+namespace cde {
+int check_status_loo(unsigned int*);
+int check_status_batch(unsigned int*);
+int check_status_density(unsigned int*);
+int check_status_products(unsigned int*);
+int check_status_grad(unsigned int*);
+}  // namespace cde
+#endif
+
 using namespace cde;
 
 extern "C" {
@@ -281,6 +291,28 @@ int cde_dataset_info(cde_ctx* ctx, cde_dataset ds, int64_t* N, int* d, double* m
         if (mean) mean[c] = D->mean[c];
         if (sd) sd[c] = D->sd[c];
     }
+    return CDE_OK;
+}
+
+int cde_check_status(cde_ctx* ctx, unsigned int* code, int* enabled) {
+    if (!ctx || !code) return set_error(CDE_EINVAL, "cde_check_status: null argument");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    *code = 0;
+#ifdef CDE_CHECKS
+    if (enabled) *enabled = 1;
+    CDE_CUDA(cudaDeviceSynchronize());
+    int (*readers[])(unsigned int*) = {check_status_loo, check_status_batch, check_status_density,
+                                       check_status_products, check_status_grad};
+    for (auto rd : readers) {
+        unsigned int c = 0;
+        const int rc = rd(&c);
+        if (rc != CDE_OK) return rc;
+        if (!*code && c) *code = c;
+    }
+#else
+    if (enabled) *enabled = 0;
+#endif
     return CDE_OK;
 }
 

@@ -30,6 +30,37 @@ struct NvtxRange {
 };
 #define CDE_NVTX(name) ::cde::NvtxRange cde_nvtx_range_(name)
 
+// Checked builds (compiled with -DCDE_CHECKS: libcde_checked.so): CDE_CK(i, n,
+// code) tests 0 <= i < n, records the first failing code in this translation
+// unit's g_cde_check and returns 0 instead (the access stays inside the
+// buffer; nothing traps).  cde_check_status reads and clears the codes of all
+// translation units.  Normal builds: CDE_CK(i, n, code) is i.
+#if defined(CDE_CHECKS) && defined(__CUDACC__)
+static __device__ unsigned int g_cde_check;
+__device__ __forceinline__ int64_t cde_ck(int64_t i, int64_t n, unsigned int code) {
+    if (i < 0 || i >= n) {
+        atomicCAS(&g_cde_check, 0u, code);
+        return 0;
+    }
+    return i;
+}
+#define CDE_CK(i, n, code) ::cde::cde_ck((int64_t)(i), (int64_t)(n), (code))
+// read and clear this translation unit's code (host side)
+#define CDE_CHECK_READER(name)                                                   \
+    int name(unsigned int* code) {                                               \
+        unsigned int v = 0;                                                      \
+        CDE_CUDA(cudaMemcpyFromSymbol(&v, g_cde_check, sizeof(v)));              \
+        if (v) {                                                                 \
+            const unsigned int z = 0;                                            \
+            CDE_CUDA(cudaMemcpyToSymbol(g_cde_check, &z, sizeof(z)));            \
+        }                                                                        \
+        *code = v;                                                               \
+        return CDE_OK;                                                           \
+    }
+#else
+#define CDE_CK(i, n, code) (i)
+#endif
+
 #define CDE_CUDA(call)                                         \
     do {                                                       \
         cudaError_t _e = (call);                               \

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
         __syncthreads();
         for (int e = tid; e < (d + 1) * kDIC; e += 256) {
             const int c = e / kDIC, ii = e % kDIC;
-            const int64_t i = c0 + ii;  // < Np
+            const int64_t i = CDE_CK(c0 + ii, a.Np, 201);  // < Np
             if (c < d) S.xis[c][ii] = a.xs[(int64_t)c * a.Np + i];
             else S.yis[ii] = a.y[i];
         }
@@ -422,6 +422,10 @@ int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const 
     cudaFreeAsync(den, st);
     return CDE_OK;
 }
+
+#ifdef CDE_CHECKS
+CDE_CHECK_READER(check_status_density)
+#endif
 
 }  // namespace cde
 

@@ -221,7 +221,7 @@ __device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, f
         float dxs[FB], dys[FB];
 #pragma unroll
         for (int f = 0; f < FB; ++f) {
-            const int is = fbi[f];
+            const int is = (int)CDE_CK(fbi[f], N, 108);
             float t2 = 0.f;
             for (int cc = 0; cc < d; ++cc) {
                 const float t = xjr[cc] - a.xs[(int64_t)cc * Np + is];
@@ -317,7 +317,7 @@ __device__ __forceinline__ void loo_unit_epilogue(const LooArgs& a, const Coef& 
         //      the unit, in row order) and adds them to the tile partial ----
         {
             const bool first = (u == u_begin);
-            double* part = a.part + (int64_t)tile * 2 * GG;
+            double* part = a.part + CDE_CK(tile, a.n_tiles, 106) * 2 * GG;
             constexpr int NOWN = GG >= 256 ? GG / 256 : 1;
 #pragma unroll
             for (int s = 0; s < NOWN; ++s) {
@@ -339,7 +339,7 @@ __device__ __forceinline__ void loo_unit_epilogue(const LooArgs& a, const Coef& 
                     sc += ell;
                     se += lnA;
                     if (a.ell_rows && k < a.G1r && l < a.G2r) {
-                        const int64_t r = (int64_t)u * JW + jl;
+                        const int64_t r = CDE_CK((int64_t)u * JW + jl, a.n_rows, 107);
                         a.ell_rows[r * a.ell_ld_row + (int64_t)k * a.ell_ld_k + l] = ell;
                     }
                 }

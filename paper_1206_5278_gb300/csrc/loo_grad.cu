@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
     const float a1 = g.a1, a2 = g.a2;
     for (int64_t t0 = i0; t0 < i1; t0 += kGradThreads) {
         __syncthreads();
-        const int64_t it = t0 + tid;  // < Np: i_per_split and Np are multiples of 128
+        const int64_t it = CDE_CK(t0 + tid, g.Np, 401);  // < Np: i_per_split and Np are multiples of 128
 #pragma unroll
         for (int c = 0; c < DREG; ++c) xt[tid][c] = c < d ? g.xs[(int64_t)c * g.Np + it] : 0.f;
         yt[tid] = g.y[it];
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
         __syncthreads();
         for (int e = tid; e < DK * kGMTile; e += kGMWarps * 32) {
             const int c = e / kGMTile, p = e - c * kGMTile;
-            const float v = c < d ? g.xs[(int64_t)c * Np + t0 + p] : 0.f;  // t0 + p < Np
+            const float v = c < d ? g.xs[(int64_t)c * Np + CDE_CK(t0 + p, Np, 402)] : 0.f;  // t0 + p < Np
             uint32_t hv, lv;
             split_tf32_g(v, hv, lv);
             xh[p * RS + c] = hv;
@@ -350,7 +350,7 @@ __global__ void k_grad_rows(const float* __restrict__ part, int n_split, int64_t
         g2 = live ? SAy / SA - 1.0 : 0.0;
     } else {
         if (!(SA >= 0x1p-40)) {
-            fb_rows[atomicAdd(fb_count, 1)] = (int)j;
+            fb_rows[CDE_CK(atomicAdd(fb_count, 1), N, 404)] = (int)j;
             return;
         }
         ell = log(SA) - log(SB) - LN2 * (double)a2f * (double)my[j] - (LNS2PI + log(h2));
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(kFbThreads) k_grad_fallback(const GradArgs g, 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = *fb_count;
     for (int r = blockIdx.x; r < n; r += gridDim.x) {
-        const int j = fb_rows[r];
+        const int j = (int)CDE_CK(fb_rows[r], g.N, 403);
         __syncthreads();
         for (int c = tid; c < g.d; c += kFbThreads) xj_s[c] = g.xs[(int64_t)c * g.Np + j];
         __syncthreads();
@@ -527,6 +527,10 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     if (!d_rowv_ext) CDE_CUDA(cudaFreeAsync(rowv, st));
     return CDE_OK;
 }
+
+#ifdef CDE_CHECKS
+CDE_CHECK_READER(check_status_grad)
+#endif
 
 }  // namespace cde
 

@@ -347,4 +347,8 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
     return CDE_OK;
 }
 
+#ifdef CDE_CHECKS
+CDE_CHECK_READER(check_status_loo)
+#endif
+
 }  // namespace cde

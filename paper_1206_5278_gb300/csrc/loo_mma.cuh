@@ -139,7 +139,7 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
             const int64_t r = (int64_t)u * JW + tid;
             const bool v = r < a.n_rows;
             const int64_t r0 = v ? r : 0;
-            const int64_t j = a.rows ? a.rows[r0] : r0;
+            const int64_t j = CDE_CK(a.rows ? a.rows[CDE_CK(r0, a.n_rows, 101)] : r0, a.N, 102);
             ji_s[tid] = j;
             vr_s[tid] = v;
             yj_s[tid] = a.y[j];
@@ -171,7 +171,7 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
         float xin[8], yin = 0.f;
         int64_t ch = warp;
         if (ch < n_chunks) {
-            const int64_t i = ch * IC + lane;  // < Np
+            const int64_t i = CDE_CK(ch * IC + lane, Np, 103);  // < Np
 #pragma unroll
             for (int c = 0; c < 8; ++c) xin[c] = c < d ? a.xs[(int64_t)c * Np + i] : 0.f;
             yin = a.y[i];
@@ -191,7 +191,7 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                         dx2 = fmaf(q, q, dx2);
                     }
                 for (int c = 8; c < d; ++c) {
-                    const float q = xjr[c] - a.xs[(int64_t)c * Np + i];
+                    const float q = xjr[c] - a.xs[(int64_t)c * Np + CDE_CK(i, Np, 104)];
                     dx2 = fmaf(q, q, dx2);
                 }
                 const float dy = yj_s[r] - yin;
@@ -204,7 +204,7 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                 tt[r * 3 * IC + 2 * IC + lane] = t2;
             }
             if (ch + C::kWarps < n_chunks) {
-                const int64_t i2 = (ch + C::kWarps) * IC + lane;
+                const int64_t i2 = CDE_CK((ch + C::kWarps) * IC + lane, Np, 105);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) xin[c] = c < d ? a.xs[(int64_t)c * Np + i2] : 0.f;
                 yin = a.y[i2];

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kCSThreads) k_cond_stats(const StatArgs a) {
     }
     for (int64_t t0 = i0; t0 < i1; t0 += kCSThreads) {
         __syncthreads();
-        const int64_t it = t0 + tid;  // < Np: splits and Np are multiples of 128
+        const int64_t it = CDE_CK(t0 + tid, a.Np, 301);  // < Np: splits and Np are multiples of 128
 #pragma unroll
         for (int c = 0; c < DREG; ++c) xt[tid][c] = c < d ? a.xs[(int64_t)c * a.Np + it] : 0.f;
         yt[tid] = a.y[it];
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kSmpThreads) k_cond_sample(const SampleArgs a)
         if (s < a.S) {
             const float V = uniform24(a.seed, 2 * ((uint64_t)q * a.S + s) + 1);
             const float e = KERN == 0 ? normcdfinvf(V) : 2.f * sinf(asinf(2.f * V - 1.f) * (1.f / 3.f));
-            v = a.y[S.idx[s]] + a.h2 * e;
+            v = a.y[CDE_CK(S.idx[s], a.N, 302)] + a.h2 * e;
         }
         S.val[s] = v;
     }
@@ -535,6 +535,10 @@ static int cond_interval_enqueue(cde_ctx* ctx, const Dataset& D, double h1, doub
     cudaFreeAsync(mq, st);
     return CDE_OK;
 }
+
+#ifdef CDE_CHECKS
+CDE_CHECK_READER(check_status_products)
+#endif
 
 }  // namespace cde
 
