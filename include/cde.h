@@ -129,7 +129,8 @@ int cde_dataset_kernel(cde_ctx *ctx, cde_dataset ds, int *kernel);
  *   NULL.  Host memory unless flags has CDE_OUT_DEVICE.
  * Numerics: pair sums in FP32 with per-row shifts (exp2 on the SFU),
  * exact joint-shift recomputation of any cell whose shifted numerator falls
- * below 2^-40, log-ratio and the sum over j in FP64 in a fixed order (the
+ * below 2^(ceil(log2 N) - 91) (so that terms lost to the FP32 range stay
+ * below 2^-24 of it), log-ratio and the sum over j in FP64 in a fixed order (the
  * result is bitwise reproducible).  Epanechnikov datasets: the kernel
  * profile (1 - t^2/h^2)_+ by one saturating FP32 FMA per factor, no shifts,
  * and -inf scores where a sum is zero (see the notation above).

@@ -18,9 +18,11 @@
 // removes the shifts and the kernel constants in FP64:
 //   ell_j = ln2 (log2 At - log2 Bt - a2_l m_y,j) - ln(sqrt(2 pi) h2_l)
 //   ln A_j = ln2 (log2 At - a1_k m_x,j - a2_l m_y,j) - d ln(sqrt(2pi) h1_k) - ln(sqrt(2pi) h2_l)
-// A cell whose shifted numerator At falls below 2^-40 (the x-nearest and the
-// y-nearest neighbours differ and both factors are small) is recomputed
-// exactly with a joint shift anchored at argmin_i [a1 (dx2-m_x) + a2 (dy2-m_y)].
+// A cell whose shifted numerator At falls below 2^(ceil(log2 N) - 91) (the
+// x-nearest and the y-nearest neighbours differ and both factors are small;
+// below it the terms that lost precision to the FP32 range could matter) is
+// recomputed exactly with a joint shift anchored at
+// argmin_i [a1 (dx2-m_x) + a2 (dy2-m_y)].
 //
 // Work decomposition: a CTA of 8 warps owns a "unit" of JW = 1024/(G1 G2)
 // rows (G1 padded to 16 or 32, G2 to 8, 16 or 32); the 8 warps split the i
@@ -245,7 +247,15 @@ void fill_loo_args(LooArgs& a, const Dataset& D, const double* h1, int g1, const
         (void)T1; (void)T2;
         return;
     }
-    a.thresh = 0x1p-40f;
+    // Recompute a cell exactly when its shifted numerator At is below
+    // 2^(ceil(log2 N) - 91).  A term below 2^-115 loses its cross terms (their
+    // lo factors leave the normal range) and one below 2^-126 flushes; N such
+    // terms are at most N 2^-115 = 2^-24 of this threshold.
+    {
+        int lg = 0;
+        while (((int64_t)1 << lg) < D.N) ++lg;
+        a.thresh = ldexpf(1.f, lg - 91);
+    }
     const double L2E = 1.4426950408889634074;      // log2(e)
     const double LNS2PI = 0.91893853320467274178;  // ln sqrt(2 pi)
     for (int k = 0; k < 32; ++k) {

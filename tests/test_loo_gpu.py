@@ -103,6 +103,35 @@ def test_small_bandwidth_corner_uses_exact_fallback(ctx):
     cde.cde_destroy_dataset(ctx, ds)
 
 
+def test_cells_on_both_sides_of_the_recompute_threshold(ctx):
+    """Rows whose shifted numerator At = sum_i 2^{-a1(dx2 - m_x) - a2(dy2 - m_y)}
+    lies between the recompute threshold 2^(ceil(log2 N) - 91) = 2^-81 (N = 600)
+    and 2^-41 (main path), and below it (exact recomputation) -- counted here in
+    FP64 -- agree with the oracle row by row."""
+    w = synth.tiny_workload(N=600)
+    x, y = w.x.astype(np.float64)[:, 0], w.y.astype(np.float64)
+    h1, h2 = np.array([0.2, 0.3]), np.array([0.05, 0.1])
+    l2e = math.log2(math.e)
+    mid = low = 0
+    for a in h1:
+        for b in h2:
+            for j in range(600):
+                dx2, dy2 = (x - x[j]) ** 2, (y - y[j]) ** 2
+                dx2[j] = dy2[j] = np.inf
+                e = l2e / (2 * a * a) * (dx2 - dx2.min()) + l2e / (2 * b * b) * (dy2 - dy2.min())
+                l2 = -e.min() + np.log2(np.exp2(-(e - e.min())).sum())
+                mid += -81 <= l2 < -41
+                low += l2 < -81
+    assert mid >= 100 and low >= 100
+    ds = cde.cde_create_dataset(ctx, w.x, w.y)
+    g = cde.cde_loo_rows(ctx, ds, h1, h2, np.arange(600))
+    ref, _ = oracle.loo_rows(w.x, w.y, h1, h2)
+    np.testing.assert_allclose(g, ref, rtol=2e-5, atol=2e-5)
+    Lc, Le = cde.cde_loo_loglik(ctx, ds, h1, h2)
+    _check_grid(Lc, Le, w.x, w.y, h1, h2)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
 def test_standardisation_matches_oracle(ctx):
     x, y = synth.gmm_sine(3000, 5, seed=7)
     x = x * np.array([1.0, 10.0, 0.1, 3.0, 100.0], dtype=np.float32) + 5.0
