@@ -176,8 +176,20 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
             for (int c = 0; c < 8; ++c) xin[c] = c < d ? a.xs[(int64_t)c * Np + i] : 0.f;
             yin = a.y[i];
         }
+        // one row per unit (G1 G2 = 1024): its constants stay in registers for
+        // the whole chunk loop instead of being re-read from shared memory
+        float yr1 = 0.f, mxr1 = 0.f, myr1 = 0.f;
+        int jr1 = 0;
+        if constexpr (JW == 1) {
+            yr1 = yj_s[0];
+            mxr1 = mx_s[0];
+            myr1 = my_s[0];
+            jr1 = (int)ji_s[0];
+        }
+        const int N32 = (int)N;  // N < 2^31
         for (; ch < n_chunks; ch += C::kWarps) {
             const int64_t i = ch * IC + lane;
+            const int i32 = (int)i;
             // ---- distance pass: lane = point; masked pairs get t1 = -inf ----
             __syncwarp();
 #pragma unroll
@@ -194,12 +206,13 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                     const float q = xjr[c] - a.xs[(int64_t)c * Np + CDE_CK(i, Np, 104)];
                     dx2 = fmaf(q, q, dx2);
                 }
-                const float dy = yj_s[r] - yin;
-                const bool ok = i < N && i != ji_s[r];
+                const float dy = (JW == 1 ? yr1 : yj_s[r]) - yin;
+                const bool ok = i32 < N32 && i32 != (JW == 1 ? jr1 : (int)ji_s[r]);
                 // Gaussian: shifted exponents (masked pairs -inf); Epanechnikov:
                 // squared distances (masked pairs +inf)
-                const float t1 = KERN == 0 ? (ok ? mx_s[r] - dx2 : -INFINITY) : (ok ? dx2 : INFINITY);
-                const float t2 = KERN == 0 ? my_s[r] - dy * dy : dy * dy;
+                const float mxv = JW == 1 ? mxr1 : mx_s[r], myv = JW == 1 ? myr1 : my_s[r];
+                const float t1 = KERN == 0 ? (ok ? mxv - dx2 : -INFINITY) : (ok ? dx2 : INFINITY);
+                const float t2 = KERN == 0 ? myv - dy * dy : dy * dy;
                 reinterpret_cast<float2*>(tt + r * 3 * IC)[lane] = make_float2(t1, t1);
                 tt[r * 3 * IC + 2 * IC + lane] = t2;
             }
