@@ -213,7 +213,7 @@ def run_ours(args, w):
     peak_max = 2 * lanes * sms * 2070e6 / 1e12
     # DRAM bytes of one k_loo_mma<32,32> launch at N=50,000 from an ncu capture
     # (profiles/k_loo_mma_32x32_N50000.md); not measured for other sizes.
-    traffic = 53105152 if (w.N == 50000 and G1 == 32 and G2 == 32 and args.kernel == "gauss") else None
+    traffic = 53256960 if (w.N == 50000 and G1 == 32 and G2 == 32 and args.kernel == "gauss") else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
             "frac": achieved / peak_max, "traffic": traffic,
             "peak_basis": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x 2070 MHz (max clock)" % sms}
