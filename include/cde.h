@@ -118,6 +118,13 @@ int cde_dataset_info(cde_ctx *ctx, cde_dataset ds, int64_t *N, int *d_x, double 
  */
 int cde_check_status(cde_ctx *ctx, unsigned int *code, int *enabled);
 
+/* Per-row nearest squared distances of a Gaussian dataset, the exp2 shifts:
+ * nn_x2[j] = min_{i != j} |x_j - x_i|^2 (stored, possibly standardised x; FP32,
+ * accumulated dimension by dimension with fused multiply-adds as in every pair
+ * kernel), nn_y2[j] = min_{i != j} (y_j - y_i)^2.  Host arrays of N floats;
+ * either may be NULL.  Zeros for Epanechnikov datasets (no shift). */
+int cde_dataset_nn(cde_ctx *ctx, cde_dataset ds, float *nn_x2, float *nn_y2);
+
 /* Kernel family of a dataset: *kernel = CDE_KERNEL_GAUSS or CDE_KERNEL_EPAN. */
 int cde_dataset_kernel(cde_ctx *ctx, cde_dataset ds, int *kernel);
 

@@ -42,6 +42,7 @@ EXPORTED = [
     "cde_measure_peaks", "cde_autotune", "cde_tuning_get", "cde_tuning_set",
     "cde_loo_loglik_noalloc", "cde_dataset_kernel", "cde_select_random", "cde_reference_rule",
     "cde_cond_stats", "cde_cond_interval", "cde_tuning_save", "cde_tuning_load", "cde_check_status",
+    "cde_dataset_nn",
 ]
 
 
@@ -131,6 +132,7 @@ def lib():
         "cde_loo_loglik_noalloc": ([_vp, _i64, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp],
                                    ctypes.c_int),
         "cde_dataset_kernel": ([_vp, _i64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cde_dataset_nn": ([_vp, _i64, _vp, _vp], ctypes.c_int),
         "cde_select_random": ([_vp, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, ctypes.c_uint64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
                               ctypes.c_int),
@@ -293,6 +295,15 @@ def cde_reference_rule(ctx, ds: int):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib().cde_reference_rule(ctx, int(ds), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def cde_dataset_nn(ctx, ds: int):
+    """(nearest squared x distance, nearest squared y distance) per row."""
+    N, _, _, _ = cde_dataset_info(ctx, ds)
+    a = np.empty(N, np.float32)
+    b = np.empty(N, np.float32)
+    _check(lib().cde_dataset_nn(ctx, int(ds), _ptr(a), _ptr(b)))
+    return a, b
 
 
 def cde_dataset_kernel(ctx, ds: int) -> str:

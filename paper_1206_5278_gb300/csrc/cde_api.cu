@@ -231,7 +231,7 @@ int cde_create_dataset(cde_ctx* ctx, const float* x, const float* y, int64_t N, 
                 return fail(set_error(CDE_EINVAL, "cde_create_dataset: zero spread in a dimension"));
     }
     if (D->kernel == CDE_KERNEL_GAUSS) {
-        rc = nn_shift_enqueue(*D, st);
+        rc = nn_shift_enqueue(*D, st, ctx->sm_count);
         if (rc != CDE_OK) return fail(rc);
     } else {
         e = cudaMemsetAsync(D->mx, 0, (size_t)N * 4, st);
@@ -313,6 +313,18 @@ int cde_check_status(cde_ctx* ctx, unsigned int* code, int* enabled) {
 #else
     if (enabled) *enabled = 0;
 #endif
+    return CDE_OK;
+}
+
+int cde_dataset_nn(cde_ctx* ctx, cde_dataset ds, float* nn_x2, float* nn_y2) {
+    if (!ctx || (!nn_x2 && !nn_y2)) return set_error(CDE_EINVAL, "cde_dataset_nn: null argument");
+    auto D = find_dataset(ctx, ds);
+    if (!D) return set_error(CDE_ENOTFOUND, "cde_dataset_nn: unknown dataset");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    if (nn_x2) CDE_CUDA(cudaMemcpyAsync(nn_x2, D->mx, (size_t)D->N * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    if (nn_y2) CDE_CUDA(cudaMemcpyAsync(nn_y2, D->my, (size_t)D->N * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CDE_CUDA(cudaStreamSynchronize(ctx->stream));
     return CDE_OK;
 }
 

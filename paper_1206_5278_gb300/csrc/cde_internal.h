@@ -143,7 +143,7 @@ constexpr size_t kWorkspaceMax = (size_t)64 << 20;
 int workspace_reserve(cde_ctx* ctx, size_t dev, size_t host);
 
 // Nearest squared distances per row (cached at dataset creation).
-int nn_shift_enqueue(const Dataset& D, cudaStream_t st);
+int nn_shift_enqueue(const Dataset& D, cudaStream_t st, int sm_count);
 
 // Standardise / pack raw row-major x into the SoA layout (device input).
 int pack_enqueue(Dataset& D, const float* d_x_rowmajor, const float* d_y, cudaStream_t st,

@@ -155,7 +155,104 @@ __global__ void __launch_bounds__(256) k_nn_shift(const float* __restrict__ xs,
     }
 }
 
-int nn_shift_enqueue(const Dataset& D, cudaStream_t st) {
+// d <= 8: four rows per thread, point-major shared tiles (128-bit loads), the
+// data range split over gridDim.y; split minima merge with an integer
+// atomicMin on the float bits (exact and order-free: squared distances are
+// non-negative, so their bit patterns order like the values).  The distance
+// is accumulated in the same order (dimension 0 first, one fmaf per
+// dimension; padding dimensions add exactly 0) as in every pair kernel.
+constexpr int kNnThreads = 128, kNnJB = 4;
+
+template <int DREG>
+__global__ void __launch_bounds__(kNnThreads) k_nn_shift_split(const float* __restrict__ xs,
+                                                               const float* __restrict__ y, int64_t N,
+                                                               int64_t Np, int d, int64_t i_per_split,
+                                                               unsigned int* __restrict__ mx_bits,
+                                                               unsigned int* __restrict__ my_bits) {
+    __shared__ __align__(16) float xt[kNnThreads][DREG];
+    __shared__ float yt[kNnThreads];
+    const int tid = threadIdx.x;
+    const int64_t jbase = (int64_t)blockIdx.x * kNnThreads * kNnJB + tid;
+    const int64_t i0 = (int64_t)blockIdx.y * i_per_split;
+    const int64_t i1 = min(N, i0 + i_per_split);
+    float xj[kNnJB][DREG], yj[kNnJB], bx[kNnJB], by[kNnJB];
+    int jj[kNnJB];
+#pragma unroll
+    for (int b = 0; b < kNnJB; ++b) {
+        const int64_t j = jbase + (int64_t)b * kNnThreads;
+        const int64_t jc = j < N ? j : 0;
+        jj[b] = (int)j;
+#pragma unroll
+        for (int c = 0; c < DREG; ++c) xj[b][c] = c < d ? xs[(int64_t)c * Np + jc] : 0.f;
+        yj[b] = y[jc];
+        bx[b] = by[b] = INFINITY;
+    }
+    for (int64_t t0 = i0; t0 < i1; t0 += kNnThreads) {
+        __syncthreads();
+        const int64_t it = CDE_CK(t0 + tid, Np, 110);  // < Np: splits and Np are multiples of 128
+#pragma unroll
+        for (int c = 0; c < DREG; ++c) xt[tid][c] = c < d ? xs[(int64_t)c * Np + it] : 0.f;
+        yt[tid] = y[it];
+        __syncthreads();
+        const int n = (int)min((int64_t)kNnThreads, i1 - t0);
+        for (int t = 0; t < n; ++t) {
+            const int i32 = (int)(t0 + t);
+            float xi[DREG];
+#pragma unroll
+            for (int c = 0; c < DREG; c += 4) {
+                const float4 v4 = *reinterpret_cast<const float4*>(&xt[t][c]);
+                xi[c] = v4.x;
+                xi[c + 1] = v4.y;
+                xi[c + 2] = v4.z;
+                xi[c + 3] = v4.w;
+            }
+            const float yi = yt[t];
+#pragma unroll
+            for (int b = 0; b < kNnJB; ++b) {
+                float dx2 = 0.f;
+#pragma unroll
+                for (int c = 0; c < DREG; ++c) {
+                    const float q = xj[b][c] - xi[c];
+                    dx2 = fmaf(q, q, dx2);
+                }
+                const float dy = yj[b] - yi;
+                const bool other = i32 != jj[b];
+                bx[b] = other ? fminf(bx[b], dx2) : bx[b];
+                by[b] = other ? fminf(by[b], dy * dy) : by[b];
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < kNnJB; ++b) {
+        const int64_t j = jbase + (int64_t)b * kNnThreads;
+        if (j >= N) continue;
+        atomicMin(mx_bits + j, __float_as_uint(bx[b]));
+        atomicMin(my_bits + j, __float_as_uint(by[b]));
+    }
+}
+
+int nn_shift_enqueue(const Dataset& D, cudaStream_t st, int sm_count) {
+    if (D.d <= 8) {
+        const int64_t per_cta = (int64_t)kNnThreads * kNnJB;
+        const int64_t gx = (D.N + per_cta - 1) / per_cta;
+        const int64_t tiles = (D.N + kNnThreads - 1) / kNnThreads;
+        int64_t ns = (4LL * sm_count + gx - 1) / gx;
+        if (ns > tiles) ns = tiles;
+        if (ns < 1) ns = 1;
+        const int64_t tps = (tiles + ns - 1) / ns;
+        ns = (tiles + tps - 1) / tps;
+        CDE_CUDA(cudaMemsetAsync(D.mx, 0x7f, (size_t)D.N * sizeof(float), st));  // 3.4e38: above any distance
+        CDE_CUDA(cudaMemsetAsync(D.my, 0x7f, (size_t)D.N * sizeof(float), st));
+        const dim3 grid((unsigned)gx, (unsigned)ns);
+        auto* mxb = reinterpret_cast<unsigned int*>(D.mx);
+        auto* myb = reinterpret_cast<unsigned int*>(D.my);
+        if (D.d <= 4)
+            k_nn_shift_split<4><<<grid, kNnThreads, 0, st>>>(D.xs, D.y, D.N, D.Np, D.d, tps * kNnThreads, mxb, myb);
+        else
+            k_nn_shift_split<8><<<grid, kNnThreads, 0, st>>>(D.xs, D.y, D.N, D.Np, D.d, tps * kNnThreads, mxb, myb);
+        CDE_CUDA(cudaGetLastError());
+        return CDE_OK;
+    }
     const int64_t blocks = (D.N + 255) / 256;
     const size_t smem = (size_t)(D.d + 1) * 256 * sizeof(float);
     if (smem > 48 * 1024)

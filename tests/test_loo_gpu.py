@@ -132,6 +132,29 @@ def test_cells_on_both_sides_of_the_recompute_threshold(ctx):
     cde.cde_destroy_dataset(ctx, ds)
 
 
+@pytest.mark.parametrize("N,d", [(3000, 5), (1031, 3), (517, 12), (700, 8), (2, 1)])
+def test_nearest_neighbour_shifts(ctx, N, d):
+    """The per-row exp2 shifts are the nearest squared distances, accumulated
+    in FP32 dimension by dimension with fused multiply-adds (emulated here:
+    FP32 differences, exact squares, one FP32 rounding per dimension).  d <= 8
+    runs the split kernel, d = 12 the one-row-per-thread kernel."""
+    x, y = synth.random_small(N, d, seed=N + 3 * d)
+    ds = cde.cde_create_dataset(ctx, x, y)
+    mx, my = cde.cde_dataset_nn(ctx, ds)
+    acc = np.zeros((N, N), np.float32)
+    for c in range(d):
+        q = (x[:, None, c] - x[None, :, c]).astype(np.float32)
+        acc = (q.astype(np.float64) ** 2 + acc.astype(np.float64)).astype(np.float32)
+    np.fill_diagonal(acc, np.inf)
+    dy = (y[:, None] - y[None, :]).astype(np.float32)
+    dy2 = (dy * dy).astype(np.float32)
+    np.fill_diagonal(dy2, np.inf)
+    np.testing.assert_allclose(mx, acc.min(1), rtol=2.0 ** -21, atol=0)
+    assert np.mean(mx == acc.min(1)) >= 0.99
+    np.testing.assert_array_equal(my, dy2.min(1))
+    cde.cde_destroy_dataset(ctx, ds)
+
+
 def test_standardisation_matches_oracle(ctx):
     x, y = synth.gmm_sine(3000, 5, seed=7)
     x = x * np.array([1.0, 10.0, 0.1, 3.0, 100.0], dtype=np.float32) + 5.0
