@@ -675,7 +675,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-rows", type=int, default=24)
+    ap.add_argument("--cpu-rows", type=int, default=320)
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--N", type=int, default=50000, help="dataset size (profiling runs use less)")

@@ -57,7 +57,8 @@ typedef enum {
     CDE_ENOMEM = 2,     /* memory budget or device allocation refused */
     CDE_ECUDA = 3,      /* CUDA runtime error (message has the CUDA text) */
     CDE_EBUSY = 4,      /* request queue full */
-    CDE_ETIMEOUT = 5,   /* cde_wait ran out before the request finished */
+    CDE_ETIMEOUT = 5,   /* cde_wait ran out before the request finished, or a tensor-core
+                           kernel's bounded on-device wait ran out (results invalid) */
     CDE_ENOTFOUND = 6,  /* unknown dataset handle or ticket */
     CDE_ECANCELED = 7   /* request cancelled before it ran */
 } cde_status;
@@ -113,9 +114,13 @@ int cde_dataset_info(cde_ctx *ctx, cde_dataset ds, int64_t *N, int *d_x, double 
  * -DCDE_CHECKS; the closed sanitizers' stand-in): *enabled = 1 there, and
  * *code receives the first failed check's code since the last call (0: none)
  * and clears it -- a failed check redirects its access to index 0 instead of
- * faulting.  In the normal library *enabled = 0 and *code = 0.  Waits for the
- * device to be idle.  enabled may be NULL.
+ * faulting.  In the normal library *enabled = 0.  In both builds a
+ * tensor-core kernel (cde_density) whose bounded on-device wait ran out
+ * reports CDE_CHECK_TENSOR_WAIT | (which waits) here when no index check
+ * failed, and the report is cleared.  Waits for the device to be idle.
+ * enabled may be NULL.
  */
+#define CDE_CHECK_TENSOR_WAIT 0x10000u
 int cde_check_status(cde_ctx *ctx, unsigned int *code, int *enabled);
 
 /* Per-row nearest squared distances of a Gaussian dataset, the exp2 shifts:

@@ -312,7 +312,14 @@ int cde_check_status(cde_ctx* ctx, unsigned int* code, int* enabled) {
     }
 #else
     if (enabled) *enabled = 0;
+    CDE_CUDA(cudaDeviceSynchronize());
 #endif
+    int tw = 0;
+    CDE_CUDA(cudaMemcpy(&tw, ctx->d_err + kErrTensorWait, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tw) {
+        CDE_CUDA(cudaMemset(ctx->d_err + kErrTensorWait, 0, sizeof(int)));
+        if (!*code) *code = CDE_CHECK_TENSOR_WAIT | (unsigned int)tw;
+    }
     return CDE_OK;
 }
 

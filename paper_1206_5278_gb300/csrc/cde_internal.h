@@ -87,6 +87,8 @@ struct Dataset {
 
 constexpr int kPadRows = 256;
 constexpr int kMaxD = 64;          // largest d_x handled by the SIMT kernels
+// word of cde_ctx::d_err set by a tensor-core kernel whose bounded mbarrier wait ran out
+constexpr int kErrTensorWait = 16;
 
 struct Server;  // serve.cpp
 
@@ -104,6 +106,7 @@ struct cde_ctx {
     int64_t next_id = 1;
     cde::Server* server = nullptr;
     int* d_err = nullptr;     // device-side error flag (bounded waits, checks)
+
     int tune_upt[3][3] = {};  // autotuned units per tile by grid shape (8/16/32), 0 = default
     int tune_ctas[3][3] = {}; // autotuned resident CTAs per SM, 0 = default (2)
     void* batch_plan = nullptr;  // cached batched launch (graph), batch.cu
@@ -155,6 +158,10 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
                      cudaStream_t st, double* d_rowv);
 
 // ---- density (density.cu) ----
+// per-query nearest squared distances m_q (FP32, pair-kernel formula) of
+// packed queries xq [d][Qp]; mq holds Q floats
+int query_shift_enqueue(int sm_count, const Dataset& D, const float* xq, int64_t Q, int64_t Qp, float* mq,
+                        cudaStream_t st);
 int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const float* d_xq,
                     int64_t Q, const float* d_yg, int G, float* d_f, cudaStream_t st);
 

@@ -9,11 +9,24 @@
 // underflows), a = log2(e)/(2 h^2).  Epanechnikov datasets use the profiles
 // u_qi = (1 - |x_q - x_i|^2/h1^2)_+ and w_ig = (1 - (y_g - y_i)^2/h2^2)_+ (no
 // shift; a = 1/h^2) and the constant c_1/h2 = 3/(4 h2); a query with no
-// x-neighbour inside h1 (0/0) gets f = 0.  The numerator is a (Q x N) x (N x G)
-// product whose factors are generated on the fly; each CTA owns 32 queries x
-// 256 grid points and runs the product on the tensor cores (k_density).  Small
-// Q splits the data range across CTAs; split partials are summed in split
-// order.
+// x-neighbour inside h1 (0/0) gets f = 0.
+//
+// The numerator is a (Q x N) x (N x G) matrix product whose factors are made
+// on the fly, so it runs on the 5th-generation tensor cores (k_density_tc):
+// a tile is 128 queries x up to 256 grid points, accumulated in tensor memory
+// over the data points in chunks of 32.  Sixteen warps evaluate the chunk's u
+// (A operand, 128 x 32) and w (B operand, 256 x 32), split each value
+// v = hi + lo into two BF16 numbers (round to nearest, |lo| <= 2^-9 v, lo
+// rounded again: about 2^-17 v left out) and store them in shared memory;
+// thread 0 issues hi*hi + hi*lo + lo*hi as BF16 MMAs with FP32 accumulation
+// (about 2^-16 relative per product).  (Streaming precomputed w blocks
+// instead was measured slower: 32 KB per chunk from L2 per SM.)  The tensor
+// cores' own accumulation is kept to 16 chunks (96 MMAs); the warps then add
+// the accumulator into FP32 register totals while the MMAs continue in a
+// second TMEM buffer.  Work is split evenly over one CTA per SM in (tile,
+// chunk) units; the partial tiles of each CTA are summed in CTA order
+// afterwards (bitwise reproducible).
+#include <algorithm>
 #include <cmath>
 
 #include <cuda_bf16.h>
@@ -21,26 +34,9 @@
 #include <cstdint>
 
 #include "cde_internal.h"
+#include "tc_util.cuh"
 
 namespace cde {
-
-constexpr int kDQ = 32;    // queries per CTA
-constexpr int kDG = 256;   // grid points per CTA
-constexpr int kDIC = 32;   // data points per chunk
-
-struct DensArgs {
-    const float* xs;   // dataset [d][Np]
-    const float* y;    // [Np]
-    const float* xq;   // queries [d][Qp] (standardised like the data)
-    const float* mq;   // [Q]
-    const float* yg;   // [G]
-    int64_t N, Np, Q, Qp;
-    int d, G;
-    float a1, a2;
-    int64_t i_per_split;   // multiple of kDIC
-    float* num;            // [n_split][Q][G]
-    float* den;            // [n_split][Q]
-};
 
 __device__ __forceinline__ float ex2d(float x) {
     float r;
@@ -53,14 +49,6 @@ __device__ __forceinline__ float fma_sat_d(float a, float b, float c) {
     float r;
     asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
-}
-
-// x factor from its shared-memory argument: Gaussian 2^T (T = a1 (m_q - dx2),
-// -inf masked), Epanechnikov (1 - a1 T)_+ (T = dx2, +inf masked)
-template <int KERN>
-__device__ __forceinline__ float dens_ufac(float T, float a1) {
-    if constexpr (KERN == 0) return ex2d(T);
-    else return fma_sat_d(-a1, T, 1.f);
 }
 
 // y factor at squared distance t2
@@ -119,234 +107,521 @@ __global__ void __launch_bounds__(256) k_query_shift(const float* __restrict__ x
     if (q < Q) atomicMin(mq_bits + q, __float_as_uint(best));
 }
 
-struct DensSmem {
-    float T[kDQ][kDIC + 4];     // x factor argument (dens_ufac), masked points give 0
-    uint4 Af[kDIC / 8][2][32];  // per chunk, k-step, m-tile, lane: TF32 A fragment (hi u)
-    uint4 Ax[kDIC / 8][2][32];  //   and the BF16 cross-term A fragment [hi u | lo u]
-    float yis[kDIC];
-    float xqs[kMaxD][kDQ];
-    float xis[kMaxD][kDIC];
-    float dens[kDQ];
-};
+// d <= 8: the same minima with JB queries per thread (two per packed FP32x2
+// instruction; JB = 8, or 2 for few queries), point-major shared tiles of
+// data points (128-bit loads) and the data range split over gridDim.y; split
+// minima merge with an integer atomicMin on the float bits as above.  Same
+// distance formula: dimension 0 first, one fused multiply-add per dimension
+// on xq - x_i.
+constexpr int kQsThreads = 128;
 
-__device__ __forceinline__ void split_tf32_d(float v, uint32_t& hi, uint32_t& lo) {
-    hi = __float_as_uint(v) & 0xffffe000u;
-    lo = __float_as_uint(v - __uint_as_float(hi));
+template <int DREG, int kQsJB>
+__global__ void __launch_bounds__(kQsThreads) k_query_shift_split(const float* __restrict__ xs, int64_t N,
+                                                                  int64_t Np, int d, const float* __restrict__ xq,
+                                                                  int64_t Q, int64_t Qp, int64_t i_per_split,
+                                                                  unsigned int* __restrict__ mq_bits) {
+    __shared__ __align__(16) float xt[kQsThreads][DREG];
+    const int tid = threadIdx.x;
+    const int64_t qbase = (int64_t)blockIdx.x * kQsThreads * kQsJB + tid;
+    const int64_t i0 = (int64_t)blockIdx.y * i_per_split;
+    const int64_t i1 = min(N, i0 + i_per_split);
+    float2 q2[kQsJB / 2][DREG];
+    float best[kQsJB];
+#pragma unroll
+    for (int p = 0; p < kQsJB / 2; ++p) {
+        const int64_t qa = qbase + (int64_t)(2 * p) * kQsThreads, qb = qa + kQsThreads;
+#pragma unroll
+        for (int c = 0; c < DREG; ++c)
+            q2[p][c] = make_float2(c < d && qa < Qp ? xq[(int64_t)c * Qp + qa] : 0.f,
+                                   c < d && qb < Qp ? xq[(int64_t)c * Qp + qb] : 0.f);
+        best[2 * p] = best[2 * p + 1] = INFINITY;
+    }
+    const float2 m1 = make_float2(-1.f, -1.f);
+    for (int64_t t0 = i0; t0 < i1; t0 += kQsThreads) {
+        __syncthreads();
+        const int64_t it = CDE_CK(t0 + tid, Np, 202);  // < Np: splits and Np are multiples of 128
+#pragma unroll
+        for (int c = 0; c < DREG; ++c) xt[tid][c] = c < d ? xs[(int64_t)c * Np + it] : 0.f;
+        __syncthreads();
+        const int n = (int)min((int64_t)kQsThreads, i1 - t0);
+        for (int t = 0; t < n; ++t) {
+            float xi[DREG];
+#pragma unroll
+            for (int c = 0; c < DREG; c += 4) {
+                const float4 v4 = *reinterpret_cast<const float4*>(&xt[t][c]);
+                xi[c] = v4.x;
+                xi[c + 1] = v4.y;
+                xi[c + 2] = v4.z;
+                xi[c + 3] = v4.w;
+            }
+#pragma unroll
+            for (int p = 0; p < kQsJB / 2; ++p) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < DREG; ++c) {
+                    const float2 tq = __ffma2_rn(make_float2(xi[c], xi[c]), m1, q2[p][c]);
+                    acc = __ffma2_rn(tq, tq, acc);
+                }
+                best[2 * p] = fminf(best[2 * p], acc.x);
+                best[2 * p + 1] = fminf(best[2 * p + 1], acc.y);
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < kQsJB; ++b) {
+        const int64_t q = qbase + (int64_t)b * kQsThreads;
+        if (q < Q) atomicMin(mq_bits + q, __float_as_uint(best[b]));
+    }
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2_d(float x, float y) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(x, y);  // x in the low half
+// m_q = min_i |x_q - x_i|^2 for the packed queries xq [d][Qp] (Gaussian datasets)
+int query_shift_enqueue(int sm_count, const Dataset& D, const float* xq, int64_t Q, int64_t Qp, float* mq,
+                        cudaStream_t st) {
+    if (Q == 0) return CDE_OK;
+    CDE_CUDA(cudaMemsetAsync(mq, 0x7f, (size_t)Q * sizeof(float), st));  // 3.4e38: above any distance
+    auto* mqb = reinterpret_cast<unsigned int*>(mq);
+    if (D.d <= 8) {
+        const int jb = Q >= 4096 ? 8 : 2;
+        const int64_t per_cta = (int64_t)kQsThreads * jb;
+        const int64_t gx = (Q + per_cta - 1) / per_cta;
+        const int64_t tiles = (D.N + kQsThreads - 1) / kQsThreads;
+        int64_t ns = (4LL * sm_count + gx - 1) / gx;
+        if (ns > tiles) ns = tiles;
+        if (ns < 1) ns = 1;
+        const int64_t tps = (tiles + ns - 1) / ns;
+        ns = (tiles + tps - 1) / tps;
+        const dim3 grid((unsigned)gx, (unsigned)ns);
+        const int64_t ips = tps * kQsThreads;
+        if (D.d <= 4 && jb == 8)
+            k_query_shift_split<4, 8><<<grid, kQsThreads, 0, st>>>(D.xs, D.N, D.Np, D.d, xq, Q, Qp, ips, mqb);
+        else if (D.d <= 4)
+            k_query_shift_split<4, 2><<<grid, kQsThreads, 0, st>>>(D.xs, D.N, D.Np, D.d, xq, Q, Qp, ips, mqb);
+        else if (jb == 8)
+            k_query_shift_split<8, 8><<<grid, kQsThreads, 0, st>>>(D.xs, D.N, D.Np, D.d, xq, Q, Qp, ips, mqb);
+        else
+            k_query_shift_split<8, 2><<<grid, kQsThreads, 0, st>>>(D.xs, D.N, D.Np, D.d, xq, Q, Qp, ips, mqb);
+        CDE_CUDA(cudaGetLastError());
+        return CDE_OK;
+    }
+    const size_t sm = (size_t)D.d * 256 * sizeof(float);
+    if (sm > 48 * 1024)
+        CDE_CUDA(cudaFuncSetAttribute(k_query_shift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int64_t qb = (Q + 255) / 256;
+    const int64_t tiles = (D.N + 255) / 256;
+    int64_t sy = (4LL * sm_count + qb - 1) / qb;
+    if (sy > tiles) sy = tiles;
+    if (sy < 1) sy = 1;
+    const int64_t tps = (tiles + sy - 1) / sy;
+    sy = (tiles + tps - 1) / tps;
+    k_query_shift<<<dim3((unsigned)qb, (unsigned)sy), 256, sm, st>>>(D.xs, D.N, D.Np, D.d, xq, Q, Qp, tps * 256, mqb);
+    CDE_CUDA(cudaGetLastError());
+    return CDE_OK;
+}
+
+constexpr int kTcM = 128;        // queries per tile (TMEM lanes)
+constexpr int kTcN = 256;        // grid points per tile (largest MMA N)
+constexpr int kTcKC = 32;        // data points per chunk (two k16 MMA steps)
+constexpr int kTcStages = 3;     // operand ring depth
+constexpr int kTcF = 16;         // chunks accumulated in TMEM before a flush
+constexpr int kTcProd = 512;     // threads: all make operands; thread 0 also issues the MMAs
+constexpr int kTcCols = kTcN / (kTcProd / 128);  // accumulator columns per thread (its warp's TMEM lanes)
+constexpr uint32_t kTcSBO = (kTcKC / 8) * 128;   // 8-row group stride of an operand tile
+
+struct DensTcArgs {
+    const float* xs;   // dataset [d][Np]
+    const float* y;    // [Np]
+    const float* xq;   // queries [d][Qp] (standardised like the data)
+    const float* mq;   // [Q] nearest squared distances (Gaussian)
+    const float* yg;   // [G]
+    int64_t N, Np, Q, Qp;
+    int d, G, GT;      // GT: grid tiles of 256
+    float a1, a2;
+    int64_t C;         // chunks per tile
+    int64_t U;         // units = tiles * C
+    int P;             // CTAs
+    int MT;            // partial slots per CTA
+    float* part;       // [P * MT][128][256]
+    float* dpart;      // [P * MT][128]
+    int* err;          // timeout word
+};
+
+struct TcSmem {
+    unsigned char A[kTcStages][2][kTcM * kTcKC * 2];   // u: hi, lo (BF16, K-major core matrices)
+    unsigned char B[kTcStages][2][kTcN * kTcKC * 2];   // w: hi, lo
+    float pt[3][kMaxD + 1][kTcKC];                     // chunk's x (d rows) and y: ring of 3 chunks
+    float xq[kMaxD][kTcM];                             // the tile's query coordinates
+    float den[3][kTcM];
+    unsigned long long empty[kTcStages], accfull[2];
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2_d(float lo_elem, float hi_elem) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);  // first argument in the low half
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-__device__ __forceinline__ void mma_bf16_d(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// v = hi + lo for two adjacent K elements (k even in the low half): the BF16
+// roundings of v and of the exact remainder v - hi
+__device__ __forceinline__ void split_pair(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+    hi = pack_bf16x2_d(v0, v1);
+    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+    lo = pack_bf16x2_d(v0 - h0, v1 - h1);
 }
 
-__device__ __forceinline__ void mma_tf32_d(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// One chunk's place in the CTA's unit range: tile t, chunk c, and the
+// accumulation period it belongs to.  Periods are runs of at most kTcF chunks
+// of one tile; a tile's run inside the CTA's range is its segment.
+struct TcPeriod {
+    int64_t t, c;
+    int len;
+    bool first, last;   // first / last period of its segment
+};
+
+__device__ __forceinline__ TcPeriod tc_period(int64_t u, int64_t u0, int64_t u1, int64_t C) {
+    TcPeriod p;
+    p.t = u / C;
+    p.c = u - p.t * C;
+    int64_t ce = min(C, p.c + kTcF);
+    if (p.t * C + ce > u1) ce = u1 - p.t * C;
+    p.len = (int)(ce - p.c);
+    p.first = p.c == 0 || u == u0;
+    p.last = ce == C || p.t * C + ce == u1;
+    return p;
 }
 
-// Numerator tile F[32 queries][256 grid points] += U[32 x IC] W[IC x 256] on
-// the tensor cores with split operands v = hi + lo: hi*hi as TF32 m16n8k8, the
-// two cross terms together as one BF16 m16n8k16 (about 2^-17 per term),
-// A (u, M = queries) and B (w, N = grid points) operands; warp w owns grid
-// points [32 w, 32 w + 32) and makes its B fragments in-lane with exp2.  Per chunk the 32 x IC
-// arguments of u go to shared memory, then one thread per (k-step, m-tile,
-// lane) slot turns them into the split A fragments (TF32 hi, BF16 [hi | lo])
-// that every warp loads, so each u is evaluated once per CTA.  Each 32-point
-// chunk accumulates from zero and is added to an FP32 running total.
+// MMA N of grid tile gt (a multiple of 16)
+__device__ __forceinline__ int tc_ntile(int G, int gt) { return min(kTcN, (G - gt * kTcN + 15) / 16 * 16); }
+
+// Issue the MMAs of the chunk in stage s (thread 0, after the barrier that
+// ends the chunk): hi*hi + hi*lo + lo*hi for both k16 steps into TMEM buffer
+// b, then release the stage; the last chunk of a period also signals the flush.
+__device__ __forceinline__ void tc_issue(TcSmem& S, uint32_t tbase, int s, int b, bool first, bool last,
+                                         uint32_t idesc) {
+    const uint32_t dt = tbase + (uint32_t)(b * kTcN);
+    tc_fence_after();
+#pragma unroll
+    for (int ks = 0; ks < kTcKC / 16; ++ks) {
+        const uint64_t ah = tc_sdesc(smem_u32(&S.A[s][0][0]) + 256 * ks, 128, kTcSBO);
+        const uint64_t al = tc_sdesc(smem_u32(&S.A[s][1][0]) + 256 * ks, 128, kTcSBO);
+        const uint64_t bh = tc_sdesc(smem_u32(&S.B[s][0][0]) + 256 * ks, 128, kTcSBO);
+        const uint64_t bl = tc_sdesc(smem_u32(&S.B[s][1][0]) + 256 * ks, 128, kTcSBO);
+        tc_mma_bf16(dt, ah, bh, idesc, (!first || ks > 0) ? 1u : 0u);
+        tc_mma_bf16(dt, ah, bl, idesc, 1u);
+        tc_mma_bf16(dt, al, bh, idesc, 1u);
+    }
+    tc_commit(smem_u32(&S.empty[s]));
+    if (last) tc_commit(smem_u32(&S.accfull[b]));
+}
+
+// Start the asynchronous copy of one chunk's points (x rows, then y) into
+// point buffer `slot`; i0 < 0: no chunk (the group is still committed, so
+// every thread's group count stays in step).
+__device__ __forceinline__ void tc_fetch_points(const DensTcArgs& a, TcSmem& S, int slot, int64_t i0) {
+    if (i0 >= 0) {
+        const int nel = (a.d + 1) * kTcKC;
+        for (int e = threadIdx.x; e < nel; e += kTcProd) {
+            const int row = e / kTcKC, p = e % kTcKC;
+            const float* src = (row < a.d ? a.xs + (int64_t)row * a.Np : a.y) + CDE_CK(i0 + p, a.Np, 211);
+            cp_async4(smem_u32(&S.pt[slot][row][p]), src);
+        }
+    }
+    cp_async_commit();
+}
+
+// Make the chunk's operands: u (A, 128 queries x 32 points) and w (B, up to
+// 256 grid points x 32 points), each split into BF16 hi and lo, in operand
+// stage s from the points in buffer pb; then publish the next chunk's points
+// (copied asynchronously two chunks ahead) with the closing barrier.  Thread
+// roles: A (query tid % 128, points 8 (tid / 128) ... + 8, one core-matrix
+// column), B (grid row tid % 256, points 16 (tid / 256) ... + 16).  Pairs of
+// points go through the packed FP32x2 pipe; xq - x is formed as
+// fma(x, -1, xq), the same rounding as the scalar subtraction of every other
+// pair kernel.
 template <int KERN>
-__global__ void __launch_bounds__(256, 2) k_density(const DensArgs a) {
-    extern __shared__ float4 dsm4[];
-    DensSmem& S = *reinterpret_cast<DensSmem*>(dsm4);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int64_t q0 = (int64_t)blockIdx.x * kDQ;
-    const int g0 = blockIdx.y * kDG;
-    const int64_t s = blockIdx.z;
-    const int64_t i_begin = s * a.i_per_split;
-    const int64_t i_end = min(a.N, i_begin + a.i_per_split);
+__device__ __forceinline__ void tc_produce(const DensTcArgs& a, TcSmem& S, int s, uint32_t empty_parity, int pb,
+                                           int nvalid, int ntile, float mqv, float ygv, float& den, float& denc,
+                                           volatile int* abort_flag) {
+    const int tid = threadIdx.x;
     const int d = a.d;
-    for (int e = tid; e < d * kDQ; e += 256) {
-        const int c = e / kDQ, qq = e % kDQ;
-        S.xqs[c][qq] = (q0 + qq < a.Qp) ? a.xq[(int64_t)c * a.Qp + q0 + qq] : 0.f;
+    const float2 m1 = make_float2(-1.f, -1.f);
+    // the MMAs that read this stage last time are done
+    mbar_wait(smem_u32(&S.empty[s]), empty_parity, abort_flag, a.err, 1);
+    const int q = tid & (kTcM - 1), qr = tid >> 7;
+    float2 v2[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v2[e] = make_float2(0.f, 0.f);
+    for (int cd = 0; cd < d; ++cd) {
+        const float xqc = S.xq[cd][q];
+        const float2 xq2 = make_float2(xqc, xqc);
+        const float4* xp = reinterpret_cast<const float4*>(&S.pt[pb][cd][8 * qr]);
+        const float4 xa = xp[0], xb = xp[1];
+        float2 t;
+        t = __ffma2_rn(make_float2(xa.x, xa.y), m1, xq2);
+        v2[0] = __ffma2_rn(t, t, v2[0]);
+        t = __ffma2_rn(make_float2(xa.z, xa.w), m1, xq2);
+        v2[1] = __ffma2_rn(t, t, v2[1]);
+        t = __ffma2_rn(make_float2(xb.x, xb.y), m1, xq2);
+        v2[2] = __ffma2_rn(t, t, v2[2]);
+        t = __ffma2_rn(make_float2(xb.z, xb.w), m1, xq2);
+        v2[3] = __ffma2_rn(t, t, v2[3]);
     }
-    // distance-pass role: query dq, points dp..dp+3
-    const int dq = tid >> 3, dp = (tid & 7) * 4;
-    const float mqv = (KERN == 0 && q0 + dq < a.Q) ? a.mq[q0 + dq] : 0.f;
-    float ygv[4];
+    float u[8];
+    if constexpr (KERN == 0) {
+        // 2^{a1 (m_q - dx2)} as 2^{a1 m_q - a1 dx2}
+        const float a1 = a.a1, am = a1 * mqv;
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const int gg = g0 + 32 * warp + 8 * nt + g;
-        ygv[nt] = a.yg[gg < a.G ? gg : a.G - 1];
-    }
-    float Dt[2][4][4];
-    // fragment-pass role (one thread per k-step, m-tile and lane slot): its two
-    // queries' denominator partials, summed over its points of every chunk
-    const int fks = tid >> 6, fmt = (tid >> 5) & 1;
-    float bq0 = 0.f, bq1 = 0.f;
-    float2 yg2[4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) yg2[nt] = make_float2(ygv[nt], ygv[nt]);
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) Dt[mt][nt][0] = Dt[mt][nt][1] = Dt[mt][nt][2] = Dt[mt][nt][3] = 0.f;
-    const float a1 = a.a1, a2 = a.a2;
-    for (int64_t c0 = i_begin; c0 < i_end; c0 += kDIC) {
-        __syncthreads();
-        for (int e = tid; e < (d + 1) * kDIC; e += 256) {
-            const int c = e / kDIC, ii = e % kDIC;
-            const int64_t i = CDE_CK(c0 + ii, a.Np, 201);  // < Np
-            if (c < d) S.xis[c][ii] = a.xs[(int64_t)c * a.Np + i];
-            else S.yis[ii] = a.y[i];
+        for (int e = 0; e < 4; ++e) {
+            const float2 arg = __ffma2_rn(make_float2(-a1, -a1), v2[e], make_float2(am, am));
+            u[2 * e] = ex2d(arg.x);
+            u[2 * e + 1] = ex2d(arg.y);
         }
-        __syncthreads();
+    } else {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int ii = dp + r;
-            float dx2 = 0.f;
-            for (int c = 0; c < d; ++c) {
-                const float u = S.xqs[c][dq] - S.xis[c][ii];
-                dx2 = fmaf(u, u, dx2);
+        for (int e = 0; e < 4; ++e) {
+            u[2 * e] = fma_sat_d(-a.a1, v2[e].x, 1.f);
+            u[2 * e + 1] = fma_sat_d(-a.a1, v2[e].y, 1.f);
+        }
+    }
+    if (nvalid < kTcKC) {   // the data's last, partial chunk: points past N get u = 0
+        const int nv = nvalid - 8 * qr;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) u[p] = p < nv ? u[p] : 0.f;
+    }
+    float cs = 0.f;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) cs += u[p];
+    // compensated running sum of the denominator
+    const float yk = cs - denc, tk = den + yk;
+    denc = (tk - den) - yk;
+    den = tk;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) split_pair(u[2 * e], u[2 * e + 1], h[e], l[e]);
+    const uint32_t off = (uint32_t)(q >> 3) * kTcSBO + (uint32_t)(q & 7) * 16 + (uint32_t)qr * 128;
+    *reinterpret_cast<uint4*>(&S.A[s][0][off]) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(&S.A[s][1][off]) = make_uint4(l[0], l[1], l[2], l[3]);
+    // ---- B: w for grid row g and points 16 gh ... 16 gh + 15 (two core-matrix columns)
+    {
+        const int g = tid & (kTcN - 1), gh = tid >> 8;
+        if (g < ntile) {
+            const uint32_t rowoff = (uint32_t)(g >> 3) * kTcSBO + (uint32_t)(g & 7) * 16;
+            const float2 yg2 = make_float2(ygv, ygv);
+            const float4* yp = reinterpret_cast<const float4*>(&S.pt[pb][d][16 * gh]);
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const float4 ya = yp[2 * kk], yb = yp[2 * kk + 1];
+                const float2 yy[4] = {make_float2(ya.x, ya.y), make_float2(ya.z, ya.w), make_float2(yb.x, yb.y),
+                                      make_float2(yb.z, yb.w)};
+                uint32_t hb[4], lb[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2 t = __ffma2_rn(yy[e], m1, yg2);
+                    const float2 t2 = __fmul2_rn(t, t);
+                    float w0, w1;
+                    if constexpr (KERN == 0) {
+                        const float2 arg = __fmul2_rn(t2, make_float2(-a.a2, -a.a2));
+                        w0 = ex2d(arg.x);
+                        w1 = ex2d(arg.y);
+                    } else {
+                        w0 = fma_sat_d(-a.a2, t2.x, 1.f);
+                        w1 = fma_sat_d(-a.a2, t2.y, 1.f);
+                    }
+                    split_pair(w0, w1, hb[e], lb[e]);
+                }
+                const uint32_t boff = rowoff + (uint32_t)(2 * gh + kk) * 128;
+                *reinterpret_cast<uint4*>(&S.B[s][0][boff]) = make_uint4(hb[0], hb[1], hb[2], hb[3]);
+                *reinterpret_cast<uint4*>(&S.B[s][1][boff]) = make_uint4(lb[0], lb[1], lb[2], lb[3]);
             }
-            if constexpr (KERN == 0) S.T[dq][ii] = (c0 + ii < i_end) ? a1 * (mqv - dx2) : -INFINITY;
-            else S.T[dq][ii] = (c0 + ii < i_end) ? dx2 : INFINITY;
         }
-        __syncthreads();
-        // fragment pass: every x factor of the chunk once (not once per warp),
-        // split hi + lo and packed into the A fragments the MMA pass loads
-        {
-            const int pa = 8 * fks + 2 * t, pb = pa + 1, r0 = 16 * fmt + g, r1 = r0 + 8;
-            const float u0 = dens_ufac<KERN>(S.T[r0][pa], a1);   // (q, p0)
-            const float u1 = dens_ufac<KERN>(S.T[r1][pa], a1);   // (q + 8, p0)
-            const float u2 = dens_ufac<KERN>(S.T[r0][pb], a1);   // (q, p1)
-            const float u3 = dens_ufac<KERN>(S.T[r1][pb], a1);   // (q + 8, p1)
-            bq0 += u0 + u2;
-            bq1 += u1 + u3;
-            uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
-            split_tf32_d(u0, h0, l0);
-            split_tf32_d(u1, h1, l1);
-            split_tf32_d(u2, h2, l2);
-            split_tf32_d(u3, h3, l3);
-            S.Af[fks][fmt][lane] = make_uint4(h0, h1, h2, h3);
-            S.Ax[fks][fmt][lane] = make_uint4(pack_bf16x2_d(__uint_as_float(h0), __uint_as_float(h2)),
-                                              pack_bf16x2_d(__uint_as_float(h1), __uint_as_float(h3)),
-                                              pack_bf16x2_d(__uint_as_float(l0), __uint_as_float(l2)),
-                                              pack_bf16x2_d(__uint_as_float(l1), __uint_as_float(l3)));
-        }
-        __syncthreads();
-        float D[2][4][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) D[mt][nt][0] = D[mt][nt][1] = D[mt][nt][2] = D[mt][nt][3] = 0.f;
-#pragma unroll
-        for (int ks = 0; ks < kDIC / 8; ++ks) {
-            // this lane's two points of the k-step: p0 = 8 ks + 2t, p1 = p0 + 1
-            const int pa = 8 * ks + 2 * t;
-            uint32_t ah[2][4], ax[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const uint4 f = S.Af[ks][mt][lane], x = S.Ax[ks][mt][lane];
-                ah[mt][0] = f.x;
-                ah[mt][1] = f.y;
-                ah[mt][2] = f.z;
-                ah[mt][3] = f.w;
-                ax[mt][0] = x.x;
-                ax[mt][1] = x.y;
-                ax[mt][2] = x.z;
-                ax[mt][3] = x.w;
-            }
-            const float2 yab = *reinterpret_cast<const float2*>(&S.yis[pa]);
-            const float2 nyab = make_float2(-yab.x, -yab.y);
-            uint32_t bh[4][2], bx[4][2];
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const float2 tt = __fadd2_rn(yg2[nt], nyab);   // (y_g - y_p0, y_g - y_p1)
-                const float2 t2 = __fmul2_rn(tt, tt);
-                const float w0 = dens_wfac<KERN>(t2.x, a2), w1 = dens_wfac<KERN>(t2.y, a2);
-                const float2 h = make_float2(__uint_as_float(__float_as_uint(w0) & 0xffffe000u),
-                                             __uint_as_float(__float_as_uint(w1) & 0xffffe000u));
-                const float2 l = __ffma2_rn(h, make_float2(-1.f, -1.f), make_float2(w0, w1));  // exact
-                bh[nt][0] = __float_as_uint(h.x);
-                bh[nt][1] = __float_as_uint(h.y);
-                bx[nt][0] = pack_bf16x2_d(l.x, l.y);
-                bx[nt][1] = pack_bf16x2_d(h.x, h.y);
-            }
-            // hi*hi on TF32; both cross terms in one BF16 k16 MMA
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma_tf32_d(D[mt][nt], ah[mt], bh[nt][0], bh[nt][1]);
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma_bf16_d(D[mt][nt], ax[mt], bx[nt][0], bx[nt][1]);
-        }
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) Dt[mt][nt][q] += D[mt][nt][q];
     }
-    // denominators: a query's partials sit in the 4 lanes (t) of 4 warps (k-steps)
-    // of its m-tile; sum t by shuffles, then the k-steps in order
-    bq0 += __shfl_xor_sync(0xffffffffu, bq0, 1);
-    bq0 += __shfl_xor_sync(0xffffffffu, bq0, 2);
-    bq1 += __shfl_xor_sync(0xffffffffu, bq1, 1);
-    bq1 += __shfl_xor_sync(0xffffffffu, bq1, 2);
-    __syncthreads();                      // the last chunk's fragments are no longer read
-    float* red = reinterpret_cast<float*>(&S.Af[0][0][0]);   // [k-step][query]
-    if (t == 0) {
-        red[fks * kDQ + 16 * fmt + g] = bq0;
-        red[fks * kDQ + 16 * fmt + g + 8] = bq1;
-    }
+    fence_async_smem();   // the tensor cores read these after the barrier
+    cp_async_wait_1();    // this thread's copies of the next chunk have landed
     __syncthreads();
-    if (tid < kDQ) S.dens[tid] = ((red[tid] + red[kDQ + tid]) + red[2 * kDQ + tid]) + red[3 * kDQ + tid];
-    __syncthreads();
-    float* num = a.num + s * a.Q * a.G;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int64_t qq = q0 + 16 * mt + g + 8 * (q >> 1);
-                const int gg = g0 + 32 * warp + 8 * nt + 2 * t + (q & 1);
-                if (qq < a.Q && gg < a.G) num[qq * a.G + gg] = Dt[mt][nt][q];
-            }
-    if (blockIdx.y == 0 && tid < kDQ && q0 + tid < a.Q) a.den[s * a.Q + q0 + tid] = S.dens[tid];
 }
 
-// f[q][g] = (sum_s num) / (sum_s den) * norm, splits in order (norm the y
-// kernel's constant; a zero denominator -- no x-neighbour -- gives 0)
-__global__ void k_density_final(const float* __restrict__ num, const float* __restrict__ den,
-                                int n_split, int64_t Q, int G, float norm, float* __restrict__ f) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= Q * G) return;
-    const int64_t q = e / G;
-    float sn = 0.f, sd = 0.f;
-    for (int s = 0; s < n_split; ++s) {
-        sn += num[(int64_t)s * Q * G + e];
-        sd += den[(int64_t)s * Q + q];
+// Add accumulation period pq's TMEM buffer into the register totals (the
+// warp's 32 TMEM lanes = queries, columns 64 (warp / 4) ... + 64); at the end
+// of a segment write the totals and the denominator as a partial tile.  The
+// TMEM reads are ordered before the next MMA into the buffer by the fence
+// and the barrier that ends the next chunk.
+__device__ __forceinline__ void tc_flush(const DensTcArgs& a, TcSmem& S, uint32_t tbase, int pq, int64_t tq,
+                                         bool lastq, float den_seg, int64_t t_first, float (&tot)[kTcCols],
+                                         volatile int* abort_flag) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b = pq & 1;
+    const bool ok = mbar_wait(smem_u32(&S.accfull[b]), (uint32_t)(pq >> 1) & 1, abort_flag, a.err, 2);
+    tc_fence_after();
+    if (ok) {
+        const uint32_t ta =
+            tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * kTcN + (warp >> 2) * kTcCols);
+#pragma unroll
+        for (int cb = 0; cb < kTcCols / 32; ++cb) {
+            float v[32];
+            tmem_ld32(ta + 32 * cb, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) tot[32 * cb + j] += v[j];
+        }
     }
-    f[e] = sd > 0.f ? sn / sd * norm : 0.f;
+    tc_fence_before();
+    if (lastq) {
+        const int64_t slot = (int64_t)blockIdx.x * a.MT + (tq - t_first);
+        const int row = 32 * (warp & 3) + lane;
+        float4* dst = reinterpret_cast<float4*>(a.part + (slot * kTcM + row) * kTcN + (warp >> 2) * kTcCols);
+#pragma unroll
+        for (int v4 = 0; v4 < kTcCols / 4; ++v4) {
+            dst[v4] = make_float4(tot[4 * v4], tot[4 * v4 + 1], tot[4 * v4 + 2], tot[4 * v4 + 3]);
+            tot[4 * v4] = tot[4 * v4 + 1] = tot[4 * v4 + 2] = tot[4 * v4 + 3] = 0.f;
+        }
+        // a query's four denominator parts (point quarters), summed in order
+        const int q = tid & (kTcM - 1), qr = tid >> 7;
+        if (qr > 0) S.den[qr - 1][q] = den_seg;
+        __syncthreads();
+        if (qr == 0) a.dpart[slot * kTcM + q] = ((den_seg + S.den[0][q]) + S.den[1][q]) + S.den[2][q];
+        __syncthreads();
+    }
+}
+
+template <int KERN>
+__global__ void __launch_bounds__(kTcProd, 1) k_density_tc(const DensTcArgs a) {
+    extern __shared__ float4 tc_dyn[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(tc_dyn);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t u0 = (int64_t)blockIdx.x * a.U / a.P, u1 = ((int64_t)blockIdx.x + 1) * a.U / a.P;
+    const int64_t t_first = u0 / a.C;
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) mbar_init(smem_u32(&S.empty[s]), 1);
+        for (int b = 0; b < 2; ++b) mbar_init(smem_u32(&S.accfull[b]), 1);
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&S.tmem_base), 2 * kTcN);
+    {
+        // the first two chunks' points (units u0 and u0 + 1)
+        const int64_t c0 = u0 % a.C, c1 = c0 + 1 == a.C ? 0 : c0 + 1;
+        tc_fetch_points(a, S, 0, c0 * kTcKC);
+        tc_fetch_points(a, S, 1, u0 + 1 < u1 ? c1 * kTcKC : -1);
+        cp_async_wait_1();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = S.tmem_base;
+    volatile int* abort_flag = &S.abort;
+
+    float tot[kTcCols];
+#pragma unroll
+    for (int j = 0; j < kTcCols; ++j) tot[j] = 0.f;
+    float den = 0.f, denc = 0.f, den_done = 0.f;
+    int s = 0, pb = 0;   // operand stage, point buffer of the current chunk
+    uint32_t empty_parity = 1;
+    int64_t u = u0, cur_t = -1, prev_t = -1;
+    bool prev_last = false;
+    int pi = 0, ntile = kTcN;
+    uint32_t idesc = 0;
+    float mqv = 0.f, ygv = 0.f;
+    while (u < u1) {
+        const TcPeriod P = tc_period(u, u0, u1, a.C);
+        if (P.t != cur_t) {   // a new tile: its queries, shift and grid row
+            cur_t = P.t;
+            const int64_t qt = P.t / a.GT;
+            const int gt = (int)(P.t % a.GT);
+            for (int e = tid; e < a.d * kTcM; e += kTcProd) {
+                const int cd = e / kTcM, qq = e % kTcM;
+                S.xq[cd][qq] = a.xq[(int64_t)cd * a.Qp + CDE_CK(qt * kTcM + qq, a.Qp, 213)];
+            }
+            const int64_t qg = qt * kTcM + (tid & (kTcM - 1));
+            mqv = (KERN == 0 && qg < a.Q) ? a.mq[qg] : 0.f;
+            const int gg = gt * kTcN + (tid & (kTcN - 1));
+            ygv = a.yg[gg < a.G ? gg : a.G - 1];
+            ntile = tc_ntile(a.G, gt);
+            idesc = tc_idesc_bf16(kTcM, ntile);
+            __syncthreads();
+        }
+        if (P.first && pi > 0) {
+            den_done = den;
+            den = denc = 0.f;
+        }
+        for (int j = 0; j < P.len; ++j) {
+            const int64_t c = P.c + j;
+            const int nvalid = (int)min((int64_t)kTcKC, a.N - c * kTcKC);
+            // the unit two ahead: units run through a tile's chunks, then to chunk 0 of the next tile
+            const int64_t c1 = c + 1 == a.C ? 0 : c + 1, c2 = c1 + 1 == a.C ? 0 : c1 + 1;
+            tc_fetch_points(a, S, pb == 0 ? 2 : pb - 1, u + j + 2 < u1 ? c2 * kTcKC : -1);
+            tc_produce<KERN>(a, S, s, empty_parity, pb, nvalid, ntile, mqv, ygv, den, denc, abort_flag);
+            if (tid == 0 && !*abort_flag) tc_issue(S, tbase, s, pi & 1, j == 0, j == P.len - 1, idesc);
+            pb = pb == 2 ? 0 : pb + 1;
+            if (++s == kTcStages) {
+                s = 0;
+                empty_parity ^= 1;
+            }
+        }
+        if (pi >= 1) tc_flush(a, S, tbase, pi - 1, prev_t, prev_last, den_done, t_first, tot, abort_flag);
+        prev_t = P.t;
+        prev_last = P.last;
+        u += P.len;
+        ++pi;
+    }
+    if (pi >= 1) tc_flush(a, S, tbase, pi - 1, prev_t, prev_last, den, t_first, tot, abort_flag);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 2 * kTcN);
+    }
+}
+
+// CTA owning unit u under the even split of U units over P CTAs
+// (u0(c) = floor(c U / P)): the largest c with u0(c) <= u
+__device__ __forceinline__ int64_t tc_owner(int64_t u, int64_t U, int64_t P) { return ((u + 1) * P - 1) / U; }
+
+// f[q][g] = (sum over the CTAs covering the tile of the partial numerators) /
+// (same for the denominators) * norm; a zero denominator (no x-neighbour)
+// gives 0.  A block is 32 grid points x 8 slots; a slot is one of `parts`
+// consecutive pieces of the covering CTAs' range (parts = 1, 2, 4 or 8) of one
+// query row.  Pieces are summed in CTA order, then the pieces in order.  f
+// has row stride ldf (the caller's full grid when this pass covers part of it).
+__global__ void __launch_bounds__(256) k_density_final(const DensTcArgs a, float norm, int parts_log2,
+                                                       float* __restrict__ f, int64_t ldf) {
+    __shared__ float rn[8][32], rd[8][32];
+    const int lane = threadIdx.x & 31, slot = threadIdx.x >> 5;
+    const int parts = 1 << parts_log2, part = slot & (parts - 1);
+    const int64_t gb_n = (a.G + 31) / 32, qb = (int64_t)blockIdx.x / gb_n;
+    const int gb = (int)((int64_t)blockIdx.x - qb * gb_n);
+    const int64_t q = qb * (8 >> parts_log2) + (slot >> parts_log2);
+    const int g = gb * 32 + lane;
+    float sn = 0.f, sd = 0.f;
+    if (q < a.Q) {
+        const int64_t t = (q / kTcM) * a.GT + (gb * 32) / kTcN;
+        const int64_t c0 = tc_owner(t * a.C, a.U, a.P), c1 = tc_owner(t * a.C + a.C - 1, a.U, a.P);
+        const int64_t per = (c1 - c0 + parts) / parts;
+        const int64_t cb = c0 + part * per, ce = min(c1 + 1, cb + per);
+        for (int64_t c = cb; c < ce; ++c) {
+            const int64_t ub = c * a.U / a.P, ue = (c + 1) * a.U / a.P;
+            if (ub >= ue) continue;
+            const int64_t sl = c * a.MT + (t - ub / a.C);
+            if (g < a.G) sn += a.part[(sl * kTcM + (q % kTcM)) * kTcN + g % kTcN];
+            sd += a.dpart[sl * kTcM + (q % kTcM)];
+        }
+    }
+    rn[slot][lane] = sn;
+    rd[slot][lane] = sd;
+    __syncthreads();
+    if (part == 0 && q < a.Q && g < a.G) {
+        for (int p = 1; p < parts; ++p) {
+            sn += rn[slot + p][lane];
+            sd += rd[slot + p][lane];
+        }
+        f[q * ldf + g] = sd > 0.f ? sn / sd * norm : 0.f;
+    }
 }
 
 int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const float* d_xq,
                     int64_t Q, const float* d_yg, int G, float* d_f, cudaStream_t st) {
     if (Q == 0) return CDE_OK;
-    const int64_t Qp = (Q + kDQ - 1) / kDQ * kDQ;
-    float *xq = nullptr, *mq = nullptr, *num = nullptr, *den = nullptr;
+    const int64_t Qp = (Q + kTcM - 1) / kTcM * kTcM;
+    float *xq = nullptr, *mq = nullptr, *part = nullptr, *dpart = nullptr;
     double* stats = nullptr;
     CDE_CUDA(cudaMallocAsync((void**)&xq, (size_t)Qp * D.d * sizeof(float), st));
     CDE_CUDA(cudaMallocAsync((void**)&mq, (size_t)Q * sizeof(float), st));
@@ -355,24 +630,13 @@ int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const 
     CDE_CUDA(cudaMemcpyAsync(stats + D.d, D.sd.data(), D.d * sizeof(double), cudaMemcpyHostToDevice, st));
     k_query_pack<<<(unsigned)((Qp + 255) / 256), 256, 0, st>>>(d_xq, Q, Qp, D.d, stats, stats + D.d, xq);
     CDE_CUDA(cudaGetLastError());
-    const size_t sm = (size_t)D.d * 256 * sizeof(float);
-    if (sm > 48 * 1024)
-        CDE_CUDA(cudaFuncSetAttribute(k_query_shift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const bool epan = D.kernel == CDE_KERNEL_EPAN;
     if (!epan) {
-        const int64_t qb = (Q + 255) / 256;
-        const int64_t tiles = (D.N + 255) / 256;
-        int64_t sy = (4LL * ctx->sm_count + qb - 1) / qb;
-        if (sy > tiles) sy = tiles;
-        if (sy < 1) sy = 1;
-        const int64_t tps = (tiles + sy - 1) / sy;
-        sy = (tiles + tps - 1) / tps;
-        CDE_CUDA(cudaMemsetAsync(mq, 0x7f, (size_t)Q * sizeof(float), st));  // 3.4e38: above any distance
-        k_query_shift<<<dim3((unsigned)qb, (unsigned)sy), 256, sm, st>>>(
-            D.xs, D.N, D.Np, D.d, xq, Q, Qp, tps * 256, reinterpret_cast<unsigned int*>(mq));
-        CDE_CUDA(cudaGetLastError());
+        const int rc = query_shift_enqueue(ctx->sm_count, D, xq, Q, Qp, mq, st);
+        if (rc != CDE_OK) return rc;
     }
-    DensArgs a{};
+    const double L2E = 1.4426950408889634074;
+    DensTcArgs a{};
     a.xs = D.xs;
     a.y = D.y;
     a.xq = xq;
@@ -384,42 +648,41 @@ int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const 
     a.Qp = Qp;
     a.d = D.d;
     a.G = G;
-    const double L2E = 1.4426950408889634074;
+    a.GT = (G + kTcN - 1) / kTcN;
     a.a1 = (float)(epan ? 1.0 / (h1 * h1) : L2E / (2 * h1 * h1));
     a.a2 = (float)(epan ? 1.0 / (h2 * h2) : L2E / (2 * h2 * h2));
-    const int64_t qt = Qp / kDQ;
-    const int gt = (G + kDG - 1) / kDG;
-    const int64_t chunks = (D.N + kDIC - 1) / kDIC;
-    int64_t ns = (4LL * ctx->sm_count + qt * gt - 1) / (qt * gt);
-    if (ns > chunks) ns = chunks;
-    if (ns < 1) ns = 1;
-    const int64_t cps = (chunks + ns - 1) / ns;
-    a.i_per_split = cps * kDIC;
-    ns = (chunks + cps - 1) / cps;
-    CDE_CUDA(cudaMallocAsync((void**)&num, (size_t)ns * Q * G * sizeof(float), st));
-    CDE_CUDA(cudaMallocAsync((void**)&den, (size_t)ns * Q * sizeof(float), st));
-    a.num = num;
-    a.den = den;
+    a.C = (D.N + kTcKC - 1) / kTcKC;
+    a.U = (Qp / kTcM) * a.GT * a.C;
+    a.P = (int)std::min<int64_t>(ctx->sm_count, a.U);
+    a.MT = (int)(((a.U + a.P - 1) / a.P + a.C - 1) / a.C + 1);
+    a.err = ctx->d_err + kErrTensorWait;
+    CDE_CUDA(cudaMallocAsync((void**)&part, (size_t)a.P * a.MT * kTcM * kTcN * sizeof(float), st));
+    CDE_CUDA(cudaMallocAsync((void**)&dpart, (size_t)a.P * a.MT * kTcM * sizeof(float), st));
+    a.part = part;
+    a.dpart = dpart;
     static bool attr = false;
     if (!attr) {
-        CDE_CUDA(cudaFuncSetAttribute(k_density<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(DensSmem)));
-        CDE_CUDA(cudaFuncSetAttribute(k_density<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(DensSmem)));
+        CDE_CUDA(cudaFuncSetAttribute(k_density_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(TcSmem)));
+        CDE_CUDA(cudaFuncSetAttribute(k_density_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(TcSmem)));
         attr = true;
     }
-    const dim3 dgrid((unsigned)qt, (unsigned)gt, (unsigned)ns);
-    if (epan) k_density<1><<<dgrid, 256, sizeof(DensSmem), st>>>(a);
-    else k_density<0><<<dgrid, 256, sizeof(DensSmem), st>>>(a);
+    if (epan) k_density_tc<1><<<a.P, kTcProd, sizeof(TcSmem), st>>>(a);
+    else k_density_tc<0><<<a.P, kTcProd, sizeof(TcSmem), st>>>(a);
     CDE_CUDA(cudaGetLastError());
     const float norm = (float)(epan ? std::exp(epan_log_norm(1)) / h2 : 1.0 / (2.5066282746310002 * h2));
-    k_density_final<<<(unsigned)((Q * G + 255) / 256), 256, 0, st>>>(num, den, (int)ns, Q, G, norm, d_f);
+    // CTAs covering one tile: at most ceil(C / per-CTA units) + 1
+    const int64_t ncta = (a.C + a.U / a.P - 1) / (a.U / a.P) + 1;
+    const int plog = ncta > 16 ? 3 : ncta > 8 ? 2 : ncta > 4 ? 1 : 0;
+    const int64_t fblocks = (Q + (8 >> plog) - 1) / (8 >> plog) * ((G + 31) / 32);
+    k_density_final<<<(unsigned)fblocks, 256, 0, st>>>(a, norm, plog, d_f, G);
     CDE_CUDA(cudaGetLastError());
     cudaFreeAsync(xq, st);
     cudaFreeAsync(mq, st);
     cudaFreeAsync(stats, st);
-    cudaFreeAsync(num, st);
-    cudaFreeAsync(den, st);
+    cudaFreeAsync(part, st);
+    cudaFreeAsync(dpart, st);
     return CDE_OK;
 }
 
@@ -463,11 +726,23 @@ extern "C" int cde_density(cde_ctx* ctx, cde_dataset ds, double h1, double h2, c
         dq = dxq;
         dg = dyg;
     }
-    if (!out_dev) CDE_CUDA(cudaMallocAsync((void**)&df, (size_t)Q * G * sizeof(float), st));
+    if (!out_dev) {
+        const int rw = workspace_reserve(ctx, 0, 64);
+        if (rw != CDE_OK) {
+            if (dxq) cudaFreeAsync(dxq, st);
+            if (dyg) cudaFreeAsync(dyg, st);
+            return rw;
+        }
+        CDE_CUDA(cudaMallocAsync((void**)&df, (size_t)Q * G * sizeof(float), st));
+    }
     int rc = density_enqueue(ctx, *D, h1, h2, dq, Q, dg, G, df, st);
     cudaError_t e = cudaSuccess;
-    if (rc == CDE_OK && !out_dev)
+    int* tw_host = static_cast<int*>(ctx->ws_host);   // pinned; the context lock is held
+    if (rc == CDE_OK && !out_dev) {
         e = cudaMemcpyAsync(f_out, df, (size_t)Q * G * sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && tw_host)
+            e = cudaMemcpyAsync(tw_host, ctx->d_err + kErrTensorWait, sizeof(int), cudaMemcpyDeviceToHost, st);
+    }
     if (dxq) cudaFreeAsync(dxq, st);
     if (dyg) cudaFreeAsync(dyg, st);
     if (!out_dev) cudaFreeAsync(df, st);
@@ -477,5 +752,9 @@ extern "C" int cde_density(cde_ctx* ctx, cde_dataset ds, double h1, double h2, c
     }
     if (rc != CDE_OK) return rc;
     if (e != cudaSuccess) return cuda_error(e, "cde_density: copy");
+    if (!out_dev && tw_host && *tw_host) {
+        cudaMemsetAsync(ctx->d_err + kErrTensorWait, 0, sizeof(int), st);
+        return set_error(CDE_ETIMEOUT, "cde_density: a tensor-core wait ran out on the device");
+    }
     return CDE_OK;
 }

@@ -35,9 +35,6 @@ namespace cde {
 __global__ void k_query_pack(const float* __restrict__ xq, int64_t Q, int64_t Qp, int d,
                              const double* __restrict__ mean, const double* __restrict__ sd,
                              float* __restrict__ out);
-__global__ void k_query_shift(const float* __restrict__ xs, int64_t N, int64_t Np, int d,
-                              const float* __restrict__ xq, int64_t Q, int64_t Qp, int64_t i_per_split,
-                              unsigned int* __restrict__ mq_bits);
 
 __device__ __forceinline__ float ex2p(float x) {
     float r;
@@ -409,20 +406,8 @@ static int prep_queries(cde_ctx* ctx, const Dataset& D, const float* d_xq, int64
     k_query_pack<<<(unsigned)((Qp + 255) / 256), 256, 0, st>>>(d_xq, Q, Qp, D.d, stats, stats + D.d, xq);
     CDE_CUDA(cudaGetLastError());
     if (D.kernel == CDE_KERNEL_GAUSS) {
-        const size_t sm = (size_t)D.d * 256 * sizeof(float);
-        if (sm > 48 * 1024)
-            CDE_CUDA(cudaFuncSetAttribute(k_query_shift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        const int64_t qb = (Q + 255) / 256;
-        const int64_t tiles = (D.N + 255) / 256;
-        int64_t sy = (4LL * ctx->sm_count + qb - 1) / qb;
-        if (sy > tiles) sy = tiles;
-        if (sy < 1) sy = 1;
-        const int64_t tps = (tiles + sy - 1) / sy;
-        sy = (tiles + tps - 1) / tps;
-        CDE_CUDA(cudaMemsetAsync(mq, 0x7f, (size_t)Q * sizeof(float), st));
-        k_query_shift<<<dim3((unsigned)qb, (unsigned)sy), 256, sm, st>>>(
-            D.xs, D.N, D.Np, D.d, xq, Q, Qp, tps * 256, reinterpret_cast<unsigned int*>(mq));
-        CDE_CUDA(cudaGetLastError());
+        const int rc = query_shift_enqueue(ctx->sm_count, D, xq, Q, Qp, mq, st);
+        if (rc != CDE_OK) return rc;
     }
     CDE_CUDA(cudaFreeAsync(stats, st));
     *xq_out = xq;

@@ -154,6 +154,49 @@ def test_density_matches_oracle(ctx, N, d, Q, G, standardize):
     cde.cde_destroy_dataset(ctx, ds)
 
 
+@pytest.mark.parametrize("N,d,Q,G,n_check", [
+    (20000, 3, 700, 300, 60),     # 6 query tiles x 2 grid tiles, segments break inside tiles
+    (3000, 33, 130, 40, 130),     # large d, one query past a tile
+    (2000, 64, 5, 16, 5),         # the largest d
+    (200000, 2, 3, 17, 3),        # every CTA on one tile: 152 partials per output
+    (37, 1, 1, 1, 1),             # one chunk, one grid point
+])
+def test_density_tiles_and_splits(ctx, N, d, Q, G, n_check):
+    """Tile, segment and split structure of the tensor-core density: sampled
+    queries (first and last included) against the oracle, and a repeated call
+    is bitwise equal (fixed-order partial sums)."""
+    x, y = synth.gmm_sine(N, d, seed=3 * N + d)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    xq = synth.query_points(x, Q, seed=Q + 7)
+    h1, h2 = 0.35 * math.sqrt(d), 0.1
+    yg = synth.y_grid(y, h2, G)
+    f = cde.cde_density(ctx, ds, h1, h2, xq, yg)
+    rows = np.unique(np.concatenate([[0, Q - 1], np.random.default_rng(1).choice(Q, min(n_check, Q), replace=False)]))
+    ref = oracle.density(x, y, h1, h2, xq[rows], yg, standardize_x=True)
+    _dens_check(f[rows], ref)
+    assert np.array_equal(cde.cde_density(ctx, ds, h1, h2, xq, yg), f)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+@pytest.mark.parametrize("d,Q", [(3, 300), (6, 1100), (12, 130)])
+def test_density_tiny_bandwidth_pins_the_shift(ctx, d, Q):
+    """h1 = 0.01 (a1 = 7,200 on standardised x): only each query's nearest
+    points carry weight, and a per-query shift m_q off by 0.02 in squared
+    distance would overflow or underflow every x factor.  d <= 8 runs the
+    split nearest-distance kernel, d = 12 the one-query-per-thread kernel."""
+    x, y = synth.gmm_sine(5000, d, seed=40 + d)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    xq = synth.query_points(x, Q, seed=41 + d)
+    h1, h2 = 0.01, 0.2
+    yg = synth.y_grid(y, h2, 64)
+    f = cde.cde_density(ctx, ds, h1, h2, xq, yg)
+    assert np.all(np.isfinite(f))
+    rows = np.unique(np.concatenate([[0, Q - 1], np.random.default_rng(2).choice(Q, min(Q, 150), replace=False)]))
+    ref = oracle.density(x, y, h1, h2, xq[rows], yg, standardize_x=True)
+    _dens_check(f[rows], ref)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
 def test_density_integrates_to_one_and_device_io(ctx):
     import torch
     x, y = synth.gmm_sine(4000, 4, seed=2)
