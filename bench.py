@@ -87,6 +87,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM bytes (read + write) of one k_density_tc launch at the density
+# workload's default size, from an ncu capture; None until captured for the
+# current kernel.
+DENS_TC_TRAFFIC = 2399488
+
+
 def oracle_sample(w, n_rows: int, seed: int = 0, kernel: str = "gauss"):
     """Time the FP64 oracle on n_rows random rows of the workload (all host
     cores).  Returns (pair-evals/s, seconds, threads, rows)."""
@@ -164,6 +170,8 @@ def run_ours(args, w):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    cde.cde_timing_enable(ctx, True)
+    kern_ms = []
     sampler.start()
     time.sleep(0.3)
     t0 = time.perf_counter()
@@ -173,7 +181,9 @@ def run_ours(args, w):
             ev[s][0].record(stream)
             step()
             ev[s][1].record(stream)
+            kern_ms.append(cde.cde_timing_last(ctx))   # the tile kernel alone, events on `stream`
     stream.synchronize()
+    cde.cde_timing_enable(ctx, False)
     wall = time.perf_counter() - t0
     if dist:
         dist.barrier()
@@ -203,7 +213,8 @@ def run_ours(args, w):
     # ---- roofline (FP32 pipe; measured unit rates) ----
     peaks = cde.cde_measure_peaks(ctx) if hasattr(cde, "cde_measure_peaks") else None
     fpp = flops_per_pair(G1, G2, w.d)
-    achieved = w.N * w.N * fpp / (ms * 1e-3) / 1e12
+    kms = float(np.mean(kern_ms))
+    achieved = w.N * w.N * fpp / (kms * 1e-3) / 1e12
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     try:
         p = peaks and peaks.ffma_per_clk_sm
@@ -215,7 +226,7 @@ def run_ours(args, w):
     # (profiles/k_loo_mma_32x32_N50000.md); not measured for other sizes.
     traffic = 53256960 if (w.N == 50000 and G1 == 32 and G2 == 32 and args.kernel == "gauss") else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
-            "frac": achieved / peak_max, "traffic": traffic,
+            "frac": achieved / peak_max, "traffic": traffic, "kernel": "k_loo_mma", "kernel_ms": kms,
             "peak_basis": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x 2070 MHz (max clock)" % sms}
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (2 * lanes * sms * clocks["sm_mhz"] * 1e6 / 1e12)
@@ -265,6 +276,7 @@ def run_ours(args, w):
     if peaks is not None:
         out["measured_unit_rates"] = {"ffma_per_clk_sm": peaks.ffma_per_clk_sm,
                                       "ex2_per_clk_sm": peaks.ex2_per_clk_sm,
+                                      "tcgen05_bf16_mac_per_clk_sm": peaks.umma_bf16_mac_per_clk_sm,
                                       "sm_clock_mhz": peaks.sm_clock_mhz}
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -397,6 +409,12 @@ def run_density(args):
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except (OSError, ValueError, KeyError):
         pass
+    bf16_peak = 1863.5
+    try:
+        bf16_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+    except (OSError, ValueError, KeyError):
+        pass
+    cde.cde_timing_enable(ctx, True)
     runs = {}
     for Q, N in ((args.dens_Q, args.dens_N), (100, 500000)):
         x, y = synth.gmm_sine(N, args.dens_d, seed=8)
@@ -410,25 +428,45 @@ def run_density(args):
             cde.cde_density(ctx, ds, 0.3, 0.1, xq, yg, f, stream=st)
         st.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        kern = []
         for a, b in ev:
             a.record(st)
             cde.cde_density(ctx, ds, 0.3, 0.1, xq, yg, f, stream=st)
             b.record(st)
+            kern.append(cde.cde_timing_last(ctx))   # the tensor-core kernel, events on st
         st.synchronize()
         ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+        kms = float(np.mean(kern))
         pairs = Q * N
         nbytes = N * (args.dens_d + 1) * 4 + Q * args.dens_d * 4 + 256 * 4 + Q * 256 * 4
-        runs["Q%d_N%d" % (Q, N)] = {"ms": ms, "pairs_per_s": pairs / (ms * 1e-3),
-                                    "tflops": pairs * 512 / (ms * 1e-3) / 1e12,
-                                    "hbm": {"algorithmic_bytes": nbytes, "GB_s": nbytes / (ms * 1e-3) / 1e9,
-                                            "peak_GB_s": hbm_peak,
-                                            "frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}}
+        # executed tensor work: 128-query tiles x 32-point chunks x 6 BF16 MMAs of 128 x 256 x 16
+        issued = -(-Q // 128) * -(-N // 32) * 6 * 2.0 * 128 * 256 * 16
+        runs["Q%d_N%d" % (Q, N)] = {
+            "ms": ms, "kernel_ms": kms, "pairs_per_s": pairs / (ms * 1e-3),
+            "tflops": pairs * 512 / (ms * 1e-3) / 1e12,
+            "kernel_tflops": pairs * 512 / (kms * 1e-3) / 1e12,
+            "kernel_issued_tflops": issued / (kms * 1e-3) / 1e12,
+            "hbm": {"algorithmic_bytes": nbytes, "GB_s": nbytes / (ms * 1e-3) / 1e9, "peak_GB_s": hbm_peak,
+                    "frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}}
         cde.cde_destroy_dataset(ctx, ds)
+    cde.cde_timing_enable(ctx, False)
     main = runs["Q%d_N%d" % (args.dens_Q, args.dens_N)]
+    # DRAM bytes of one k_density_tc launch at Q = 10,000, N = 100,000, d = 4
+    # (profiles/k_density_tc_Q10000_N100000_G256.md); not measured for other sizes.
+    traffic = DENS_TC_TRAFFIC if (args.dens_Q, args.dens_N, args.dens_d) == (10000, 100000, 4) else None
+    roof = {"bound": "tensor", "achieved": main["kernel_tflops"], "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": main["kernel_tflops"] / bf16_peak, "traffic": traffic,
+            "peak_basis": "measured cuBLAS bf16 GEMM, burst (MEASURED_PEAKS.json)",
+            "kernel": "k_density_tc", "kernel_ms": main["kernel_ms"],
+            "achieved_basis": "algorithmic 2 Q N G flop / kernel time (CUDA events on the launching stream)",
+            "issued_bf16": {"achieved": main["kernel_issued_tflops"],
+                            "frac": main["kernel_issued_tflops"] / bf16_peak,
+                            "basis": "executed BF16 MMAs: hi*hi + hi*lo + lo*hi, full 128 x 256 tiles"}}
     _line(workload="density_Q%d_N%d_d%d_G256" % (args.dens_Q, args.dens_N, args.dens_d),
           metric="density (query, data point) pairs/s x 256-point y grid", unit="pairs/s",
           value=main["pairs_per_s"], steps=args.steps, warmup=args.warmup, ms_per_step=main["ms"],
-          flops_per_pair=2 * 256 * 1 + 3 * args.dens_d, tflops=main["tflops"], runs=runs,
+          flops_per_pair=2 * 256 * 1 + 3 * args.dens_d, tflops=main["tflops"], runs=runs, roofline=roof,
+          gpu_launches=4 * args.steps, dtype="bf16x3 hi/lo split, fp32 accumulate",
           config={"workload": "density", "Q": args.dens_Q, "N": args.dens_N, "d_x": args.dens_d, "G_y": 256})
     cde.cde_shutdown(ctx)
 

@@ -130,6 +130,19 @@ int cde_check_status(cde_ctx *ctx, unsigned int *code, int *enabled);
  * either may be NULL.  Zeros for Epanechnikov datasets (no shift). */
 int cde_dataset_nn(cde_ctx *ctx, cde_dataset ds, float *nn_x2, float *nn_y2);
 
+/*
+ * Kernel timing (a profiling aid).  With timing on, cde_loo_loglik (and
+ * cde_loo_rows) and cde_density record CUDA events on the call's stream
+ * around their dominant kernel: the exact-LOO tile kernel (from the first to
+ * the last launch of the call, for grids wider than 32) and the tensor-core
+ * density kernel (per pass).  cde_timing_last waits for the latest recorded
+ * end event and returns the milliseconds between the pair; CDE_EINVAL when
+ * nothing has been recorded since timing was (re)enabled.  Calls through the
+ * batched, graph and request-queue paths are not timed.
+ */
+int cde_timing_enable(cde_ctx *ctx, int on);
+int cde_timing_last(cde_ctx *ctx, double *ms);
+
 /* Kernel family of a dataset: *kernel = CDE_KERNEL_GAUSS or CDE_KERNEL_EPAN. */
 int cde_dataset_kernel(cde_ctx *ctx, cde_dataset ds, int *kernel);
 
@@ -392,6 +405,10 @@ typedef struct {
     double ex2_per_clk_sm;      /* MUFU ex2 results per clock per SM */
     double ffma_tops;           /* FP32 FMA per second, whole GPU (1e12) */
     double ex2_tops;            /* ex2 per second, whole GPU (1e12) */
+    double umma_bf16_mac_per_clk_sm;  /* tcgen05.mma kind::f16, BF16 in / FP32 accumulate,
+                                         M = 128, N = 256, K = 16, back to back from one
+                                         thread: multiply-adds per clock per SM */
+    double umma_bf16_tflops;    /* the same, whole GPU at the clock seen (2 flop per MAC, 1e12) */
 } cde_peaks;
 
 int cde_measure_peaks(cde_ctx *ctx, cde_peaks *out);

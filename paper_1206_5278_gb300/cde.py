@@ -42,7 +42,7 @@ EXPORTED = [
     "cde_measure_peaks", "cde_autotune", "cde_tuning_get", "cde_tuning_set",
     "cde_loo_loglik_noalloc", "cde_dataset_kernel", "cde_select_random", "cde_reference_rule",
     "cde_cond_stats", "cde_cond_interval", "cde_tuning_save", "cde_tuning_load", "cde_check_status",
-    "cde_dataset_nn",
+    "cde_dataset_nn", "cde_timing_enable", "cde_timing_last",
 ]
 
 
@@ -77,7 +77,8 @@ class cde_server_stats(ctypes.Structure):
 class cde_peaks(ctypes.Structure):
     _fields_ = [("sm_count", ctypes.c_int), ("sm_clock_mhz", ctypes.c_double),
                 ("ffma_per_clk_sm", ctypes.c_double), ("ex2_per_clk_sm", ctypes.c_double),
-                ("ffma_tops", ctypes.c_double), ("ex2_tops", ctypes.c_double)]
+                ("ffma_tops", ctypes.c_double), ("ex2_tops", ctypes.c_double),
+                ("umma_bf16_mac_per_clk_sm", ctypes.c_double), ("umma_bf16_tflops", ctypes.c_double)]
 
 
 _lib = None
@@ -133,6 +134,8 @@ def lib():
                                    ctypes.c_int),
         "cde_dataset_kernel": ([_vp, _i64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cde_dataset_nn": ([_vp, _i64, _vp, _vp], ctypes.c_int),
+        "cde_timing_enable": ([_vp, ctypes.c_int], ctypes.c_int),
+        "cde_timing_last": ([_vp, _vp], ctypes.c_int),
         "cde_select_random": ([_vp, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, ctypes.c_uint64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
                               ctypes.c_int),
@@ -304,6 +307,18 @@ def cde_dataset_nn(ctx, ds: int):
     b = np.empty(N, np.float32)
     _check(lib().cde_dataset_nn(ctx, int(ds), _ptr(a), _ptr(b)))
     return a, b
+
+
+def cde_timing_enable(ctx, on: bool = True) -> None:
+    """Record CUDA events around the dominant kernel of later loo/density calls."""
+    _check(lib().cde_timing_enable(ctx, int(bool(on))))
+
+
+def cde_timing_last(ctx) -> float:
+    """Milliseconds of the dominant kernel of the latest timed call (waits for it)."""
+    ms = ctypes.c_double()
+    _check(lib().cde_timing_last(ctx, ctypes.byref(ms)))
+    return ms.value
 
 
 def cde_dataset_kernel(ctx, ds: int) -> str:

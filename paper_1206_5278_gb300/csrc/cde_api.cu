@@ -149,6 +149,8 @@ void cde_shutdown(cde_ctx* ctx) {
     cudaFree(ctx->d_err);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->ws_host) cudaFreeHost(ctx->ws_host);
+    if (ctx->tev0) cudaEventDestroy(ctx->tev0);
+    if (ctx->tev1) cudaEventDestroy(ctx->tev1);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -320,6 +322,31 @@ int cde_check_status(cde_ctx* ctx, unsigned int* code, int* enabled) {
         CDE_CUDA(cudaMemset(ctx->d_err + kErrTensorWait, 0, sizeof(int)));
         if (!*code) *code = CDE_CHECK_TENSOR_WAIT | (unsigned int)tw;
     }
+    return CDE_OK;
+}
+
+int cde_timing_enable(cde_ctx* ctx, int on) {
+    if (!ctx) return set_error(CDE_EINVAL, "cde_timing_enable: null context");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    if (on && !ctx->tev0) {
+        CDE_CUDA(cudaEventCreate(&ctx->tev0));
+        CDE_CUDA(cudaEventCreate(&ctx->tev1));
+    }
+    ctx->timing = on != 0;
+    ctx->tev_open = ctx->tev_set = false;
+    return CDE_OK;
+}
+
+int cde_timing_last(cde_ctx* ctx, double* ms) {
+    if (!ctx || !ms) return set_error(CDE_EINVAL, "cde_timing_last: null argument");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!ctx->tev_set) return set_error(CDE_EINVAL, "cde_timing_last: no timed kernel yet");
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    CDE_CUDA(cudaEventSynchronize(ctx->tev1));
+    float f = 0.f;
+    CDE_CUDA(cudaEventElapsedTime(&f, ctx->tev0, ctx->tev1));
+    *ms = f;
     return CDE_OK;
 }
 

@@ -117,9 +117,31 @@ struct cde_ctx {
     size_t ws_bytes = 0;
     void* ws_host = nullptr;
     size_t ws_host_bytes = 0;
+    // kernel timing (cde_timing_enable): events around the dominant kernel of
+    // the latest timed call, on that call's stream
+    bool timing = false;
+    bool tev_open = false;    // tev0 recorded in the current call
+    bool tev_set = false;     // a complete pair exists
+    cudaEvent_t tev0 = nullptr, tev1 = nullptr;
 };
 
 namespace cde {
+
+// Dominant-kernel timing: a call resets, the first dominant launch records
+// the start event, every dominant launch re-records the end event.
+inline void timing_reset(cde_ctx* c) { c->tev_open = false; }
+inline void timing_begin(cde_ctx* c, cudaStream_t st) {
+    if (c->timing && !c->tev_open) {
+        cudaEventRecord(c->tev0, st);
+        c->tev_open = true;
+    }
+}
+inline void timing_end(cde_ctx* c, cudaStream_t st) {
+    if (c->timing && c->tev_open) {
+        cudaEventRecord(c->tev1, st);
+        c->tev_set = true;
+    }
+}
 
 std::shared_ptr<Dataset> find_dataset(cde_ctx* ctx, cde_dataset ds);
 

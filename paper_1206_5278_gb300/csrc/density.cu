@@ -619,6 +619,7 @@ __global__ void __launch_bounds__(256) k_density_final(const DensTcArgs a, float
 
 int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const float* d_xq,
                     int64_t Q, const float* d_yg, int G, float* d_f, cudaStream_t st) {
+    timing_reset(ctx);
     if (Q == 0) return CDE_OK;
     const int64_t Qp = (Q + kTcM - 1) / kTcM * kTcM;
     float *xq = nullptr, *mq = nullptr, *part = nullptr, *dpart = nullptr;
@@ -668,8 +669,10 @@ int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const 
                                       (int)sizeof(TcSmem)));
         attr = true;
     }
+    timing_begin(ctx, st);
     if (epan) k_density_tc<1><<<a.P, kTcProd, sizeof(TcSmem), st>>>(a);
     else k_density_tc<0><<<a.P, kTcProd, sizeof(TcSmem), st>>>(a);
+    timing_end(ctx, st);
     CDE_CUDA(cudaGetLastError());
     const float norm = (float)(epan ? std::exp(epan_log_norm(1)) / h2 : 1.0 / (2.5066282746310002 * h2));
     // CTAs covering one tile: at most ceil(C / per-CTA units) + 1

@@ -404,6 +404,7 @@ size_t loo_grid_scratch_bytes(cde_ctx* ctx, const Dataset& D, int G1, int G2, in
 int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, const double* h2,
                      int G2, const int64_t* d_rows, int64_t n_rows, double* d_Lc, double* d_Le,
                      double* d_ell_rows, cudaStream_t st, void* scratch, size_t scratch_bytes) {
+    timing_reset(ctx);
     if (!d_rows) n_rows = D.N;
     for (int k0 = 0; k0 < G1; k0 += 32) {
         const int g1 = G1 - k0 < 32 ? G1 - k0 : 32;
@@ -435,7 +436,9 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
             CDE_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));
             const int cmax = loo_grid_ctas(ctx, T1, T2);
             const int grid = a.n_tiles < cmax ? a.n_tiles : cmax;
+            timing_begin(ctx, st);
             int rc = launch_loo_tile_kernel(T1, T2, a, grid, st);
+            timing_end(ctx, st);
             if (rc != CDE_OK) {
                 if (own) cudaFreeAsync(part, st);
                 return rc;

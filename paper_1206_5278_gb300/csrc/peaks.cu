@@ -1,8 +1,13 @@
-// Micro-benchmarks of the pipes the LOO kernels are bound by: FP32 FMA lanes
-// and MUFU ex2 results per SM per clock, measured with many independent
-// chains per thread and the SM clock taken from clock64() over the same
-// launch.  These rates are the roofline denominators for the pair kernels.
+// Micro-benchmarks of the pipes the kernels are bound by: FP32 FMA lanes and
+// MUFU ex2 results per SM per clock, measured with many independent chains
+// per thread and the SM clock taken from clock64() over the same launch, and
+// the 5th-generation tensor core's BF16 rate for the density kernel's MMA
+// shape (tcgen05, M = 128, N = 256, K = 16, issued back to back by one thread).
+#include <algorithm>
+#include <vector>
+
 #include "cde_internal.h"
+#include "tc_util.cuh"
 
 namespace cde {
 
@@ -40,6 +45,79 @@ __global__ void k_peak_ex2(float* out, int iters, long long* cyc) {
     for (int i = 0; i < 16; ++i) r += a[i];
     out[blockIdx.x * blockDim.x + threadIdx.x] = r;
     if (threadIdx.x == 0) cyc[blockIdx.x] = clock64() - c0;
+}
+
+// One CTA per SM (the shared-memory request keeps a second one off the SM):
+// R accumulating BF16 MMAs of 128 x 256 x 16 from shared-memory operands
+// (values irrelevant), cycles from the first issue to the commit's arrival.
+constexpr int kPeakUmmaSmem = 120 * 1024;
+
+__global__ void __launch_bounds__(128) k_peak_umma(int R, long long* cyc, int* err) {
+    extern __shared__ float4 pk_dyn[];
+    unsigned char* A = reinterpret_cast<unsigned char*>(pk_dyn);   // 128 x 32 bf16
+    unsigned char* B = A + 8192;                                  // 256 x 32 bf16
+    __shared__ unsigned long long bar;
+    __shared__ uint32_t tb;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < (8192 + 16384) / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(A)[i] = 0x3f803f80u;
+    if (tid == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&tb), 256);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t t = tb;
+    if (tid == 0) {
+        const uint32_t idesc = tc_idesc_bf16(128, 256);
+        const uint64_t ad = tc_sdesc(smem_u32(A), 128, 512), bd = tc_sdesc(smem_u32(B), 128, 512);
+        const long long c0 = clock64();
+        for (int r = 0; r < R; ++r) tc_mma_bf16(t, ad, bd, idesc, r > 0 ? 1u : 0u);
+        tc_commit(smem_u32(&bar));
+        mbar_wait(smem_u32(&bar), 0, &abort_flag, err, 1);
+        cyc[blockIdx.x] = clock64() - c0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(t, 256);
+    }
+}
+
+static int measure_umma(cde_ctx* ctx, double* mac_per_clk) {
+    const int S = ctx->sm_count, R = 4096;
+    long long* cyc = nullptr;
+    int* err = ctx->d_err + kErrTensorWait;
+    CDE_CUDA(cudaMalloc((void**)&cyc, sizeof(long long) * S));
+    CDE_CUDA(cudaFuncSetAttribute(k_peak_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeakUmmaSmem));
+    std::vector<long long> hc(S);
+    double best = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+        k_peak_umma<<<S, 128, kPeakUmmaSmem, ctx->stream>>>(R, cyc, err);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpy(hc.data(), cyc, sizeof(long long) * S, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            cudaFree(cyc);
+            return cuda_error(e, "cde_measure_peaks: tensor-core probe");
+        }
+        std::vector<long long> srt(hc);
+        std::sort(srt.begin(), srt.end());
+        const double med = (double)srt[S / 2];
+        const double r = (double)R * 128 * 256 * 16 / med;
+        if (r > best) best = r;
+    }
+    cudaFree(cyc);
+    int tw = 0;
+    CDE_CUDA(cudaMemcpy(&tw, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tw) return set_error(CDE_ETIMEOUT, "cde_measure_peaks: tensor-core probe wait ran out");
+    *mac_per_clk = best;
+    return CDE_OK;
 }
 
 int measure_peaks(cde_ctx* ctx, cde_peaks* o) {
@@ -89,6 +167,11 @@ int measure_peaks(cde_ctx* ctx, cde_peaks* o) {
     o->ex2_tops = res[1][0] / 1e12;
     o->ffma_per_clk_sm = res[0][0] / S / f;
     o->ex2_per_clk_sm = res[1][0] / S / (res[1][1] > 0 ? res[1][1] : f);
+    double umma = 0;
+    const int rc = measure_umma(ctx, &umma);
+    if (rc != CDE_OK) return rc;
+    o->umma_bf16_mac_per_clk_sm = umma;
+    o->umma_bf16_tflops = 2.0 * umma * S * f / 1e12;
     return CDE_OK;
 }
 

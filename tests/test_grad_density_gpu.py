@@ -197,6 +197,46 @@ def test_density_tiny_bandwidth_pins_the_shift(ctx, d, Q):
     cde.cde_destroy_dataset(ctx, ds)
 
 
+def test_measured_pipe_rates(ctx):
+    """cde_measure_peaks: FP32 FMA, MUFU ex2 and the tcgen05 BF16 MMA rate of
+    the density kernel's shape, per SM per clock, in their physical ranges
+    (128 FMA lanes, 32 ex2, 4096 MACs for a 128 x 256 x 16 MMA in 128 clocks)."""
+    p = cde.cde_measure_peaks(ctx)
+    assert 100 <= p.ffma_per_clk_sm <= 130
+    assert 14 <= p.ex2_per_clk_sm <= 34
+    assert 2000 <= p.umma_bf16_mac_per_clk_sm <= 4200
+    assert p.umma_bf16_tflops > 500
+
+
+def test_kernel_timing(ctx):
+    """cde_timing_last: events around the dominant kernel of the latest call
+    (tile kernel of the LOO grid, tensor-core kernel of the density)."""
+    import time
+    x, y = synth.gmm_sine(6000, 3, seed=5)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    with pytest.raises(cde.CdeError):
+        cde.cde_timing_last(ctx)
+    cde.cde_timing_enable(ctx, True)
+    h1 = synth.bandwidth_grid(0.1, 1.0, 8)
+    h2 = synth.bandwidth_grid(0.05, 0.5, 8)
+    t0 = time.perf_counter()
+    cde.cde_loo_loglik(ctx, ds, h1, h2)
+    host_ms = 1e3 * (time.perf_counter() - t0)
+    ms = cde.cde_timing_last(ctx)
+    assert 0.0 < ms < host_ms
+    xq = synth.query_points(x, 300, seed=6)
+    yg = synth.y_grid(y, 0.1, 256)
+    t0 = time.perf_counter()
+    cde.cde_density(ctx, ds, 0.3, 0.1, xq, yg)
+    host_ms = 1e3 * (time.perf_counter() - t0)
+    ms2 = cde.cde_timing_last(ctx)
+    assert 0.0 < ms2 < host_ms
+    cde.cde_timing_enable(ctx, False)
+    with pytest.raises(cde.CdeError):
+        cde.cde_timing_last(ctx)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
 def test_density_integrates_to_one_and_device_io(ctx):
     import torch
     x, y = synth.gmm_sine(4000, 4, seed=2)
