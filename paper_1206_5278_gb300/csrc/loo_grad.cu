@@ -48,6 +48,8 @@ struct GradArgs {
     float a1, a2;          // Gaussian log2(e)/(2 h^2); Epanechnikov 1/h^2
     int64_t i_per_split;   // multiple of the tile
     float* part;           // [n_split][N][6]
+    const uint32_t* xsplit;   // d >= 16: TF32 hi rows [Np][DK + 4], then lo rows (k_grad_split)
+    const float* xnorm;       // d >= 16: |x_i|^2 [Np]
 };
 
 constexpr int kGradThreads = 128;
@@ -116,8 +118,45 @@ __device__ __forceinline__ void grad_accumulate(bool ok, float dx2, float dy2, f
     SAy = fmaf(v, dy2, SAy);
 }
 
+// Two rows' contributions from one point through the packed FP32x2 pipe (rows
+// in .x and .y).  Every lane rounds exactly as grad_accumulate's scalar
+// operations (nmx = -m_x, na = -a), so the sums are bitwise those of the
+// one-row form.
+template <int KERN>
+__device__ __forceinline__ void grad_accumulate2(bool ok0, bool ok1, float2 dx2, float2 dy2, float2 nmx,
+                                                 float2 nmy, float a1, float a2, float2& SA, float2& SAx,
+                                                 float2& SAy, float2& SB, float2& SBx) {
+    if constexpr (KERN == 1) {
+        const float2 u = make_float2(ok0 ? fma_sat_g(-a1, dx2.x, 1.f) : 0.f, ok1 ? fma_sat_g(-a1, dx2.y, 1.f) : 0.f);
+        const float2 w = make_float2(fma_sat_g(-a2, dy2.x, 1.f), fma_sat_g(-a2, dy2.y, 1.f));
+        const float ta1 = 2.f * a1, ta2 = 2.f * a2;
+        const float2 vx = __fmul2_rn(make_float2(ta1, ta1), dx2), zy = __fmul2_rn(make_float2(ta2, ta2), dy2);
+        const float2 v = make_float2(u.x > 0.f ? vx.x : 0.f, u.y > 0.f ? vx.y : 0.f);
+        const float2 z = make_float2(w.x > 0.f ? zy.x : 0.f, w.y > 0.f ? zy.y : 0.f);
+        SA = __ffma2_rn(u, w, SA);
+        SAx = __ffma2_rn(v, w, SAx);
+        SAy = __ffma2_rn(u, z, SAy);
+        SB = __fadd2_rn(SB, u);
+        SBx = __fadd2_rn(SBx, v);
+        return;
+    }
+    const float2 au = __fmul2_rn(__fadd2_rn(dx2, nmx), make_float2(-a1, -a1));   // -a1 (dx2 - m_x)
+    const float2 aw = __fmul2_rn(__fadd2_rn(dy2, nmy), make_float2(-a2, -a2));   // -a2 (dy2 - m_y)
+    const float2 u = make_float2(ok0 ? ex2g(au.x) : 0.f, ok1 ? ex2g(au.y) : 0.f);
+    const float2 v = __fmul2_rn(u, make_float2(ex2g(aw.x), ex2g(aw.y)));
+    SB = __fadd2_rn(SB, u);
+    SBx = __ffma2_rn(u, dx2, SBx);
+    SA = __fadd2_rn(SA, v);
+    SAx = __ffma2_rn(v, dx2, SAx);
+    SAy = __ffma2_rn(v, dy2, SAy);
+}
+
+// d < 16: JB rows per thread (processed as JB / 2 packed pairs), points
+// point-major in shared memory (128-bit broadcast loads), 32-bit index masks.
 template <int JB, int DREG, int KERN>
 __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
+    static_assert(JB % 2 == 0, "rows go through the packed pipe in pairs");
+    constexpr int JP = JB / 2;
     __shared__ __align__(16) float xt[kGradThreads][DREG];  // point-major: 128-bit broadcast loads
     __shared__ float yt[kGradThreads];
     const int tid = threadIdx.x;
@@ -125,22 +164,26 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
     const int64_t i0 = (int64_t)blockIdx.y * g.i_per_split;
     const int64_t i1 = min(g.N, i0 + g.i_per_split);
     const int d = g.d;
-    float xj[JB][DREG], yj[JB], mxj[JB], myj[JB];
-    float SA[JB], SAx[JB], SAy[JB], SB[JB], SBx[JB];
-    int64_t jj[JB];
+    float2 xj[JP][DREG], yj[JP], nmx[JP], nmy[JP];
+    float2 SA[JP], SAx[JP], SAy[JP], SB[JP], SBx[JP];
+    int jj[JB];
 #pragma unroll
     for (int b = 0; b < JB; ++b) {
         const int64_t j = jbase + (int64_t)b * kGradThreads;
         const int64_t jc = j < g.N ? j : 0;
-        jj[b] = j;
+        jj[b] = (int)j;   // N < 2^31
+        const int p = b >> 1;
+        float* xr = reinterpret_cast<float*>(&xj[p][0]) + (b & 1);
 #pragma unroll
-        for (int c = 0; c < DREG; ++c) xj[b][c] = c < d ? g.xs[(int64_t)c * g.Np + jc] : 0.f;
-        yj[b] = g.y[jc];
-        mxj[b] = g.mx[jc];
-        myj[b] = g.my[jc];
-        SA[b] = SAx[b] = SAy[b] = SB[b] = SBx[b] = 0.f;
+        for (int c = 0; c < DREG; ++c) xr[2 * c] = c < d ? g.xs[(int64_t)c * g.Np + jc] : 0.f;
+        reinterpret_cast<float*>(&yj[p])[b & 1] = g.y[jc];
+        reinterpret_cast<float*>(&nmx[p])[b & 1] = -g.mx[jc];
+        reinterpret_cast<float*>(&nmy[p])[b & 1] = -g.my[jc];
     }
+#pragma unroll
+    for (int p = 0; p < JP; ++p) SA[p] = SAx[p] = SAy[p] = SB[p] = SBx[p] = make_float2(0.f, 0.f);
     const float a1 = g.a1, a2 = g.a2;
+    const float2 m1 = make_float2(-1.f, -1.f);
     for (int64_t t0 = i0; t0 < i1; t0 += kGradThreads) {
         __syncthreads();
         const int64_t it = CDE_CK(t0 + tid, g.Np, 401);  // < Np: i_per_split and Np are multiples of 128
@@ -162,30 +205,34 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
             }
             const float yi = yt[t];
 #pragma unroll
-            for (int b = 0; b < JB; ++b) {
-                float dx2 = 0.f;
+            for (int p = 0; p < JP; ++p) {
+                // x_j - x_i as fma(x_i, -1, x_j): the scalar subtraction's rounding
+                float2 dx2 = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < DREG; ++c) {
-                    const float q = xj[b][c] - xi[c];
-                    dx2 = fmaf(q, q, dx2);
+                    const float2 q = __ffma2_rn(make_float2(xi[c], xi[c]), m1, xj[p][c]);
+                    dx2 = __ffma2_rn(q, q, dx2);
                 }
-                const float dy = yj[b] - yi;
-                const float dy2 = dy * dy;
-                grad_accumulate<KERN>(i32 != (int)jj[b], dx2, dy2, mxj[b], myj[b], a1, a2, SA[b], SAx[b],
-                                      SAy[b], SB[b], SBx[b]);
+                const float2 dy = __ffma2_rn(make_float2(yi, yi), m1, yj[p]);
+                const float2 dy2 = __fmul2_rn(dy, dy);
+                grad_accumulate2<KERN>(i32 != jj[2 * p], i32 != jj[2 * p + 1], dx2, dy2, nmx[p], nmy[p], a1, a2,
+                                       SA[p], SAx[p], SAy[p], SB[p], SBx[p]);
             }
         }
     }
 #pragma unroll
     for (int b = 0; b < JB; ++b) {
-        if (jj[b] >= g.N) continue;
-        float* p = g.part + ((int64_t)blockIdx.y * g.N + jj[b]) * 6;
-        p[0] = 0.f;  // no running shift on this path
-        p[1] = SA[b];
-        p[2] = SAx[b];
-        p[3] = SAy[b];
-        p[4] = SB[b];
-        p[5] = SBx[b];
+        const int64_t j = jbase + (int64_t)b * kGradThreads;
+        if (j >= g.N) continue;
+        const int p = b >> 1;
+        float* q = g.part + ((int64_t)blockIdx.y * g.N + j) * 6;
+        const auto pick = [b](float2 v) { return (b & 1) ? v.y : v.x; };
+        q[0] = 0.f;  // no running shift on this path
+        q[1] = pick(SA[p]);
+        q[2] = pick(SAx[p]);
+        q[3] = pick(SAy[p]);
+        q[4] = pick(SB[p]);
+        q[5] = pick(SBx[p]);
     }
 }
 
@@ -194,8 +241,10 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
 // n_j + n_i - 2 x_j.x_i with the dot products of a 16-row x 8-point tile from
 // m16n8k8 TF32 MMAs on split operands (x = hi + lo, products hi*hi + hi*lo +
 // lo*hi, FP32 accumulation), norms n in FP32, the result clamped at 0.  Each
-// warp owns 16 rows (their split fragments stay in registers); the CTA stages
-// 64 points at a time, already split, in shared memory.
+// warp owns 16 rows (their split fragments stay in registers); the CTA copies
+// 64 points at a time, split once per call by k_grad_split, into shared
+// memory, and handles each row's two points per accumulator lane pair with
+// packed FP32x2 arithmetic.
 // ---------------------------------------------------------------------------
 constexpr int kGMWarps = 4, kGMTile = 64;
 
@@ -211,66 +260,127 @@ __device__ __forceinline__ void mma_tf32_g(float (&d)[4], const uint32_t (&a)[4]
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Once per call: every point's x split into TF32 hi + lo, as rows of DK + 4
+// words (the padded shared-memory row of the tile kernel, so a 64-point tile
+// is one contiguous block to copy), and its squared norm (FP32, dimension 0
+// first).  A block handles 32 points: coalesced reads of each x row, then the
+// 32 consecutive padded rows written out contiguously.
+template <int DK>
+__global__ void __launch_bounds__(256) k_grad_split(const float* __restrict__ xs, int64_t Np, int d,
+                                                    uint32_t* __restrict__ xsplit, float* __restrict__ xnorm) {
+    constexpr int RS = DK + 4;
+    __shared__ float v[32][RS];
+    const int64_t p0 = (int64_t)blockIdx.x * 32;
+    for (int e = threadIdx.x; e < 32 * RS; e += 256) {
+        const int c = e / 32, pp = e % 32;
+        v[pp][c] = c < d ? xs[(int64_t)c * Np + p0 + pp] : 0.f;   // p0 + pp < Np (Np a multiple of 256)
+    }
+    __syncthreads();
+    uint32_t* hi = xsplit + p0 * RS;
+    uint32_t* lo = xsplit + Np * RS + p0 * RS;
+    for (int e = threadIdx.x; e < 32 * RS; e += 256) {
+        const float x = v[e / RS][e % RS];
+        const uint32_t h = __float_as_uint(x) & 0xffffe000u;
+        hi[e] = h;
+        lo[e] = __float_as_uint(x - __uint_as_float(h));
+    }
+    if (threadIdx.x < 32) {
+        float n = 0.f;
+        for (int c = 0; c < d; ++c) n = fmaf(v[threadIdx.x][c], v[threadIdx.x][c], n);
+        xnorm[p0 + threadIdx.x] = n;
+    }
+}
+
+// Two adjacent points' contributions to one row (the row's shifts in both
+// lanes) through the packed FP32x2 pipe; same operations per lane as
+// grad_accumulate.
+template <int KERN>
+__device__ __forceinline__ void grad_accumulate_pts(bool ok0, bool ok1, float2 dx2, float2 dy2, float mx, float my,
+                                                    float a1, float a2, float2& SA, float2& SAx, float2& SAy,
+                                                    float2& SB, float2& SBx) {
+    grad_accumulate2<KERN>(ok0, ok1, dx2, dy2, make_float2(-mx, -mx), make_float2(-my, -my), a1, a2, SA, SAx, SAy,
+                           SB, SBx);
+}
+
+// shared memory of one tile buffer: split rows hi, lo, then norms and y
+template <int DK>
+__host__ __device__ constexpr int grad_mma_buf_words() { return 2 * kGMTile * (DK + 4) + 2 * kGMTile; }
+
+__device__ __forceinline__ void cp_async16_g(uint32_t* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+// Start copying tile t0's split rows, norms and y into buffer `buf` (one
+// commit group per thread).
+template <int DK>
+__device__ __forceinline__ void grad_mma_fetch(const GradArgs& g, uint32_t* buf, int64_t t0) {
+    constexpr int RS = DK + 4;
+    const int tid = threadIdx.x;
+    const uint32_t* sh = g.xsplit + CDE_CK(t0, g.Np, 402) * RS;   // kGMTile * RS contiguous words
+    const uint32_t* sl = g.xsplit + (g.Np + t0) * RS;
+    for (int e = tid; e < kGMTile * RS / 4; e += kGMWarps * 32) {
+        cp_async16_g(buf + 4 * e, sh + 4 * e);
+        cp_async16_g(buf + kGMTile * RS + 4 * e, sl + 4 * e);
+    }
+    if (tid < kGMTile / 4) {
+        cp_async16_g(buf + 2 * kGMTile * RS + 4 * tid, g.xnorm + t0 + 4 * tid);
+        cp_async16_g(buf + 2 * kGMTile * RS + kGMTile + 4 * tid, g.y + t0 + 4 * tid);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <int DK, int KERN>
 __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g) {
     constexpr int KK = DK / 8, RS = DK + 4;  // padded smem row (bank spread)
-    __shared__ uint32_t xh[kGMTile * RS], xl[kGMTile * RS];
-    __shared__ float ni_s[kGMTile], yi_s[kGMTile];
+    extern __shared__ float4 gm_dyn[];      // two tile buffers (the next tile is copied during this one)
+    uint32_t* const bufs = reinterpret_cast<uint32_t*>(gm_dyn);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gq = lane >> 2, t = lane & 3;
-    const int d = g.d;
     const int64_t N = g.N, Np = g.Np;
     const int64_t i0 = (int64_t)blockIdx.y * g.i_per_split;
     const int64_t i1 = min(N, i0 + g.i_per_split);
-    int64_t jr[2];
+    int jr[2];
     float nj[2], yj[2], mxj[2], myj[2];
     uint32_t ah[KK][4], al[KK][4];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int64_t j = (int64_t)blockIdx.x * (kGMWarps * 16) + warp * 16 + gq + 8 * h;
-        jr[h] = j;
+        jr[h] = (int)j;   // N < 2^31
         const int64_t jc = j < N ? j : 0;
-        float n = 0.f;
-        for (int c = 0; c < d; ++c) {
-            const float v = g.xs[(int64_t)c * Np + jc];
-            n = fmaf(v, v, n);
-        }
-        nj[h] = n;
+        nj[h] = g.xnorm[jc];
         yj[h] = g.y[jc];
         mxj[h] = g.mx[jc];
         myj[h] = g.my[jc];
 #pragma unroll
         for (int kk = 0; kk < KK; ++kk) {
             const int c0 = 8 * kk + t, c1 = c0 + 4;
-            const float v0 = c0 < d ? g.xs[(int64_t)c0 * Np + jc] : 0.f;
-            const float v1 = c1 < d ? g.xs[(int64_t)c1 * Np + jc] : 0.f;
-            split_tf32_g(v0, ah[kk][h], al[kk][h]);        // a0 / a1: (row g [+8], k t)
-            split_tf32_g(v1, ah[kk][2 + h], al[kk][2 + h]); // a2 / a3: (row g [+8], k t+4)
+            ah[kk][h] = g.xsplit[jc * RS + c0];                 // a0 / a1: (row g [+8], k t)
+            al[kk][h] = g.xsplit[(Np + jc) * RS + c0];
+            ah[kk][2 + h] = g.xsplit[jc * RS + c1];             // a2 / a3: (row g [+8], k t+4)
+            al[kk][2 + h] = g.xsplit[(Np + jc) * RS + c1];
         }
     }
     const float a1 = g.a1, a2 = g.a2;
-    float SA[2] = {0, 0}, SAx[2] = {0, 0}, SAy[2] = {0, 0}, SB[2] = {0, 0},
-          SBx[2] = {0, 0};
+    float2 SA[2], SAx[2], SAy[2], SB[2], SBx[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) SA[h] = SAx[h] = SAy[h] = SB[h] = SBx[h] = make_float2(0.f, 0.f);
+    const float2 m1 = make_float2(-1.f, -1.f);
+    if (i0 < i1) grad_mma_fetch<DK>(g, bufs, i0);
+    int cur = 0;
     for (int64_t t0 = i0; t0 < i1; t0 += kGMTile) {
+        // the next tile into the other buffer (its last readers passed the previous barrier)
+        if (t0 + kGMTile < i1) grad_mma_fetch<DK>(g, bufs + (cur ^ 1) * grad_mma_buf_words<DK>(), t0 + kGMTile);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's copies
         __syncthreads();
-        for (int e = tid; e < DK * kGMTile; e += kGMWarps * 32) {
-            const int c = e / kGMTile, p = e - c * kGMTile;
-            const float v = c < d ? g.xs[(int64_t)c * Np + CDE_CK(t0 + p, Np, 402)] : 0.f;  // t0 + p < Np
-            uint32_t hv, lv;
-            split_tf32_g(v, hv, lv);
-            xh[p * RS + c] = hv;
-            xl[p * RS + c] = lv;
-        }
-        if (tid < kGMTile) {
-            float n = 0.f;
-            for (int c = 0; c < d; ++c) {
-                const float v = g.xs[(int64_t)c * Np + t0 + tid];
-                n = fmaf(v, v, n);
-            }
-            ni_s[tid] = n;
-            yi_s[tid] = g.y[t0 + tid];
-        }
-        __syncthreads();
+        const uint32_t* xh = bufs + cur * grad_mma_buf_words<DK>();
+        const uint32_t* xl = xh + kGMTile * RS;
+        const float* ni_s = reinterpret_cast<const float*>(xl + kGMTile * RS);
+        const float* yi_s = ni_s + kGMTile;
+        const int n_in = (int)min((int64_t)kGMTile, i1 - t0);   // points of the tile inside the split
+        const int t032 = (int)t0;
         // 4 n-tiles (32 points) at a time: independent accumulators hide the MMA latency
 #pragma unroll 1
         for (int n4 = 0; n4 < kGMTile / 32; ++n4) {
@@ -288,23 +398,34 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
                     mma_tf32_g(D[n], al[kk], bh0, bh1);
                 }
             }
+            // accumulator (row g [+8], points 2t, 2t + 1): a packed pair per row
 #pragma unroll
-            for (int n = 0; n < 4; ++n)
+            for (int n = 0; n < 4; ++n) {
+                const int p = 32 * n4 + 8 * n + 2 * t;
+                const float2 nip = *reinterpret_cast<const float2*>(&ni_s[p]);
+                const float2 yip = *reinterpret_cast<const float2*>(&yi_s[p]);
+                const int ia = t032 + p;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int h = q >> 1, p = 32 * n4 + 8 * n + 2 * t + (q & 1);
-                    const int64_t i = t0 + p;
-                    const float dx2 = fmaxf(nj[h] + ni_s[p] - 2.f * D[n][q], 0.f);
-                    const float dy = yj[h] - yi_s[p];
-                    grad_accumulate<KERN>(i < i1 && i != jr[h], dx2, dy * dy, mxj[h], myj[h], a1, a2,
-                                          SA[h], SAx[h], SAy[h], SB[h], SBx[h]);
+                for (int h = 0; h < 2; ++h) {
+                    const float2 dd = make_float2(D[n][2 * h], D[n][2 * h + 1]);
+                    // n_j + n_i - 2 dot, clamped at 0
+                    const float2 s = __ffma2_rn(dd, make_float2(-2.f, -2.f), __fadd2_rn(make_float2(nj[h], nj[h]), nip));
+                    const float2 dx2 = make_float2(fmaxf(s.x, 0.f), fmaxf(s.y, 0.f));
+                    const float2 dy = __ffma2_rn(yip, m1, make_float2(yj[h], yj[h]));
+                    const float2 dy2 = __fmul2_rn(dy, dy);
+                    grad_accumulate_pts<KERN>(p < n_in && ia != jr[h], p + 1 < n_in && ia + 1 != jr[h], dx2, dy2,
+                                              mxj[h], myj[h], a1, a2, SA[h], SAx[h], SAy[h], SB[h], SBx[h]);
                 }
+            }
         }
+        __syncthreads();   // every warp is done with this buffer before it is refilled
+        cur ^= 1;
     }
-    // combine the 4 lanes that share a row (t = 0..3), fixed xor order
+    // combine the two point lanes, then the 4 lanes that share a row (t = 0..3), fixed order
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        float v[5] = {SA[h], SAx[h], SAy[h], SB[h], SBx[h]};
+        float v[5] = {SA[h].x + SA[h].y, SAx[h].x + SAx[h].y, SAy[h].x + SAy[h].y, SB[h].x + SB[h].y,
+                      SBx[h].x + SBx[h].y};
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             v[q] += __shfl_xor_sync(0xffffffffu, v[q], 1);
@@ -459,9 +580,17 @@ static void launch_grad(const GradArgs& g, dim3 grid, cudaStream_t st, bool epan
 }
 
 template <int DK>
-static void launch_grad_mma(const GradArgs& g, dim3 grid, cudaStream_t st, bool epan) {
-    if (epan) k_loo_grad_mma<DK, 1><<<grid, kGMWarps * 32, 0, st>>>(g);
-    else k_loo_grad_mma<DK, 0><<<grid, kGMWarps * 32, 0, st>>>(g);
+static int launch_grad_mma(const GradArgs& g, dim3 grid, cudaStream_t st, bool epan) {
+    const size_t smem = (size_t)2 * grad_mma_buf_words<DK>() * sizeof(uint32_t);
+    static bool attr = false;   // per instantiation; guarded by the ctx lock
+    if (!attr) {
+        CDE_CUDA(cudaFuncSetAttribute(k_loo_grad_mma<DK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CDE_CUDA(cudaFuncSetAttribute(k_loo_grad_mma<DK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    if (epan) k_loo_grad_mma<DK, 1><<<grid, kGMWarps * 32, smem, st>>>(g);
+    else k_loo_grad_mma<DK, 0><<<grid, kGMWarps * 32, smem, st>>>(g);
+    return CDE_OK;
 }
 
 int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, double* d_out3,
@@ -502,10 +631,23 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     if (!rowv) CDE_CUDA(cudaMallocAsync((void**)&rowv, (size_t)D.N * 3 * sizeof(double), st));
     g.part = part;
     dim3 grid((unsigned)gx, (unsigned)ns);
+    uint32_t* xsplit = nullptr;
+    float* xnorm = nullptr;
     if (tc) {
-        if (D.d <= 16) launch_grad_mma<16>(g, grid, st, epan);
-        else if (D.d <= 32) launch_grad_mma<32>(g, grid, st, epan);
-        else launch_grad_mma<64>(g, grid, st, epan);
+        const int DK = D.d <= 16 ? 16 : D.d <= 32 ? 32 : 64;
+        CDE_CUDA(cudaMallocAsync((void**)&xsplit, (size_t)2 * D.Np * (DK + 4) * sizeof(uint32_t), st));
+        CDE_CUDA(cudaMallocAsync((void**)&xnorm, (size_t)D.Np * sizeof(float), st));
+        g.xsplit = xsplit;
+        g.xnorm = xnorm;
+        const unsigned sb = (unsigned)(D.Np / 32);
+        if (DK == 16) k_grad_split<16><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
+        else if (DK == 32) k_grad_split<32><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
+        else k_grad_split<64><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
+        CDE_CUDA(cudaGetLastError());
+        const int rl = DK == 16 ? launch_grad_mma<16>(g, grid, st, epan)
+                       : DK == 32 ? launch_grad_mma<32>(g, grid, st, epan)
+                                  : launch_grad_mma<64>(g, grid, st, epan);
+        if (rl != CDE_OK) return rl;
     } else if (DREG == 4) launch_grad<4, 4>(g, grid, st, epan);
     else if (DREG == 8) launch_grad<4, 8>(g, grid, st, epan);
     else launch_grad<2, 16>(g, grid, st, epan);
@@ -524,6 +666,8 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     }
     CDE_CUDA(cudaFreeAsync(part, st));
     CDE_CUDA(cudaFreeAsync(fb, st));
+    if (xsplit) CDE_CUDA(cudaFreeAsync(xsplit, st));
+    if (xnorm) CDE_CUDA(cudaFreeAsync(xnorm, st));
     if (!d_rowv_ext) CDE_CUDA(cudaFreeAsync(rowv, st));
     return CDE_OK;
 }
