@@ -305,6 +305,46 @@ def _line(**kw):
     print(json.dumps(base), flush=True)
 
 
+def _alu_roof(lane_ops_per_unit, units, kernel_ms, kernel, basis):
+    """Roofline of a kernel bound by FP32 lane work: FP32-pipe lane operations
+    per second against 128 lanes per clock per SM at the 2070 MHz maximum."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * 2070e6 / 1e12
+    ach = lane_ops_per_unit * units / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP32-lane-op/s", "frac": ach / peak,
+            "traffic": None, "kernel": kernel, "kernel_ms": kernel_ms,
+            "peak_basis": "FP32 pipe: %d SMs x 128 lanes x 2070 MHz (max clock)" % sms,
+            "achieved_basis": basis}
+
+
+def _flop_roof(flops, kernel_ms, kernel):
+    """The default line's roofline form: algorithmic FP32 flops of the LOO
+    tile body (FMA = 2) against the FP32 pipe (2 x 128 lanes x 2070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = 2 * 128 * sms * 2070e6 / 1e12
+    ach = flops / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "kernel": kernel, "kernel_ms": kernel_ms,
+            "peak_basis": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x 2070 MHz (max clock)" % sms}
+
+
+def _timed_kernel(ctx, fn, steps):
+    """Run fn `steps` times with kernel timing on; per-call host seconds and the
+    mean dominant-kernel milliseconds (CUDA events on the call's stream)."""
+    from paper_1206_5278_gb300 import cde
+    cde.cde_timing_enable(ctx, True)
+    host, kern = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        fn()
+        host.append(time.perf_counter() - t0)
+        kern.append(cde.cde_timing_last(ctx))
+    cde.cde_timing_enable(ctx, False)
+    return host, float(np.mean(kern))
+
+
 def run_tiny(args):
     """N=2000 d=1 8x8 grid: per-call latency (host-timed, synchronous C-ABI call)."""
     import torch
@@ -339,6 +379,7 @@ def run_batch(args):
     for _ in range(max(1, args.warmup)):
         cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s)
     tb = _timed(lambda: cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s), args.steps)
+    _, kb = _timed_kernel(ctx, lambda: cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s), max(3, args.steps))
 
     def loop():
         for ds, w in zip(dss, ws):
@@ -356,6 +397,8 @@ def run_batch(args):
           per_dataset_loop={"value": pe / float(np.median(tl)), "ms_per_step": 1e3 * float(np.median(tl))},
           speedup_vs_loop=float(np.median(tl) / np.median(tb)), bitwise_equal_to_single=bool(same),
           autotune=tune, gpu_launches=2,
+          roofline=_flop_roof(sum(w.N * w.N * flops_per_pair(16, 16, w.d) for w in ws), kb,
+                              "k_loo_batch (graph replay)"),
           config={"workload": "batch", "datasets": len(ws), "pair_evals": pe,
                   "N_range": [min(w.N for w in ws), max(w.N for w in ws)],
                   "timing": "host wall clock around the synchronous batched call (graph replay)"})
@@ -375,6 +418,24 @@ def run_grad(args):
         for _ in range(max(1, args.warmup)):
             cde.cde_loo_grad(ctx, ds, h1, h2)
         tg = _timed(lambda: cde.cde_loo_grad(ctx, ds, h1, h2), args.steps)
+        _, kg = _timed_kernel(ctx, lambda: cde.cde_loo_grad(ctx, ds, h1, h2), max(3, args.steps))
+        if d < 16:
+            # per pair: distance 2d, dy 2, exponent arguments 4, v 1, five sums 5
+            roof = _alu_roof(2 * d + 12, w.N * w.N, kg, "k_loo_grad",
+                             "FP32 lane operations per pair 2d + 12 (distance, dy, arguments, v, five sums)")
+        else:
+            dk = 16 if d <= 16 else 32 if d <= 32 else 64
+            pk = cde.cde_measure_peaks(ctx)
+            peak = pk.mma_tf32_mac_per_clk_sm * pk.sm_count * 2 * 2070e6 / 1e12
+            ach = 3 * dk * w.N * w.N * 2 / (kg * 1e-3) / 1e12
+            roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s (TF32 mma.sync)",
+                    "frac": ach / peak, "traffic": None, "kernel": "k_loo_grad_mma", "kernel_ms": kg,
+                    "peak_basis": "measured mma.sync m16n8k8 TF32 rate (cde_measure_peaks: %.0f MAC/clk/SM) "
+                                  "x SMs x 2070 MHz" % pk.mma_tf32_mac_per_clk_sm,
+                    "achieved_basis": "3 x %d TF32 multiply-adds per pair (3xTF32 Gram product)" % dk,
+                    "epilogue": _alu_roof(27, w.N * w.N, kg, "k_loo_grad_mma",
+                                          "FP32 lane operations per pair of the epilogue: dx2 3, dy 2, "
+                                          "arguments 4, v 1, five sums 5, packing and masks 12")}
         tgrid = _timed(lambda: cde.cde_loo_loglik(ctx, ds, w.h1, w.h2), 1)
         Lgrid, _ = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
         t0 = time.perf_counter()
@@ -390,6 +451,7 @@ def run_grad(args):
               grid32={"seconds": float(tgrid[0]), "L_best": float(Lgrid.max()),
                       "h1": float(w.h1[np.unravel_index(Lgrid.argmax(), Lgrid.shape)[0]]),
                       "h2": float(w.h2[np.unravel_index(Lgrid.argmax(), Lgrid.shape)[1]])},
+              roofline=roof,
               config={"workload": w.name, "N": w.N, "d_x": d, "h1": h1, "h2": h2})
         cde.cde_shutdown(ctx)
 
@@ -555,12 +617,19 @@ def run_products(args):
             st.synchronize()
             ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
             res[tag] = {"ms": ms, "query_point_pairs_per_s": pairs / (ms * 1e-3)}
+            if tag == "cond_stats":
+                _, kms = _timed_kernel(ctx, lambda: (fn(), st.synchronize()), max(3, args.steps))
+                # per pair: distance 2 DREG (DREG = 4 at d = 4), x argument 2, two sums 2,
+                # dy 2, y argument 1, one sum 1
+                res[tag]["roofline"] = _alu_roof(2 * (4 if d <= 4 else 8) + 8, pairs, kms, "k_cond_stats",
+                                                 "FP32 lane operations per (query, point) pair 2 DREG + 8")
         res["interval"]["draws_per_s"] = Qi * S / (res["interval"]["ms"] * 1e-3)
         out[kern] = res
         cde.cde_destroy_dataset(ctx, ds)
     _line(workload="products_N%d_d%d" % (N, d), metric="conditional mean + point density (query, point) pairs/s",
           unit="pairs/s", value=out["gauss"]["cond_stats"]["query_point_pairs_per_s"], steps=args.steps,
           warmup=args.warmup, ms_per_step=out["gauss"]["cond_stats"]["ms"], kernels=out,
+          roofline=out["gauss"]["cond_stats"]["roofline"],
           config={"workload": "products", "N": N, "d_x": d, "Q_stats": 10000, "Q_interval": 1000,
                   "draws": 1000, "alpha": 0.05})
     cde.cde_shutdown(ctx)

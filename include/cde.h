@@ -131,14 +131,15 @@ int cde_check_status(cde_ctx *ctx, unsigned int *code, int *enabled);
 int cde_dataset_nn(cde_ctx *ctx, cde_dataset ds, float *nn_x2, float *nn_y2);
 
 /*
- * Kernel timing (a profiling aid).  With timing on, cde_loo_loglik (and
- * cde_loo_rows) and cde_density record CUDA events on the call's stream
- * around their dominant kernel: the exact-LOO tile kernel (from the first to
- * the last launch of the call, for grids wider than 32) and the tensor-core
- * density kernel (per pass).  cde_timing_last waits for the latest recorded
- * end event and returns the milliseconds between the pair; CDE_EINVAL when
- * nothing has been recorded since timing was (re)enabled.  Calls through the
- * batched, graph and request-queue paths are not timed.
+ * Kernel timing (a profiling aid).  With timing on, these calls record CUDA
+ * events on their stream around their dominant kernel: cde_loo_loglik and
+ * cde_loo_rows (the exact-LOO tile kernel, from the first to the last launch
+ * of the call for grids wider than 32), cde_density (the tensor-core
+ * kernel), cde_loo_grad (the pair kernel), cde_cond_stats (the pair kernel)
+ * and cde_loo_loglik_batch (the replay of its captured graph).
+ * cde_timing_last waits for the latest recorded end event and returns the
+ * milliseconds between the pair; CDE_EINVAL when nothing has been recorded
+ * since timing was (re)enabled.  The request queue's jobs are not timed.
  */
 int cde_timing_enable(cde_ctx *ctx, int on);
 int cde_timing_last(cde_ctx *ctx, double *ms);
@@ -409,6 +410,8 @@ typedef struct {
                                          M = 128, N = 256, K = 16, back to back from one
                                          thread: multiply-adds per clock per SM */
     double umma_bf16_tflops;    /* the same, whole GPU at the clock seen (2 flop per MAC, 1e12) */
+    double mma_tf32_mac_per_clk_sm;   /* legacy mma.sync m16n8k8 TF32, FP32 accumulate */
+    double mma_bf16_mac_per_clk_sm;   /* legacy mma.sync m16n8k16 BF16, FP32 accumulate */
 } cde_peaks;
 
 int cde_measure_peaks(cde_ctx *ctx, cde_peaks *out);

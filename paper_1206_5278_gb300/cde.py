@@ -78,7 +78,8 @@ class cde_peaks(ctypes.Structure):
     _fields_ = [("sm_count", ctypes.c_int), ("sm_clock_mhz", ctypes.c_double),
                 ("ffma_per_clk_sm", ctypes.c_double), ("ex2_per_clk_sm", ctypes.c_double),
                 ("ffma_tops", ctypes.c_double), ("ex2_tops", ctypes.c_double),
-                ("umma_bf16_mac_per_clk_sm", ctypes.c_double), ("umma_bf16_tflops", ctypes.c_double)]
+                ("umma_bf16_mac_per_clk_sm", ctypes.c_double), ("umma_bf16_tflops", ctypes.c_double),
+                ("mma_tf32_mac_per_clk_sm", ctypes.c_double), ("mma_bf16_mac_per_clk_sm", ctypes.c_double)]
 
 
 _lib = None

@@ -336,7 +336,10 @@ int loo_batch_run(cde_ctx* ctx, const std::vector<BatchItem>& items, std::vector
     cudaEventRecord(ev, user_st);
     cudaStreamWaitEvent(P->stream, ev, 0);
     cudaEventDestroy(ev);
+    timing_reset(ctx);
+    timing_begin(ctx, P->stream);
     CDE_CUDA(cudaGraphLaunch(P->exec, P->stream));
+    timing_end(ctx, P->stream);
     CDE_CUDA(cudaStreamSynchronize(P->stream));
     for (size_t b = 0; b < items.size(); ++b) {
         const int n = P->gsz[b];

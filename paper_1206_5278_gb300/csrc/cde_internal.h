@@ -128,16 +128,20 @@ struct cde_ctx {
 namespace cde {
 
 // Dominant-kernel timing: a call resets, the first dominant launch records
-// the start event, every dominant launch re-records the end event.
-inline void timing_reset(cde_ctx* c) { c->tev_open = false; }
+// the start event, every dominant launch re-records the end event.  Threads
+// that set t_untimed (the request-queue worker) never touch the events.
+inline thread_local bool t_untimed = false;
+inline void timing_reset(cde_ctx* c) {
+    if (!t_untimed) c->tev_open = false;
+}
 inline void timing_begin(cde_ctx* c, cudaStream_t st) {
-    if (c->timing && !c->tev_open) {
+    if (c->timing && !t_untimed && !c->tev_open) {
         cudaEventRecord(c->tev0, st);
         c->tev_open = true;
     }
 }
 inline void timing_end(cde_ctx* c, cudaStream_t st) {
-    if (c->timing && c->tev_open) {
+    if (c->timing && !t_untimed && c->tev_open) {
         cudaEventRecord(c->tev1, st);
         c->tev_set = true;
     }

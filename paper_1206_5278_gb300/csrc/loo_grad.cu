@@ -595,6 +595,7 @@ static int launch_grad_mma(const GradArgs& g, dim3 grid, cudaStream_t st, bool e
 
 int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, double* d_out3,
                      cudaStream_t st, double* d_rowv_ext) {
+    timing_reset(ctx);
     GradArgs g{};
     g.xs = D.xs;
     g.y = D.y;
@@ -644,13 +645,19 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
         else if (DK == 32) k_grad_split<32><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
         else k_grad_split<64><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
         CDE_CUDA(cudaGetLastError());
+        timing_begin(ctx, st);
         const int rl = DK == 16 ? launch_grad_mma<16>(g, grid, st, epan)
                        : DK == 32 ? launch_grad_mma<32>(g, grid, st, epan)
                                   : launch_grad_mma<64>(g, grid, st, epan);
+        timing_end(ctx, st);
         if (rl != CDE_OK) return rl;
-    } else if (DREG == 4) launch_grad<4, 4>(g, grid, st, epan);
-    else if (DREG == 8) launch_grad<4, 8>(g, grid, st, epan);
-    else launch_grad<2, 16>(g, grid, st, epan);
+    } else {
+        timing_begin(ctx, st);
+        if (DREG == 4) launch_grad<4, 4>(g, grid, st, epan);
+        else if (DREG == 8) launch_grad<4, 8>(g, grid, st, epan);
+        else launch_grad<2, 16>(g, grid, st, epan);
+        timing_end(ctx, st);
+    }
     CDE_CUDA(cudaGetLastError());
     k_grad_rows<<<(unsigned)((D.N + 255) / 256), 256, 0, st>>>(part, (int)ns, D.N, D.my, g.a2, h1, h2,
                                                              epan ? 1 : 0, epan_log_norm(1), rowv, fb, fb + 1);

@@ -89,6 +89,69 @@ __global__ void __launch_bounds__(128) k_peak_umma(int R, long long* cyc, int* e
     }
 }
 
+// Legacy warp-level MMAs (the LOO tile and d >= 16 gradient kernels): eight
+// independent accumulator chains per warp, 8 warps per CTA, 2 CTAs per SM.
+template <int KIND>   // 0: m16n8k8 TF32, 1: m16n8k16 BF16
+__global__ void __launch_bounds__(256) k_peak_mma(int iters, float* out, long long* cyc) {
+    const long long c0 = clock64();
+    float d[8][4];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) d[c][0] = d[c][1] = d[c][2] = d[c][3] = 0.f;
+    const uint32_t a0 = 0x3c003c00u ^ threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, b0 = a0 + 5, b1 = a0 + 7;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if constexpr (KIND == 0)
+                asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                             "{%8,%9}, {%0,%1,%2,%3};"
+                             : "+f"(d[c][0]), "+f"(d[c][1]), "+f"(d[c][2]), "+f"(d[c][3])
+                             : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+            else
+                asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                             "{%8,%9}, {%0,%1,%2,%3};"
+                             : "+f"(d[c][0]), "+f"(d[c][1]), "+f"(d[c][2]), "+f"(d[c][3])
+                             : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+    }
+    float r = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) r += d[c][0] + d[c][1] + d[c][2] + d[c][3];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+    if (threadIdx.x == 0) cyc[blockIdx.x] = clock64() - c0;
+}
+
+static int measure_mma(cde_ctx* ctx, int kind, double* mac_per_clk) {
+    const int S = ctx->sm_count, blocks = 2 * S, threads = 256, iters = 2000;
+    float* out = nullptr;
+    long long* cyc = nullptr;
+    CDE_CUDA(cudaMalloc((void**)&out, sizeof(float) * blocks * threads));
+    CDE_CUDA(cudaMalloc((void**)&cyc, sizeof(long long) * blocks));
+    std::vector<long long> hc(blocks);
+    double best = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+        if (kind == 0) k_peak_mma<0><<<blocks, threads, 0, ctx->stream>>>(iters, out, cyc);
+        else k_peak_mma<1><<<blocks, threads, 0, ctx->stream>>>(iters, out, cyc);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpy(hc.data(), cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            cudaFree(out);
+            cudaFree(cyc);
+            return cuda_error(e, "cde_measure_peaks: mma.sync probe");
+        }
+        long long mx = 0;
+        for (auto v : hc) mx = v > mx ? v : mx;
+        // MACs of one MMA: 16 x 8 x 8 (TF32) or 16 x 8 x 16 (BF16); 2 CTAs x 8 warps per SM
+        const double macs = (kind == 0 ? 1024.0 : 2048.0) * 8 * iters * 8 * 2;
+        const double r = macs / (double)mx;
+        if (r > best) best = r;
+    }
+    cudaFree(out);
+    cudaFree(cyc);
+    *mac_per_clk = best;
+    return CDE_OK;
+}
+
 static int measure_umma(cde_ctx* ctx, double* mac_per_clk) {
     const int S = ctx->sm_count, R = 4096;
     long long* cyc = nullptr;
@@ -172,6 +235,12 @@ int measure_peaks(cde_ctx* ctx, cde_peaks* o) {
     if (rc != CDE_OK) return rc;
     o->umma_bf16_mac_per_clk_sm = umma;
     o->umma_bf16_tflops = 2.0 * umma * S * f / 1e12;
+    double m0 = 0, m1 = 0;
+    int rc2 = measure_mma(ctx, 0, &m0);
+    if (rc2 == CDE_OK) rc2 = measure_mma(ctx, 1, &m1);
+    if (rc2 != CDE_OK) return rc2;
+    o->mma_tf32_mac_per_clk_sm = m0;
+    o->mma_bf16_mac_per_clk_sm = m1;
     return CDE_OK;
 }
 

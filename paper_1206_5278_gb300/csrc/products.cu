@@ -131,20 +131,64 @@ __global__ void __launch_bounds__(kCSThreads) k_cond_stats(const StatArgs a) {
                 xi[c + 2] = v4.z;
                 xi[c + 3] = v4.w;
             }
+            if constexpr (kCSJB % 2 == 0) {
+                // two queries per packed FP32x2 instruction; each lane rounds as the
+                // scalar form below (xq - x_i as fma(x_i, -1, xq)), so the sums are
+                // bitwise the same
+                const float2 m1 = make_float2(-1.f, -1.f), yi2 = make_float2(yi, yi);
 #pragma unroll
-            for (int b = 0; b < kCSJB; ++b) {
-                float dx2 = 0.f;
+                for (int b = 0; b < kCSJB; b += 2) {
+                    float2 dx2 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int c = 0; c < DREG; ++c) {
-                    const float v = xq[b][c] - xi[c];
-                    dx2 = fmaf(v, v, dx2);
+                    for (int c = 0; c < DREG; ++c) {
+                        const float2 v = __ffma2_rn(make_float2(xi[c], xi[c]), m1, make_float2(xq[b][c], xq[b + 1][c]));
+                        dx2 = __ffma2_rn(v, v, dx2);
+                    }
+                    float2 u;
+                    if constexpr (KERN == 0) {
+                        const float2 arg = __fmul2_rn(make_float2(a.a1, a.a1),
+                                                      __ffma2_rn(dx2, m1, make_float2(mq[b], mq[b + 1])));
+                        u = make_float2(ex2p(arg.x), ex2p(arg.y));
+                    } else {
+                        u = make_float2(fma_sat_p(-a.a1, dx2.x, 1.f), fma_sat_p(-a.a1, dx2.y, 1.f));
+                    }
+                    const float2 s0 = __fadd2_rn(make_float2(S0[b], S0[b + 1]), u);
+                    const float2 s1 = __ffma2_rn(u, yi2, make_float2(S1[b], S1[b + 1]));
+                    S0[b] = s0.x;
+                    S0[b + 1] = s0.y;
+                    S1[b] = s1.x;
+                    S1[b + 1] = s1.y;
+                    if (has_yq) {
+                        const float2 dy = __ffma2_rn(yi2, m1, make_float2(yq[b], yq[b + 1]));
+                        const float2 t2 = __fmul2_rn(dy, dy);
+                        float2 w;
+                        if constexpr (KERN == 0) {
+                            const float2 arg = __fmul2_rn(make_float2(-a.a2, -a.a2), t2);
+                            w = make_float2(ex2p(arg.x), ex2p(arg.y));
+                        } else {
+                            w = make_float2(fma_sat_p(-a.a2, t2.x, 1.f), fma_sat_p(-a.a2, t2.y, 1.f));
+                        }
+                        const float2 s2 = __ffma2_rn(u, w, make_float2(S2[b], S2[b + 1]));
+                        S2[b] = s2.x;
+                        S2[b + 1] = s2.y;
+                    }
                 }
-                const float u = xweight<KERN>(dx2, a.a1, mq[b]);
-                S0[b] += u;
-                S1[b] = fmaf(u, yi, S1[b]);
-                if (has_yq) {
-                    const float dy = yq[b] - yi;
-                    S2[b] = fmaf(u, yprofile<KERN>(dy * dy, a.a2), S2[b]);
+            } else {
+#pragma unroll
+                for (int b = 0; b < kCSJB; ++b) {
+                    float dx2 = 0.f;
+#pragma unroll
+                    for (int c = 0; c < DREG; ++c) {
+                        const float v = xq[b][c] - xi[c];
+                        dx2 = fmaf(v, v, dx2);
+                    }
+                    const float u = xweight<KERN>(dx2, a.a1, mq[b]);
+                    S0[b] += u;
+                    S1[b] = fmaf(u, yi, S1[b]);
+                    if (has_yq) {
+                        const float dy = yq[b] - yi;
+                        S2[b] = fmaf(u, yprofile<KERN>(dy * dy, a.a2), S2[b]);
+                    }
                 }
             }
         }
@@ -428,6 +472,7 @@ static void launch_stats_d(const StatArgs& a, dim3 grid, cudaStream_t st) {
 
 static int cond_stats_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const float* d_xq,
                               const float* d_yq, int64_t Q, double* d_mean, double* d_fat, cudaStream_t st) {
+    timing_reset(ctx);
     const int64_t Qp = (Q + 255) / 256 * 256;
     float *xq = nullptr, *mq = nullptr, *part = nullptr;
     int rc = prep_queries(ctx, D, d_xq, Q, Qp, &xq, &mq, st);
@@ -459,8 +504,10 @@ static int cond_stats_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double 
     CDE_CUDA(cudaMallocAsync((void**)&part, (size_t)ns * Q * 3 * sizeof(float), st));
     a.part = part;
     const dim3 grid((unsigned)gx, (unsigned)ns);
+    timing_begin(ctx, st);
     if (epan) launch_stats_d<1>(a, grid, st);
     else launch_stats_d<0>(a, grid, st);
+    timing_end(ctx, st);
     CDE_CUDA(cudaGetLastError());
     const double norm = epan ? std::exp(epan_log_norm(1)) / h2 : 1.0 / (2.5066282746310002 * h2);
     k_cond_stats_final<<<(unsigned)((Q + 255) / 256), 256, 0, st>>>(part, (int)ns, Q, norm, d_mean,

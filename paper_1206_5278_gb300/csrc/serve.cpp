@@ -240,6 +240,7 @@ static void finish(Server& S, const std::shared_ptr<Job>& J, int status) {
 }
 
 static void loop(Server* Sp) {
+    t_untimed = true;   // jobs are not timed by cde_timing_enable
     Server& S = *Sp;
     cudaSetDevice(S.ctx->device);
     std::unique_lock<std::mutex> lk(S.mu);
