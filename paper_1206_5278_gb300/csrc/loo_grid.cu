@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) k_nn_shift(const float* __restrict__ xs,
 // non-negative, so their bit patterns order like the values).  The distance
 // is accumulated in the same order (dimension 0 first, one fmaf per
 // dimension; padding dimensions add exactly 0) as in every pair kernel.
-constexpr int kNnThreads = 128, kNnJB = 4;
+constexpr int kNnThreads = 128, kNnJB = 4;   // rows per thread (even: packed pairs)
 
 template <int DREG>
 __global__ void __launch_bounds__(kNnThreads) k_nn_shift_split(const float* __restrict__ xs,
@@ -207,18 +207,24 @@ __global__ void __launch_bounds__(kNnThreads) k_nn_shift_split(const float* __re
                 xi[c + 3] = v4.w;
             }
             const float yi = yt[t];
+            // rows in packed FP32x2 pairs; x_j - x_i as fma(x_i, -1, x_j), the
+            // scalar subtraction's rounding, so the minima are bitwise the same
+            const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-            for (int b = 0; b < kNnJB; ++b) {
-                float dx2 = 0.f;
+            for (int b = 0; b < kNnJB; b += 2) {
+                float2 dx2 = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < DREG; ++c) {
-                    const float q = xj[b][c] - xi[c];
-                    dx2 = fmaf(q, q, dx2);
+                    const float2 q = __ffma2_rn(make_float2(xi[c], xi[c]), m1, make_float2(xj[b][c], xj[b + 1][c]));
+                    dx2 = __ffma2_rn(q, q, dx2);
                 }
-                const float dy = yj[b] - yi;
-                const bool other = i32 != jj[b];
-                bx[b] = other ? fminf(bx[b], dx2) : bx[b];
-                by[b] = other ? fminf(by[b], dy * dy) : by[b];
+                const float2 dy = __ffma2_rn(make_float2(yi, yi), m1, make_float2(yj[b], yj[b + 1]));
+                const float2 dy2 = __fmul2_rn(dy, dy);
+                const bool o0 = i32 != jj[b], o1 = i32 != jj[b + 1];
+                bx[b] = o0 ? fminf(bx[b], dx2.x) : bx[b];
+                bx[b + 1] = o1 ? fminf(bx[b + 1], dx2.y) : bx[b + 1];
+                by[b] = o0 ? fminf(by[b], dy2.x) : by[b];
+                by[b + 1] = o1 ? fminf(by[b + 1], dy2.y) : by[b + 1];
             }
         }
     }

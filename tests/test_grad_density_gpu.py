@@ -99,10 +99,12 @@ def test_gradient_matches_central_differences_on_gpu(ctx):
     cde.cde_destroy_dataset(ctx, ds)
 
 
-def test_gradient_full_size_sampled_rows(ctx):
-    """N=200,000, d=8 (the differentiation workload): per-row terms of 64
-    sampled rows against the oracle's per-row gradient."""
-    w = synth.grad_workload(N=200000, d=8)
+@pytest.mark.parametrize("d", [8, 32])
+def test_gradient_full_size_sampled_rows(ctx, d):
+    """N=200,000, d=8 and d=32 (the differentiation workload; d=32 runs the
+    tensor-core Gram kernel): per-row terms of 64 sampled rows against the
+    oracle's per-row gradient."""
+    w = synth.grad_workload(N=200000, d=d)
     ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True)
     h1, h2 = 0.3, 0.08
     out = cde.cde_loo_grad(ctx, ds, h1, h2)
@@ -111,7 +113,15 @@ def test_gradient_full_size_sampled_rows(ctx):
     rows = np.random.default_rng(3).choice(w.N, 64, replace=False)
     _, ref = oracle.grad(w.x, w.y, h1, h2, rows=rows, standardize_x=True, per_row=True)
     sel = g_rows[rows]
-    np.testing.assert_allclose(sel[:, 0], ref[:, 0], rtol=2e-5, atol=2e-5)
+    if d >= 16:
+        # Gram-form distances (d >= 16): the per-row bound of the d >= 16 path
+        xs = oracle.standardize(w.x)
+        n = (xs ** 2).sum(1)
+        tol = 2e-5 + (n[rows] + n.max()) * 2.0 ** -19 / (2 * h1 * h1)
+        err = np.abs(sel[:, 0] - ref[:, 0])
+        assert np.all(err <= tol), "row error %g over its bound" % (err / tol).max()
+    else:
+        np.testing.assert_allclose(sel[:, 0], ref[:, 0], rtol=2e-5, atol=2e-5)
     np.testing.assert_allclose(sel[:, 1:], ref[:, 1:], rtol=1e-4, atol=1e-4 * np.abs(ref[:, 1:]).max())
     cde.cde_destroy_dataset(ctx, ds)
 
@@ -234,6 +244,23 @@ def test_kernel_timing(ctx):
     cde.cde_timing_enable(ctx, False)
     with pytest.raises(cde.CdeError):
         cde.cde_timing_last(ctx)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_density_bench_size_sampled(ctx):
+    """The density workload as the benchmark runs it (Q = 10,000 x N = 100,000,
+    d = 4, 256-point grid, h = (0.3, 0.1)): 40 sampled queries, first and last
+    included, against the oracle."""
+    N, d, Q = 100000, 4, 10000
+    x, y = synth.gmm_sine(N, d, seed=8)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    xq = synth.query_points(x, Q, seed=9)
+    yg = synth.y_grid(y, 0.1, 256)
+    f = cde.cde_density(ctx, ds, 0.3, 0.1, xq, yg)
+    assert np.all(np.isfinite(f))
+    rows = np.unique(np.concatenate([[0, Q - 1], np.random.default_rng(4).choice(Q, 38, replace=False)]))
+    ref = oracle.density(x, y, 0.3, 0.1, xq[rows], yg, standardize_x=True)
+    _dens_check(f[rows], ref)
     cde.cde_destroy_dataset(ctx, ds)
 
 
