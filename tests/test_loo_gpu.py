@@ -64,10 +64,10 @@ def test_all_tile_shapes(ctx, G1, G2):
 
 
 @pytest.mark.parametrize("N,d,G1,G2", [(2, 1, 3, 2), (3, 2, 1, 1), (33, 1, 5, 7), (257, 3, 9, 17),
-                                       (1031, 9, 33, 5), (517, 12, 6, 40), (300, 64, 4, 4)])
+                                       (1031, 9, 33, 5), (517, 12, 6, 40), (300, 64, 4, 4), (2100, 32, 32, 32)])
 def test_ragged_sizes_and_grids(ctx, N, d, G1, G2):
     """Ragged N (not a multiple of any tile), padded and split grids,
-    d above the register path (9, 12, 64)."""
+    d above the register path (9, 12, 32, 64)."""
     x, y = synth.random_small(N, d, seed=N + d)
     h1 = synth.bandwidth_grid(0.3, 3.0, G1) * math.sqrt(d)
     h2 = synth.bandwidth_grid(0.1, 2.0, G2)
