@@ -51,13 +51,6 @@ __device__ __forceinline__ float fma_sat_d(float a, float b, float c) {
     return r;
 }
 
-// y factor at squared distance t2
-template <int KERN>
-__device__ __forceinline__ float dens_wfac(float t2, float a2) {
-    if constexpr (KERN == 0) return ex2d(-a2 * t2);
-    else return fma_sat_d(-a2, t2, 1.f);
-}
-
 __global__ void k_query_pack(const float* __restrict__ xq, int64_t Q, int64_t Qp, int d,
                              const double* __restrict__ mean, const double* __restrict__ sd,
                              float* __restrict__ out) {

@@ -90,38 +90,13 @@ __device__ __forceinline__ void grad_accumulate_joint(bool ok, float dx2, float 
     SAy = fmaf(v, dy2, SAy);
 }
 
-// One pair's contribution.  Gaussian: the separable shifted factors u, w and
-// v = u w.  Epanechnikov: plain sums of the profiles and their log-derivative
-// weights (the support test is the profile itself being positive).
-template <int KERN>
-__device__ __forceinline__ void grad_accumulate(bool ok, float dx2, float dy2, float mx, float my,
-                                                float a1, float a2, float& SA, float& SAx,
-                                                float& SAy, float& SB, float& SBx) {
-    if constexpr (KERN == 1) {
-        const float u = ok ? fma_sat_g(-a1, dx2, 1.f) : 0.f;
-        const float w = fma_sat_g(-a2, dy2, 1.f);
-        const float v = u > 0.f ? 2.f * a1 * dx2 : 0.f;
-        const float z = w > 0.f ? 2.f * a2 * dy2 : 0.f;
-        SA = fmaf(u, w, SA);
-        SAx = fmaf(v, w, SAx);
-        SAy = fmaf(u, z, SAy);
-        SB += u;
-        SBx += v;
-        return;
-    }
-    const float u = ok ? ex2g(-a1 * (dx2 - mx)) : 0.f;
-    const float v = u * ex2g(-a2 * (dy2 - my));
-    SB += u;
-    SBx = fmaf(u, dx2, SBx);
-    SA += v;
-    SAx = fmaf(v, dx2, SAx);
-    SAy = fmaf(v, dy2, SAy);
-}
-
 // Two rows' contributions from one point through the packed FP32x2 pipe (rows
-// in .x and .y).  Every lane rounds exactly as grad_accumulate's scalar
-// operations (nmx = -m_x, na = -a), so the sums are bitwise those of the
-// one-row form.
+// in .x and .y; nmx = -m_x, nmy = -m_y).  Gaussian: the separable shifted
+// factors u = 2^{-a1 (dx2 - m_x)}, w = 2^{-a2 (dy2 - m_y)}, v = u w, and
+// S_B += u, S_Bx += u dx2, S_A += v, S_Ax += v dx2, S_Ay += v dy2.
+// Epanechnikov: plain sums of the profiles and their log-derivative weights
+// (the support test is the profile itself being positive).  Each lane rounds
+// as the one-row scalar form of the same operations would.
 template <int KERN>
 __device__ __forceinline__ void grad_accumulate2(bool ok0, bool ok1, float2 dx2, float2 dy2, float2 nmx,
                                                  float2 nmy, float a1, float a2, float2& SA, float2& SAx,
@@ -248,11 +223,6 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
 // ---------------------------------------------------------------------------
 constexpr int kGMWarps = 4, kGMTile = 64;
 
-__device__ __forceinline__ void split_tf32_g(float v, uint32_t& hi, uint32_t& lo) {
-    hi = __float_as_uint(v) & 0xffffe000u;
-    lo = __float_as_uint(v - __uint_as_float(hi));
-}
-
 __device__ __forceinline__ void mma_tf32_g(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
         "{%8,%9}, {%0,%1,%2,%3};"
@@ -292,8 +262,7 @@ __global__ void __launch_bounds__(256) k_grad_split(const float* __restrict__ xs
 }
 
 // Two adjacent points' contributions to one row (the row's shifts in both
-// lanes) through the packed FP32x2 pipe; same operations per lane as
-// grad_accumulate.
+// lanes) through the packed FP32x2 pipe; the operations of grad_accumulate2.
 template <int KERN>
 __device__ __forceinline__ void grad_accumulate_pts(bool ok0, bool ok1, float2 dx2, float2 dy2, float mx, float my,
                                                     float a1, float a2, float2& SA, float2& SAx, float2& SAy,
