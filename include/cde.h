@@ -121,6 +121,13 @@ int cde_dataset_info(cde_ctx *ctx, cde_dataset ds, int64_t *N, int *d_x, double 
  * enabled may be NULL.
  */
 #define CDE_CHECK_TENSOR_WAIT 0x10000u
+
+/* Self-test of the bounded on-device waits (failure detection without a GPU
+ * fault): one thread waits on an mbarrier that nothing arrives on, with the
+ * limit the tensor-core kernels use (about 2^31 SM cycles, a second), then
+ * records wait code 64; returns CDE_OK once the kernel has finished.  A
+ * following cde_check_status reports CDE_CHECK_TENSOR_WAIT | 64. */
+int cde_selftest_wait(cde_ctx *ctx);
 int cde_check_status(cde_ctx *ctx, unsigned int *code, int *enabled);
 
 /* Per-row nearest squared distances of a Gaussian dataset, the exp2 shifts:

@@ -26,6 +26,7 @@ CDE_KERNEL_GAUSS, CDE_KERNEL_EPAN = 0, 1
 KERNELS = {"gauss": CDE_KERNEL_GAUSS, "epan": CDE_KERNEL_EPAN}
 CDE_REQ_DENSITY, CDE_REQ_SELECT = 0, 1
 CDE_L_COND, CDE_L_EQ3 = 0, 1
+CDE_CHECK_TENSOR_WAIT = 0x10000
 STATUS_NAMES = {0: "CDE_OK", 1: "CDE_EINVAL", 2: "CDE_ENOMEM", 3: "CDE_ECUDA", 4: "CDE_EBUSY",
                 5: "CDE_ETIMEOUT", 6: "CDE_ENOTFOUND", 7: "CDE_ECANCELED"}
 
@@ -42,7 +43,7 @@ EXPORTED = [
     "cde_measure_peaks", "cde_autotune", "cde_tuning_get", "cde_tuning_set",
     "cde_loo_loglik_noalloc", "cde_dataset_kernel", "cde_select_random", "cde_reference_rule",
     "cde_cond_stats", "cde_cond_interval", "cde_tuning_save", "cde_tuning_load", "cde_check_status",
-    "cde_dataset_nn", "cde_timing_enable", "cde_timing_last",
+    "cde_dataset_nn", "cde_timing_enable", "cde_timing_last", "cde_selftest_wait",
 ]
 
 
@@ -137,6 +138,7 @@ def lib():
         "cde_dataset_nn": ([_vp, _i64, _vp, _vp], ctypes.c_int),
         "cde_timing_enable": ([_vp, ctypes.c_int], ctypes.c_int),
         "cde_timing_last": ([_vp, _vp], ctypes.c_int),
+        "cde_selftest_wait": ([_vp], ctypes.c_int),
         "cde_select_random": ([_vp, _i64, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, ctypes.c_uint64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
                               ctypes.c_int),
@@ -310,6 +312,11 @@ def cde_dataset_nn(ctx, ds: int):
     return a, b
 
 
+def cde_selftest_wait(ctx) -> None:
+    """Run the bounded-wait self-test (a wait that runs out on the device)."""
+    _check(lib().cde_selftest_wait(ctx))
+
+
 def cde_timing_enable(ctx, on: bool = True) -> None:
     """Record CUDA events around the dominant kernel of later loo/density calls."""
     _check(lib().cde_timing_enable(ctx, int(bool(on))))
@@ -464,7 +471,8 @@ def cde_tuning_get(ctx, G1: int, G2: int):
 
 def cde_check_status(ctx):
     """(code, enabled): the first failed device index check since the last
-    call (0: none) in a checked build; enabled = False in the normal library."""
+    call (0: none) in a checked build, else a bounded on-device wait that ran
+    out (CDE_CHECK_TENSOR_WAIT | which); enabled = False in the normal library."""
     c, e = ctypes.c_uint(), ctypes.c_int()
     _check(lib().cde_check_status(ctx, ctypes.byref(c), ctypes.byref(e)))
     return c.value, bool(e.value)

@@ -682,6 +682,21 @@ int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const 
     return CDE_OK;
 }
 
+// Self-test of the bounded on-device wait: one thread waits on an mbarrier
+// that nothing arrives on, exactly as the tensor-core kernel's waits do; the
+// wait gives up after its limit (about a second), records `code` in the
+// context's wait word and returns normally.
+__global__ void k_wait_selftest(int* err, int code) {
+    __shared__ unsigned long long bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_wait(smem_u32(&bar), 0, &abort_flag, err, code);
+    }
+}
+
 #ifdef CDE_CHECKS
 CDE_CHECK_READER(check_status_density)
 #endif
@@ -689,6 +704,17 @@ CDE_CHECK_READER(check_status_density)
 }  // namespace cde
 
 using namespace cde;
+
+extern "C" int cde_selftest_wait(cde_ctx* ctx) {
+    CDE_NVTX("cde_selftest_wait");
+    if (!ctx) return set_error(CDE_EINVAL, "cde_selftest_wait: null context");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    k_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->d_err + kErrTensorWait, 64);
+    CDE_CUDA(cudaGetLastError());
+    CDE_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CDE_OK;
+}
 
 extern "C" int cde_density(cde_ctx* ctx, cde_dataset ds, double h1, double h2, const float* xq,
                            int64_t Q, const float* ygrid, int G, float* f_out, int flags, void* stream) {

@@ -218,6 +218,24 @@ def test_measured_pipe_rates(ctx):
     assert p.umma_bf16_tflops > 500
 
 
+def test_bounded_device_wait_reports_and_context_stays_usable(ctx):
+    """Failure detection without a GPU fault: a device wait on an mbarrier that
+    nothing arrives on gives up after its limit (the tensor-core kernels'
+    helper), the host reads the status, and the context keeps working."""
+    cde.cde_check_status(ctx)   # clear earlier reports
+    cde.cde_selftest_wait(ctx)
+    code, _ = cde.cde_check_status(ctx)
+    assert code == cde.CDE_CHECK_TENSOR_WAIT | 64
+    assert cde.cde_check_status(ctx)[0] == 0   # reported once, then cleared
+    x, y = synth.gmm_sine(3000, 2, seed=12)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    xq = synth.query_points(x, 150, seed=13)
+    yg = synth.y_grid(y, 0.1, 64)
+    f = cde.cde_density(ctx, ds, 0.3, 0.1, xq, yg)
+    _dens_check(f, oracle.density(x, y, 0.3, 0.1, xq, yg, standardize_x=True))
+    cde.cde_destroy_dataset(ctx, ds)
+
+
 def test_kernel_timing(ctx):
     """cde_timing_last: events around the dominant kernel of the latest call
     (tile kernel of the LOO grid, tensor-core kernel of the density)."""
