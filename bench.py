@@ -698,6 +698,67 @@ def run_evaluate(args):
     cde.cde_shutdown(ctx)
 
 
+def run_dualtree(args):
+    """Context for the paper's own approximations (Sec. 3.3-3.4, the Fig. 2
+    time trials): per bandwidth pair, single-threaded CPU seconds and |error|
+    of the exact double loop (the FP64 oracle), the deterministic dual tree
+    (Thm. 1) and the sampled one (Alg. 2: m = 25, B = 10, z = 1.5), eps = 0.1,
+    Epanechnikov kernel on standardised x, against the exact GPU score of the
+    same pair (a 32 x 32 grid around it, per cell, and one single-pair call).
+    The pair is the exact optimum of a 32 x 32 log grid (the bandwidths a
+    selection would land on).  N and d are the paper's (500 ... 10,000; 3
+    and 9); synthetic data stand in for its SDSS and census sets.""" 
+    import torch
+    from oracle import dualtree, oracle
+    from paper_1206_5278_gb300 import cde, synth
+    oracle.build()
+    dualtree.build()
+    ctx = cde.cde_init(0)
+    rows = []
+    for d in (3, 9):
+        for N in (500, 1000, 2000, 10000):
+            x, y = synth.gmm_sine(N, d, seed=40 + d)
+            ds = cde.cde_create_dataset(ctx, x, y, standardize=True, kernel="epan")
+            # the pair bandwidth selection lands on: the exact optimum of a 32 x 32 grid
+            G1 = synth.bandwidth_grid(0.2 * math.sqrt(d), 4.0 * math.sqrt(d), 32)
+            G2 = synth.bandwidth_grid(0.05, 3.0, 32)
+            _, Le0 = cde.cde_loo_loglik(ctx, ds, G1, G2)
+            k, l = np.unravel_index(np.argmax(Le0), Le0.shape)
+            h1, h2 = float(G1[k]), float(G2[l])
+            t0 = time.perf_counter()
+            _, Le = oracle.loo_grid(x, y, [h1], [h2], standardize_x=True, kernel="epan", n_threads=1)
+            t_naive = time.perf_counter() - t0
+            ex = float(Le[0, 0])
+            det = dualtree.loo_eq3(x, y, h1, h2, 0.1, kernel="epan")
+            smp = dualtree.loo_eq3(x, y, h1, h2, 0.1, sampled=True, kernel="epan", seed=1)
+            g1 = h1 * np.exp(np.linspace(-0.5, 0.5, 32))
+            g2 = h2 * np.exp(np.linspace(-0.5, 0.5, 32))
+            cde.cde_loo_loglik(ctx, ds, g1, g2)
+            tg = _timed(lambda: cde.cde_loo_loglik(ctx, ds, g1, g2), 3)
+            t1 = _timed(lambda: cde.cde_loo_loglik(ctx, ds, [h1], [h2]), 5)
+            _, Lg = cde.cde_loo_loglik(ctx, ds, [h1], [h2])
+            cde.cde_destroy_dataset(ctx, ds)
+
+            def err(v):
+                return None if not (math.isfinite(v) and math.isfinite(ex)) else abs(v - ex)
+            rows.append({"d": d, "N": N, "h1": h1, "h2": h2, "L_exact": ex,
+                         "naive_cpu_s": t_naive,
+                         "deterministic": {"s": det["seconds"], "abs_err": err(det["L"]),
+                                           "exact_term_frac": det["exact_terms"] / float(N * N)},
+                         "sampled": {"s": smp["seconds"], "abs_err": err(smp["L"]),
+                                     "exact_term_frac": smp["exact_terms"] / float(N * N)},
+                         "gpu_exact": {"s_per_pair_in_32x32_grid": float(np.median(tg)) / 1024,
+                                       "s_single_pair_call": float(np.median(t1)),
+                                       "abs_err": err(float(Lg[0, 0]))}})
+    big = [r for r in rows if r["N"] == 10000]
+    _line(workload="dualtree_context", metric="seconds per bandwidth pair (exact GPU vs the paper's CPU dual trees)",
+          unit="s", value=big[0]["gpu_exact"]["s_per_pair_in_32x32_grid"], higher_is_better=False,
+          steps=1, warmup=0, rows=rows, dtype="f64 (CPU) / f32 (GPU)",
+          config={"workload": "dualtree", "eps": 0.1, "kernel": "epan", "sizes": [500, 1000, 2000, 10000],
+                  "dims": [3, 9], "cpu_threads": 1})
+    cde.cde_shutdown(ctx)
+
+
 def run_serve(args):
     """Poisson stream, 70% density jobs (Q log-uniform [1, Q_max] x 256-point y
     grid), 30% selection jobs (16x16 grid + 20 Adam steps) over resident
@@ -795,7 +856,7 @@ def main():
     ap.add_argument("--N", type=int, default=50000, help="dataset size (profiling runs use less)")
     ap.add_argument("--workload", default="scale",
                     choices=["scale", "tiny", "batch", "grad", "serve", "density", "select", "evaluate",
-                             "products"])
+                             "products", "dualtree"])
     ap.add_argument("--select-N", type=int, default=10000)
     ap.add_argument("--select-rounds", type=int, default=8)
     ap.add_argument("--eval-N", type=int, default=0, help="0: the sizes of the paper's Table 1 sets")
@@ -823,7 +884,7 @@ def main():
             build()
         {"tiny": run_tiny, "batch": run_batch, "grad": run_grad, "serve": run_serve,
          "density": run_density, "select": run_select, "evaluate": run_evaluate,
-         "products": run_products}[args.workload](args)
+         "products": run_products, "dualtree": run_dualtree}[args.workload](args)
         return
     w = synth.scale_workload(N=args.N, seed=1 + 1000 * rank)
     if args.kernel == "epan":
