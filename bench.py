@@ -426,9 +426,9 @@ def run_grad(args):
         tg = _timed(lambda: cde.cde_loo_grad(ctx, ds, h1, h2), args.steps)
         _, kg = _timed_kernel(ctx, lambda: cde.cde_loo_grad(ctx, ds, h1, h2), max(3, args.steps))
         if d < 16:
-            # per pair: distance 2d, dy 2, exponent arguments 4, v 1, five sums 5
-            roof = _alu_roof(2 * d + 12, w.N * w.N, kg, "k_loo_grad",
-                             "FP32 lane operations per pair 2d + 12 (distance, dy, arguments, v, five sums)")
+            # per pair: distance 2d, dy 2, exponent arguments 2 (one FMA each), v 1, five sums 5
+            roof = _alu_roof(2 * d + 10, w.N * w.N, kg, "k_loo_grad",
+                             "FP32 lane operations per pair 2d + 10 (distance, dy, arguments, v, five sums)")
         else:
             dk = 16 if d <= 16 else 32 if d <= 32 else 64
             pk = cde.cde_measure_peaks(ctx)
@@ -439,9 +439,10 @@ def run_grad(args):
                     "peak_basis": "measured mma.sync m16n8k8 TF32 rate (cde_measure_peaks: %.0f MAC/clk/SM) "
                                   "x SMs x 2070 MHz" % pk.mma_tf32_mac_per_clk_sm,
                     "achieved_basis": "3 x %d TF32 multiply-adds per pair (3xTF32 Gram product)" % dk,
-                    "epilogue": _alu_roof(27, w.N * w.N, kg, "k_loo_grad_mma",
-                                          "FP32 lane operations per pair of the epilogue: dx2 3, dy 2, "
-                                          "arguments 4, v 1, five sums 5, packing and masks 12")}
+                    "epilogue": _alu_roof(13, w.N * w.N, kg, "k_loo_grad_mma",
+                                          "FP32 lane operations per pair of the epilogue: dx2 3 "
+                                          "(n_j + n_i, the dot product, the clamp), dy 2, arguments 2, "
+                                          "v 1, five sums 5")}
         tgrid = _timed(lambda: cde.cde_loo_loglik(ctx, ds, w.h1, w.h2), 1)
         Lgrid, _ = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
         # the plain per-bandwidth launch loop: one exact 1 x 1 evaluation per (h1, h2)
@@ -632,10 +633,10 @@ def run_products(args):
             res[tag] = {"ms": ms, "query_point_pairs_per_s": pairs / (ms * 1e-3)}
             if tag == "cond_stats":
                 _, kms = _timed_kernel(ctx, lambda: (fn(), st.synchronize()), max(3, args.steps))
-                # per pair: distance 2 DREG (DREG = 4 at d = 4), x argument 2, two sums 2,
+                # per pair: distance 2 DREG (DREG = 4 at d = 4), x argument 1 (one FMA), two sums 2,
                 # dy 2, y argument 1, one sum 1
-                res[tag]["roofline"] = _alu_roof(2 * (4 if d <= 4 else 8) + 8, pairs, kms, "k_cond_stats",
-                                                 "FP32 lane operations per (query, point) pair 2 DREG + 8")
+                res[tag]["roofline"] = _alu_roof(2 * (4 if d <= 4 else 8) + 7, pairs, kms, "k_cond_stats",
+                                                 "FP32 lane operations per (query, point) pair 2 DREG + 7")
         res["interval"]["draws_per_s"] = Qi * S / (res["interval"]["ms"] * 1e-3)
         out[kern] = res
         cde.cde_destroy_dataset(ctx, ds)

@@ -91,15 +91,15 @@ __device__ __forceinline__ void grad_accumulate_joint(bool ok, float dx2, float 
 }
 
 // Two rows' contributions from one point through the packed FP32x2 pipe (rows
-// in .x and .y; nmx = -m_x, nmy = -m_y).  Gaussian: the separable shifted
-// factors u = 2^{-a1 (dx2 - m_x)}, w = 2^{-a2 (dy2 - m_y)}, v = u w, and
-// S_B += u, S_Bx += u dx2, S_A += v, S_Ax += v dx2, S_Ay += v dy2.
-// Epanechnikov: plain sums of the profiles and their log-derivative weights
-// (the support test is the profile itself being positive).  Each lane rounds
-// as the one-row scalar form of the same operations would.
+// in .x and .y; Gaussian: am = a1 m_x, bm = a2 m_y of the rows).  Gaussian:
+// the separable shifted factors u = 2^{a1 m_x - a1 dx2}, w = 2^{a2 m_y - a2 dy2}
+// (one FMA each), v = u w, and S_B += u, S_Bx += u dx2, S_A += v,
+// S_Ax += v dx2, S_Ay += v dy2.  Epanechnikov: plain sums of the profiles and
+// their log-derivative weights (the support test is the profile itself being
+// positive).
 template <int KERN>
-__device__ __forceinline__ void grad_accumulate2(bool ok0, bool ok1, float2 dx2, float2 dy2, float2 nmx,
-                                                 float2 nmy, float a1, float a2, float2& SA, float2& SAx,
+__device__ __forceinline__ void grad_accumulate2(bool ok0, bool ok1, float2 dx2, float2 dy2, float2 am,
+                                                 float2 bm, float a1, float a2, float2& SA, float2& SAx,
                                                  float2& SAy, float2& SB, float2& SBx) {
     if constexpr (KERN == 1) {
         const float2 u = make_float2(ok0 ? fma_sat_g(-a1, dx2.x, 1.f) : 0.f, ok1 ? fma_sat_g(-a1, dx2.y, 1.f) : 0.f);
@@ -115,8 +115,8 @@ __device__ __forceinline__ void grad_accumulate2(bool ok0, bool ok1, float2 dx2,
         SBx = __fadd2_rn(SBx, v);
         return;
     }
-    const float2 au = __fmul2_rn(__fadd2_rn(dx2, nmx), make_float2(-a1, -a1));   // -a1 (dx2 - m_x)
-    const float2 aw = __fmul2_rn(__fadd2_rn(dy2, nmy), make_float2(-a2, -a2));   // -a2 (dy2 - m_y)
+    const float2 au = __ffma2_rn(dx2, make_float2(-a1, -a1), am);   // a1 m_x - a1 dx2
+    const float2 aw = __ffma2_rn(dy2, make_float2(-a2, -a2), bm);   // a2 m_y - a2 dy2
     const float2 u = make_float2(ok0 ? ex2g(au.x) : 0.f, ok1 ? ex2g(au.y) : 0.f);
     const float2 v = __fmul2_rn(u, make_float2(ex2g(aw.x), ex2g(aw.y)));
     SB = __fadd2_rn(SB, u);
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
     const int64_t i0 = (int64_t)blockIdx.y * g.i_per_split;
     const int64_t i1 = min(g.N, i0 + g.i_per_split);
     const int d = g.d;
-    float2 xj[JP][DREG], yj[JP], nmx[JP], nmy[JP];
+    float2 xj[JP][DREG], yj[JP], am[JP], bm[JP];
     float2 SA[JP], SAx[JP], SAy[JP], SB[JP], SBx[JP];
     int jj[JB];
 #pragma unroll
@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
 #pragma unroll
         for (int c = 0; c < DREG; ++c) xr[2 * c] = c < d ? g.xs[(int64_t)c * g.Np + jc] : 0.f;
         reinterpret_cast<float*>(&yj[p])[b & 1] = g.y[jc];
-        reinterpret_cast<float*>(&nmx[p])[b & 1] = -g.mx[jc];
-        reinterpret_cast<float*>(&nmy[p])[b & 1] = -g.my[jc];
+        reinterpret_cast<float*>(&am[p])[b & 1] = g.a1 * g.mx[jc];   // a1 m_x (Gaussian; unused otherwise)
+        reinterpret_cast<float*>(&bm[p])[b & 1] = g.a2 * g.my[jc];   // a2 m_y
     }
 #pragma unroll
     for (int p = 0; p < JP; ++p) SA[p] = SAx[p] = SAy[p] = SB[p] = SBx[p] = make_float2(0.f, 0.f);
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
                 }
                 const float2 dy = __ffma2_rn(make_float2(yi, yi), m1, yj[p]);
                 const float2 dy2 = __fmul2_rn(dy, dy);
-                grad_accumulate2<KERN>(i32 != jj[2 * p], i32 != jj[2 * p + 1], dx2, dy2, nmx[p], nmy[p], a1, a2,
+                grad_accumulate2<KERN>(i32 != jj[2 * p], i32 != jj[2 * p + 1], dx2, dy2, am[p], bm[p], a1, a2,
                                        SA[p], SAx[p], SAy[p], SB[p], SBx[p]);
             }
         }
@@ -261,13 +261,13 @@ __global__ void __launch_bounds__(256) k_grad_split(const float* __restrict__ xs
     }
 }
 
-// Two adjacent points' contributions to one row (the row's shifts in both
-// lanes) through the packed FP32x2 pipe; the operations of grad_accumulate2.
+// Two adjacent points' contributions to one row (the row's a1 m_x, a2 m_y in
+// both lanes) through the packed FP32x2 pipe; the operations of grad_accumulate2.
 template <int KERN>
-__device__ __forceinline__ void grad_accumulate_pts(bool ok0, bool ok1, float2 dx2, float2 dy2, float mx, float my,
+__device__ __forceinline__ void grad_accumulate_pts(bool ok0, bool ok1, float2 dx2, float2 dy2, float am, float bm,
                                                     float a1, float a2, float2& SA, float2& SAx, float2& SAy,
                                                     float2& SB, float2& SBx) {
-    grad_accumulate2<KERN>(ok0, ok1, dx2, dy2, make_float2(-mx, -mx), make_float2(-my, -my), a1, a2, SA, SAx, SAy,
+    grad_accumulate2<KERN>(ok0, ok1, dx2, dy2, make_float2(am, am), make_float2(bm, bm), a1, a2, SA, SAx, SAy,
                            SB, SBx);
 }
 
@@ -332,6 +332,7 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
         }
     }
     const float a1 = g.a1, a2 = g.a2;
+    const float amj[2] = {a1 * mxj[0], a1 * mxj[1]}, bmj[2] = {a2 * myj[0], a2 * myj[1]};
     float2 SA[2], SAx[2], SAy[2], SB[2], SBx[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) SA[h] = SAx[h] = SAy[h] = SB[h] = SBx[h] = make_float2(0.f, 0.f);
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
                     const float2 dy = __ffma2_rn(yip, m1, make_float2(yj[h], yj[h]));
                     const float2 dy2 = __fmul2_rn(dy, dy);
                     grad_accumulate_pts<KERN>(p < n_in && ia != jr[h], p + 1 < n_in && ia + 1 != jr[h], dx2, dy2,
-                                              mxj[h], myj[h], a1, a2, SA[h], SAx[h], SAy[h], SB[h], SBx[h]);
+                                              amj[h], bmj[h], a1, a2, SA[h], SAx[h], SAy[h], SB[h], SBx[h]);
                 }
             }
         }

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kCSThreads) k_cond_stats(const StatArgs a) {
     const int64_t i1 = min(a.N, i0 + a.i_per_split);
     const int d = a.d;
     const bool has_yq = a.yq != nullptr;
-    float xq[kCSJB][DREG], yq[kCSJB], mq[kCSJB], S0[kCSJB], S1[kCSJB], S2[kCSJB];
+    float xq[kCSJB][DREG], yq[kCSJB], mq[kCSJB], amq[kCSJB], S0[kCSJB], S1[kCSJB], S2[kCSJB];
 #pragma unroll
     for (int b = 0; b < kCSJB; ++b) {
         const int64_t q = qbase + (int64_t)b * kCSThreads;
@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(kCSThreads) k_cond_stats(const StatArgs a) {
         for (int c = 0; c < DREG; ++c) xq[b][c] = c < d ? a.xq[(int64_t)c * a.Qp + qc] : 0.f;
         yq[b] = has_yq ? a.yq[qc] : 0.f;
         mq[b] = KERN == 0 ? a.mq[qc] : 0.f;
+        amq[b] = a.a1 * mq[b];
         S0[b] = S1[b] = S2[b] = 0.f;
     }
     for (int64_t t0 = i0; t0 < i1; t0 += kCSThreads) {
@@ -132,9 +133,8 @@ __global__ void __launch_bounds__(kCSThreads) k_cond_stats(const StatArgs a) {
                 xi[c + 3] = v4.w;
             }
             if constexpr (kCSJB % 2 == 0) {
-                // two queries per packed FP32x2 instruction; each lane rounds as the
-                // scalar form below (xq - x_i as fma(x_i, -1, xq)), so the sums are
-                // bitwise the same
+                // two queries per packed FP32x2 instruction (xq - x_i as fma(x_i, -1, xq),
+                // the scalar subtraction's rounding; the x argument a1 m_q - a1 dx2 as one FMA)
                 const float2 m1 = make_float2(-1.f, -1.f), yi2 = make_float2(yi, yi);
 #pragma unroll
                 for (int b = 0; b < kCSJB; b += 2) {
@@ -146,8 +146,7 @@ __global__ void __launch_bounds__(kCSThreads) k_cond_stats(const StatArgs a) {
                     }
                     float2 u;
                     if constexpr (KERN == 0) {
-                        const float2 arg = __fmul2_rn(make_float2(a.a1, a.a1),
-                                                      __ffma2_rn(dx2, m1, make_float2(mq[b], mq[b + 1])));
+                        const float2 arg = __ffma2_rn(dx2, make_float2(-a.a1, -a.a1), make_float2(amq[b], amq[b + 1]));
                         u = make_float2(ex2p(arg.x), ex2p(arg.y));
                     } else {
                         u = make_float2(fma_sat_p(-a.a1, dx2.x, 1.f), fma_sat_p(-a.a1, dx2.y, 1.f));
