@@ -179,7 +179,7 @@ def test_epan_noalloc_matches(ctx):
     cde.cde_destroy_dataset(ctx, ds)
 
 
-@pytest.mark.parametrize("N,d,Q,G", [(1000, 3, 50, 37), (517, 1, 1, 256), (2048, 8, 70, 300)])
+@pytest.mark.parametrize("N,d,Q,G", [(1000, 3, 50, 37), (517, 1, 1, 256), (2048, 8, 70, 300), (3000, 4, 300, 200)])
 def test_epan_density_matches_oracle(ctx, N, d, Q, G):
     x, y = synth.gmm_sine(N, d, seed=N + d + 1)
     ds = _ds(ctx, x, y, standardize=True)

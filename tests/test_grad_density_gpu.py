@@ -170,6 +170,10 @@ def test_density_matches_oracle(ctx, N, d, Q, G, standardize):
     (2000, 64, 5, 16, 5),         # the largest d
     (200000, 2, 3, 17, 3),        # every CTA on one tile: 152 partials per output
     (37, 1, 1, 1, 1),             # one chunk, one grid point
+    (6000, 3, 257, 100, 60),      # CTA pairs: three query tiles (one padded), G < 128 split by row parity
+    (50, 2, 300, 33, 30),         # CTA pairs with fewer chunks than operand stages
+    (9000, 5, 1000, 17, 50),      # CTA pairs, odd grid smaller than one core-matrix group per CTA
+    (70000, 2, 129, 257, 40),     # one tile pair (second tile one query), two grid tiles
 ])
 def test_density_tiles_and_splits(ctx, N, d, Q, G, n_check):
     """Tile, segment and split structure of the tensor-core density: sampled
