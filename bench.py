@@ -230,6 +230,18 @@ def run_ours(args, w):
             "peak_basis": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x 2070 MHz (max clock)" % sms}
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (2 * lanes * sms * clocks["sm_mhz"] * 1e6 / 1e12)
+    # the naive form's ceiling: one kernel evaluation per (pair, bandwidth pair) (Gaussian:
+    # one ex2 on the MUFU at its measured rate; Epanechnikov: one saturating FMA per lane),
+    # against which the separable factorisation K_h1 K_h2 = u w is measured
+    if args.kernel == "gauss":
+        r_unit = float(peaks.ex2_per_clk_sm) if peaks is not None else 32.0
+        naive_basis = "one ex2 per (pair, bandwidth pair): %d SMs x %.1f ex2/clk/SM (measured) x 2070 MHz" % (
+            sms, r_unit)
+    else:
+        r_unit = float(peaks.ffma_per_clk_sm) if peaks is not None else 128.0
+        naive_basis = "one saturating FMA per (pair, bandwidth pair): %d SMs x %.1f lanes/clk/SM (measured) x 2070 MHz" % (
+            sms, r_unit)
+    naive_ceiling = sms * r_unit * 2070e6
 
     # ---- parity spot check on sampled rows + CPU baseline (rank 0, N=1) ----
     cpu = None
@@ -272,6 +284,8 @@ def run_ours(args, w):
                    "d2h_bytes_per_step": int(d2h), "s_per_step": e2e_s,
                    "includes": "dataset upload + standardise + nearest-neighbour shifts + grid + copy back"},
            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+           "naive_form_ceiling": {"value": naive_ceiling, "unit": UNIT, "basis": naive_basis,
+                                  "value_over_ceiling": value / naive_ceiling},
            "gpu_launches": 2 * args.steps, "parity_rows_max_rel_err": parity,
            "parity_rows_score_rel_err": parity_sum, "parity_rows_aggregate_rel_err": parity_agg,
            "parity_check": {"rows": 32, "tolerance_per_row": 2e-5, "tolerance_score": 1e-5,
@@ -857,7 +871,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-rows", type=int, default=320)
+    ap.add_argument("--cpu-rows", type=int, default=1000)
     ap.add_argument("--ref-rows", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--N", type=int, default=50000, help="dataset size (profiling runs use less)")
