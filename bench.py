@@ -286,6 +286,11 @@ def run_ours(args, w):
            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
            "naive_form_ceiling": {"value": naive_ceiling, "unit": UNIT, "basis": naive_basis,
                                   "value_over_ceiling": value / naive_ceiling},
+           # the paper's own speedups of its approximations over its naive loop (Sec. 4), on
+           # hardware it does not state: context only, not a comparable measurement
+           "paper_context": {"dual_tree_speedup_max": 667, "sampled_dual_tree_speedup_max": 3.8e6,
+                             "hardware": "not stated", "basis": "over the paper's own naive exact loop",
+                             "this_value_over_cpu_oracle": (value / cpu["value"]) if cpu else None},
            "gpu_launches": 2 * args.steps, "parity_rows_max_rel_err": parity,
            "parity_rows_score_rel_err": parity_sum, "parity_rows_aggregate_rel_err": parity_agg,
            "parity_check": {"rows": 32, "tolerance_per_row": 2e-5, "tolerance_score": 1e-5,
