@@ -419,6 +419,8 @@ typedef struct {
     double umma_bf16_tflops;    /* the same, whole GPU at the clock seen (2 flop per MAC, 1e12) */
     double mma_tf32_mac_per_clk_sm;   /* legacy mma.sync m16n8k8 TF32, FP32 accumulate */
     double mma_bf16_mac_per_clk_sm;   /* legacy mma.sync m16n8k16 BF16, FP32 accumulate */
+    double umma_tf32_mac_per_clk_sm;  /* tcgen05.mma kind::tf32, M = 128, N = 256, K = 8, back to
+                                         back from one thread (the d >= 16 gradient's dot products) */
 } cde_peaks;
 
 int cde_measure_peaks(cde_ctx *ctx, cde_peaks *out);

@@ -80,7 +80,8 @@ class cde_peaks(ctypes.Structure):
                 ("ffma_per_clk_sm", ctypes.c_double), ("ex2_per_clk_sm", ctypes.c_double),
                 ("ffma_tops", ctypes.c_double), ("ex2_tops", ctypes.c_double),
                 ("umma_bf16_mac_per_clk_sm", ctypes.c_double), ("umma_bf16_tflops", ctypes.c_double),
-                ("mma_tf32_mac_per_clk_sm", ctypes.c_double), ("mma_bf16_mac_per_clk_sm", ctypes.c_double)]
+                ("mma_tf32_mac_per_clk_sm", ctypes.c_double), ("mma_bf16_mac_per_clk_sm", ctypes.c_double),
+                ("umma_tf32_mac_per_clk_sm", ctypes.c_double)]
 
 
 _lib = None

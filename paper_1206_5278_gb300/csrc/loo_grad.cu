@@ -35,6 +35,7 @@
 #include <cmath>
 
 #include "cde_internal.h"
+#include "tc_util.cuh"
 
 namespace cde {
 
@@ -48,8 +49,9 @@ struct GradArgs {
     float a1, a2;          // Gaussian log2(e)/(2 h^2); Epanechnikov 1/h^2
     int64_t i_per_split;   // multiple of the tile
     float* part;           // [n_split][N][6]
-    const uint32_t* xsplit;   // d >= 16: TF32 hi rows [Np][DK + 4], then lo rows (k_grad_split)
+    const uint32_t* xsplit;   // d >= 16: TF32 hi words [Np][DK] in the MMA core-matrix layout, then lo
     const float* xnorm;       // d >= 16: |x_i|^2 [Np]
+    int* err;                 // the context's device-wait word (k_grad_tc)
 };
 
 constexpr int kGradThreads = 128;
@@ -211,56 +213,6 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// d >= 16: the x cross-term on the tensor cores.  |x_j - x_i|^2 =
-// n_j + n_i - 2 x_j.x_i with the dot products of a 16-row x 8-point tile from
-// m16n8k8 TF32 MMAs on split operands (x = hi + lo, products hi*hi + hi*lo +
-// lo*hi, FP32 accumulation), norms n in FP32, the result clamped at 0.  Each
-// warp owns 16 rows (their split fragments stay in registers); the CTA copies
-// 64 points at a time, split once per call by k_grad_split, into shared
-// memory, and handles each row's two points per accumulator lane pair with
-// packed FP32x2 arithmetic.
-// ---------------------------------------------------------------------------
-constexpr int kGMWarps = 4, kGMTile = 64;
-
-__device__ __forceinline__ void mma_tf32_g(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// Once per call: every point's x split into TF32 hi + lo, as rows of DK + 4
-// words (the padded shared-memory row of the tile kernel, so a 64-point tile
-// is one contiguous block to copy), and its squared norm (FP32, dimension 0
-// first).  A block handles 32 points: coalesced reads of each x row, then the
-// 32 consecutive padded rows written out contiguously.
-template <int DK>
-__global__ void __launch_bounds__(256) k_grad_split(const float* __restrict__ xs, int64_t Np, int d,
-                                                    uint32_t* __restrict__ xsplit, float* __restrict__ xnorm) {
-    constexpr int RS = DK + 4;
-    __shared__ float v[32][RS];
-    const int64_t p0 = (int64_t)blockIdx.x * 32;
-    for (int e = threadIdx.x; e < 32 * RS; e += 256) {
-        const int c = e / 32, pp = e % 32;
-        v[pp][c] = c < d ? xs[(int64_t)c * Np + p0 + pp] : 0.f;   // p0 + pp < Np (Np a multiple of 256)
-    }
-    __syncthreads();
-    uint32_t* hi = xsplit + p0 * RS;
-    uint32_t* lo = xsplit + Np * RS + p0 * RS;
-    for (int e = threadIdx.x; e < 32 * RS; e += 256) {
-        const float x = v[e / RS][e % RS];
-        const uint32_t h = __float_as_uint(x) & 0xffffe000u;
-        hi[e] = h;
-        lo[e] = __float_as_uint(x - __uint_as_float(h));
-    }
-    if (threadIdx.x < 32) {
-        float n = 0.f;
-        for (int c = 0; c < d; ++c) n = fmaf(v[threadIdx.x][c], v[threadIdx.x][c], n);
-        xnorm[p0 + threadIdx.x] = n;
-    }
-}
-
 // Two adjacent points' contributions to one row (the row's a1 m_x, a2 m_y in
 // both lanes) through the packed FP32x2 pipe; the operations of grad_accumulate2.
 template <int KERN>
@@ -271,138 +223,236 @@ __device__ __forceinline__ void grad_accumulate_pts(bool ok0, bool ok1, float2 d
                            SB, SBx);
 }
 
-// shared memory of one tile buffer: split rows hi, lo, then norms and y
-template <int DK>
-__host__ __device__ constexpr int grad_mma_buf_words() { return 2 * kGMTile * (DK + 4) + 2 * kGMTile; }
+// ---- d >= 16 on the 5th-generation tensor cores (k_grad_tc) ------------------
+//
+// The cross term x_j . x_i of |x_j - x_i|^2 = n_j + n_i - 2 x_j . x_i is a
+// true contraction over the dimensions with rows j and points i as the two
+// free indices, so it runs as tcgen05 MMAs (kind::tf32, M = 128 rows, N = PT
+// points, K = 8 per instruction) with the accumulator in tensor memory, on
+// split operands x = hi + lo (hi the TF32 truncation, lo the exact FP32
+// remainder): hi hi + hi lo + lo hi, FP32 accumulation, about 2^-20 of
+// sum_k |x_jk x_ik| per dot product; the norms n are FP32 and the distance is
+// clamped at 0.  Warp 0 copies the CTA's 128
+// split rows once and each point tile by bulk copies into a two-stage ring,
+// and one thread issues the MMAs into one of two TMEM buffers.  Sixteen
+// epilogue warps (four per TMEM lane quadrant, one quarter of the tile's
+// columns each) read their dot products with tcgen05.ld, release the buffer
+// and form the per-pair sums of grad_accumulate_pts.  Every wait is bounded.
 
-__device__ __forceinline__ void cp_async16_g(uint32_t* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
+constexpr int kGTRows = 128;                      // rows per CTA: the TMEM lanes, MMA M
+constexpr int kGTEpi = 16;                        // epilogue warps
+constexpr int kGTThreads = 32 * (1 + kGTEpi);     // warp 0: copies and MMA issue
+
+template <int DK>
+struct GradTc {
+    static constexpr int PT = DK <= 32 ? 256 : 128;   // points per tile (MMA N)
+    static constexpr int COLS = PT / 4;               // columns per epilogue warp
+    static constexpr int A_WORDS = kGTRows * DK;      // one split (hi or lo) of the rows
+    static constexpr int B_WORDS = PT * DK;           // one split of a point tile
+    static constexpr uint32_t SBO = DK * 32;          // bytes between 8-row groups: DK / 4 core matrices
+};
+
+template <int DK>
+struct GradTcSmem {
+    uint32_t ah[GradTc<DK>::A_WORDS], al[GradTc<DK>::A_WORDS];
+    uint32_t bh[2][GradTc<DK>::B_WORDS], bl[2][GradTc<DK>::B_WORDS];
+    float red[kGTEpi][5][32];
+    unsigned long long full[2], empty[2], tfull[2], tempty[2], afull;
+    uint32_t tmem_base;
+    int abort;
+};
+
+// Once per call: every point's x split into TF32 hi + lo in the K-major,
+// no-swizzle core-matrix layout of the MMA operands (word (p, k) at
+// (p / 8) 8 DK + (k / 4) 32 + (p % 8) 4 + k % 4: a tile of points starting at
+// a multiple of 8 is one contiguous block), and its squared norm.  A block
+// handles 32 points.
+template <int DK>
+__global__ void __launch_bounds__(256) k_grad_split_tc(const float* __restrict__ xs, int64_t Np, int d,
+                                                       uint32_t* __restrict__ xsplit, float* __restrict__ xnorm) {
+    __shared__ float v[32][DK + 1];
+    const int64_t p0 = (int64_t)blockIdx.x * 32;
+    for (int e = threadIdx.x; e < 32 * DK; e += 256) {
+        const int c = e / 32, pp = e % 32;
+        v[pp][c] = c < d ? xs[(int64_t)c * Np + p0 + pp] : 0.f;   // p0 + pp < Np (a multiple of 256)
+    }
+    __syncthreads();
+    uint32_t* hi = xsplit + p0 * DK;
+    uint32_t* lo = xsplit + Np * DK + p0 * DK;
+    for (int w = threadIdx.x; w < 32 * DK; w += 256) {
+        const int grp = w / (8 * DK), rem = w % (8 * DK);
+        const int kc = rem / 32, r8 = (rem % 32) / 4, k4 = rem % 4;
+        const float x = v[8 * grp + r8][4 * kc + k4];
+        const uint32_t h = __float_as_uint(x) & 0xffffe000u;
+        hi[w] = h;
+        lo[w] = __float_as_uint(x - __uint_as_float(h));
+    }
+    if (threadIdx.x < 32) {
+        float n = 0.f;
+        for (int c = 0; c < d; ++c) n = fmaf(v[threadIdx.x][c], v[threadIdx.x][c], n);
+        xnorm[p0 + threadIdx.x] = n;
+    }
 }
 
-// Start copying tile t0's split rows, norms and y into buffer `buf` (one
-// commit group per thread).
-template <int DK>
-__device__ __forceinline__ void grad_mma_fetch(const GradArgs& g, uint32_t* buf, int64_t t0) {
-    constexpr int RS = DK + 4;
-    const int tid = threadIdx.x;
-    const uint32_t* sh = g.xsplit + CDE_CK(t0, g.Np, 402) * RS;   // kGMTile * RS contiguous words
-    const uint32_t* sl = g.xsplit + (g.Np + t0) * RS;
-    for (int e = tid; e < kGMTile * RS / 4; e += kGMWarps * 32) {
-        cp_async16_g(buf + 4 * e, sh + 4 * e);
-        cp_async16_g(buf + kGMTile * RS + 4 * e, sl + 4 * e);
+// One epilogue pass over `n` columns already in registers (point p0 + c for
+// column c; the caller's row j): distances from the dot products and the norms,
+// then the sums of grad_accumulate_pts.
+template <int KERN, int NC>
+__device__ __forceinline__ void grad_tc_columns(const GradArgs& g, const float (&dot)[NC], int64_t p0, int64_t i1,
+                                                int j, float nj, float yj, float am, float bm, float2& SA, float2& SAx,
+                                                float2& SAy, float2& SB, float2& SBx) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float a1 = g.a1, a2 = g.a2;
+#pragma unroll
+    for (int c = 0; c < NC; c += 4) {
+        const int64_t p = p0 + c;   // < Np: tiles never pass the padded length
+        const float4 n4 = __ldg(reinterpret_cast<const float4*>(g.xnorm + CDE_CK(p, g.Np - 3, 410)));
+        const float4 y4 = __ldg(reinterpret_cast<const float4*>(g.y + p));
+        const int ip = (int)p;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 dd = make_float2(dot[c + 2 * h], dot[c + 2 * h + 1]);
+            const float2 nip = h ? make_float2(n4.z, n4.w) : make_float2(n4.x, n4.y);
+            const float2 yip = h ? make_float2(y4.z, y4.w) : make_float2(y4.x, y4.y);
+            const float2 s2 = __ffma2_rn(dd, make_float2(-2.f, -2.f), __fadd2_rn(make_float2(nj, nj), nip));
+            const float2 dx2 = make_float2(fmaxf(s2.x, 0.f), fmaxf(s2.y, 0.f));
+            const float2 dy = __ffma2_rn(yip, m1, make_float2(yj, yj));
+            const float2 dy2 = __fmul2_rn(dy, dy);
+            const int ia = ip + 2 * h;
+            grad_accumulate_pts<KERN>(ia < i1 && ia != j, ia + 1 < i1 && ia + 1 != j, dx2, dy2, am, bm, a1, a2, SA,
+                                      SAx, SAy, SB, SBx);
+        }
     }
-    if (tid < kGMTile / 4) {
-        cp_async16_g(buf + 2 * kGMTile * RS + 4 * tid, g.xnorm + t0 + 4 * tid);
-        cp_async16_g(buf + 2 * kGMTile * RS + kGMTile + 4 * tid, g.y + t0 + 4 * tid);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 template <int DK, int KERN>
-__global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g) {
-    constexpr int KK = DK / 8, RS = DK + 4;  // padded smem row (bank spread)
-    extern __shared__ float4 gm_dyn[];      // two tile buffers (the next tile is copied during this one)
-    uint32_t* const bufs = reinterpret_cast<uint32_t*>(gm_dyn);
+__global__ void __launch_bounds__(kGTThreads, 1) k_grad_tc(const GradArgs g) {
+    using C = GradTc<DK>;
+    extern __shared__ float4 gt_dyn[];
+    GradTcSmem<DK>& S = *reinterpret_cast<GradTcSmem<DK>*>(gt_dyn);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int gq = lane >> 2, t = lane & 3;
     const int64_t N = g.N, Np = g.Np;
-    const int64_t i0 = (int64_t)blockIdx.y * g.i_per_split;
-    const int64_t i1 = min(N, i0 + g.i_per_split);
-    int jr[2];
-    float nj[2], yj[2], mxj[2], myj[2];
-    uint32_t ah[KK][4], al[KK][4];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int64_t j = (int64_t)blockIdx.x * (kGMWarps * 16) + warp * 16 + gq + 8 * h;
-        jr[h] = (int)j;   // N < 2^31
-        const int64_t jc = j < N ? j : 0;
-        nj[h] = g.xnorm[jc];
-        yj[h] = g.y[jc];
-        mxj[h] = g.mx[jc];
-        myj[h] = g.my[jc];
-#pragma unroll
-        for (int kk = 0; kk < KK; ++kk) {
-            const int c0 = 8 * kk + t, c1 = c0 + 4;
-            ah[kk][h] = g.xsplit[jc * RS + c0];                 // a0 / a1: (row g [+8], k t)
-            al[kk][h] = g.xsplit[(Np + jc) * RS + c0];
-            ah[kk][2 + h] = g.xsplit[jc * RS + c1];             // a2 / a3: (row g [+8], k t+4)
-            al[kk][2 + h] = g.xsplit[(Np + jc) * RS + c1];
+    const int64_t r0 = (int64_t)blockIdx.x * kGTRows;
+    const int64_t i0 = (int64_t)blockIdx.y * g.i_per_split, i1 = min(N, i0 + g.i_per_split);
+    const int ntiles = i0 < i1 ? (int)((i1 - i0 + C::PT - 1) / C::PT) : 0;
+    const uint32_t* xh = g.xsplit;
+    const uint32_t* xl = g.xsplit + Np * DK;
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&S.full[s]), 1);
+            mbar_init(smem_u32(&S.empty[s]), 1);
+            mbar_init(smem_u32(&S.tfull[s]), 1);
+            mbar_init(smem_u32(&S.tempty[s]), kGTEpi);
         }
+        mbar_init(smem_u32(&S.afull), 1);
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const float a1 = g.a1, a2 = g.a2;
-    const float amj[2] = {a1 * mxj[0], a1 * mxj[1]}, bmj[2] = {a2 * myj[0], a2 * myj[1]};
-    float2 SA[2], SAx[2], SAy[2], SB[2], SBx[2];
+    if (warp == 0) tmem_alloc(smem_u32(&S.tmem_base), 2 * C::PT);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = S.tmem_base;
+    volatile int* abort_flag = &S.abort;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // the CTA's rows, then the first two point tiles
+            const uint32_t ab = smem_u32(&S.afull);
+            mbar_arrive_expect_tx(ab, 2u * C::A_WORDS * 4u);
+            bulk_g2s(smem_u32(S.ah), xh + CDE_CK(r0, Np - kGTRows + 1, 411) * DK, C::A_WORDS * 4u, ab);
+            bulk_g2s(smem_u32(S.al), xl + r0 * DK, C::A_WORDS * 4u, ab);
+            for (int k = 0; k < 2 && k < ntiles; ++k) {
+                const int64_t t0 = i0 + (int64_t)k * C::PT;
+                const uint32_t fb = smem_u32(&S.full[k]);
+                mbar_arrive_expect_tx(fb, 2u * C::B_WORDS * 4u);
+                bulk_g2s(smem_u32(S.bh[k]), xh + CDE_CK(t0, Np - C::PT + 1, 412) * DK, C::B_WORDS * 4u, fb);
+                bulk_g2s(smem_u32(S.bl[k]), xl + t0 * DK, C::B_WORDS * 4u, fb);
+            }
+            constexpr uint32_t idesc = tc_idesc_tf32(kGTRows, C::PT);
+            bool ok = mbar_wait(ab, 0, abort_flag, g.err, 0x100);
+            for (int k = 0; k < ntiles && ok; ++k) {
+                const int s = k & 1, b = k & 1;
+                const uint32_t ph = (uint32_t)(k >> 1) & 1u;
+                ok = mbar_wait(smem_u32(&S.full[s]), ph, abort_flag, g.err, 0x200) &&
+                     mbar_wait(smem_u32(&S.tempty[b]), ph ^ 1u, abort_flag, g.err, 0x400);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t dt = tbase + (uint32_t)(b * C::PT);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) SA[h] = SAx[h] = SAy[h] = SB[h] = SBx[h] = make_float2(0.f, 0.f);
-    const float2 m1 = make_float2(-1.f, -1.f);
-    if (i0 < i1) grad_mma_fetch<DK>(g, bufs, i0);
-    int cur = 0;
-    for (int64_t t0 = i0; t0 < i1; t0 += kGMTile) {
-        // the next tile into the other buffer (its last readers passed the previous barrier)
-        if (t0 + kGMTile < i1) grad_mma_fetch<DK>(g, bufs + (cur ^ 1) * grad_mma_buf_words<DK>(), t0 + kGMTile);
-        else asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's copies
-        __syncthreads();
-        const uint32_t* xh = bufs + cur * grad_mma_buf_words<DK>();
-        const uint32_t* xl = xh + kGMTile * RS;
-        const float* ni_s = reinterpret_cast<const float*>(xl + kGMTile * RS);
-        const float* yi_s = ni_s + kGMTile;
-        const int n_in = (int)min((int64_t)kGMTile, i1 - t0);   // points of the tile inside the split
-        const int t032 = (int)t0;
-        // 4 n-tiles (32 points) at a time: independent accumulators hide the MMA latency
-#pragma unroll 1
-        for (int n4 = 0; n4 < kGMTile / 32; ++n4) {
-            float D[4][4];
-#pragma unroll
-            for (int n = 0; n < 4; ++n) D[n][0] = D[n][1] = D[n][2] = D[n][3] = 0.f;
-#pragma unroll
-            for (int kk = 0; kk < KK; ++kk) {
-#pragma unroll
-                for (int n = 0; n < 4; ++n) {
-                    const int pr = (32 * n4 + 8 * n + gq) * RS + 8 * kk + t;
-                    const uint32_t bh0 = xh[pr], bh1 = xh[pr + 4], bl0 = xl[pr], bl1 = xl[pr + 4];
-                    mma_tf32_g(D[n], ah[kk], bh0, bh1);
-                    mma_tf32_g(D[n], ah[kk], bl0, bl1);
-                    mma_tf32_g(D[n], al[kk], bh0, bh1);
+                for (int ks = 0; ks < DK / 8; ++ks) {
+                    const uint64_t dah = tc_sdesc(smem_u32(S.ah) + 256 * ks, 128, C::SBO);
+                    const uint64_t dal = tc_sdesc(smem_u32(S.al) + 256 * ks, 128, C::SBO);
+                    const uint64_t dbh = tc_sdesc(smem_u32(S.bh[s]) + 256 * ks, 128, C::SBO);
+                    const uint64_t dbl = tc_sdesc(smem_u32(S.bl[s]) + 256 * ks, 128, C::SBO);
+                    tc_mma_tf32(dt, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+                    tc_mma_tf32(dt, dah, dbl, idesc, 1u);
+                    tc_mma_tf32(dt, dal, dbh, idesc, 1u);
+                }
+                tc_commit(smem_u32(&S.empty[s]));
+                tc_commit(smem_u32(&S.tfull[b]));
+                if (k + 2 < ntiles) {   // tile k + 2 into this stage once these MMAs have read it
+                    ok = mbar_wait(smem_u32(&S.empty[s]), ph, abort_flag, g.err, 0x800);
+                    if (!ok) break;
+                    const int64_t t2 = i0 + (int64_t)(k + 2) * C::PT;
+                    const uint32_t fb = smem_u32(&S.full[s]);
+                    mbar_arrive_expect_tx(fb, 2u * C::B_WORDS * 4u);
+                    bulk_g2s(smem_u32(S.bh[s]), xh + CDE_CK(t2, Np - C::PT + 1, 413) * DK, C::B_WORDS * 4u, fb);
+                    bulk_g2s(smem_u32(S.bl[s]), xl + t2 * DK, C::B_WORDS * 4u, fb);
                 }
             }
-            // accumulator (row g [+8], points 2t, 2t + 1): a packed pair per row
-#pragma unroll
-            for (int n = 0; n < 4; ++n) {
-                const int p = 32 * n4 + 8 * n + 2 * t;
-                const float2 nip = *reinterpret_cast<const float2*>(&ni_s[p]);
-                const float2 yip = *reinterpret_cast<const float2*>(&yi_s[p]);
-                const int ia = t032 + p;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float2 dd = make_float2(D[n][2 * h], D[n][2 * h + 1]);
-                    // n_j + n_i - 2 dot, clamped at 0
-                    const float2 s = __ffma2_rn(dd, make_float2(-2.f, -2.f), __fadd2_rn(make_float2(nj[h], nj[h]), nip));
-                    const float2 dx2 = make_float2(fmaxf(s.x, 0.f), fmaxf(s.y, 0.f));
-                    const float2 dy = __ffma2_rn(yip, m1, make_float2(yj[h], yj[h]));
-                    const float2 dy2 = __fmul2_rn(dy, dy);
-                    grad_accumulate_pts<KERN>(p < n_in && ia != jr[h], p + 1 < n_in && ia + 1 != jr[h], dx2, dy2,
-                                              amj[h], bmj[h], a1, a2, SA[h], SAx[h], SAy[h], SB[h], SBx[h]);
-                }
+            // every copy this thread started has been waited for (full) or was never
+            // started; the last MMAs are waited for by the epilogue (tfull)
+            if (ok && ntiles > 0) {
+                // the last two tiles' stage releases, so no MMA reads shared memory at exit
+                for (int k = ntiles - 2 < 0 ? 0 : ntiles - 2; k < ntiles; ++k)
+                    mbar_wait(smem_u32(&S.empty[k & 1]), (uint32_t)(k >> 1) & 1u, abort_flag, g.err, 0x800);
             }
         }
-        __syncthreads();   // every warp is done with this buffer before it is refilled
-        cur ^= 1;
-    }
-    // combine the two point lanes, then the 4 lanes that share a row (t = 0..3), fixed order
+        __syncwarp();
+    } else {
+        // epilogue: TMEM lane quadrant q (its 32 rows), column block cb of every tile
+        const int e = warp - 1, q = warp & 3, cb = e >> 2;
+        const int64_t jr = r0 + 32 * q + lane;
+        const int j = (int)jr;   // N < 2^31
+        const int64_t jc = jr < N ? jr : 0;
+        const float nj = g.xnorm[jc], yj = g.y[jc];
+        const float am = g.a1 * g.mx[jc], bm = g.a2 * g.my[jc];
+        float2 SA = make_float2(0.f, 0.f), SAx = SA, SAy = SA, SB = SA, SBx = SA;
+        for (int k = 0; k < ntiles; ++k) {
+            const int b = k & 1;
+            if (!mbar_wait(smem_u32(&S.tfull[b]), (uint32_t)(k >> 1) & 1u, abort_flag, g.err, 0x1000)) break;
+            tc_fence_after();
+            const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * C::PT + cb * C::COLS);
+            const int64_t p0 = i0 + (int64_t)k * C::PT + cb * C::COLS;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float v[5] = {SA[h].x + SA[h].y, SAx[h].x + SAx[h].y, SAy[h].x + SAy[h].y, SB[h].x + SB[h].y,
-                      SBx[h].x + SBx[h].y};
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            v[q] += __shfl_xor_sync(0xffffffffu, v[q], 1);
-            v[q] += __shfl_xor_sync(0xffffffffu, v[q], 2);
+            for (int h = 0; h < C::COLS / 32; ++h) {
+                float dot[32];
+                tmem_ld32(ta + 32 * h, dot);
+                tmem_wait_ld();
+                if (h == C::COLS / 32 - 1) {   // all of this warp's columns are in registers: release the buffer
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&S.tempty[b]));
+                }
+                grad_tc_columns<KERN, 32>(g, dot, p0 + 32 * h, i1, j, nj, yj, am, bm, SA, SAx, SAy, SB, SBx);
+            }
         }
-        if (t == 0 && jr[h] < N) {
-            float* pp = g.part + ((int64_t)blockIdx.y * N + jr[h]) * 6;
+        S.red[e][0][lane] = SA.x + SA.y;
+        S.red[e][1][lane] = SAx.x + SAx.y;
+        S.red[e][2][lane] = SAy.x + SAy.y;
+        S.red[e][3][lane] = SB.x + SB.y;
+        S.red[e][4][lane] = SBx.x + SBx.y;
+        asm volatile("bar.sync 1, %0;" ::"r"(kGTEpi * 32) : "memory");   // the epilogue warps only
+        if (cb == 0 && jr < N) {
+            float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {   // column blocks in order
+                const int ee = 4 * c + (e & 3);
+#pragma unroll
+                for (int m = 0; m < 5; ++m) v[m] += S.red[ee][m][lane];
+            }
+            float* pp = g.part + ((int64_t)blockIdx.y * N + jr) * 6;
             pp[0] = 0.f;
             pp[1] = v[0];
             pp[2] = v[1];
@@ -410,6 +460,12 @@ __global__ void __launch_bounds__(kGMWarps * 32) k_loo_grad_mma(const GradArgs g
             pp[4] = v[3];
             pp[5] = v[4];
         }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 2 * C::PT);
     }
 }
 
@@ -550,17 +606,36 @@ static void launch_grad(const GradArgs& g, dim3 grid, cudaStream_t st, bool epan
 }
 
 template <int DK>
-static int launch_grad_mma(const GradArgs& g, dim3 grid, cudaStream_t st, bool epan) {
-    const size_t smem = (size_t)2 * grad_mma_buf_words<DK>() * sizeof(uint32_t);
+static int launch_grad_tc(const GradArgs& g, dim3 grid, cudaStream_t st, bool epan) {
+    const size_t smem = sizeof(GradTcSmem<DK>);
     static bool attr = false;   // per instantiation; guarded by the ctx lock
     if (!attr) {
-        CDE_CUDA(cudaFuncSetAttribute(k_loo_grad_mma<DK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        CDE_CUDA(cudaFuncSetAttribute(k_loo_grad_mma<DK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CDE_CUDA(cudaFuncSetAttribute(k_grad_tc<DK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CDE_CUDA(cudaFuncSetAttribute(k_grad_tc<DK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
-    if (epan) k_loo_grad_mma<DK, 1><<<grid, kGMWarps * 32, smem, st>>>(g);
-    else k_loo_grad_mma<DK, 0><<<grid, kGMWarps * 32, smem, st>>>(g);
+    if (epan) k_grad_tc<DK, 1><<<grid, kGTThreads, smem, st>>>(g);
+    else k_grad_tc<DK, 0><<<grid, kGTThreads, smem, st>>>(g);
     return CDE_OK;
+}
+
+// Point splits for k_grad_tc (one CTA per SM): the count, among those that
+// leave every CTA at least 8 point tiles, whose CTAs fill the last wave best.
+static int64_t grad_tc_splits(int64_t row_ctas, int64_t tiles, int sms) {
+    int64_t best = 1;
+    double best_eff = -1.0;
+    for (int64_t ns = 1; ns <= 16; ++ns) {
+        const int64_t per = (tiles + ns - 1) / ns;
+        if (ns > 1 && per < 8) break;
+        const int64_t n_eff = (tiles + per - 1) / per, ctas = row_ctas * n_eff;
+        const int64_t waves = (ctas + sms - 1) / sms;
+        const double eff = (double)ctas / (double)(waves * sms);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = ns;
+        }
+    }
+    return best;
 }
 
 int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, double* d_out3,
@@ -581,13 +656,19 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     const bool tc = D.d >= 16;   // tensor-core cross term
     const int DREG = D.d <= 4 ? 4 : D.d <= 8 ? 8 : D.d <= 16 ? 16 : D.d <= 32 ? 32 : 64;
     const int JB = DREG <= 8 ? 4 : DREG <= 32 ? 2 : 1;
-    const int64_t rows_per_cta = tc ? (int64_t)kGMWarps * 16 : (int64_t)kGradThreads * JB;
-    const int tile = tc ? kGMTile : kGradThreads;
+    const int DK = D.d <= 16 ? 16 : D.d <= 32 ? 32 : 64;
+    const int64_t rows_per_cta = tc ? (int64_t)kGTRows : (int64_t)kGradThreads * JB;
+    const int tile = tc ? (DK <= 32 ? 256 : 128) : kGradThreads;
     const int64_t gx = (D.N + rows_per_cta - 1) / rows_per_cta;
-    // split i so that the launch has about 8 CTAs per SM
-    int64_t want = (tc ? 16LL : 8LL) * ctx->sm_count;
-    int64_t ns = (want + gx - 1) / gx;
     const int64_t tiles = (D.N + tile - 1) / tile;
+    int64_t ns;
+    if (tc) {
+        ns = grad_tc_splits(gx, tiles, ctx->sm_count);
+    } else {
+        // split i so that the launch has about 8 CTAs per SM
+        const int64_t want = 8LL * ctx->sm_count;
+        ns = (want + gx - 1) / gx;
+    }
     if (ns > tiles) ns = tiles;
     if (ns < 1) ns = 1;
     const int64_t tiles_per = (tiles + ns - 1) / ns;
@@ -605,20 +686,20 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     uint32_t* xsplit = nullptr;
     float* xnorm = nullptr;
     if (tc) {
-        const int DK = D.d <= 16 ? 16 : D.d <= 32 ? 32 : 64;
-        CDE_CUDA(cudaMallocAsync((void**)&xsplit, (size_t)2 * D.Np * (DK + 4) * sizeof(uint32_t), st));
+        CDE_CUDA(cudaMallocAsync((void**)&xsplit, (size_t)2 * D.Np * DK * sizeof(uint32_t), st));
         CDE_CUDA(cudaMallocAsync((void**)&xnorm, (size_t)D.Np * sizeof(float), st));
         g.xsplit = xsplit;
         g.xnorm = xnorm;
+        g.err = ctx->d_err + kErrTensorWait;
         const unsigned sb = (unsigned)(D.Np / 32);
-        if (DK == 16) k_grad_split<16><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
-        else if (DK == 32) k_grad_split<32><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
-        else k_grad_split<64><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
+        if (DK == 16) k_grad_split_tc<16><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
+        else if (DK == 32) k_grad_split_tc<32><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
+        else k_grad_split_tc<64><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
         CDE_CUDA(cudaGetLastError());
         timing_begin(ctx, st);
-        const int rl = DK == 16 ? launch_grad_mma<16>(g, grid, st, epan)
-                       : DK == 32 ? launch_grad_mma<32>(g, grid, st, epan)
-                                  : launch_grad_mma<64>(g, grid, st, epan);
+        const int rl = DK == 16 ? launch_grad_tc<16>(g, grid, st, epan)
+                       : DK == 32 ? launch_grad_tc<32>(g, grid, st, epan)
+                                  : launch_grad_tc<64>(g, grid, st, epan);
         timing_end(ctx, st);
         if (rl != CDE_OK) return rl;
     } else {

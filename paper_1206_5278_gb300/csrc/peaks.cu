@@ -52,6 +52,7 @@ __global__ void k_peak_ex2(float* out, int iters, long long* cyc) {
 // (values irrelevant), cycles from the first issue to the commit's arrival.
 constexpr int kPeakUmmaSmem = 120 * 1024;
 
+template <int KIND>   // 0: kind::f16 BF16 (K = 16), 1: kind::tf32 (K = 8); M = 128, N = 256
 __global__ void __launch_bounds__(128) k_peak_umma(int R, long long* cyc, int* err) {
     extern __shared__ float4 pk_dyn[];
     unsigned char* A = reinterpret_cast<unsigned char*>(pk_dyn);   // 128 x 32 bf16
@@ -73,10 +74,13 @@ __global__ void __launch_bounds__(128) k_peak_umma(int R, long long* cyc, int* e
     tc_fence_after();
     const uint32_t t = tb;
     if (tid == 0) {
-        const uint32_t idesc = tc_idesc_bf16(128, 256);
+        const uint32_t idesc = KIND == 0 ? tc_idesc_bf16(128, 256) : tc_idesc_tf32(128, 256);
         const uint64_t ad = tc_sdesc(smem_u32(A), 128, 512), bd = tc_sdesc(smem_u32(B), 128, 512);
         const long long c0 = clock64();
-        for (int r = 0; r < R; ++r) tc_mma_bf16(t, ad, bd, idesc, r > 0 ? 1u : 0u);
+        for (int r = 0; r < R; ++r) {
+            if constexpr (KIND == 0) tc_mma_bf16(t, ad, bd, idesc, r > 0 ? 1u : 0u);
+            else tc_mma_tf32(t, ad, bd, idesc, r > 0 ? 1u : 0u);
+        }
         tc_commit(smem_u32(&bar));
         mbar_wait(smem_u32(&bar), 0, &abort_flag, err, 1);
         cyc[blockIdx.x] = clock64() - c0;
@@ -152,16 +156,17 @@ static int measure_mma(cde_ctx* ctx, int kind, double* mac_per_clk) {
     return CDE_OK;
 }
 
-static int measure_umma(cde_ctx* ctx, double* mac_per_clk) {
+static int measure_umma(cde_ctx* ctx, int kind, double* mac_per_clk) {
     const int S = ctx->sm_count, R = 4096;
     long long* cyc = nullptr;
     int* err = ctx->d_err + kErrTensorWait;
     CDE_CUDA(cudaMalloc((void**)&cyc, sizeof(long long) * S));
-    CDE_CUDA(cudaFuncSetAttribute(k_peak_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeakUmmaSmem));
+    auto kern = kind == 0 ? k_peak_umma<0> : k_peak_umma<1>;
+    CDE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeakUmmaSmem));
     std::vector<long long> hc(S);
     double best = 0;
     for (int rep = 0; rep < 3; ++rep) {
-        k_peak_umma<<<S, 128, kPeakUmmaSmem, ctx->stream>>>(R, cyc, err);
+        kern<<<S, 128, kPeakUmmaSmem, ctx->stream>>>(R, cyc, err);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e == cudaSuccess) e = cudaMemcpy(hc.data(), cyc, sizeof(long long) * S, cudaMemcpyDeviceToHost);
@@ -172,7 +177,7 @@ static int measure_umma(cde_ctx* ctx, double* mac_per_clk) {
         std::vector<long long> srt(hc);
         std::sort(srt.begin(), srt.end());
         const double med = (double)srt[S / 2];
-        const double r = (double)R * 128 * 256 * 16 / med;
+        const double r = (double)R * 128 * 256 * (kind == 0 ? 16 : 8) / med;
         if (r > best) best = r;
     }
     cudaFree(cyc);
@@ -230,11 +235,13 @@ int measure_peaks(cde_ctx* ctx, cde_peaks* o) {
     o->ex2_tops = res[1][0] / 1e12;
     o->ffma_per_clk_sm = res[0][0] / S / f;
     o->ex2_per_clk_sm = res[1][0] / S / (res[1][1] > 0 ? res[1][1] : f);
-    double umma = 0;
-    const int rc = measure_umma(ctx, &umma);
+    double umma = 0, umma32 = 0;
+    int rc = measure_umma(ctx, 0, &umma);
+    if (rc == CDE_OK) rc = measure_umma(ctx, 1, &umma32);
     if (rc != CDE_OK) return rc;
     o->umma_bf16_mac_per_clk_sm = umma;
     o->umma_bf16_tflops = 2.0 * umma * S * f / 1e12;
+    o->umma_tf32_mac_per_clk_sm = umma32;
     double m0 = 0, m1 = 0;
     int rc2 = measure_mma(ctx, 0, &m0);
     if (rc2 == CDE_OK) rc2 = measure_mma(ctx, 1, &m1);

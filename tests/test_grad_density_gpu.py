@@ -83,6 +83,49 @@ def test_gradient_rows_with_underflowing_numerators(ctx, d, h1, h2, d_mma):
     cde.cde_destroy_dataset(ctx, ds)
 
 
+@pytest.mark.parametrize("N,d,kernel", [
+    (127, 16, "gauss"),     # fewer rows than one row tile, one point tile
+    (300, 24, "gauss"),     # two point tiles: every stage used once, ragged rows
+    (2049, 33, "gauss"),    # 64-wide operands (128-point tiles), ragged tail of one point
+    (1500, 64, "gauss"),    # the largest d
+    (20000, 20, "gauss"),   # several point splits per row tile
+    (2049, 33, "epan"),
+])
+def test_gradient_tensor_core_tiles_and_splits(ctx, N, d, kernel):
+    """Tile, stage and split structure of the d >= 16 gradient kernel (dot
+    products on the 5th-generation tensor cores): the two derivatives within
+    1e-4 and L within 1e-5 of their scales, per-row terms within the Gram-form
+    bound (Gaussian), sampled rows for the largest case; a repeated call is
+    bitwise equal."""
+    w = synth.grad_workload(N=N, d=d, seed=N + d)
+    ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True, kernel=kernel)
+    h1, h2 = (0.6 * math.sqrt(d / 8), 0.15) if kernel == "gauss" else (1.6 * math.sqrt(d), 0.6)
+    out = cde.cde_loo_grad(ctx, ds, h1, h2)
+    g_rows = cde.cde_loo_grad_rows(ctx, ds, h1, h2)
+    rows = None if N <= 2049 else np.unique(np.concatenate(
+        [[0, N - 1], np.random.default_rng(5).choice(N, 62, replace=False)]))
+    ref, ref_rows = oracle.grad(w.x, w.y, h1, h2, rows=rows, standardize_x=True, per_row=True, kernel=kernel)
+    sel = g_rows if rows is None else g_rows[rows]
+    assert np.array_equal(np.isinf(sel[:, 0]), np.isinf(ref_rows[:, 0]))
+    fin = np.isfinite(ref_rows[:, 0])
+    xs = oracle.standardize(w.x)
+    n = (xs ** 2).sum(1)
+    nsel = n if rows is None else n[rows]
+    if kernel == "gauss":   # (Epanechnikov rows near a support edge are ill-conditioned: aggregates only)
+        tol = 2e-5 + (nsel + n.max()) * 2.0 ** -19 / (2 * h1 * h1)
+        assert np.all(np.abs(sel[fin, 0] - ref_rows[fin, 0]) <= tol[fin])
+    if rows is None:
+        scale = np.abs(ref_rows[fin]).sum(0)
+        if np.isfinite(ref[0]):
+            assert abs(out[0] - ref[0]) <= 1e-5 * scale[0], (out[0], ref[0])
+        assert abs(out[1] - ref[1]) <= 1e-4 * scale[1], (out[1], ref[1])
+        assert abs(out[2] - ref[2]) <= 1e-4 * scale[2], (out[2], ref[2])
+    else:
+        np.testing.assert_allclose(sel[:, 1:], ref_rows[:, 1:], rtol=1e-4, atol=1e-4 * np.abs(ref_rows[:, 1:]).max())
+    assert np.array_equal(cde.cde_loo_grad_rows(ctx, ds, h1, h2), g_rows)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
 def test_gradient_matches_central_differences_on_gpu(ctx):
     w = synth.grad_workload(N=3000, d=8, seed=5)
     ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True)
@@ -219,6 +262,7 @@ def test_measured_pipe_rates(ctx):
     assert 100 <= p.ffma_per_clk_sm <= 130
     assert 14 <= p.ex2_per_clk_sm <= 34
     assert 2000 <= p.umma_bf16_mac_per_clk_sm <= 4200
+    assert 1000 <= p.umma_tf32_mac_per_clk_sm <= 2200
     assert p.umma_bf16_tflops > 500
 
 
