@@ -115,9 +115,12 @@ int cde_dataset_info(cde_ctx *ctx, cde_dataset ds, int64_t *N, int *d_x, double 
  * *code receives the first failed check's code since the last call (0: none)
  * and clears it -- a failed check redirects its access to index 0 instead of
  * faulting.  In the normal library *enabled = 0.  In both builds a
- * tensor-core kernel (cde_density) whose bounded on-device wait ran out
- * reports CDE_CHECK_TENSOR_WAIT | (which waits) here when no index check
- * failed, and the report is cleared.  Waits for the device to be idle.
+ * tensor-core kernel whose bounded on-device wait ran out reports
+ * CDE_CHECK_TENSOR_WAIT | (which waits) here when no index check failed, and
+ * the report is cleared: bits 0x1 and 0x2 for cde_density, 0x100 ... 0x1000
+ * for the d_x >= 16 gradient (cde_loo_grad, cde_loo_grad_rows), 64 for
+ * cde_selftest_wait.  The synchronous calls also return CDE_ETIMEOUT then.
+ * Waits for the device to be idle.
  * enabled may be NULL.
  */
 #define CDE_CHECK_TENSOR_WAIT 0x10000u
@@ -214,6 +217,10 @@ int cde_loo_rows(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const d
  *   dL/dln h2 = sum_j (E_Aj[dy^2] / h2^2 - 1),
  * E_Aj weighting i by K_h1 K_h2 and E_Bj by K_h1.
  *   out3 = {L_cond, dL/dln h1, dL/dln h2} (host, or device with CDE_OUT_DEVICE).
+ * For d_x >= 16 the squared distances come from the Gram form
+ * n_j + n_i - 2 x_j.x_i with 3xTF32 dot products on the tensor cores (absolute
+ * error up to about 2^-19 (n_j + n_i)); CDE_ETIMEOUT if one of that kernel's
+ * bounded device waits ran out (results invalid).
  */
 int cde_loo_grad(cde_ctx *ctx, cde_dataset ds, double h1, double h2, double *out3, int flags,
                  void *stream);

@@ -33,6 +33,7 @@
 // log-ratio and derivatives are formed in FP64, and rows are summed in a
 // fixed order, so the result is bitwise reproducible.
 #include <cmath>
+#include <string>
 
 #include "cde_internal.h"
 #include "tc_util.cuh"
@@ -738,6 +739,18 @@ CDE_CHECK_READER(check_status_grad)
 
 using namespace cde;
 
+// After a synchronous d >= 16 call: a bounded tensor-core wait that ran out on
+// the device (k_grad_tc) becomes CDE_ETIMEOUT, and the report is cleared.
+static int grad_wait_status(cde_ctx* ctx, const Dataset& D, cudaStream_t st, const char* who) {
+    if (D.d < 16) return CDE_OK;
+    int tw = 0;
+    CDE_CUDA(cudaMemcpyAsync(&tw, ctx->d_err + kErrTensorWait, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CDE_CUDA(cudaStreamSynchronize(st));
+    if (!tw) return CDE_OK;
+    CDE_CUDA(cudaMemsetAsync(ctx->d_err + kErrTensorWait, 0, sizeof(int), st));
+    return set_error(CDE_ETIMEOUT, std::string(who) + ": a tensor-core wait ran out on the device");
+}
+
 extern "C" int cde_loo_grad(cde_ctx* ctx, cde_dataset ds, double h1, double h2, double* out3,
                             int flags, void* stream) {
     CDE_NVTX("cde_loo_grad");
@@ -760,7 +773,7 @@ extern "C" int cde_loo_grad(cde_ctx* ctx, cde_dataset ds, double h1, double h2, 
     if (rc != CDE_OK) return rc;
     if (e != cudaSuccess) return cuda_error(e, "cde_loo_grad: copy");
     if (e2 != cudaSuccess) return cuda_error(e2, "cde_loo_grad: kernels");
-    return CDE_OK;
+    return grad_wait_status(ctx, *D, st, "cde_loo_grad");
 }
 
 extern "C" int cde_loo_grad_rows(cde_ctx* ctx, cde_dataset ds, double h1, double h2, double* rows_out,
@@ -785,5 +798,5 @@ extern "C" int cde_loo_grad_rows(cde_ctx* ctx, cde_dataset ds, double h1, double
     if (rc != CDE_OK) return rc;
     if (e != cudaSuccess) return cuda_error(e, "cde_loo_grad_rows: copy");
     if (e2 != cudaSuccess) return cuda_error(e2, "cde_loo_grad_rows: kernels");
-    return CDE_OK;
+    return grad_wait_status(ctx, *D, st, "cde_loo_grad_rows");
 }
