@@ -295,10 +295,12 @@ __global__ void __launch_bounds__(256) k_grad_split_tc(const float* __restrict__
     }
 }
 
-// One epilogue pass over `n` columns already in registers (point p0 + c for
+// One epilogue pass over NC columns already in registers (point p0 + c for
 // column c; the caller's row j): distances from the dot products and the norms,
-// then the sums of grad_accumulate_pts.
-template <int KERN, int NC>
+// then the sums of grad_accumulate_pts.  MASKED: some column is past the split's
+// end or is one of the warp's own rows (the leave-one-out exclusion); otherwise
+// every pair counts and no per-pair test is made.
+template <int KERN, int NC, bool MASKED>
 __device__ __forceinline__ void grad_tc_columns(const GradArgs& g, const float (&dot)[NC], int64_t p0, int64_t i1,
                                                 int j, float nj, float yj, float am, float bm, float2& SA, float2& SAx,
                                                 float2& SAy, float2& SB, float2& SBx) {
@@ -320,8 +322,8 @@ __device__ __forceinline__ void grad_tc_columns(const GradArgs& g, const float (
             const float2 dy = __ffma2_rn(yip, m1, make_float2(yj, yj));
             const float2 dy2 = __fmul2_rn(dy, dy);
             const int ia = ip + 2 * h;
-            grad_accumulate_pts<KERN>(ia < i1 && ia != j, ia + 1 < i1 && ia + 1 != j, dx2, dy2, am, bm, a1, a2, SA,
-                                      SAx, SAy, SB, SBx);
+            const bool ok0 = !MASKED || (ia < i1 && ia != j), ok1 = !MASKED || (ia + 1 < i1 && ia + 1 != j);
+            grad_accumulate_pts<KERN>(ok0, ok1, dx2, dy2, am, bm, a1, a2, SA, SAx, SAy, SB, SBx);
         }
     }
 }
@@ -436,7 +438,11 @@ __global__ void __launch_bounds__(kGTThreads, 1) k_grad_tc(const GradArgs g) {
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_u32(&S.tempty[b]));
                 }
-                grad_tc_columns<KERN, 32>(g, dot, p0 + 32 * h, i1, j, nj, yj, am, bm, SA, SAx, SAy, SB, SBx);
+                const int64_t pb = p0 + 32 * h, jlo = r0 + 32 * q;   // warp-uniform
+                if (pb + 32 > i1 || (pb < jlo + 32 && pb + 32 > jlo))
+                    grad_tc_columns<KERN, 32, true>(g, dot, pb, i1, j, nj, yj, am, bm, SA, SAx, SAy, SB, SBx);
+                else
+                    grad_tc_columns<KERN, 32, false>(g, dot, pb, i1, j, nj, yj, am, bm, SA, SAx, SAy, SB, SBx);
             }
         }
         S.red[e][0][lane] = SA.x + SA.y;
