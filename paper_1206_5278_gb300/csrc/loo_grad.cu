@@ -34,6 +34,7 @@
 // fixed order, so the result is bitwise reproducible.
 #include <cmath>
 #include <string>
+#include <type_traits>
 
 #include "cde_internal.h"
 #include "tc_util.cuh"
@@ -170,33 +171,41 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
         yt[tid] = g.y[it];
         __syncthreads();
         const int n = (int)min((int64_t)kGradThreads, i1 - t0);
-        for (int t = 0; t < n; ++t) {
-            const int i32 = (int)(t0 + t);  // N < 2^31
-            float xi[DREG];
+        // the leave-one-out test is needed only where the tile meets this CTA's rows
+        const int64_t r0 = (int64_t)blockIdx.x * kGradThreads * JB;
+        const auto body = [&](auto masked) {
+            for (int t = 0; t < n; ++t) {
+                const int i32 = (int)(t0 + t);  // N < 2^31
+                float xi[DREG];
 #pragma unroll
-            for (int c = 0; c < DREG; c += 4) {
-                const float4 v4 = *reinterpret_cast<const float4*>(&xt[t][c]);
-                xi[c] = v4.x;
-                xi[c + 1] = v4.y;
-                xi[c + 2] = v4.z;
-                xi[c + 3] = v4.w;
-            }
-            const float yi = yt[t];
-#pragma unroll
-            for (int p = 0; p < JP; ++p) {
-                // x_j - x_i as fma(x_i, -1, x_j): the scalar subtraction's rounding
-                float2 dx2 = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int c = 0; c < DREG; ++c) {
-                    const float2 q = __ffma2_rn(make_float2(xi[c], xi[c]), m1, xj[p][c]);
-                    dx2 = __ffma2_rn(q, q, dx2);
+                for (int c = 0; c < DREG; c += 4) {
+                    const float4 v4 = *reinterpret_cast<const float4*>(&xt[t][c]);
+                    xi[c] = v4.x;
+                    xi[c + 1] = v4.y;
+                    xi[c + 2] = v4.z;
+                    xi[c + 3] = v4.w;
                 }
-                const float2 dy = __ffma2_rn(make_float2(yi, yi), m1, yj[p]);
-                const float2 dy2 = __fmul2_rn(dy, dy);
-                grad_accumulate2<KERN>(i32 != jj[2 * p], i32 != jj[2 * p + 1], dx2, dy2, am[p], bm[p], a1, a2,
-                                       SA[p], SAx[p], SAy[p], SB[p], SBx[p]);
+                const float yi = yt[t];
+#pragma unroll
+                for (int p = 0; p < JP; ++p) {
+                    // x_j - x_i as fma(x_i, -1, x_j): the scalar subtraction's rounding
+                    float2 dx2 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int c = 0; c < DREG; ++c) {
+                        const float2 q = __ffma2_rn(make_float2(xi[c], xi[c]), m1, xj[p][c]);
+                        dx2 = __ffma2_rn(q, q, dx2);
+                    }
+                    const float2 dy = __ffma2_rn(make_float2(yi, yi), m1, yj[p]);
+                    const float2 dy2 = __fmul2_rn(dy, dy);
+                    const bool ok0 = !decltype(masked)::value || i32 != jj[2 * p];
+                    const bool ok1 = !decltype(masked)::value || i32 != jj[2 * p + 1];
+                    grad_accumulate2<KERN>(ok0, ok1, dx2, dy2, am[p], bm[p], a1, a2, SA[p], SAx[p], SAy[p], SB[p],
+                                           SBx[p]);
+                }
             }
-        }
+        };
+        if (t0 < r0 + kGradThreads * JB && t0 + kGradThreads > r0) body(std::true_type{});
+        else body(std::false_type{});
     }
 #pragma unroll
     for (int b = 0; b < JB; ++b) {
