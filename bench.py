@@ -113,7 +113,8 @@ def run_reference(args, w):
         return
     from oracle import oracle
     oracle.build()
-    rows_per_step = args.ref_rows
+    # two rows per host thread of the oracle, so that every core works in every step
+    rows_per_step = args.ref_rows if args.ref_rows > 0 else 2 * oracle.default_threads()
     times = []
     for s in range(args.warmup + args.steps):
         _, dt, th, _ = oracle_sample(w, rows_per_step, seed=s, kernel=args.kernel)
@@ -880,7 +881,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-rows", type=int, default=1000)
-    ap.add_argument("--ref-rows", type=int, default=8)
+    ap.add_argument("--ref-rows", type=int, default=0, help="0: two rows per host thread")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--N", type=int, default=50000, help="dataset size (profiling runs use less)")
     ap.add_argument("--workload", default="scale",
