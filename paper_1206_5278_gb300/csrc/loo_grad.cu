@@ -266,6 +266,7 @@ template <int DK>
 struct GradTcSmem {
     uint32_t ah[GradTc<DK>::A_WORDS], al[GradTc<DK>::A_WORDS];
     uint32_t bh[2][GradTc<DK>::B_WORDS], bl[2][GradTc<DK>::B_WORDS];
+    float ny[2][2][GradTc<DK>::PT];   // the tile's norms and y, per stage
     float red[kGTEpi][5][32];
     unsigned long long full[2], empty[2], tfull[2], tempty[2], afull;
     uint32_t tmem_base;
@@ -305,21 +306,23 @@ __global__ void __launch_bounds__(256) k_grad_split_tc(const float* __restrict__
 }
 
 // One epilogue pass over NC columns already in registers (point p0 + c for
-// column c; the caller's row j): distances from the dot products and the norms,
+// column c, its norm and y at ns[c], ys[c]; the caller's row j): distances from
+// the dot products and the norms,
 // then the sums of grad_accumulate_pts.  MASKED: some column is past the split's
 // end or is one of the warp's own rows (the leave-one-out exclusion); otherwise
 // every pair counts and no per-pair test is made.
 template <int KERN, int NC, bool MASKED>
-__device__ __forceinline__ void grad_tc_columns(const GradArgs& g, const float (&dot)[NC], int64_t p0, int64_t i1,
-                                                int j, float nj, float yj, float am, float bm, float2& SA, float2& SAx,
-                                                float2& SAy, float2& SB, float2& SBx) {
+__device__ __forceinline__ void grad_tc_columns(const GradArgs& g, const float (&dot)[NC], const float* ns,
+                                                const float* ys, int64_t p0, int64_t i1, int j, float nj, float yj,
+                                                float am, float bm, float2& SA, float2& SAx, float2& SAy, float2& SB,
+                                                float2& SBx) {
     const float2 m1 = make_float2(-1.f, -1.f);
     const float a1 = g.a1, a2 = g.a2;
 #pragma unroll
     for (int c = 0; c < NC; c += 4) {
-        const int64_t p = p0 + c;   // < Np: tiles never pass the padded length
-        const float4 n4 = __ldg(reinterpret_cast<const float4*>(g.xnorm + CDE_CK(p, g.Np - 3, 410)));
-        const float4 y4 = __ldg(reinterpret_cast<const float4*>(g.y + p));
+        const int64_t p = p0 + c;
+        const float4 n4 = *reinterpret_cast<const float4*>(ns + c);   // shared memory, broadcast
+        const float4 y4 = *reinterpret_cast<const float4*>(ys + c);
         const int ip = (int)p;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -337,6 +340,20 @@ __device__ __forceinline__ void grad_tc_columns(const GradArgs& g, const float (
     }
 }
 
+// Bulk-copy point tile t0 (hi and lo split rows, norms, y) into stage s,
+// completing on full[s]; one thread.
+template <int DK>
+__device__ __forceinline__ void grad_tc_load(const GradArgs& g, GradTcSmem<DK>& S, int s, int64_t t0) {
+    using C = GradTc<DK>;
+    const uint32_t fb = smem_u32(&S.full[s]);
+    mbar_arrive_expect_tx(fb, 2u * C::B_WORDS * 4u + 2u * C::PT * 4u);
+    const int64_t tc = CDE_CK(t0, g.Np - C::PT + 1, 412);   // t0 + PT <= Np
+    bulk_g2s(smem_u32(S.bh[s]), g.xsplit + tc * DK, C::B_WORDS * 4u, fb);
+    bulk_g2s(smem_u32(S.bl[s]), g.xsplit + (g.Np + tc) * DK, C::B_WORDS * 4u, fb);
+    bulk_g2s(smem_u32(S.ny[s][0]), g.xnorm + tc, C::PT * 4u, fb);
+    bulk_g2s(smem_u32(S.ny[s][1]), g.y + tc, C::PT * 4u, fb);
+}
+
 template <int DK, int KERN>
 __global__ void __launch_bounds__(kGTThreads, 1) k_grad_tc(const GradArgs g) {
     using C = GradTc<DK>;
@@ -352,7 +369,7 @@ __global__ void __launch_bounds__(kGTThreads, 1) k_grad_tc(const GradArgs g) {
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&S.full[s]), 1);
-            mbar_init(smem_u32(&S.empty[s]), 1);
+            mbar_init(smem_u32(&S.empty[s]), 1 + kGTEpi);   // its MMAs and every epilogue warp
             mbar_init(smem_u32(&S.tfull[s]), 1);
             mbar_init(smem_u32(&S.tempty[s]), kGTEpi);
         }
@@ -374,13 +391,7 @@ __global__ void __launch_bounds__(kGTThreads, 1) k_grad_tc(const GradArgs g) {
             mbar_arrive_expect_tx(ab, 2u * C::A_WORDS * 4u);
             bulk_g2s(smem_u32(S.ah), xh + CDE_CK(r0, Np - kGTRows + 1, 411) * DK, C::A_WORDS * 4u, ab);
             bulk_g2s(smem_u32(S.al), xl + r0 * DK, C::A_WORDS * 4u, ab);
-            for (int k = 0; k < 2 && k < ntiles; ++k) {
-                const int64_t t0 = i0 + (int64_t)k * C::PT;
-                const uint32_t fb = smem_u32(&S.full[k]);
-                mbar_arrive_expect_tx(fb, 2u * C::B_WORDS * 4u);
-                bulk_g2s(smem_u32(S.bh[k]), xh + CDE_CK(t0, Np - C::PT + 1, 412) * DK, C::B_WORDS * 4u, fb);
-                bulk_g2s(smem_u32(S.bl[k]), xl + t0 * DK, C::B_WORDS * 4u, fb);
-            }
+            for (int k = 0; k < 2 && k < ntiles; ++k) grad_tc_load<DK>(g, S, k, i0 + (int64_t)k * C::PT);
             constexpr uint32_t idesc = tc_idesc_tf32(kGTRows, C::PT);
             bool ok = mbar_wait(ab, 0, abort_flag, g.err, 0x100);
             for (int k = 0; k < ntiles && ok; ++k) {
@@ -403,20 +414,18 @@ __global__ void __launch_bounds__(kGTThreads, 1) k_grad_tc(const GradArgs g) {
                 }
                 tc_commit(smem_u32(&S.empty[s]));
                 tc_commit(smem_u32(&S.tfull[b]));
-                if (k + 2 < ntiles) {   // tile k + 2 into this stage once these MMAs have read it
-                    ok = mbar_wait(smem_u32(&S.empty[s]), ph, abort_flag, g.err, 0x800);
+                // tile k + 1 into the other stage once tile k - 1's MMAs and epilogue are done
+                // with it (MMA k is already queued, so the tensor cores do not wait on this)
+                if (k >= 1 && k + 1 < ntiles) {
+                    const int sp = (k - 1) & 1;
+                    ok = mbar_wait(smem_u32(&S.empty[sp]), (uint32_t)((k - 1) >> 1) & 1u, abort_flag, g.err, 0x800);
                     if (!ok) break;
-                    const int64_t t2 = i0 + (int64_t)(k + 2) * C::PT;
-                    const uint32_t fb = smem_u32(&S.full[s]);
-                    mbar_arrive_expect_tx(fb, 2u * C::B_WORDS * 4u);
-                    bulk_g2s(smem_u32(S.bh[s]), xh + CDE_CK(t2, Np - C::PT + 1, 413) * DK, C::B_WORDS * 4u, fb);
-                    bulk_g2s(smem_u32(S.bl[s]), xl + t2 * DK, C::B_WORDS * 4u, fb);
+                    grad_tc_load<DK>(g, S, sp, i0 + (int64_t)(k + 1) * C::PT);
                 }
             }
             // every copy this thread started has been waited for (full) or was never
-            // started; the last MMAs are waited for by the epilogue (tfull)
+            // started; the last two tiles' stage releases (their MMAs and epilogues)
             if (ok && ntiles > 0) {
-                // the last two tiles' stage releases, so no MMA reads shared memory at exit
                 for (int k = ntiles - 2 < 0 ? 0 : ntiles - 2; k < ntiles; ++k)
                     mbar_wait(smem_u32(&S.empty[k & 1]), (uint32_t)(k >> 1) & 1u, abort_flag, g.err, 0x800);
             }
@@ -437,6 +446,8 @@ __global__ void __launch_bounds__(kGTThreads, 1) k_grad_tc(const GradArgs g) {
             tc_fence_after();
             const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * C::PT + cb * C::COLS);
             const int64_t p0 = i0 + (int64_t)k * C::PT + cb * C::COLS;
+            const float* ns = &S.ny[k & 1][0][cb * C::COLS];
+            const float* ys = &S.ny[k & 1][1][cb * C::COLS];
 #pragma unroll
             for (int h = 0; h < C::COLS / 32; ++h) {
                 float dot[32];
@@ -449,10 +460,14 @@ __global__ void __launch_bounds__(kGTThreads, 1) k_grad_tc(const GradArgs g) {
                 }
                 const int64_t pb = p0 + 32 * h, jlo = r0 + 32 * q;   // warp-uniform
                 if (pb + 32 > i1 || (pb < jlo + 32 && pb + 32 > jlo))
-                    grad_tc_columns<KERN, 32, true>(g, dot, pb, i1, j, nj, yj, am, bm, SA, SAx, SAy, SB, SBx);
+                    grad_tc_columns<KERN, 32, true>(g, dot, ns + 32 * h, ys + 32 * h, pb, i1, j, nj, yj, am, bm, SA,
+                                                    SAx, SAy, SB, SBx);
                 else
-                    grad_tc_columns<KERN, 32, false>(g, dot, pb, i1, j, nj, yj, am, bm, SA, SAx, SAy, SB, SBx);
+                    grad_tc_columns<KERN, 32, false>(g, dot, ns + 32 * h, ys + 32 * h, pb, i1, j, nj, yj, am, bm, SA,
+                                                     SAx, SAy, SB, SBx);
             }
+            __syncwarp();   // this warp is done with the stage's norms and y
+            if (lane == 0) mbar_arrive(smem_u32(&S.empty[k & 1]));
         }
         S.red[e][0][lane] = SA.x + SA.y;
         S.red[e][1][lane] = SAx.x + SAx.y;
