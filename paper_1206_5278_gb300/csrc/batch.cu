@@ -92,12 +92,8 @@ template <int G1, int G2, int KERN>
 static int launch_batch_shape_k(const LooArgs* d_items, const int2* d_work, int n_work, int* counter,
                                 int grid, cudaStream_t st, int dmax) {
     using C = MmaCfg<G1, G2>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        CDE_CUDA(cudaFuncSetAttribute(k_loo_batch<G1, G2, KERN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)C::smem_bytes(kMaxD)));
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    CDE_CUDA(smem_attr_once(attr, k_loo_batch<G1, G2, KERN>, (int)C::smem_bytes(kMaxD)));
     k_loo_batch<G1, G2, KERN><<<grid, C::kThreads, C::smem_bytes(dmax), st>>>(d_items, d_work, n_work, counter);
     CDE_CUDA(cudaGetLastError());
     return CDE_OK;

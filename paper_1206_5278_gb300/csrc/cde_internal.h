@@ -131,6 +131,20 @@ namespace cde {
 // the start event, every dominant launch re-records the end event.  Threads
 // that set t_untimed (the request-queue worker) never touch the events.
 inline thread_local bool t_untimed = false;
+
+// A kernel's dynamic shared-memory limit is a per-device attribute: set it once
+// per device (the current one) and call site; `done` marks devices 0..63.
+template <class Kernel>
+inline cudaError_t smem_attr_once(std::atomic<uint64_t>& done, Kernel kern, int bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 inline void timing_reset(cde_ctx* c) {
     if (!t_untimed) c->tev_open = false;
 }

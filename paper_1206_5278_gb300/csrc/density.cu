@@ -654,14 +654,9 @@ int density_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, const 
     CDE_CUDA(cudaMallocAsync((void**)&dpart, (size_t)a.P * a.MT * kTcM * sizeof(float), st));
     a.part = part;
     a.dpart = dpart;
-    static bool attr = false;
-    if (!attr) {
-        CDE_CUDA(cudaFuncSetAttribute(k_density_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(TcSmem)));
-        CDE_CUDA(cudaFuncSetAttribute(k_density_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(TcSmem)));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr0{0}, attr1{0};
+    CDE_CUDA(smem_attr_once(attr0, k_density_tc<0>, (int)sizeof(TcSmem)));
+    CDE_CUDA(smem_attr_once(attr1, k_density_tc<1>, (int)sizeof(TcSmem)));
     timing_begin(ctx, st);
     if (epan) k_density_tc<1><<<a.P, kTcProd, sizeof(TcSmem), st>>>(a);
     else k_density_tc<0><<<a.P, kTcProd, sizeof(TcSmem), st>>>(a);

@@ -639,12 +639,9 @@ static void launch_grad(const GradArgs& g, dim3 grid, cudaStream_t st, bool epan
 template <int DK>
 static int launch_grad_tc(const GradArgs& g, dim3 grid, cudaStream_t st, bool epan) {
     const size_t smem = sizeof(GradTcSmem<DK>);
-    static bool attr = false;   // per instantiation; guarded by the ctx lock
-    if (!attr) {
-        CDE_CUDA(cudaFuncSetAttribute(k_grad_tc<DK, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        CDE_CUDA(cudaFuncSetAttribute(k_grad_tc<DK, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr0{0}, attr1{0};   // per instantiation
+    CDE_CUDA(smem_attr_once(attr0, k_grad_tc<DK, 0>, (int)smem));
+    CDE_CUDA(smem_attr_once(attr1, k_grad_tc<DK, 1>, (int)smem));
     if (epan) k_grad_tc<DK, 1><<<grid, kGTThreads, smem, st>>>(g);
     else k_grad_tc<DK, 0><<<grid, kGTThreads, smem, st>>>(g);
     return CDE_OK;

@@ -292,13 +292,8 @@ template <int G1, int G2, int KERN>
 static int launch_shape_k(const LooArgs& a, int grid, cudaStream_t st) {
     using C = MmaCfg<G1, G2>;
     const size_t smem = C::smem_bytes(a.d);
-    static bool attr_set = false;  // per instantiation; guarded by the ctx lock
-    if (!attr_set) {
-        CDE_CUDA(cudaFuncSetAttribute(k_loo_mma<G1, G2, KERN>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)C::smem_bytes(kMaxD)));
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attr{0};   // per instantiation
+    CDE_CUDA(smem_attr_once(attr, k_loo_mma<G1, G2, KERN>, (int)C::smem_bytes(kMaxD)));
     k_loo_mma<G1, G2, KERN><<<grid, C::kThreads, smem, st>>>(a);
     CDE_CUDA(cudaGetLastError());
     return CDE_OK;

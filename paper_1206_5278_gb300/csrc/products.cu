@@ -550,14 +550,9 @@ static int cond_interval_enqueue(cde_ctx* ctx, const Dataset& D, double h1, doub
     a.lo = d_lo;
     a.hi = d_hi;
     a.samples = d_samples;
-    static bool attr = false;
-    if (!attr) {
-        CDE_CUDA(cudaFuncSetAttribute(k_cond_sample<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(SampleSmem)));
-        CDE_CUDA(cudaFuncSetAttribute(k_cond_sample<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sizeof(SampleSmem)));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr0{0}, attr1{0};
+    CDE_CUDA(smem_attr_once(attr0, k_cond_sample<0>, (int)sizeof(SampleSmem)));
+    CDE_CUDA(smem_attr_once(attr1, k_cond_sample<1>, (int)sizeof(SampleSmem)));
     // one CTA per query (grid.x allows 2^31 - 1)
     if (epan) k_cond_sample<1><<<(unsigned)Q, kSmpThreads, sizeof(SampleSmem), st>>>(a);
     else k_cond_sample<0><<<(unsigned)Q, kSmpThreads, sizeof(SampleSmem), st>>>(a);
