@@ -242,7 +242,20 @@ def run_ours(args, w):
         r_unit = float(peaks.ffma_per_clk_sm) if peaks is not None else 128.0
         naive_basis = "one saturating FMA per (pair, bandwidth pair): %d SMs x %.1f lanes/clk/SM (measured) x 2070 MHz" % (
             sms, r_unit)
-    naive_ceiling = sms * r_unit * 2070e6
+    naive_ceiling = sms * r_unit * 2070e6   # one GPU
+    # the pipes the kernel itself runs on, each against its measured rate at the max clock:
+    # the MUFU (G1 + G2 ex2 per pair, Gaussian) and the legacy tensor cores (G1 G2 TF32 plus
+    # 2 G1 G2 BF16 multiply-adds per pair: hi*hi, and hi*lo + lo*hi on one k16 MMA)
+    pipe_fracs = None
+    if peaks is not None:
+        pairs_s = value / world / (G1 * G2)   # per GPU
+        clk_sm = sms * 2070e6
+        mma_clk = (G1 * G2 / peaks.mma_tf32_mac_per_clk_sm + 2 * G1 * G2 / peaks.mma_bf16_mac_per_clk_sm)
+        pipe_fracs = {"tensor_mma_sync": pairs_s * mma_clk / clk_sm,
+                      "basis": "pairs/s x (G1 G2 / TF32 rate + 2 G1 G2 / BF16 rate) / (SMs x 2070 MHz), "
+                               "measured mma.sync rates"}
+        if args.kernel == "gauss":
+            pipe_fracs["mufu_ex2"] = pairs_s * (G1 + G2) / (peaks.ex2_per_clk_sm * clk_sm)
 
     # ---- parity spot check on sampled rows + CPU baseline (rank 0, N=1) ----
     cpu = None
@@ -286,7 +299,8 @@ def run_ours(args, w):
                    "includes": "dataset upload + standardise + nearest-neighbour shifts + grid + copy back"},
            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
            "naive_form_ceiling": {"value": naive_ceiling, "unit": UNIT, "basis": naive_basis,
-                                  "value_over_ceiling": value / naive_ceiling},
+                                  "value_over_ceiling": value / world / naive_ceiling},
+           "pipe_fractions": pipe_fracs,
            # the paper's own speedups of its approximations over its naive loop (Sec. 4), on
            # hardware it does not state: context only, not a comparable measurement
            "paper_context": {"dual_tree_speedup_max": 667, "sampled_dual_tree_speedup_max": 3.8e6,
