@@ -44,6 +44,33 @@ def test_batch_bitwise_equals_single(ctx):
         cde.cde_destroy_dataset(ctx, ds)
 
 
+def test_batch_bench_size(ctx):
+    """The batching workload as the benchmark runs it (256 datasets, N
+    log-uniform in [500, 20000], d in {1, 2, 4, 8}, 16 x 16 grids): every
+    member bitwise equal to its single launch, and the oracle's full grid for
+    the three smallest members, sampled rows for the largest."""
+    ws = synth.batch_workloads()
+    dss = _make(ctx, ws)
+    Lc, Le = cde.cde_loo_loglik_batch(ctx, dss, [w.h1 for w in ws], [w.h2 for w in ws])
+    for b, (w, ds) in enumerate(zip(ws, dss)):
+        sc, se = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
+        assert np.array_equal(sc, Lc[b]) and np.array_equal(se, Le[b]), w.name
+    order = np.argsort([w.N for w in ws])
+    for b in order[:3]:
+        w = ws[b]
+        ell, _ = oracle.loo_rows(w.x, w.y, w.h1, w.h2, standardize_x=w.standardize)
+        err = np.abs(Lc[b] - ell.sum(0)) / np.abs(ell).sum(0)
+        assert err.max() <= 1e-5, (w.name, err.max())
+    b = order[-1]
+    w = ws[b]
+    rows = np.random.default_rng(8).choice(w.N, 16, replace=False)
+    g = cde.cde_loo_rows(ctx, dss[b], w.h1, w.h2, rows)
+    ref, _ = oracle.loo_rows(w.x, w.y, w.h1, w.h2, rows=rows, standardize_x=w.standardize)
+    np.testing.assert_allclose(g, ref, rtol=2e-5, atol=2e-5)
+    for ds in dss:
+        cde.cde_destroy_dataset(ctx, ds)
+
+
 def test_batch_mixed_shapes(ctx):
     rng = np.random.default_rng(0)
     ws, grids = [], []

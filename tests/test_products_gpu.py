@@ -55,6 +55,31 @@ def test_cond_stats_match_oracle(ctx, kernel, N, d, Q):
     cde.cde_destroy_dataset(ctx, ds)
 
 
+@pytest.mark.parametrize("kernel,h1", [("gauss", 0.3), ("epan", 0.6)])
+def test_cond_stats_bench_size_sampled(ctx, kernel, h1):
+    """The products workload as the benchmark runs it (N = 100,000, d = 4,
+    10,000 queries, h2 = 0.1): 40 sampled queries, first and last included,
+    against the oracle with the tolerances above."""
+    N, d, Q = 100000, 4, 10000
+    x, y = synth.gmm_sine(N, d, seed=8)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True, kernel=kernel)
+    xq = synth.query_points(x, Q, seed=9)
+    yq = np.resize(y, Q).astype(np.float32)
+    mean, fat = cde.cde_cond_stats(ctx, ds, h1, 0.1, xq, yq)
+    rows = np.unique(np.concatenate([[0, Q - 1], np.random.default_rng(6).choice(Q, 38, replace=False)]))
+    ref = oracle.cond_products(x, y, h1, 0.1, xq[rows], yq=yq[rows], standardize_x=True, kernel=kernel)
+    m, f = mean[rows], fat[rows]
+    assert np.array_equal(np.isnan(m), np.isnan(ref["mean"]))
+    ok = ~np.isnan(ref["mean"])
+    sy = float(np.std(y))
+    assert np.all(np.abs(m[ok] - ref["mean"][ok]) <= 1e-5 * sy + 1e-5 * np.abs(ref["mean"][ok]))
+    fr = ref["fat"]
+    big = fr > 1e-6 * fr.max()
+    assert np.all(np.abs(f[big] - fr[big]) <= 1e-4 * fr[big])
+    assert np.all(np.abs(f[~big] - fr[~big]) <= 1e-6 * fr.max())
+    cde.cde_destroy_dataset(ctx, ds)
+
+
 def test_cond_stats_empty_support_and_device_io(ctx):
     import torch
     x, y = synth.gmm_sine(2000, 2, seed=5)
