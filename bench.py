@@ -517,16 +517,8 @@ def run_density(args):
     import torch
     from paper_1206_5278_gb300 import cde, synth
     ctx = cde.cde_init(0)
-    hbm_peak = 6688.8
-    try:
-        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
-    except (OSError, ValueError, KeyError):
-        pass
-    bf16_peak = 1863.5
-    try:
-        bf16_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
-    except (OSError, ValueError, KeyError):
-        pass
+    hbm_peak = _measured_peak("hbm_gbs", 6688.8)
+    bf16_peak = _measured_peak("bf16_tflops", 1863.5)
     cde.cde_timing_enable(ctx, True)
     runs = {}
     for Q, N in ((args.dens_Q, args.dens_N), (100, 500000)):
@@ -803,6 +795,15 @@ def run_dualtree(args):
     cde.cde_shutdown(ctx)
 
 
+def _measured_peak(key, default):
+    """A peak from the pool's measured-peaks file at the repository root, else
+    the value it held when this benchmark was written."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])
+    except (OSError, ValueError, KeyError, TypeError):
+        return default
+
+
 def run_serve(args):
     """Poisson stream, 70% density jobs (Q log-uniform [1, Q_max] x 256-point y
     grid), 30% selection jobs (16x16 grid + 20 Adam steps) over resident
@@ -875,14 +876,28 @@ def run_serve(args):
                    for p in payload]
         for t in tickets:
             t.result()
-        sat = len(payload) / (time.perf_counter() - t0)
+        sat_s = time.perf_counter() - t0
+        sat = len(payload) / sat_s
     finally:
         srv.stop()
+    # algorithmic HBM bytes of the saturation run: per density job the queries and the
+    # 256-point grid in, the Q x 256 densities out, and the dataset read once; per
+    # selection job the dataset read once per grid or gradient evaluation (21)
+    alg = 0
+    for p in payload:
+        w = ws[dss.index(p[1])]
+        dset = w.N * (w.d + 1) * 4
+        alg += (p[2].nbytes + 256 * 4 + p[2].shape[0] * 256 * 4 + dset) if p[0] == 0 else 21 * dset
+    hbm_peak = _measured_peak("hbm_gbs", 6688.8)
+    hbm = {"algorithmic_bytes": int(alg), "GB_s": alg / sat_s / 1e9, "peak_GB_s": hbm_peak,
+           "frac": alg / sat_s / 1e9 / hbm_peak,
+           "basis": "queries, grid, densities and one dataset read per density job; one dataset read "
+                    "per evaluation of a selection job; peak = measured copy bandwidth"}
     _line(workload="serve", metric="serving jobs/s with p50/p99 latency (density 70% / selection 30%)",
           unit="jobs/s", value=sat, steps=len(payload), warmup=1, ms_per_step=1e3 / sat,
           sequential={"jobs_per_s": cap, "p50_ms": 1e3 * float(np.percentile(seq_lat, 50)),
                       "p99_ms": 1e3 * float(np.percentile(seq_lat, 99))},
-          speedup_vs_sequential=sat / cap, loads=loads,
+          speedup_vs_sequential=sat / cap, loads=loads, hbm=hbm,
           config={"workload": "serve", "datasets": [w.N for w in ws], "d": [w.d for w in ws],
                   "jobs": len(payload), "Q_max": args.serve_Q_max, "streams": args.serve_streams})
     cde.cde_shutdown(ctx)
