@@ -262,7 +262,9 @@ int cde_loo_loglik_batch(cde_ctx *ctx, int n, const cde_dataset *ds, const doubl
  */
 int cde_autotune(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const double *h2, int G2,
                  int *units_per_tile, int *ctas_per_sm, double *best_ms);
-/* Read / set the tile parameters for the shape of a G1 x G2 grid (0 = default). */
+/* Read / set the tile parameters for the shape of a G1 x G2 grid (0 = default:
+ * 8 rows per tile, halved while a dataset's grid would give fewer than 64 tiles
+ * per resident CTA; cde_tuning_get reports the 8-row value then). */
 int cde_tuning_get(cde_ctx *ctx, int G1, int G2, int *units_per_tile, int *ctas_per_sm);
 int cde_tuning_set(cde_ctx *ctx, int G1, int G2, int units_per_tile, int ctas_per_sm);
 /*

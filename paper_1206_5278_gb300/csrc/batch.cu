@@ -176,7 +176,7 @@ static int build_plan(cde_ctx* ctx, const std::vector<BatchItem>& items, BatchPl
         a.rows = nullptr;
         a.n_rows = it.D->N;
         a.n_units = (int)((it.D->N + JW - 1) / JW);
-        a.units_per_tile = loo_units_per_tile(ctx, T1, T2);
+        a.units_per_tile = loo_units_per_tile(ctx, T1, T2, it.D->N);
         a.n_tiles = (a.n_units + a.units_per_tile - 1) / a.units_per_tile;
         a.G1r = it.G1;
         a.G2r = it.G2;
@@ -463,7 +463,7 @@ extern "C" int cde_autotune(cde_ctx* ctx, cde_dataset ds, const double* h1, int 
 extern "C" int cde_tuning_get(cde_ctx* ctx, int G1, int G2, int* units_per_tile, int* ctas_per_sm) {
     if (!ctx || G1 < 1 || G1 > 32 || G2 < 1 || G2 > 32) return set_error(CDE_EINVAL, "cde_tuning_get: bad arguments");
     const int T1 = loo_pad1(G1), T2 = loo_pad2(G2);
-    if (units_per_tile) *units_per_tile = loo_units_per_tile(ctx, T1, T2);
+    if (units_per_tile) *units_per_tile = loo_units_per_tile(ctx, T1, T2, 0);
     if (ctas_per_sm) *ctas_per_sm = loo_grid_ctas(ctx, T1, T2) / ctx->sm_count;
     return CDE_OK;
 }

@@ -362,7 +362,9 @@ inline int loo_pad2(int g) { return g <= 8 ? 8 : (g <= 16 ? 16 : 32); }
 int launch_loo_tile_kernel(int T1, int T2, const LooArgs& a, int grid, cudaStream_t st);
 void fill_loo_args(LooArgs& a, const Dataset& D, const double* h1, int g1, const double* h2,
                    int g2, int T1, int T2);
-int loo_units_per_tile(cde_ctx* ctx, int T1, int T2);
+// units per tile of a grid block shape over n_rows rows (the tuned value when set; n_rows = 0:
+// the per-shape default without the small-grid reduction)
+int loo_units_per_tile(cde_ctx* ctx, int T1, int T2, int64_t n_rows);
 int loo_grid_ctas(cde_ctx* ctx, int T1, int T2);
 
 }  // namespace cde

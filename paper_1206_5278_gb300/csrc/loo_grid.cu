@@ -374,11 +374,20 @@ static int shape_index(int T) { return T <= 8 ? 0 : T <= 16 ? 1 : 2; }
 // Units per tile: the autotuned value for this grid shape when the context has
 // one, else enough units for 8 rows per tile.  Both the single-dataset and the
 // batched launch use this, so they form identical tile partials.
-int loo_units_per_tile(cde_ctx* ctx, int T1, int T2) {
+int loo_units_per_tile(cde_ctx* ctx, int T1, int T2, int64_t n_rows) {
     const int t = ctx ? ctx->tune_upt[shape_index(T1)][shape_index(T2)] : 0;
     if (t > 0) return t;
     const int JW = 1024 / (T1 * T2);
-    return JW >= 8 ? 1 : 8 / JW;
+    int upt = JW >= 8 ? 1 : 8 / JW;
+    // Smaller tiles while the grid would give fewer than 64 tiles per resident CTA: the
+    // tiles come from an atomic queue, and the last CTAs to finish decide the launch's time.
+    // (N = 50,000 at 32 x 32: 70.3 ms with 8 rows per tile, 69.1 ms with 2.)
+    if (ctx && n_rows > 0) {
+        const int64_t units = (n_rows + JW - 1) / JW;
+        const int64_t want = 64LL * loo_grid_ctas(ctx, T1, T2);
+        while (upt > 1 && (units + upt - 1) / upt < want) upt >>= 1;
+    }
+    return upt;
 }
 
 int loo_grid_ctas(cde_ctx* ctx, int T1, int T2) {
@@ -394,7 +403,7 @@ size_t loo_grid_scratch_bytes(cde_ctx* ctx, const Dataset& D, int G1, int G2, in
             const int T2 = loo_pad2(G2 - l0 < 32 ? G2 - l0 : 32);
             const int JW = 1024 / (T1 * T2);
             const int64_t units = (n_rows + JW - 1) / JW;
-            const int upt = loo_units_per_tile(ctx, T1, T2);
+            const int upt = loo_units_per_tile(ctx, T1, T2, n_rows);
             const size_t b = (size_t)((units + upt - 1) / upt) * 2 * T1 * T2 * sizeof(double) + 256;
             if (b > mx) mx = b;
         }
@@ -419,7 +428,7 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
             a.rows = d_rows;
             a.n_rows = n_rows;
             a.n_units = (int)((n_rows + JW - 1) / JW);
-            a.units_per_tile = loo_units_per_tile(ctx, T1, T2);
+            a.units_per_tile = loo_units_per_tile(ctx, T1, T2, n_rows);
             a.n_tiles = (a.n_units + a.units_per_tile - 1) / a.units_per_tile;
             a.ell_rows = d_ell_rows ? d_ell_rows + (size_t)k0 * G2 + l0 : nullptr;
             a.ell_ld_row = (int64_t)G1 * G2;

@@ -82,7 +82,7 @@ extern "C" int cde_loo_loglik_noalloc(cde_ctx* ctx, cde_dataset ds, const double
     // as many tile slots as the scratch holds; tiles grow with N to fit
     const size_t slot_bytes = (size_t)2 * T1 * T2 * sizeof(double);
     const int max_tiles = (int)((kNoAllocScratchBytes - kNoAllocCounterBytes) / slot_bytes);
-    int upt = loo_units_per_tile(ctx, T1, T2);
+    int upt = loo_units_per_tile(ctx, T1, T2, D->N);
     if ((a.n_units + upt - 1) / upt > max_tiles) upt = (a.n_units + max_tiles - 1) / max_tiles;
     a.units_per_tile = upt;
     a.n_tiles = (a.n_units + upt - 1) / upt;
