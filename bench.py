@@ -223,9 +223,10 @@ def run_ours(args, w):
         p = None
     lanes = 128.0
     peak_max = 2 * lanes * sms * 2070e6 / 1e12
-    # DRAM bytes of one k_loo_mma<32,32> launch at N=50,000 from an ncu capture
-    # (profiles/k_loo_mma_32x32_N50000.md); not measured for other sizes.
-    traffic = 53256960 if (w.N == 50000 and G1 == 32 and G2 == 32 and args.kernel == "gauss") else None
+    # DRAM bytes of one k_loo_mma<32,32> launch at N=50,000 (2-row tiles) from an ncu
+    # capture (profiles/k_loo_mma_32x32_N50000.md): 10.3 MB read, 357.5 MB of FP64 tile
+    # partials written; not measured for other sizes.
+    traffic = 367792640 if (w.N == 50000 and G1 == 32 and G2 == 32 and args.kernel == "gauss") else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
             "frac": achieved / peak_max, "traffic": traffic, "kernel": "k_loo_mma", "kernel_ms": kms,
             "peak_basis": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x 2070 MHz (max clock)" % sms}
