@@ -647,17 +647,33 @@ static int launch_grad_tc(const GradArgs& g, dim3 grid, cudaStream_t st, bool ep
     return CDE_OK;
 }
 
-// Point splits for k_grad_tc (one CTA per SM): the count, among those that
-// leave every CTA at least 8 point tiles, whose CTAs fill the last wave best.
-static int64_t grad_tc_splits(int64_t row_ctas, int64_t tiles, int sms) {
+// Resident CTAs per SM of the SIMT gradient kernel (the Gaussian instantiation;
+// the Epanechnikov one uses no more registers), queried once per instantiation.
+template <int JB, int DREG>
+static int grad_simt_ctas_per_sm() {
+    static std::atomic<int> n{0};
+    int v = n.load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_loo_grad<JB, DREG, 0>, kGradThreads, 0) !=
+                cudaSuccess || v < 1)
+            v = 1;
+        n.store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+// Point splits: the count, among those that leave every CTA at least 8 point
+// tiles, whose CTAs fill the last wave of `slots` resident CTAs best (one CTA
+// per SM for k_grad_tc; the occupancy of k_loo_grad).
+static int64_t grad_splits(int64_t row_ctas, int64_t tiles, int64_t slots) {
     int64_t best = 1;
     double best_eff = -1.0;
     for (int64_t ns = 1; ns <= 16; ++ns) {
         const int64_t per = (tiles + ns - 1) / ns;
         if (ns > 1 && per < 8) break;
         const int64_t n_eff = (tiles + per - 1) / per, ctas = row_ctas * n_eff;
-        const int64_t waves = (ctas + sms - 1) / sms;
-        const double eff = (double)ctas / (double)(waves * sms);
+        const int64_t waves = (ctas + slots - 1) / slots;
+        const double eff = (double)ctas / (double)(waves * slots);
         if (eff > best_eff + 1e-9) {
             best_eff = eff;
             best = ns;
@@ -691,11 +707,11 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     const int64_t tiles = (D.N + tile - 1) / tile;
     int64_t ns;
     if (tc) {
-        ns = grad_tc_splits(gx, tiles, ctx->sm_count);
+        ns = grad_splits(gx, tiles, ctx->sm_count);
     } else {
-        // split i so that the launch has about 8 CTAs per SM
-        const int64_t want = 8LL * ctx->sm_count;
-        ns = (want + gx - 1) / gx;
+        const int per_sm = DREG == 4 ? grad_simt_ctas_per_sm<4, 4>()
+                           : DREG == 8 ? grad_simt_ctas_per_sm<4, 8>() : grad_simt_ctas_per_sm<2, 16>();
+        ns = grad_splits(gx, tiles, (int64_t)per_sm * ctx->sm_count);
     }
     if (ns > tiles) ns = tiles;
     if (ns < 1) ns = 1;
