@@ -242,12 +242,16 @@ __device__ __forceinline__ void grad_accumulate_pts(bool ok0, bool ok1, float2 d
 // split operands x = hi + lo (hi the TF32 truncation, lo the exact FP32
 // remainder): hi hi + hi lo + lo hi, FP32 accumulation, about 2^-20 of
 // sum_k |x_jk x_ik| per dot product; the norms n are FP32 and the distance is
-// clamped at 0.  Warp 0 copies the CTA's 128
-// split rows once and each point tile by bulk copies into a two-stage ring,
-// and one thread issues the MMAs into one of two TMEM buffers.  Sixteen
-// epilogue warps (four per TMEM lane quadrant, one quarter of the tile's
-// columns each) read their dot products with tcgen05.ld, release the buffer
-// and form the per-pair sums of grad_accumulate_pts.  Every wait is bounded.
+// clamped at 0.  Warp 0 copies the CTA's 128 split rows once and each point
+// tile (split rows, norms, y) by bulk copies into a two-stage ring, and one
+// thread issues the MMAs into one of two TMEM buffers.  Sixteen epilogue warps
+// (four per TMEM lane quadrant, one quarter of the tile's columns each) read
+// their dot products with tcgen05.ld, release the TMEM buffer, and form the
+// per-pair sums of grad_accumulate_pts from the stage's norms and y; a stage
+// is refilled once its MMAs and all epilogue warps are done with it (warp 0
+// refills one tile behind, after queueing the next MMAs).  Per-pair
+// leave-one-out and split-end tests run only in the column blocks that need
+// them.  Every wait is bounded.
 
 constexpr int kGTRows = 128;                      // rows per CTA: the TMEM lanes, MMA M
 constexpr int kGTEpi = 16;                        // epilogue warps
