@@ -1,7 +1,8 @@
-"""Stored oracle values (tests/golden/loo_small.json, written by
-tests/golden/make_golden.py from oracle/ only): the oracle still reproduces
-them on CPU, and the library matches them on the GPU within the LOO and
-gradient tolerances."""
+"""Stored oracle values (tests/golden/loo_small.json and scale_grid.json,
+written by tests/golden/make_golden.py from oracle/ only): the oracle still
+reproduces the small ones on CPU, and the library matches them on the GPU
+within the LOO and gradient tolerances, including every cell of the full
+benchmark grid."""
 import json
 import os
 
@@ -52,5 +53,33 @@ def test_library_matches_golden(case):
         scale = np.abs(rows).sum(0)   # tolerance scale: sum_j |d ell_j| (as in the gradient tests)
         assert abs(g[0] - gr[0]) <= 1e-5 * scale[0]
         assert np.all(np.abs(g[1:] - gr[1:]) <= 1e-4 * scale[1:])
+    finally:
+        cde.cde_shutdown(ctx)
+
+
+@pytest.mark.gpu
+def test_library_matches_full_scale_grid():
+    """The benchmark's workload (synth.scale_workload(): N = 50,000, d = 5,
+    standardised, 32 x 32): every cell of the GPU grid against the oracle's
+    grid over every row, stored by make_golden.py --scale.  Tolerance per cell
+    1e-5 of sum_j |ell_j| (L_cond) and of (1/N) sum_j |ln A_j - ln(N - 1)|
+    (L_eq3)."""
+    from __graft_entry__ import build
+    build()
+    from paper_1206_5278_gb300 import cde
+    S = json.load(open(os.path.join(HERE, "golden", "scale_grid.json")))
+    w = synth.scale_workload()
+    assert w.N == S["N"] and w.d == S["d"] and bool(w.standardize) == S["standardize"]
+    # (numpy's transcendental functions may differ in the last place between machines)
+    np.testing.assert_allclose(w.h1, np.array(S["h1"]), rtol=1e-12)
+    np.testing.assert_allclose(w.h2, np.array(S["h2"]), rtol=1e-12)
+    ctx = cde.cde_init(0)
+    try:
+        ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=w.standardize)
+        Lc, Le = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
+        err_c = np.abs(Lc - np.array(S["L_cond"])) / np.array(S["scale_cond"])
+        err_e = np.abs(Le - np.array(S["L_eq3"])) / np.array(S["scale_eq3"])
+        assert err_c.max() <= 1e-5, "L_cond: worst cell %g of its scale" % err_c.max()
+        assert err_e.max() <= 1e-5, "L_eq3: worst cell %g of its scale" % err_e.max()
     finally:
         cde.cde_shutdown(ctx)
