@@ -57,6 +57,22 @@ def test_library_matches_golden(case):
         cde.cde_shutdown(ctx)
 
 
+def test_full_scale_grid_record():
+    """The stored full grid belongs to synth.scale_workload() and is a valid
+    record: finite, each |L| within its tolerance scale (a sum of the same
+    terms' magnitudes), and L_eq3 between -scale_eq3 and the largest cell."""
+    S = json.load(open(os.path.join(HERE, "golden", "scale_grid.json")))
+    w = synth.scale_workload()
+    assert (w.N, w.d, bool(w.standardize)) == (S["N"], S["d"], S["standardize"])
+    np.testing.assert_allclose(w.h1, np.array(S["h1"]), rtol=1e-12)
+    np.testing.assert_allclose(w.h2, np.array(S["h2"]), rtol=1e-12)
+    Lc, Le = np.array(S["L_cond"]), np.array(S["L_eq3"])
+    sc, se = np.array(S["scale_cond"]), np.array(S["scale_eq3"])
+    assert Lc.shape == Le.shape == sc.shape == se.shape == (w.h1.size, w.h2.size)
+    assert np.all(np.isfinite(Lc)) and np.all(np.isfinite(Le))
+    assert np.all(np.abs(Lc) <= sc * (1 + 1e-12)) and np.all(np.abs(Le) <= se * (1 + 1e-12))
+
+
 @pytest.mark.gpu
 def test_library_matches_full_scale_grid():
     """The benchmark's workload (synth.scale_workload(): N = 50,000, d = 5,
