@@ -107,6 +107,16 @@ def oracle_sample(w, n_rows: int, seed: int = 0, kernel: str = "gauss"):
     return pe / dt, dt, th, rows
 
 
+def workload_config(w, args, world):
+    """The `config` object of the default workload's line; the reference arm
+    prints the same object, so that both arms name one workload."""
+    return {"workload": w.name, "N": w.N, "d_x": w.d, "G1": int(w.h1.size), "G2": int(w.h2.size),
+            "kernel": args.kernel, "standardized": bool(w.standardize),
+            "l2": "flushed (256 MB write) before every timed GPU step; the dataset (%.1f MB) is "
+                  "L2-resident by design" % ((w.d + 3) * 4 * w.N / 1e6),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args, w):
     rank, world, _ = _env_rank()
     if rank != 0:
@@ -129,9 +139,7 @@ def run_reference(args, w):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": w.name, "N": w.N, "d_x": w.d,
-                                           "G1": int(w.h1.size), "G2": int(w.h2.size),
-                                           "kernel": args.kernel},
+           "data": "synthetic", "config": workload_config(w, args, world),
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": th, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -290,10 +298,7 @@ def run_ours(args, w):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": w.name, "N": w.N, "d_x": w.d, "G1": G1, "G2": G2,
-                      "kernel": args.kernel, "standardized": bool(w.standardize),
-                      "l2": "flushed (256 MB write) before every timed step",
-                      "parallelism": "replicas" if world > 1 else "single"},
+           "config": workload_config(w, args, world),
            "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
            "e2e": {"value": pe_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "s_per_step": e2e_s,

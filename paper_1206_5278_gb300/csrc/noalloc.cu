@@ -96,7 +96,11 @@ extern "C" int cde_loo_loglik_noalloc(cde_ctx* ctx, cde_dataset ds, const double
     CDE_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));
     const int cmax = loo_grid_ctas(ctx, T1, T2);
     const int grid = a.n_tiles < cmax ? a.n_tiles : cmax;
+    // kernel timing (cde_timing_last) covers this call's tile kernel, as in cde_loo_loglik
+    timing_reset(ctx);
+    timing_begin(ctx, st);
     rc = launch_loo_tile_kernel(T1, T2, a, grid, st);
+    timing_end(ctx, st);
     if (rc != CDE_OK) return rc;
     if (d_L_cond || d_L_eq3) {
         const int GG = T1 * T2;

@@ -3,7 +3,7 @@ workloads, so that later changes to the oracle or the library are checked
 against fixed numbers.  With --scale it also writes
 tests/golden/scale_grid.json: the full 32 x 32 grid of the N = 50,000, d = 5
 standardised workload (synth.scale_workload(), the benchmark's), from the
-oracle's per-row terms of every row (about half an hour on 8 cores).  Calls
+oracle's per-row terms of every row (about 1.4 hours on 8 cores).  Calls
 only oracle/ and the seeded generators.
 
     python tests/golden/make_golden.py [--scale [--checkpoint PATH.npz]]
@@ -57,8 +57,15 @@ def main_scale(chunk: int = 1000, checkpoint: str = None):
     lnm = math.log(N - 1)
     t0 = time.time()
     start = 0
+    if checkpoint and not checkpoint.endswith(".npz"):
+        checkpoint += ".npz"   # np.savez appends the suffix; the resume check must see the same name
     if checkpoint and os.path.exists(checkpoint):   # resume the sums of the rows already done
         c = np.load(checkpoint)
+        # a checkpoint of another workload or chunk size must not be resumed into this record
+        same = (int(c["N"]) == N and int(c["d"]) == w.d and int(c["chunk"]) == chunk and
+                np.array_equal(c["h1"], w.h1) and np.array_equal(c["h2"], w.h2))
+        if not same:
+            raise SystemExit("checkpoint %s belongs to another workload or chunk size" % checkpoint)
         sc, sa, se, sea, start = c["sc"], c["sa"], c["se"], c["sea"], int(c["next"])
     for r0 in range(start, N, chunk):
         rows = np.arange(r0, min(N, r0 + chunk), dtype=np.int64)
@@ -68,7 +75,8 @@ def main_scale(chunk: int = 1000, checkpoint: str = None):
         se += lna.sum(0)
         sea += np.abs(lna - lnm).sum(0)
         if checkpoint:
-            np.savez(checkpoint, sc=sc, sa=sa, se=se, sea=sea, next=r0 + chunk)
+            np.savez(checkpoint, sc=sc, sa=sa, se=se, sea=sea, next=r0 + chunk, N=N, d=w.d,
+                     chunk=chunk, h1=w.h1, h2=w.h2)
         print("rows %d / %d, %.0f s" % (rows[-1] + 1, N, time.time() - t0), flush=True)
     out = {"note": "FP64 oracle (oracle/oracle.c) per-row terms of every row of synth.scale_workload() "
                    "(N = 50,000, d = 5, standardised, 32 x 32 grid), summed in FP64 over chunks of rows",

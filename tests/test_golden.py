@@ -59,8 +59,8 @@ def test_library_matches_golden(case):
 
 def test_full_scale_grid_record():
     """The stored full grid belongs to synth.scale_workload() and is a valid
-    record: finite, each |L| within its tolerance scale (a sum of the same
-    terms' magnitudes), and L_eq3 between -scale_eq3 and the largest cell."""
+    record: finite, and each |L_cond| and |L_eq3| within its tolerance scale
+    (a sum of the magnitudes of the same per-row terms)."""
     S = json.load(open(os.path.join(HERE, "golden", "scale_grid.json")))
     w = synth.scale_workload()
     assert (w.N, w.d, bool(w.standardize)) == (S["N"], S["d"], S["standardize"])
