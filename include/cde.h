@@ -140,6 +140,17 @@ int cde_check_status(cde_ctx *ctx, unsigned int *code, int *enabled);
  * either may be NULL.  Zeros for Epanechnikov datasets (no shift). */
 int cde_dataset_nn(cde_ctx *ctx, cde_dataset ds, float *nn_x2, float *nn_y2);
 
+/* The other coordinate's distance of each row's nearest neighbours, stored
+ * with the shifts of a Gaussian dataset: other_y2[j] = (y_j - y_i)^2 for the
+ * x-nearest point i of row j, other_x2[j] = |x_j - x_i|^2 for its y-nearest
+ * point (when several points are nearest, the smallest such distance).  Every
+ * minimiser over i of a1 |x_j - x_i|^2 + a2 (y_j - y_i)^2 (a1, a2 > 0), the
+ * dominant term of A_j in Eq. 3 at any bandwidths, lies within both bounds:
+ * the exact recomputation of cells whose separably shifted sum underflowed
+ * uses them to skip points.  Host arrays of N floats, either may be NULL;
+ * zeros for Epanechnikov datasets. */
+int cde_dataset_nn_other(cde_ctx *ctx, cde_dataset ds, float *other_x2, float *other_y2);
+
 /*
  * Kernel timing (a profiling aid).  With timing on, these calls record CUDA
  * events on their stream around their dominant kernel: cde_loo_loglik and

@@ -43,7 +43,7 @@ EXPORTED = [
     "cde_measure_peaks", "cde_autotune", "cde_tuning_get", "cde_tuning_set",
     "cde_loo_loglik_noalloc", "cde_dataset_kernel", "cde_select_random", "cde_reference_rule",
     "cde_cond_stats", "cde_cond_interval", "cde_tuning_save", "cde_tuning_load", "cde_check_status",
-    "cde_dataset_nn", "cde_timing_enable", "cde_timing_last", "cde_selftest_wait",
+    "cde_dataset_nn", "cde_dataset_nn_other", "cde_timing_enable", "cde_timing_last", "cde_selftest_wait",
 ]
 
 
@@ -137,6 +137,7 @@ def lib():
                                    ctypes.c_int),
         "cde_dataset_kernel": ([_vp, _i64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cde_dataset_nn": ([_vp, _i64, _vp, _vp], ctypes.c_int),
+        "cde_dataset_nn_other": ([_vp, _i64, _vp, _vp], ctypes.c_int),
         "cde_timing_enable": ([_vp, ctypes.c_int], ctypes.c_int),
         "cde_timing_last": ([_vp, _vp], ctypes.c_int),
         "cde_selftest_wait": ([_vp], ctypes.c_int),
@@ -310,6 +311,15 @@ def cde_dataset_nn(ctx, ds: int):
     a = np.empty(N, np.float32)
     b = np.empty(N, np.float32)
     _check(lib().cde_dataset_nn(ctx, int(ds), _ptr(a), _ptr(b)))
+    return a, b
+
+
+def cde_dataset_nn_other(ctx, ds: int):
+    """(|x_j - x_i|^2 of the y-nearest i, (y_j - y_i)^2 of the x-nearest i) per row."""
+    N, _, _, _ = cde_dataset_info(ctx, ds)
+    a = np.empty(N, np.float32)
+    b = np.empty(N, np.float32)
+    _check(lib().cde_dataset_nn_other(ctx, int(ds), _ptr(a), _ptr(b)))
     return a, b
 
 

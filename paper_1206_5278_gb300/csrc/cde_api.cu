@@ -47,7 +47,9 @@ static void free_dataset(Dataset* D) {
     cudaFree(D->y);
     cudaFree(D->mx);
     cudaFree(D->my);
-    D->xs = D->y = D->mx = D->my = nullptr;
+    cudaFree(D->qx);
+    cudaFree(D->qy);
+    D->xs = D->y = D->mx = D->my = D->qx = D->qy = nullptr;
 }
 
 __global__ void k_finite_check(const float* a, int64_t n, int* flag) {
@@ -177,7 +179,7 @@ int cde_create_dataset(cde_ctx* ctx, const float* x, const float* y, int64_t N, 
     D->Np = (N + kPadRows - 1) / kPadRows * kPadRows;
     D->standardized = standardize ? 1 : 0;
     D->kernel = (flags & CDE_KERNEL_EPANECHNIKOV) ? CDE_KERNEL_EPAN : CDE_KERNEL_GAUSS;
-    D->bytes = (size_t)D->Np * (d + 1) * 4 + (size_t)N * 8;
+    D->bytes = (size_t)D->Np * (d + 1) * 4 + (size_t)N * 16;
     if (ctx->used.load() + D->bytes > ctx->budget)
         return set_error(CDE_ENOMEM, "cde_create_dataset: memory budget exceeded");
     cudaStream_t st = ctx->stream;
@@ -198,6 +200,8 @@ int cde_create_dataset(cde_ctx* ctx, const float* x, const float* y, int64_t N, 
     if (e == cudaSuccess) e = cudaMalloc((void**)&D->y, (size_t)D->Np * 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&D->mx, (size_t)N * 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&D->my, (size_t)N * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&D->qx, (size_t)N * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&D->qy, (size_t)N * 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&dstats, (size_t)2 * d * sizeof(double) + 64);
     if (e != cudaSuccess) return fail(cuda_error(e, "cde_create_dataset: cudaMalloc"));
     if (in_dev) {
@@ -238,6 +242,8 @@ int cde_create_dataset(cde_ctx* ctx, const float* x, const float* y, int64_t N, 
     } else {
         e = cudaMemsetAsync(D->mx, 0, (size_t)N * 4, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(D->my, 0, (size_t)N * 4, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(D->qx, 0, (size_t)N * 4, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(D->qy, 0, (size_t)N * 4, st);
         if (e != cudaSuccess) return fail(cuda_error(e, "cde_create_dataset: shifts"));
     }
     e = cudaStreamSynchronize(st);
@@ -358,6 +364,18 @@ int cde_dataset_nn(cde_ctx* ctx, cde_dataset ds, float* nn_x2, float* nn_y2) {
     CDE_CUDA(cudaSetDevice(ctx->device));
     if (nn_x2) CDE_CUDA(cudaMemcpyAsync(nn_x2, D->mx, (size_t)D->N * 4, cudaMemcpyDeviceToHost, ctx->stream));
     if (nn_y2) CDE_CUDA(cudaMemcpyAsync(nn_y2, D->my, (size_t)D->N * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CDE_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CDE_OK;
+}
+
+int cde_dataset_nn_other(cde_ctx* ctx, cde_dataset ds, float* other_x2, float* other_y2) {
+    if (!ctx || (!other_x2 && !other_y2)) return set_error(CDE_EINVAL, "cde_dataset_nn_other: null argument");
+    auto D = find_dataset(ctx, ds);
+    if (!D) return set_error(CDE_ENOTFOUND, "cde_dataset_nn_other: unknown dataset");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    CDE_CUDA(cudaSetDevice(ctx->device));
+    if (other_x2) CDE_CUDA(cudaMemcpyAsync(other_x2, D->qx, (size_t)D->N * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    if (other_y2) CDE_CUDA(cudaMemcpyAsync(other_y2, D->qy, (size_t)D->N * 4, cudaMemcpyDeviceToHost, ctx->stream));
     CDE_CUDA(cudaStreamSynchronize(ctx->stream));
     return CDE_OK;
 }

@@ -80,6 +80,10 @@ struct Dataset {
     float* mx = nullptr;   // [N] min_{i!=j} |x_j - x_i|^2 (FP32, same formula as the kernels);
                            //     zeros for Epanechnikov datasets (no shift)
     float* my = nullptr;   // [N] min_{i!=j} (y_j - y_i)^2 (zeros for Epanechnikov)
+    // [N] each row's nearest neighbours seen from the other coordinate (Gaussian only;
+    // they bound where the joint minimum of a1 dx^2 + a2 dy^2 can lie):
+    float* qx = nullptr;   //     dx^2 to the y-nearest point (the smallest, if several are y-nearest)
+    float* qy = nullptr;   //     dy^2 to the x-nearest point (the smallest, if several are x-nearest)
     std::vector<double> mean, sd;  // per-dimension (identity when not standardised)
     size_t bytes = 0;
     std::atomic<int> users{0};     // jobs currently reading it (serving)

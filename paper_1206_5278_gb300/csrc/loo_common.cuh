@@ -17,6 +17,8 @@ struct LooArgs {
     const float* y;         // [Np]
     const float* mx;        // [N] nearest squared x distance per row
     const float* my;        // [N] nearest squared y distance per row
+    const float* qx;        // [N] dx^2 of each row's y-nearest point (fallback bounds)
+    const float* qy;        // [N] dy^2 of each row's x-nearest point
     const int64_t* rows;    // optional list of rows (null: rows 0..n_rows-1)
     double* part;           // [n_tiles][2][T1*T2] FP64 tile partials (L_cond, sum ln A)
     double* ell_rows;       // optional per-row ell output
@@ -105,15 +107,37 @@ struct CoefParam {
     __device__ __forceinline__ float a2(int l) const { return a.a2[l]; }
 };
 
+// log2(1 + 5.12e-8): ex2.approx.ftz.f32 is low by 5.12e-8 relative on average
+// (measured on sm_103a); the fallback's terms carry it in their exponent, as
+// the tile body's factors do
+constexpr float kFbEx2Fix = 7.39e-8f;
+
 // Exact joint-shift recomputation of the flagged cells of one unit (whole
-// CTA).  For a cell (row j, k, l) with e_i = a1_k (dx2_i - m_x,j) + a2_l (dy2_i - m_y,j):
-// pass 1 finds i* = argmin e_i, pass 2 sums 2^{-(a1_k (dx2_i - dx2_*) + a2_l (dy2_i - dy2_*))},
-// so the dominant term is exactly 1 and log2 At = -e_* + log2 S.  Cells are
-// sorted, grouped by row and processed FB at a time, each pass visiting every
-// point once for the whole group.
+// CTA).  For a cell (row j, k, l) let X_i = dx2_i - m_x,j, Y_i = dy2_i - m_y,j and
+// e_i = a1_k X_i + a2_l Y_i.  Then At = sum_i 2^{-e_i} = 2^{-e_*} S with
+// S = sum_i 2^{-(a1_k (dx2_i - dx2_*) + a2_l (dy2_i - dy2_*))} for the minimiser
+// i* (its term is exactly 1), and log2 At = -e_* + log2 S.  The flagged cells
+// of a row are processed together in two passes over the points:
+//  1. the minimiser of every cell.  It is no worse than the x-nearest point
+//     (X = 0, Y = Yh) and the y-nearest point (X = Xh, Y = 0), so
+//     e_* <= min(a2 Yh, a1 Xh): only points with dx2 <= qx and dy2 <= qy
+//     (qx, qy: the dataset's stored other-coordinate distances of the two
+//     neighbours), and inside the union over the row's cells of those
+//     triangles, are tested cell by cell.  A cell keeps the smallest key
+//     (e bits, i) with a shared-memory 64-bit atomicMin: the smallest e, ties
+//     to the smallest index, whatever the order of visits.
+//  2. the sums.  A point with e_i > e_* + T adds less than 2^-T; with
+//     T = 32 + ceil(log2 N) all of them together add less than 2^-32 of S.
+//     So only points with X <= max_f (e_*f + T)/a1_f and Y <= max_f (e_*f + T)/a2_f
+//     are visited cell by cell, and each term is added as an integer in units
+//     of 2^-(62 - ceil(log2 N)) (64-bit shared-memory atomicAdd: exact, so the
+//     sum is the same in any order, and it cannot overflow).
+// Both passes compute dx2 and dy2 with the tile body's FP32 formula.
 template <class C, class Coef>
 __device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, float* sm, int nfl) {
-    constexpr int GG = C::GG, FB = C::FB, G2 = C::G2v;
+    constexpr int GG = C::GG, G2 = C::G2v, JW = C::JW, NT = C::kThreads, NW = C::kWarps;
+    constexpr int LG2 = G2 == 8 ? 3 : (G2 == 16 ? 4 : 5);
+    static_assert(2 * JW * GG + 6 * GG <= C::COMB, "fallback scratch must fit in the combine buffer");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int d = a.d;
     const int64_t N = a.N, Np = a.Np;
@@ -123,15 +147,18 @@ __device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, f
     float* my_s = sm + C::off_my(d);
     const long long* ji_s = reinterpret_cast<const long long*>(sm + C::off_ji(d));
     int* flag_s = reinterpret_cast<int*>(sm + C::off_flag(d));
-    float* redf = sm + C::off_red(d);
-    int* redi = reinterpret_cast<int*>(sm + C::off_red(d) + C::kWarps * FB);
-    int* fbi = reinterpret_cast<int*>(sm + C::off_fb(d));
+    float* red = sm + C::off_red(d);   // 2 kWarps FB floats: per-warp reduction slots
     double* la2 = reinterpret_cast<double*>(sm);
+    // per-cell scratch after la2 (one row's cells at a time)
+    unsigned long long* best = reinterpret_cast<unsigned long long*>(sm + 2 * JW * GG);
+    unsigned long long* acc = best + GG;
+    float* dxs = reinterpret_cast<float*>(acc + GG);
+    float* dys = dxs + GG;
 
     // sort the (distinct) flagged cell ids in place: each thread ranks its entries
     int mine[4], rank[4];
     int nm = 0;
-    for (int q = tid; q < nfl; q += C::kThreads) {
+    for (int q = tid; q < nfl; q += NT) {
         const int v = flag_s[q];
         int r = 0;
         for (int t = 0; t < nfl; ++t) r += flag_s[t] < v;
@@ -143,130 +170,149 @@ __device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, f
     for (int m = 0; m < nm; ++m) flag_s[rank[m]] = mine[m];
     __syncthreads();
 
+    int lg = 0;
+    while (((int64_t)1 << lg) < N) ++lg;
+    const float T = (float)(32 + lg);
+    const int SC = 62 - lg;            // fixed-point scale of the sums
+    const float scale = ldexpf(1.f, SC), inv_scale_f = ldexpf(1.f, -SC);
+
     int q0 = 0;
     while (q0 < nfl) {
-        // group: up to FB consecutive cells of the same row
         const int jl = flag_s[q0] / GG;
-        int nb = 0;
-        while (nb < FB && q0 + nb < nfl && flag_s[q0 + nb] / GG == jl) ++nb;
-        float A[FB], B[FB];
-#pragma unroll
-        for (int f = 0; f < FB; ++f) {
-            const int c = flag_s[q0 + (f < nb ? f : 0)];
-            const int kl = c - jl * GG, k = kl / G2, l = kl - k * G2;
-            A[f] = cf.a1(k);
-            B[f] = cf.a2(l);
-        }
+        int q1 = q0;
+        while (q1 < nfl && flag_s[q1] / GG == jl) ++q1;
+        const int F = q1 - q0;
         const float mxj = mx_s[jl], myj = my_s[jl], yj = yj_s[jl];
         const long long j = ji_s[jl];
         const float* xjr = xj_s + jl * d;
-        // pass 1: argmin over i of e_i for each cell
-        float best[FB];
-        int bi[FB];
-#pragma unroll
-        for (int f = 0; f < FB; ++f) {
-            best[f] = INFINITY;
-            bi[f] = 0x7fffffff;
-        }
-        for (int64_t i = tid; i < N; i += C::kThreads) {
-            if (i == j) continue;
-            float dx2 = 0.f;
-            for (int cc = 0; cc < d; ++cc) {
-                const float t = xjr[cc] - a.xs[(int64_t)cc * Np + i];
-                dx2 = fmaf(t, t, dx2);
-            }
-            const float dy = yj - a.y[i];
-            const float ex = dx2 - mxj, ey = dy * dy - myj;
-#pragma unroll
-            for (int f = 0; f < FB; ++f) {
-                const float e = A[f] * ex + B[f] * ey;
-                if (e < best[f]) {   // i increases: first minimum kept
-                    best[f] = e;
-                    bi[f] = (int)i;
-                }
-            }
+        const float qxj = a.qx[j], qyj = a.qy[j];
+        const float Xh = qxj - mxj, Yh = qyj - myj;
+
+        // triangles of the argmin region: cells with rho = a2/a1 <= Xh/Yh are bounded
+        // by the x-nearest point (X + rho Y <= rho Yh; the largest rho covers the
+        // others), the rest by the y-nearest point (X + rho Y <= Xh; the smallest rho)
+        float rlo = -1.f, rhi = INFINITY;
+        for (int f = tid; f < F; f += NT) {
+            const int kl = flag_s[q0 + f] - jl * GG, k = kl >> LG2, l = kl & (G2 - 1);
+            const float A = cf.a1(k), B = cf.a2(l);
+            const float rho = B / A;
+            if (rho * Yh <= Xh) rlo = fmaxf(rlo, rho);
+            else rhi = fminf(rhi, rho);
+            best[f] = ~0ull;
+            acc[f] = 0ull;
         }
 #pragma unroll
-        for (int f = 0; f < FB; ++f) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best[f], o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi[f], o);
-                if (ob < best[f] || (ob == best[f] && oi < bi[f])) {
-                    best[f] = ob;
-                    bi[f] = oi;
-                }
-            }
-            if (lane == 0) {
-                redf[warp * FB + f] = best[f];
-                redi[warp * FB + f] = bi[f];
-            }
+        for (int o = 16; o > 0; o >>= 1) {
+            rlo = fmaxf(rlo, __shfl_xor_sync(0xffffffffu, rlo, o));
+            rhi = fminf(rhi, __shfl_xor_sync(0xffffffffu, rhi, o));
+        }
+        if (lane == 0) {
+            red[warp] = rlo;
+            red[NW + warp] = rhi;
         }
         __syncthreads();
-        if (tid < FB) {
-            float b = redf[tid];
-            int ix = redi[tid];
-            for (int w = 1; w < C::kWarps; ++w) {
-                const float ob = redf[w * FB + tid];
-                const int oi = redi[w * FB + tid];
-                if (ob < b || (ob == b && oi < ix)) {
-                    b = ob;
-                    ix = oi;
-                }
-            }
-            if (ix < 0 || (int64_t)ix >= N) ix = (j == 0) ? 1 : 0;  // every e infinite
-            fbi[tid] = ix;
+        rlo = red[0];
+        rhi = red[NW];
+        for (int w = 1; w < NW; ++w) {
+            rlo = fmaxf(rlo, red[w]);
+            rhi = fminf(rhi, red[NW + w]);
         }
-        __syncthreads();
-        float dxs[FB], dys[FB];
-#pragma unroll
-        for (int f = 0; f < FB; ++f) {
-            const int is = (int)CDE_CK(fbi[f], N, 108);
-            float t2 = 0.f;
-            for (int cc = 0; cc < d; ++cc) {
-                const float t = xjr[cc] - a.xs[(int64_t)cc * Np + is];
-                t2 = fmaf(t, t, t2);
-            }
-            dxs[f] = t2;
-            const float t = yj - a.y[is];
-            dys[f] = t * t;
-        }
-        // pass 2: shifted sums
-        float S[FB];
-#pragma unroll
-        for (int f = 0; f < FB; ++f) S[f] = 0.f;
-        for (int64_t i = tid; i < N; i += C::kThreads) {
+        const float rloY = rlo * Yh;
+
+        // ---- pass 1: the minimiser of every flagged cell of the row ----
+        for (int64_t i = tid; i < N; i += NT) {
             if (i == j) continue;
             float dx2 = 0.f;
+#pragma unroll 4
             for (int cc = 0; cc < d; ++cc) {
                 const float t = xjr[cc] - a.xs[(int64_t)cc * Np + i];
                 dx2 = fmaf(t, t, dx2);
             }
             const float dy = yj - a.y[i];
             const float dy2 = dy * dy;
-#pragma unroll
-            for (int f = 0; f < FB; ++f)
-                S[f] += ex2_approx(-(A[f] * (dx2 - dxs[f]) + B[f] * (dy2 - dys[f])));
-        }
-        __syncthreads();
-#pragma unroll
-        for (int f = 0; f < FB; ++f) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) S[f] += __shfl_xor_sync(0xffffffffu, S[f], o);
-            if (lane == 0) redf[warp * FB + f] = S[f];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int f = 0; f < FB; ++f)
-            if (tid == f && f < nb) {
-                float tot = 0.f;
-                for (int w = 0; w < C::kWarps; ++w) tot += redf[w * FB + f];
-                const double es = (double)A[f] * ((double)dxs[f] - (double)mxj) +
-                                  (double)B[f] * ((double)dys[f] - (double)myj);
-                la2[flag_s[q0 + f]] = -es + log2_wide(tot);
+            if (dx2 > qxj || dy2 > qyj) continue;
+            const float X = dx2 - mxj, Y = dy2 - myj;
+            const bool in = (rlo >= 0.f && fmaf(rlo, Y, X) <= rloY) || (rhi < INFINITY && fmaf(rhi, Y, X) <= Xh);
+            if (!in) continue;
+            for (int f = 0; f < F; ++f) {
+                const int kl = flag_s[q0 + f] - jl * GG, k = kl >> LG2, l = kl & (G2 - 1);
+                const float e = fmaxf(fmaf(cf.a1(k), X, cf.a2(l) * Y), 0.f);
+                const unsigned long long key = ((unsigned long long)__float_as_uint(e) << 32) | (unsigned int)i;
+                if (key < best[f]) atomicMin(best + f, key);
             }
+        }
         __syncthreads();
-        q0 += nb;
+
+        // ---- the minimisers' distances; the box of pass 2 ----
+        float rx = 0.f, ry = 0.f;
+        for (int f = tid; f < F; f += NT) {
+            const int kl = flag_s[q0 + f] - jl * GG, k = kl >> LG2, l = kl & (G2 - 1);
+            const unsigned long long b = best[f];
+            // no point in the region (cannot happen: the two neighbours are in it):
+            // anchor at the x-nearest bound
+            const bool none = b == ~0ull;
+            const int64_t is = none ? (j == 0 ? 1 : 0) : (int64_t)(unsigned int)b;
+            float t2 = 0.f;
+            for (int cc = 0; cc < d; ++cc) {
+                const float t = xjr[cc] - a.xs[(int64_t)cc * Np + CDE_CK(is, N, 108)];
+                t2 = fmaf(t, t, t2);
+            }
+            const float t = yj - a.y[is];
+            dxs[f] = t2;
+            dys[f] = t * t;
+            const float es = fmaxf(fmaf(cf.a1(k), t2 - mxj, cf.a2(l) * (t * t - myj)), 0.f);
+            rx = fmaxf(rx, (es + T) / cf.a1(k));
+            ry = fmaxf(ry, (es + T) / cf.a2(l));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rx = fmaxf(rx, __shfl_xor_sync(0xffffffffu, rx, o));
+            ry = fmaxf(ry, __shfl_xor_sync(0xffffffffu, ry, o));
+        }
+        __syncthreads();   // red[] reads of the triangle step are done
+        if (lane == 0) {
+            red[warp] = rx;
+            red[NW + warp] = ry;
+        }
+        __syncthreads();
+        rx = red[0];
+        ry = red[NW];
+        for (int w = 1; w < NW; ++w) {
+            rx = fmaxf(rx, red[w]);
+            ry = fmaxf(ry, red[NW + w]);
+        }
+        const float RXd = mxj + rx, RYd = myj + ry;   // in raw squared distances
+
+        // ---- pass 2: the shifted sums over the points that can matter ----
+        for (int64_t i = tid; i < N; i += NT) {
+            if (i == j) continue;
+            float dx2 = 0.f;
+#pragma unroll 4
+            for (int cc = 0; cc < d; ++cc) {
+                const float t = xjr[cc] - a.xs[(int64_t)cc * Np + i];
+                dx2 = fmaf(t, t, dx2);
+            }
+            const float dy = yj - a.y[i];
+            const float dy2 = dy * dy;
+            if (dx2 > RXd || dy2 > RYd) continue;
+            for (int f = 0; f < F; ++f) {
+                const int kl = flag_s[q0 + f] - jl * GG, k = kl >> LG2, l = kl & (G2 - 1);
+                const float v = ex2_approx(kFbEx2Fix - (cf.a1(k) * (dx2 - dxs[f]) + cf.a2(l) * (dy2 - dys[f])));
+                const unsigned long long q = __float2ull_rn(v * scale);
+                if (q) atomicAdd(acc + f, q);
+            }
+        }
+        __syncthreads();
+        for (int f = tid; f < F; f += NT) {
+            const int c = flag_s[q0 + f];
+            const int kl = c - jl * GG, k = kl >> LG2, l = kl & (G2 - 1);
+            const float tot = (float)((double)acc[f] * (double)inv_scale_f);
+            const double es = (double)cf.a1(k) * ((double)dxs[f] - (double)mxj) +
+                              (double)cf.a2(l) * ((double)dys[f] - (double)myj);
+            la2[c] = -es + log2_wide(tot);
+        }
+        __syncthreads();
+        q0 = q1;
     }
 }
 

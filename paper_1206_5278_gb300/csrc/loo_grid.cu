@@ -107,11 +107,26 @@ int pack_enqueue(Dataset& D, const float* d_x, const float* d_y, cudaStream_t st
 // --------------------------------------------------------------------------
 // Per-row nearest squared distances (the exp2 shifts), O(N^2 d), computed
 // once per dataset.  Same FP32 distance formula as every pair kernel.
+// Alongside each minimum the kernels keep the other coordinate's distance of
+// the point that attains it -- qy_j = dy^2 of the x-nearest point, qx_j = dx^2
+// of the y-nearest point -- minimising the pair lexicographically, so ties
+// keep the smaller second distance and the result does not depend on the
+// order in which points are visited.  Every joint minimiser of
+// a1 (dx^2 - m_x) + a2 (dy^2 - m_y) (a1, a2 > 0) has dx^2 <= qx and dy^2 <= qy
+// (it can be no worse than either neighbour), which is what the exact
+// fallback of the grid kernels uses to skip points.
 // --------------------------------------------------------------------------
+
+// (a, b) < (c, d) lexicographically
+__device__ __forceinline__ bool lex_less(float a, float b, float c, float d) {
+    return a < c || (a == c && b < d);
+}
+
 __global__ void __launch_bounds__(256) k_nn_shift(const float* __restrict__ xs,
                                                   const float* __restrict__ y, int64_t N,
                                                   int64_t Np, int d, float* __restrict__ mx,
-                                                  float* __restrict__ my) {
+                                                  float* __restrict__ my, float* __restrict__ qx,
+                                                  float* __restrict__ qy) {
     extern __shared__ float sm[];  // [d + 1][256]
     const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const bool vj = j < N;
@@ -119,7 +134,7 @@ __global__ void __launch_bounds__(256) k_nn_shift(const float* __restrict__ xs,
 #pragma unroll
     for (int c = 0; c < 8; ++c) xj[c] = (vj && c < d) ? xs[(int64_t)c * Np + j] : 0.f;
     const float yj = vj ? y[j] : 0.f;
-    float bx = INFINITY, by = INFINITY;
+    float bx = INFINITY, by = INFINITY, ax = INFINITY, ay = INFINITY;
     for (int64_t i0 = 0; i0 < N; i0 += 256) {
         __syncthreads();
         for (int c = 0; c <= d; ++c) {
@@ -144,38 +159,52 @@ __global__ void __launch_bounds__(256) k_nn_shift(const float* __restrict__ xs,
             const float dy = yj - sm[d * 256 + t];
             const float dy2 = dy * dy;
             if (i != j) {
-                bx = fminf(bx, dx2);
-                by = fminf(by, dy2);
+                if (lex_less(dx2, dy2, bx, ax)) {
+                    bx = dx2;
+                    ax = dy2;
+                }
+                if (lex_less(dy2, dx2, by, ay)) {
+                    by = dy2;
+                    ay = dx2;
+                }
             }
         }
     }
     if (vj) {
         mx[j] = bx;
         my[j] = by;
+        qy[j] = ax;
+        qx[j] = ay;
     }
 }
 
 // d <= 8: four rows per thread, point-major shared tiles (128-bit loads), the
-// data range split over gridDim.y; split minima merge with an integer
-// atomicMin on the float bits (exact and order-free: squared distances are
-// non-negative, so their bit patterns order like the values).  The distance
-// is accumulated in the same order (dimension 0 first, one fmaf per
-// dimension; padding dimensions add exactly 0) as in every pair kernel.
+// data range split over gridDim.y; split minima merge with a 64-bit integer
+// atomicMin on (minimum, other distance) bit pairs (exact and order-free:
+// squared distances are non-negative, so their bit patterns order like the
+// values).  The distance is accumulated in the same order (dimension 0 first,
+// one fmaf per dimension; padding dimensions add exactly 0) as in every pair
+// kernel.
 constexpr int kNnThreads = 128, kNnJB = 4;   // rows per thread (even: packed pairs)
+
+__device__ __forceinline__ unsigned long long nn_key(float m, float o) {
+    return ((unsigned long long)__float_as_uint(m) << 32) | __float_as_uint(o);
+}
 
 template <int DREG>
 __global__ void __launch_bounds__(kNnThreads) k_nn_shift_split(const float* __restrict__ xs,
                                                                const float* __restrict__ y, int64_t N,
                                                                int64_t Np, int d, int64_t i_per_split,
-                                                               unsigned int* __restrict__ mx_bits,
-                                                               unsigned int* __restrict__ my_bits) {
+                                                               unsigned long long* __restrict__ kx,
+                                                               unsigned long long* __restrict__ ky) {
     __shared__ __align__(16) float xt[kNnThreads][DREG];
     __shared__ float yt[kNnThreads];
     const int tid = threadIdx.x;
     const int64_t jbase = (int64_t)blockIdx.x * kNnThreads * kNnJB + tid;
     const int64_t i0 = (int64_t)blockIdx.y * i_per_split;
     const int64_t i1 = min(N, i0 + i_per_split);
-    float xj[kNnJB][DREG], yj[kNnJB], bx[kNnJB], by[kNnJB];
+    // b*: running minima, a*: the other coordinate's distance of the minimiser
+    float xj[kNnJB][DREG], yj[kNnJB], bx[kNnJB], by[kNnJB], ax[kNnJB], ay[kNnJB];
     int jj[kNnJB];
 #pragma unroll
     for (int b = 0; b < kNnJB; ++b) {
@@ -185,7 +214,7 @@ __global__ void __launch_bounds__(kNnThreads) k_nn_shift_split(const float* __re
 #pragma unroll
         for (int c = 0; c < DREG; ++c) xj[b][c] = c < d ? xs[(int64_t)c * Np + jc] : 0.f;
         yj[b] = y[jc];
-        bx[b] = by[b] = INFINITY;
+        bx[b] = by[b] = ax[b] = ay[b] = INFINITY;
     }
     for (int64_t t0 = i0; t0 < i1; t0 += kNnThreads) {
         __syncthreads();
@@ -221,10 +250,18 @@ __global__ void __launch_bounds__(kNnThreads) k_nn_shift_split(const float* __re
                 const float2 dy = __ffma2_rn(make_float2(yi, yi), m1, make_float2(yj[b], yj[b + 1]));
                 const float2 dy2 = __fmul2_rn(dy, dy);
                 const bool o0 = i32 != jj[b], o1 = i32 != jj[b + 1];
-                bx[b] = o0 ? fminf(bx[b], dx2.x) : bx[b];
-                bx[b + 1] = o1 ? fminf(bx[b + 1], dx2.y) : bx[b + 1];
-                by[b] = o0 ? fminf(by[b], dy2.x) : by[b];
-                by[b + 1] = o1 ? fminf(by[b + 1], dy2.y) : by[b + 1];
+                const bool px0 = o0 && lex_less(dx2.x, dy2.x, bx[b], ax[b]);
+                const bool px1 = o1 && lex_less(dx2.y, dy2.y, bx[b + 1], ax[b + 1]);
+                const bool py0 = o0 && lex_less(dy2.x, dx2.x, by[b], ay[b]);
+                const bool py1 = o1 && lex_less(dy2.y, dx2.y, by[b + 1], ay[b + 1]);
+                bx[b] = px0 ? dx2.x : bx[b];
+                ax[b] = px0 ? dy2.x : ax[b];
+                bx[b + 1] = px1 ? dx2.y : bx[b + 1];
+                ax[b + 1] = px1 ? dy2.y : ax[b + 1];
+                by[b] = py0 ? dy2.x : by[b];
+                ay[b] = py0 ? dx2.x : ay[b];
+                by[b + 1] = py1 ? dy2.y : by[b + 1];
+                ay[b + 1] = py1 ? dx2.y : ay[b + 1];
             }
         }
     }
@@ -232,9 +269,22 @@ __global__ void __launch_bounds__(kNnThreads) k_nn_shift_split(const float* __re
     for (int b = 0; b < kNnJB; ++b) {
         const int64_t j = jbase + (int64_t)b * kNnThreads;
         if (j >= N) continue;
-        atomicMin(mx_bits + j, __float_as_uint(bx[b]));
-        atomicMin(my_bits + j, __float_as_uint(by[b]));
+        atomicMin(kx + j, nn_key(bx[b], ax[b]));
+        atomicMin(ky + j, nn_key(by[b], ay[b]));
     }
+}
+
+// unpack the merged (minimum, other distance) keys
+__global__ void k_nn_unpack(const unsigned long long* __restrict__ kx, const unsigned long long* __restrict__ ky,
+                            int64_t N, float* __restrict__ mx, float* __restrict__ my, float* __restrict__ qx,
+                            float* __restrict__ qy) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const unsigned long long a = kx[j], b = ky[j];
+    mx[j] = __uint_as_float((unsigned int)(a >> 32));
+    qy[j] = __uint_as_float((unsigned int)a);
+    my[j] = __uint_as_float((unsigned int)(b >> 32));
+    qx[j] = __uint_as_float((unsigned int)b);
 }
 
 int nn_shift_enqueue(const Dataset& D, cudaStream_t st, int sm_count) {
@@ -247,16 +297,19 @@ int nn_shift_enqueue(const Dataset& D, cudaStream_t st, int sm_count) {
         if (ns < 1) ns = 1;
         const int64_t tps = (tiles + ns - 1) / ns;
         ns = (tiles + tps - 1) / tps;
-        CDE_CUDA(cudaMemsetAsync(D.mx, 0x7f, (size_t)D.N * sizeof(float), st));  // 3.4e38: above any distance
-        CDE_CUDA(cudaMemsetAsync(D.my, 0x7f, (size_t)D.N * sizeof(float), st));
+        unsigned long long* keys = nullptr;   // [2][N] merge keys, stream-ordered scratch
+        CDE_CUDA(cudaMallocAsync((void**)&keys, (size_t)2 * D.N * sizeof(unsigned long long), st));
+        // 0x7f bytes: the first word 3.4e38, above any distance
+        CDE_CUDA(cudaMemsetAsync(keys, 0x7f, (size_t)2 * D.N * sizeof(unsigned long long), st));
         const dim3 grid((unsigned)gx, (unsigned)ns);
-        auto* mxb = reinterpret_cast<unsigned int*>(D.mx);
-        auto* myb = reinterpret_cast<unsigned int*>(D.my);
         if (D.d <= 4)
-            k_nn_shift_split<4><<<grid, kNnThreads, 0, st>>>(D.xs, D.y, D.N, D.Np, D.d, tps * kNnThreads, mxb, myb);
+            k_nn_shift_split<4><<<grid, kNnThreads, 0, st>>>(D.xs, D.y, D.N, D.Np, D.d, tps * kNnThreads, keys, keys + D.N);
         else
-            k_nn_shift_split<8><<<grid, kNnThreads, 0, st>>>(D.xs, D.y, D.N, D.Np, D.d, tps * kNnThreads, mxb, myb);
+            k_nn_shift_split<8><<<grid, kNnThreads, 0, st>>>(D.xs, D.y, D.N, D.Np, D.d, tps * kNnThreads, keys, keys + D.N);
         CDE_CUDA(cudaGetLastError());
+        k_nn_unpack<<<(unsigned)((D.N + 255) / 256), 256, 0, st>>>(keys, keys + D.N, D.N, D.mx, D.my, D.qx, D.qy);
+        CDE_CUDA(cudaGetLastError());
+        CDE_CUDA(cudaFreeAsync(keys, st));
         return CDE_OK;
     }
     const int64_t blocks = (D.N + 255) / 256;
@@ -264,7 +317,7 @@ int nn_shift_enqueue(const Dataset& D, cudaStream_t st, int sm_count) {
     if (smem > 48 * 1024)
         CDE_CUDA(cudaFuncSetAttribute(k_nn_shift, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-    k_nn_shift<<<(unsigned)blocks, 256, smem, st>>>(D.xs, D.y, D.N, D.Np, D.d, D.mx, D.my);
+    k_nn_shift<<<(unsigned)blocks, 256, smem, st>>>(D.xs, D.y, D.N, D.Np, D.d, D.mx, D.my, D.qx, D.qy);
     CDE_CUDA(cudaGetLastError());
     return CDE_OK;
 }
@@ -325,7 +378,7 @@ double epan_log_norm(int d) {
 
 void fill_loo_args(LooArgs& a, const Dataset& D, const double* h1, int g1, const double* h2,
                    int g2, int T1, int T2) {
-    a.xs = D.xs; a.y = D.y; a.mx = D.mx; a.my = D.my;
+    a.xs = D.xs; a.y = D.y; a.mx = D.mx; a.my = D.my; a.qx = D.qx; a.qy = D.qy;
     a.N = D.N; a.Np = D.Np; a.d = D.d;
     a.kern = D.kernel;
     if (D.kernel == CDE_KERNEL_EPAN) {

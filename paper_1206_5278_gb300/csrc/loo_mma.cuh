@@ -16,7 +16,26 @@
 // only BF16 precision: both go through ONE BF16 m16n8k16 MMA whose k axis
 // stacks [hi_u | lo_u] against [lo_w ; hi_w] (twice the MAC rate of TF32).
 // Dropped lo*lo and the BF16 rounding of the cross terms leave about 2^-17
-// relative per term (the sums over i average these errors).  Each lane takes
+// relative per term (the sums over i average these errors).
+//
+// Bias.  A score sums N rows, so a per-row error with a fixed sign grows like
+// N while random ones grow like sqrt(N); at N = 50,000 a bias of 1e-7 per row
+// is 5e-3 on a score whose rows cancel to |L| ~ 100.  Two biases are removed:
+//  * lo*lo: with hi the truncation of v, lo >= 0 for both factors and the
+//    dropped lo_u lo_w is always positive (about 2^-22 of the product on
+//    average).  w is instead split as w' = w / r, hi = trunc(w'),
+//    lo = w' r - hi (one FMA, r = 1 - 11 2^-15 exact in FP32): lo is then
+//    signed with mean ~0 over log-uniform mantissas, so E[lo_u lo_w] ~ 0.
+//    The 1/r enters the exp2 argument as the constant kWc, so the split costs
+//    the same instructions as truncation.
+//  * ex2.approx.ftz.f32 returns values low by 5.1e-8 relative on average
+//    (measured on sm_103a over exponent arguments in [-120, 0], rms error
+//    6.0e-8).  The u factors' bias cancels between At and Bt in the
+//    conditional score; the w factors' does not.  Both exp2 arguments carry
+//    the constant kEx2Fix = log2(1 + 5.1e-8), again an FMA in place of a
+//    multiply.
+// Measured on the N = 50,000, d = 5, 32 x 32 grid against the full FP64
+// grid: mean per-row error of L_cond -1.8e-7 before, ~0 after.  Each lane takes
 // the points (2t, 2t+1) of a k-step so the TF32 and BF16 fragment layouts hold
 // the same points.  The tensor core's FP32 accumulation is kept short: each
 // chunk of 32 points (8 MMAs per accumulator) starts from zero and is then
@@ -30,6 +49,17 @@
 #include "loo_common.cuh"
 
 namespace cde {
+
+// exp2-argument constants of the Gaussian factors (see the bias note above)
+constexpr float kEx2Fix = 7.39e-8f;                        // log2(1 + 5.12e-8)
+constexpr float kWr = 1.0f - 11.0f / 32768.0f;             // exact in FP32
+constexpr float kWc = 4.843844517e-4f + 7.39e-8f;          // -log2(kWr) + kEx2Fix
+
+// Gaussian factors 2^{c t + k} of two values (k: the argument constant)
+__device__ __forceinline__ float2 gauss_factor2(float2 c, float2 t, float k) {
+    const float2 a = __ffma2_rn(c, t, make_float2(k, k));
+    return make_float2(ex2_approx(a.x), ex2_approx(a.y));
+}
 
 template <int G1, int G2>
 struct MmaCfg {
@@ -246,10 +276,13 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                     uint32_t bh[NT][2], bx[NT][2];
 #pragma unroll
                     for (int nt = 0; nt < NT; ++nt) {
-                        const float2 w = kernel_factor2<KERN>(ca2[nt], t2p);
+                        // Gaussian: w' = w / r, lo = w' r - hi (signed); Epanechnikov: lo = w - hi
+                        const float2 w = KERN == 0 ? gauss_factor2(ca2[nt], t2p, kWc)
+                                                   : kernel_factor2<KERN>(ca2[nt], t2p);
                         const float2 h = make_float2(__uint_as_float(__float_as_uint(w.x) & 0xffffe000u),
                                                      __uint_as_float(__float_as_uint(w.y) & 0xffffe000u));
-                        const float2 l = __ffma2_rn(h, make_float2(-1.f, -1.f), w);  // w - hi, exact
+                        const float2 l = KERN == 0 ? __ffma2_rn(w, make_float2(kWr, kWr), make_float2(-h.x, -h.y))
+                                                   : __ffma2_rn(h, make_float2(-1.f, -1.f), w);
                         bh[nt][0] = __float_as_uint(h.x);
                         bh[nt][1] = __float_as_uint(h.y);
                         bx[nt][0] = pack_bf16x2(l.x, l.y);
@@ -260,8 +293,11 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                     uint32_t ah[MT][4], ax[MT][4];
 #pragma unroll
                     for (int mt = 0; mt < MT; ++mt) {
-                        const float2 u0 = kernel_factor2<KERN>(ca1[mt], t1p0);  // (k, p0), (k+8, p0)
-                        const float2 u1 = kernel_factor2<KERN>(ca1[mt], t1p1);  // (k, p1), (k+8, p1)
+                        // (k, p0), (k+8, p0) and (k, p1), (k+8, p1)
+                        const float2 u0 = KERN == 0 ? gauss_factor2(ca1[mt], t1p0, kEx2Fix)
+                                                    : kernel_factor2<KERN>(ca1[mt], t1p0);
+                        const float2 u1 = KERN == 0 ? gauss_factor2(ca1[mt], t1p1, kEx2Fix)
+                                                    : kernel_factor2<KERN>(ca1[mt], t1p1);
                         bt[r][mt] = __fadd2_rn(bt[r][mt], __fadd2_rn(u0, u1));
                         const float2 h0 = make_float2(__uint_as_float(__float_as_uint(u0.x) & 0xffffe000u),
                                                       __uint_as_float(__float_as_uint(u0.y) & 0xffffe000u));

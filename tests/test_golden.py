@@ -77,9 +77,12 @@ def test_full_scale_grid_record():
 def test_library_matches_full_scale_grid():
     """The benchmark's workload (synth.scale_workload(): N = 50,000, d = 5,
     standardised, 32 x 32): every cell of the GPU grid against the oracle's
-    grid over every row, stored by make_golden.py --scale.  Tolerance per cell
-    1e-5 of sum_j |ell_j| (L_cond) and of (1/N) sum_j |ln A_j - ln(N - 1)|
-    (L_eq3)."""
+    grid over every row, stored by make_golden.py --scale.  Every cell must
+    meet both 1e-5 relative to its own |L| and 1e-5 of its tolerance scale
+    (sum_j |ell_j| for L_cond, (1/N) sum_j |ln A_j - ln(N - 1)| for L_eq3).
+    In some cells the rows cancel to |L_cond| ~ sum_j |ell_j| / 200, so the
+    first bound asks for errors far below the FP32 precision of one row: it
+    holds only because the per-row errors have no systematic sign."""
     from __graft_entry__ import build
     build()
     from paper_1206_5278_gb300 import cde
@@ -93,9 +96,15 @@ def test_library_matches_full_scale_grid():
     try:
         ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=w.standardize)
         Lc, Le = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
-        err_c = np.abs(Lc - np.array(S["L_cond"])) / np.array(S["scale_cond"])
-        err_e = np.abs(Le - np.array(S["L_eq3"])) / np.array(S["scale_eq3"])
+        Rc, Re = np.array(S["L_cond"]), np.array(S["L_eq3"])
+        err_c = np.abs(Lc - Rc) / np.array(S["scale_cond"])
+        err_e = np.abs(Le - Re) / np.array(S["scale_eq3"])
+        rel_c, rel_e = np.abs(Lc - Rc) / np.abs(Rc), np.abs(Le - Re) / np.abs(Re)
+        print("full grid: worst |dL|/|L| %.3g (L_cond), %.3g (L_eq3); worst of scale %.3g, %.3g"
+              % (rel_c.max(), rel_e.max(), err_c.max(), err_e.max()))
         assert err_c.max() <= 1e-5, "L_cond: worst cell %g of its scale" % err_c.max()
         assert err_e.max() <= 1e-5, "L_eq3: worst cell %g of its scale" % err_e.max()
+        assert rel_c.max() <= 1e-5, "L_cond: worst cell %g of |L|" % rel_c.max()
+        assert rel_e.max() <= 1e-5, "L_eq3: worst cell %g of |L|" % rel_e.max()
     finally:
         cde.cde_shutdown(ctx)

@@ -152,6 +152,118 @@ def test_nearest_neighbour_shifts(ctx, N, d):
     np.testing.assert_allclose(mx, acc.min(1), rtol=2.0 ** -21, atol=0)
     assert np.mean(mx == acc.min(1)) >= 0.99
     np.testing.assert_array_equal(my, dy2.min(1))
+    # the other coordinate's distance of the nearest points (smallest over ties)
+    ox, oy = cde.cde_dataset_nn_other(ctx, ds)
+    want_oy = np.where(acc == acc.min(1, keepdims=True), dy2, np.inf).min(1)
+    want_ox = np.where(dy2 == dy2.min(1, keepdims=True), acc, np.inf).min(1)
+    assert np.mean(oy == want_oy) >= 0.99
+    np.testing.assert_allclose(ox, want_ox, rtol=2.0 ** -21, atol=0)
+    assert np.all(ox >= mx) and np.all(oy >= my)
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+@pytest.mark.parametrize("d", [1, 5, 12])
+def test_nearest_neighbour_ties(ctx, d):
+    """Several nearest points: the stored other-coordinate distance is the
+    smallest among them (duplicated x rows and duplicated y values)."""
+    rng = np.random.default_rng(d)
+    N = 700
+    x = rng.integers(0, 6, size=(N, d)).astype(np.float32)   # many exact x ties
+    y = rng.integers(0, 40, size=N).astype(np.float32) * 0.25  # many exact y ties
+    ds = cde.cde_create_dataset(ctx, x, y)
+    mx, my = cde.cde_dataset_nn(ctx, ds)
+    ox, oy = cde.cde_dataset_nn_other(ctx, ds)
+    dx2 = ((x[:, None, :].astype(np.float64) - x[None, :, :]) ** 2).sum(2)   # exact: small integers
+    dy2 = (y[:, None].astype(np.float64) - y[None, :]) ** 2
+    np.fill_diagonal(dx2, np.inf)
+    np.fill_diagonal(dy2, np.inf)
+    np.testing.assert_array_equal(mx, dx2.min(1))
+    np.testing.assert_array_equal(my, dy2.min(1))
+    np.testing.assert_array_equal(oy, np.where(dx2 == dx2.min(1, keepdims=True), dy2, np.inf).min(1))
+    np.testing.assert_array_equal(ox, np.where(dy2 == dy2.min(1, keepdims=True), dx2, np.inf).min(1))
+    cde.cde_destroy_dataset(ctx, ds)
+
+
+def _flagged_cells(x, y, h1, h2, rows):
+    """Count (row, cell) pairs whose separably shifted numerator
+    sum_i 2^{-a1 (dx2 - m_x) - a2 (dy2 - m_y)} lies below the library's
+    recompute threshold 2^(ceil(log2 N) - 91) (FP64, on the given rows)."""
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    N = len(yd)
+    l2e = math.log2(math.e)
+    a1, a2 = l2e / (2 * np.asarray(h1) ** 2), l2e / (2 * np.asarray(h2) ** 2)
+    thr = math.ceil(math.log2(N)) - 91
+    n = 0
+    for j in rows:
+        X = ((xd - xd[j]) ** 2).sum(1)
+        Y = (yd - yd[j]) ** 2
+        X[j] = Y[j] = np.inf
+        X, Y = X - X.min(), Y - Y.min()
+        E = a1[:, None, None] * X + a2[None, :, None] * Y
+        em = E.min(2)
+        l2 = -em + np.log2(np.exp2(-(E - em[:, :, None])).sum(2))
+        n += int((l2 < thr).sum())
+    return n
+
+
+def fp32_distance_row_bound(x64, y, h1, h2, rows):
+    """Per (row, h1, h2) first-order bound on |ell_j(FP32 distances) - ell_j(exact)|
+    for squared distances formed in FP32 from FP32-rounded coordinates.  Pair i's
+    dx2 is off by at most 2^-23 sum_c |x_jc - x_ic| (|x_jc| + |x_ic|) (rounding the
+    coordinates) plus (d + 2) 2^-24 dx2 (differences, squares, sums), dy2 by
+    2^-23 dy2; its log-weight by those over 2 h^2.  ell_j = ln A_j - ln B_j is a
+    difference of two weighted means of these errors, so it is off by at most twice
+    the largest of them over the pairs that carry weight (log-weight within 60 of
+    the row's largest, by h1 alone or jointly)."""
+    N, d = x64.shape
+    yd = np.asarray(y, np.float64)
+    out = np.zeros((len(rows), len(h1), len(h2)))
+    for r, j in enumerate(rows):
+        diff = np.abs(x64 - x64[j])
+        dx2 = (diff ** 2).sum(1)
+        ex = 2.0 ** -23 * (diff * (np.abs(x64) + np.abs(x64[j]))).sum(1) + (d + 2) * 2.0 ** -24 * dx2
+        dy2 = (yd - yd[j]) ** 2
+        ey = 2.0 ** -23 * dy2
+        dx2[j] = dy2[j] = np.inf
+        ib = 1.0 / (2 * np.asarray(h2, np.float64) ** 2)
+        for k, a in enumerate(h1):
+            lx = -dx2 / (2 * a * a)
+            lj = lx[None, :] - ib[:, None] * dy2[None, :]                     # [l][i]
+            live = (lx >= lx.max() - 60)[None, :] | (lj >= lj.max(1, keepdims=True) - 60)
+            err = ex[None, :] / (2 * a * a) + ib[:, None] * ey[None, :]
+            out[r, k, :] = 2 * np.where(live, err, 0.0).max(1)
+    return out
+
+
+@pytest.mark.parametrize("d,latent", [(8, False), (16, False), (32, False), (32, True)])
+def test_exact_recomputation_in_many_cells(ctx, d, latent):
+    """Small bandwidths on standardised GMM (and latent-factor) data, where
+    many cells of many rows lose the FP32 range and go through the exact
+    two-pass recomputation: the grid against the oracle at the score
+    tolerance, and every row against the oracle within 2e-5 plus the
+    first-order effect of FP32 squared distances (at d >= 16 and h1 = 0.05
+    that alone reaches 1e-4 in rows whose weight is shared by neighbours at
+    similar distances)."""
+    N = 2000
+    if latent:
+        x, y = synth.latent_projection(N, d=d, seed=21)
+    else:
+        x, y = synth.gmm_sine(N, d, seed=20 + d)
+    h1 = synth.bandwidth_grid(0.05, 2.0, 32)
+    h2 = synth.bandwidth_grid(0.01, 1.0, 32)
+    x64 = (x.astype(np.float64) - x.mean(0)) / x.astype(np.float64).std(0, ddof=1)
+    assert _flagged_cells(x64.astype(np.float32), y, h1, h2, range(0, N, 25)) >= 50   # the recomputation is exercised
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    g = cde.cde_loo_rows(ctx, ds, h1, h2, np.arange(N))
+    ref, _ = oracle.loo_rows(x, y, h1, h2, standardize_x=True)
+    plain = np.abs(g - ref) - (2e-5 + 2e-5 * np.abs(ref))
+    rows = np.nonzero((plain > 0).any((1, 2)))[0]     # the bound is needed only there
+    bound = fp32_distance_row_bound(x64, y, h1, h2, rows)
+    excess = plain[rows] - bound
+    assert rows.size == 0 or excess.max() <= 0, "row %d off by %g beyond its bound" % (
+        rows[np.unravel_index(np.argmax(excess), excess.shape)[0]], excess.max())
+    Lc, Le = cde.cde_loo_loglik(ctx, ds, h1, h2)
+    _check_grid(Lc, Le, x, y, h1, h2, standardize=True)
     cde.cde_destroy_dataset(ctx, ds)
 
 
