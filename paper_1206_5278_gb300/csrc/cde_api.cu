@@ -87,6 +87,7 @@ int check_status_batch(unsigned int*);
 int check_status_density(unsigned int*);
 int check_status_products(unsigned int*);
 int check_status_grad(unsigned int*);
+int check_status_gram(unsigned int*);
 }  // namespace cde
 #endif
 
@@ -311,7 +312,7 @@ int cde_check_status(cde_ctx* ctx, unsigned int* code, int* enabled) {
     if (enabled) *enabled = 1;
     CDE_CUDA(cudaDeviceSynchronize());
     int (*readers[])(unsigned int*) = {check_status_loo, check_status_batch, check_status_density,
-                                       check_status_products, check_status_grad};
+                                       check_status_products, check_status_grad, check_status_gram};
     for (auto rd : readers) {
         unsigned int c = 0;
         const int rc = rd(&c);

@@ -21,6 +21,7 @@ struct LooArgs {
     const float* qy;        // [N] dy^2 of each row's x-nearest point
     const int64_t* rows;    // optional list of rows (null: rows 0..n_rows-1)
     double* part;           // [n_tiles][2][T1*T2] FP64 tile partials (L_cond, sum ln A)
+    double* fb;             // d >= 16 kernel: [grid][16384] per-CTA recomputed log2 At
     double* ell_rows;       // optional per-row ell output
     int64_t ell_ld_row;     // row stride of ell_rows (doubles)
     int ell_ld_k;           // k stride of ell_rows
@@ -344,7 +345,11 @@ __device__ __forceinline__ void loo_unit_epilogue(const LooArgs& a, const Coef& 
             const int jl = c / GG;
             if (!vr_s[jl]) continue;
             const float v = At[m];
-            if (v >= a.thresh) {
+            // cells of the padded grid (the last bandwidth repeated) are never
+            // output: they are not recomputed either
+            const int kl = c - jl * GG;
+            const bool padded = kl / G2 >= a.G1r || kl % G2 >= a.G2r;
+            if (v >= a.thresh || padded) {
                 la2[c] = log2_wide(v);
             } else {
                 const int q = atomicAdd(nflag_s, 1);
@@ -406,6 +411,14 @@ inline int loo_pad1(int g) { return g <= 16 ? 16 : 32; }
 inline int loo_pad2(int g) { return g <= 8 ? 8 : (g <= 16 ? 16 : 32); }
 
 int launch_loo_tile_kernel(int T1, int T2, const LooArgs& a, int grid, cudaStream_t st);
+// d_x >= 16: the kernel with the x cross-term on the tensor cores (loo_gram.cu)
+constexpr int kGramMinD = 16;
+int launch_loo_gram(int T1, int T2, const LooArgs& a, int grid, cudaStream_t st);
+int loo_gram_rows_per_unit(int T1, int T2);
+size_t loo_gram_fb_bytes_per_cta();
+size_t loo_gram_smem_bytes(int T1, int T2, int d);
+// whether a grid block of this shape over this dataset runs on the d >= 16 kernel
+bool loo_use_gram(const Dataset& D, int T1, int T2);
 void fill_loo_args(LooArgs& a, const Dataset& D, const double* h1, int g1, const double* h2,
                    int g2, int T1, int T2);
 // units per tile of a grid block shape over n_rows rows (the tuned value when set; n_rows = 0:

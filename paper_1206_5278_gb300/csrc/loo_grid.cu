@@ -448,16 +448,37 @@ int loo_grid_ctas(cde_ctx* ctx, int T1, int T2) {
     return (c > 0 ? c : 2) * ctx->sm_count;
 }
 
+// Launch plan of one grid block: rows per unit, units per tile, tiles, CTAs and
+// the scratch they need (tile partials, then the d >= 16 kernel's per-CTA buffer
+// of recomputed cells, then the tile counter).
+struct LooPlan {
+    bool gram;
+    int rpu, upt, n_units, n_tiles, grid;
+    size_t part_bytes, fb_bytes;
+    size_t bytes() const { return part_bytes + fb_bytes + 256; }
+};
+
+static LooPlan loo_plan(cde_ctx* ctx, const Dataset& D, int T1, int T2, int64_t n_rows) {
+    LooPlan p{};
+    p.gram = loo_use_gram(D, T1, T2);
+    p.rpu = p.gram ? loo_gram_rows_per_unit(T1, T2) : 1024 / (T1 * T2);
+    p.upt = p.gram ? 1 : loo_units_per_tile(ctx, T1, T2, n_rows);
+    p.n_units = (int)((n_rows + p.rpu - 1) / p.rpu);
+    p.n_tiles = (p.n_units + p.upt - 1) / p.upt;
+    const int cmax = p.gram ? ctx->sm_count : loo_grid_ctas(ctx, T1, T2);
+    p.grid = p.n_tiles < cmax ? p.n_tiles : cmax;
+    p.part_bytes = (size_t)p.n_tiles * 2 * T1 * T2 * sizeof(double);
+    p.fb_bytes = p.gram ? (size_t)p.grid * loo_gram_fb_bytes_per_cta() : 0;
+    return p;
+}
+
 size_t loo_grid_scratch_bytes(cde_ctx* ctx, const Dataset& D, int G1, int G2, int64_t n_rows) {
     size_t mx = 0;
     for (int k0 = 0; k0 < G1; k0 += 32) {
         const int T1 = loo_pad1(G1 - k0 < 32 ? G1 - k0 : 32);
         for (int l0 = 0; l0 < G2; l0 += 32) {
             const int T2 = loo_pad2(G2 - l0 < 32 ? G2 - l0 : 32);
-            const int JW = 1024 / (T1 * T2);
-            const int64_t units = (n_rows + JW - 1) / JW;
-            const int upt = loo_units_per_tile(ctx, T1, T2, n_rows);
-            const size_t b = (size_t)((units + upt - 1) / upt) * 2 * T1 * T2 * sizeof(double) + 256;
+            const size_t b = loo_plan(ctx, D, T1, T2, n_rows).bytes();
             if (b > mx) mx = b;
         }
     }
@@ -477,30 +498,29 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
             const int T2 = loo_pad2(g2);
             LooArgs a{};
             fill_loo_args(a, D, h1 + k0, g1, h2 + l0, g2, T1, T2);
-            const int JW = 1024 / (T1 * T2);
+            const LooPlan pl = loo_plan(ctx, D, T1, T2, n_rows);
             a.rows = d_rows;
             a.n_rows = n_rows;
-            a.n_units = (int)((n_rows + JW - 1) / JW);
-            a.units_per_tile = loo_units_per_tile(ctx, T1, T2, n_rows);
-            a.n_tiles = (a.n_units + a.units_per_tile - 1) / a.units_per_tile;
+            a.n_units = pl.n_units;
+            a.units_per_tile = pl.upt;
+            a.n_tiles = pl.n_tiles;
             a.ell_rows = d_ell_rows ? d_ell_rows + (size_t)k0 * G2 + l0 : nullptr;
             a.ell_ld_row = (int64_t)G1 * G2;
             a.ell_ld_k = G2;
             a.G1r = g1;
             a.G2r = g2;
-            const size_t part_bytes = (size_t)a.n_tiles * 2 * T1 * T2 * sizeof(double);
             double* part = nullptr;
-            const bool own = !(scratch && part_bytes + 256 <= scratch_bytes);
-            if (own) CDE_CUDA(cudaMallocAsync((void**)&part, part_bytes + 256, st));
+            const bool own = !(scratch && pl.bytes() <= scratch_bytes);
+            if (own) CDE_CUDA(cudaMallocAsync((void**)&part, pl.bytes(), st));
             else part = static_cast<double*>(scratch);
             a.part = part;
+            a.fb = reinterpret_cast<double*>(reinterpret_cast<char*>(part) + pl.part_bytes);
             a.tile_base = 0;
-            a.work = reinterpret_cast<int*>(reinterpret_cast<char*>(part) + part_bytes);
+            a.work = reinterpret_cast<int*>(reinterpret_cast<char*>(part) + pl.part_bytes + pl.fb_bytes);
             CDE_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));
-            const int cmax = loo_grid_ctas(ctx, T1, T2);
-            const int grid = a.n_tiles < cmax ? a.n_tiles : cmax;
+            const int grid = pl.grid;
             timing_begin(ctx, st);
-            int rc = launch_loo_tile_kernel(T1, T2, a, grid, st);
+            int rc = pl.gram ? launch_loo_gram(T1, T2, a, grid, st) : launch_loo_tile_kernel(T1, T2, a, grid, st);
             timing_end(ctx, st);
             if (rc != CDE_OK) {
                 if (own) cudaFreeAsync(part, st);

@@ -242,7 +242,8 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                 // squared distances (masked pairs +inf)
                 const float mxv = JW == 1 ? mxr1 : mx_s[r], myv = JW == 1 ? myr1 : my_s[r];
                 const float t1 = KERN == 0 ? (ok ? mxv - dx2 : -INFINITY) : (ok ? dx2 : INFINITY);
-                const float t2 = KERN == 0 ? myv - dy * dy : dy * dy;
+                // masked pairs: w = 0 as well (at i = j, m_y - 0 could overflow 2^{a2 t2})
+                const float t2 = KERN == 0 ? (ok ? myv - dy * dy : -INFINITY) : dy * dy;
                 reinterpret_cast<float2*>(tt + r * 3 * IC)[lane] = make_float2(t1, t1);
                 tt[r * 3 * IC + 2 * IC + lane] = t2;
             }
