@@ -326,12 +326,38 @@ def run_ours(args, w):
                                       "tcgen05_tf32_mac_per_clk_sm": peaks.umma_tf32_mac_per_clk_sm,
                                       "mma_sync_tf32_mac_per_clk_sm": peaks.mma_tf32_mac_per_clk_sm,
                                       "sm_clock_mhz": peaks.sm_clock_mhz}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
     cde.cde_destroy_dataset(ctx, ds)
     cde.cde_shutdown(ctx)
+    if rank == 0 and world == 1 and not args.no_secondary:
+        out["secondary"] = secondary(args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def secondary(args):
+    """The other workloads of the method, measured in the default run with few
+    steps each: the d = 32 grid (tensor-core distances), the 256-dataset batch,
+    the gradient at N = 200,000 (d = 8 and 32), density queries and serving
+    over datasets of up to 500,000 points.  Every entry carries its own
+    roofline and parity against the FP64 oracle."""
+    import copy
+    a = copy.copy(args)
+    a.steps, a.warmup = 3, 1
+    out = {}
+    t0 = time.perf_counter()
+    a.grid32_rows = 8
+    out["grid_d32"] = measure_grid32(a)
+    out["batch"] = measure_batch(a)
+    a.ascent_steps = 30
+    out["grad"] = measure_grad(a)
+    out["density"] = measure_density(a)
+    a.serve_jobs, a.serve_loads = 16, "0.8"
+    out["serve"] = measure_serve(a)
+    out["wall_s"] = time.perf_counter() - t0
+    out["note"] = "each entry: its own synthetic workload and timing (CUDA events or host clock, stated in it)"
+    return out
 
 
 def _timed(fn, reps):
@@ -412,9 +438,11 @@ def run_tiny(args):
     cde.cde_shutdown(ctx)
 
 
-def run_batch(args):
+def measure_batch(args):
     """256 datasets (N log-uniform [500, 20000], d in {1,2,4,8}, 16x16 grids):
-    one graph-captured persistent launch vs one launch per dataset."""
+    one graph-captured persistent launch vs one launch per dataset; parity of
+    the two smallest datasets' grids against the oracle."""
+    from oracle import oracle
     from paper_1206_5278_gb300 import cde, synth
     ws = synth.batch_workloads(n_datasets=args.n_datasets)
     ctx = cde.cde_init(0)
@@ -438,26 +466,44 @@ def run_batch(args):
     Lc, _ = cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s)
     same = all(np.array_equal(Lc[b], cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)[0])
                for b, (ds, w) in enumerate(zip(dss, ws)))
+    # parity: the batch's grids of the two smallest datasets against the oracle
+    oracle.build()
+    worst = 0.0
+    for b in np.argsort([w.N for w in ws])[:2]:
+        w = ws[b]
+        ell, _ = oracle.loo_rows(w.x, w.y, w.h1, w.h2, standardize_x=w.standardize)
+        worst = max(worst, float(np.max(np.abs(Lc[b] - ell.sum(0)) / np.abs(ell).sum(0))))
     pe = sum(w.N * w.N * w.h1.size * w.h2.size for w in ws)
-    _line(workload="batch_%d_datasets_16x16" % len(ws), value=pe / float(np.median(tb)),
-          steps=len(tb), warmup=args.warmup, ms_per_step=1e3 * float(np.median(tb)),
-          latency_ms={"p50": 1e3 * float(np.percentile(tb, 50)), "p99": 1e3 * float(np.percentile(tb, 99))},
-          per_dataset_loop={"value": pe / float(np.median(tl)), "ms_per_step": 1e3 * float(np.median(tl))},
-          speedup_vs_loop=float(np.median(tl) / np.median(tb)), bitwise_equal_to_single=bool(same),
-          autotune=tune, gpu_launches=2,
-          roofline=_flop_roof(sum(w.N * w.N * flops_per_pair(16, 16, w.d) for w in ws), kb,
-                              "k_loo_batch (graph replay)"),
-          config={"workload": "batch", "datasets": len(ws), "pair_evals": pe,
-                  "N_range": [min(w.N for w in ws), max(w.N for w in ws)],
-                  "timing": "host wall clock around the synchronous batched call (graph replay)"})
+    out = dict(workload="batch_%d_datasets_16x16" % len(ws), value=pe / float(np.median(tb)),
+               steps=len(tb), warmup=args.warmup, ms_per_step=1e3 * float(np.median(tb)),
+               latency_ms={"p50": 1e3 * float(np.percentile(tb, 50)), "p99": 1e3 * float(np.percentile(tb, 99))},
+               per_dataset_loop={"value": pe / float(np.median(tl)), "ms_per_step": 1e3 * float(np.median(tl))},
+               speedup_vs_loop=float(np.median(tl) / np.median(tb)), bitwise_equal_to_single=bool(same),
+               autotune=tune, gpu_launches=2,
+               parity={"datasets": 2, "score_rel_err": worst, "tolerance": 1e-5,
+                       "basis": "batch grids of the two smallest datasets vs the FP64 oracle, "
+                                "|dL| / sum_j |ell_j| per cell"},
+               roofline=_flop_roof(sum(w.N * w.N * flops_per_pair(16, 16, w.d) for w in ws), kb,
+                                   "k_loo_batch (graph replay)"),
+               config={"workload": "batch", "datasets": len(ws), "pair_evals": pe,
+                       "N_range": [min(w.N for w in ws), max(w.N for w in ws)],
+                       "timing": "host wall clock around the synchronous batched call (graph replay)"})
     cde.cde_shutdown(ctx)
+    return out
 
 
-def run_grad(args):
+def run_batch(args):
+    _line(**measure_batch(args))
+
+
+def measure_grad(args):
     """N=200,000, d in {8, 32}: adjoint evaluations (pairs/s) and gradient
-    ascent vs the exhaustive 32x32 grid."""
+    ascent vs the exhaustive 32x32 grid; parity of the gradient on a
+    2,000-point subsample against the oracle.  Returns one entry per d."""
+    from oracle import oracle
     from paper_1206_5278_gb300 import cde, synth
     from paper_1206_5278_gb300.autograd import select_bandwidth
+    outs = {}
     for d in (8, 32):
         w = synth.grad_workload(N=args.N_grad, d=d)
         ctx = cde.cde_init(0)
@@ -496,7 +542,18 @@ def run_grad(args):
                                steps=args.ascent_steps, lr=0.1)
         ta = time.perf_counter() - t0
         pairs = w.N * w.N
-        _line(workload=w.name, metric="LOO-CV gradient pair-evals/s (N^2 per (h1,h2)) at 1e-4 rel err",
+        # parity: the gradient of a 2,000-point subsample against the oracle
+        sub = np.random.default_rng(5).choice(w.N, 2000, replace=False)
+        dsub = cde.cde_create_dataset(ctx, w.x[sub], w.y[sub], standardize=True)
+        gs = cde.cde_loo_grad(ctx, dsub, h1, h2)
+        ref, rows = oracle.grad(w.x[sub], w.y[sub], h1, h2, standardize_x=True, per_row=True)
+        scale = np.abs(rows).sum(0)
+        cde.cde_destroy_dataset(ctx, dsub)
+        par = {"L_rel_err": float(abs(gs[0] - ref[0]) / scale[0]),
+               "grad_rel_err": [float(abs(gs[k] - ref[k]) / scale[k]) for k in (1, 2)],
+               "tolerance": {"L": 1e-5, "grad": 1e-4},
+               "basis": "2,000-point subsample, |error| / sum_j |per-row term| (FP64 oracle)"}
+        outs["d%d" % d] = dict(workload=w.name, metric="LOO-CV gradient pair-evals/s (N^2 per (h1,h2)) at 1e-4 rel err",
               value=pairs / float(np.median(tg)), steps=len(tg), warmup=args.warmup,
               ms_per_step=1e3 * float(np.median(tg)),
               ascent={"steps": args.ascent_steps, "seconds": ta, "h1": res["h1"], "h2": res["h2"], "L": res["L"],
@@ -508,12 +565,18 @@ def run_grad(args):
               grid32={"seconds": float(tgrid[0]), "L_best": float(Lgrid.max()),
                       "h1": float(w.h1[np.unravel_index(Lgrid.argmax(), Lgrid.shape)[0]]),
                       "h2": float(w.h2[np.unravel_index(Lgrid.argmax(), Lgrid.shape)[1]])},
-              roofline=roof,
+              roofline=roof, parity=par,
               config={"workload": w.name, "N": w.N, "d_x": d, "h1": h1, "h2": h2})
         cde.cde_shutdown(ctx)
+    return outs
 
 
-def run_density(args):
+def run_grad(args):
+    for v in measure_grad(args).values():
+        _line(**v)
+
+
+def measure_density(args):
     """Density queries: Q query points x 256-point y grid against N data points
     (one cde_density call with device inputs/outputs, CUDA-event timed), at
     the configured Q x N and at a small-Q / large-N point (Q = 100 x N = 500,000).
@@ -521,8 +584,10 @@ def run_density(args):
     call (data read once, queries and grid read, density written) per second
     against the measured copy bandwidth."""
     import torch
+    from oracle import oracle
     from paper_1206_5278_gb300 import cde, synth
     ctx = cde.cde_init(0)
+    parity = None
     hbm_peak = _measured_peak("hbm_gbs", 6688.8)
     bf16_peak = _measured_peak("bf16_tflops", 1863.5)
     cde.cde_timing_enable(ctx, True)
@@ -559,6 +624,13 @@ def run_density(args):
             "kernel_issued_tflops": issued / (kms * 1e-3) / 1e12,
             "hbm": {"algorithmic_bytes": nbytes, "GB_s": nbytes / (ms * 1e-3) / 1e9, "peak_GB_s": hbm_peak,
                     "frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}}
+        if (Q, N) == (args.dens_Q, args.dens_N):
+            # parity: 16 sampled queries of the timed launch against the oracle
+            qs = np.random.default_rng(2).choice(Q, 16, replace=False)
+            fg = f.cpu().numpy()[qs]
+            ref = oracle.density(x, y, 0.3, 0.1, xq.cpu().numpy()[qs], yg.cpu().numpy(), standardize_x=True)
+            parity = {"queries": 16, "rel_err": float(np.max(np.abs(fg - ref) / ref.max(1, keepdims=True))),
+                      "tolerance": 1e-4, "basis": "|f_gpu - f_oracle| / max_g f_oracle per query (FP64 oracle)"}
         cde.cde_destroy_dataset(ctx, ds)
     cde.cde_timing_enable(ctx, False)
     main = runs["Q%d_N%d" % (args.dens_Q, args.dens_N)]
@@ -573,13 +645,18 @@ def run_density(args):
             "issued_bf16": {"achieved": main["kernel_issued_tflops"],
                             "frac": main["kernel_issued_tflops"] / bf16_peak,
                             "basis": "executed BF16 MMAs: hi*hi + hi*lo + lo*hi, full 128 x 256 tiles"}}
-    _line(workload="density_Q%d_N%d_d%d_G256" % (args.dens_Q, args.dens_N, args.dens_d),
-          metric="density (query, data point) pairs/s x 256-point y grid", unit="pairs/s",
-          value=main["pairs_per_s"], steps=args.steps, warmup=args.warmup, ms_per_step=main["ms"],
-          flops_per_pair=2 * 256 * 1 + 3 * args.dens_d, tflops=main["tflops"], runs=runs, roofline=roof,
-          gpu_launches=4 * args.steps, dtype="bf16x3 hi/lo split, fp32 accumulate",
-          config={"workload": "density", "Q": args.dens_Q, "N": args.dens_N, "d_x": args.dens_d, "G_y": 256})
+    out = dict(workload="density_Q%d_N%d_d%d_G256" % (args.dens_Q, args.dens_N, args.dens_d),
+               metric="density (query, data point) pairs/s x 256-point y grid", unit="pairs/s",
+               value=main["pairs_per_s"], steps=args.steps, warmup=args.warmup, ms_per_step=main["ms"],
+               flops_per_pair=2 * 256 * 1 + 3 * args.dens_d, tflops=main["tflops"], runs=runs, roofline=roof,
+               parity=parity, gpu_launches=4 * args.steps, dtype="bf16x3 hi/lo split, fp32 accumulate",
+               config={"workload": "density", "Q": args.dens_Q, "N": args.dens_N, "d_x": args.dens_d, "G_y": 256})
     cde.cde_shutdown(ctx)
+    return out
+
+
+def run_density(args):
+    _line(**measure_density(args))
 
 
 def run_select(args):
@@ -810,11 +887,16 @@ def _measured_peak(key, default):
         return default
 
 
-def run_serve(args):
+def measure_serve(args):
     """Poisson stream, 70% density jobs (Q log-uniform [1, Q_max] x 256-point y
     grid), 30% selection jobs (16x16 grid + 20 Adam steps) over resident
-    datasets; capacity from sequential synchronous calls, then the stream at
-    50/80/95% of it through the request loop."""
+    datasets with N log-uniform in [1,000, serve_N_max]; capacity from
+    sequential synchronous calls, then the stream at the given fractions of it
+    through the request loop, then everything at once (saturation).  Parity:
+    a served density job against the oracle on sampled queries, and a density
+    and a selection job served in the mix against the same jobs served alone
+    (bitwise)."""
+    from oracle import oracle
     from paper_1206_5278_gb300 import cde, synth
     from paper_1206_5278_gb300.serve import Server
     ws = synth.serving_datasets(n=args.serve_datasets, N_max=args.serve_N_max)
@@ -827,9 +909,10 @@ def run_serve(args):
     for r in reqs:
         w = ws[r.dataset]
         if r.kind == 0:
-            payload.append((0, dss[r.dataset], synth.query_points(w.x, r.Q, seed=r.seed), synth.y_grid(w.y, 0.1)))
+            payload.append((0, dss[r.dataset], synth.query_points(w.x, r.Q, seed=r.seed), synth.y_grid(w.y, 0.1),
+                            r.dataset))
         else:
-            payload.append((1, dss[r.dataset], None, None))
+            payload.append((1, dss[r.dataset], None, None, r.dataset))
     # sequential plain launches (synchronous API, one job at a time)
     from paper_1206_5278_gb300.autograd import select_bandwidth
 
@@ -847,10 +930,16 @@ def run_serve(args):
         seq_lat.append(time.perf_counter() - t1)
     seq_s = time.perf_counter() - t0
     cap = len(payload) / seq_s
+    seq_den = [t for t, p in zip(seq_lat, payload) if p[0] == 0]
     loads = {}
+    parity = None
     srv = Server(ctx, n_streams=args.serve_streams)
+
+    def submit(p):
+        return srv.density(p[1], 0.3, 0.1, p[2], p[3]) if p[0] == 0 else srv.select(p[1], h1g, h2g, 20, 0.05)
     try:
-        for frac in (0.5, 0.8, 0.95):
+        fracs = [float(v) for v in args.serve_loads.split(",") if v]
+        for frac in fracs:
             rate = frac * cap
             gaps = np.random.default_rng(int(frac * 100)).exponential(1.0 / rate, len(payload))
             srv.reset_stats()
@@ -861,29 +950,47 @@ def run_serve(args):
                 tnext += g
                 while time.perf_counter() < tnext:
                     time.sleep(min(0.0005, max(0.0, tnext - time.perf_counter())))
-                if p[0] == 0:
-                    tickets.append(srv.density(p[1], 0.3, 0.1, p[2], p[3]))
-                else:
-                    tickets.append(srv.select(p[1], h1g, h2g, 20, 0.05))
-            for t in tickets:
-                t.result()
+                tickets.append(submit(p))
+            results = [t.result() for t in tickets]
             wall = time.perf_counter() - t0
             st = srv.stats()
-            loads["%d%%" % int(frac * 100)] = {
+            loads["%d%%" % int(round(frac * 100))] = {
                 "offered_jobs_per_s": rate, "jobs_per_s": len(payload) / wall,
                 "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                 "p50_density_ms": st["p50_density_ms"], "p99_density_ms": st["p99_density_ms"],
                 "p50_select_ms": st["p50_select_ms"], "p99_select_ms": st["p99_select_ms"],
                 "peak_concurrent": st["peak_concurrent"]}
+            if parity is None:
+                # a served density job (in the mix) against the oracle; a density and a
+                # selection job of the mix served again alone: the same bits
+                ide = next(i for i, p in enumerate(payload) if p[0] == 0 and p[2].shape[0] >= 8)
+                isel = next((i for i, p in enumerate(payload) if p[0] == 1), None)
+                pd = payload[ide]
+                w = ws[pd[4]]
+                qs = np.random.default_rng(4).choice(pd[2].shape[0], 8, replace=False)
+                ref = oracle.density(w.x, w.y, 0.3, 0.1, pd[2][qs], pd[3], standardize_x=True)
+                fmix = results[ide][qs]
+                alone_d = submit(pd).result()
+                same = bool(np.array_equal(alone_d, results[ide]))
+                if isel is not None:
+                    alone_s = submit(payload[isel]).result()
+                    same = same and all(np.array_equal(np.asarray(alone_s[k]), np.asarray(results[isel][k]))
+                                        for k in ("h1", "h2", "L", "L_grid"))
+                parity = {"density_rel_err": float(np.max(np.abs(fmix - ref) / ref.max(1, keepdims=True))),
+                          "tolerance": 1e-4, "density_job": {"dataset_N": w.N, "Q": int(pd[2].shape[0]),
+                                                             "sampled_queries": 8},
+                          "in_mix_equals_alone": same,
+                          "basis": "served density vs FP64 oracle (|df| / max_g f per query); a density and a "
+                                   "selection job of the mix served again alone, compared bitwise"}
         # saturation: everything submitted at once
         srv.reset_stats()
         t0 = time.perf_counter()
-        tickets = [srv.density(p[1], 0.3, 0.1, p[2], p[3]) if p[0] == 0 else srv.select(p[1], h1g, h2g, 20, 0.05)
-                   for p in payload]
+        tickets = [submit(p) for p in payload]
         for t in tickets:
             t.result()
         sat_s = time.perf_counter() - t0
         sat = len(payload) / sat_s
+        sat_st = srv.stats()
     finally:
         srv.stop()
     # algorithmic HBM bytes of the saturation run: per density job the queries and the
@@ -891,7 +998,7 @@ def run_serve(args):
     # selection job the dataset read once per grid or gradient evaluation (21)
     alg = 0
     for p in payload:
-        w = ws[dss.index(p[1])]
+        w = ws[p[4]]
         dset = w.N * (w.d + 1) * 4
         alg += (p[2].nbytes + 256 * 4 + p[2].shape[0] * 256 * 4 + dset) if p[0] == 0 else 21 * dset
     hbm_peak = _measured_peak("hbm_gbs", 6688.8)
@@ -899,14 +1006,78 @@ def run_serve(args):
            "frac": alg / sat_s / 1e9 / hbm_peak,
            "basis": "queries, grid, densities and one dataset read per density job; one dataset read "
                     "per evaluation of a selection job; peak = measured copy bandwidth"}
-    _line(workload="serve", metric="serving jobs/s with p50/p99 latency (density 70% / selection 30%)",
-          unit="jobs/s", value=sat, steps=len(payload), warmup=1, ms_per_step=1e3 / sat,
-          sequential={"jobs_per_s": cap, "p50_ms": 1e3 * float(np.percentile(seq_lat, 50)),
-                      "p99_ms": 1e3 * float(np.percentile(seq_lat, 99))},
-          speedup_vs_sequential=sat / cap, loads=loads, hbm=hbm,
-          config={"workload": "serve", "datasets": [w.N for w in ws], "d": [w.d for w in ws],
-                  "jobs": len(payload), "Q_max": args.serve_Q_max, "streams": args.serve_streams})
+    out = dict(workload="serve", metric="serving jobs/s with p50/p99 latency (density 70% / selection 30%)",
+               unit="jobs/s", value=sat, steps=len(payload), warmup=1, ms_per_step=1e3 / sat,
+               sequential={"jobs_per_s": cap, "p50_ms": 1e3 * float(np.percentile(seq_lat, 50)),
+                           "p99_ms": 1e3 * float(np.percentile(seq_lat, 99)),
+                           "p50_density_ms": 1e3 * float(np.percentile(seq_den, 50)) if seq_den else None},
+               speedup_vs_sequential=sat / cap, loads=loads,
+               saturation={"jobs_per_s": sat, "p50_ms": sat_st["p50_ms"], "p99_ms": sat_st["p99_ms"],
+                           "p50_density_ms": sat_st["p50_density_ms"], "p99_density_ms": sat_st["p99_density_ms"]},
+               hbm=hbm, parity=parity,
+               config={"workload": "serve", "datasets": [w.N for w in ws], "d": [w.d for w in ws],
+                       "jobs": len(payload), "selection_jobs": sum(1 for p in payload if p[0] == 1),
+                       "Q_max": args.serve_Q_max, "streams": args.serve_streams})
     cde.cde_shutdown(ctx)
+    return out
+
+
+def run_serve(args):
+    _line(**measure_serve(args))
+
+
+def measure_grid32(args):
+    """The d = 32 workload of the x cross-term's tensor-core path: latent
+    factors projected to 32 dimensions plus noise, standardised, N = 200,000,
+    32 x 32 grid h1 in [0.05, 2], h2 in [0.01, 1] (the gradient workload's data
+    over the whole grid); parity on sampled rows against the oracle."""
+    from oracle import oracle
+    from paper_1206_5278_gb300 import cde, synth
+    w = synth.grad_workload(N=args.N_grid32, d=32)
+    h1, h2 = synth.bandwidth_grid(0.05, 2.0, 32), synth.bandwidth_grid(0.01, 1.0, 32)
+    ctx = cde.cde_init(0)
+    ds = cde.cde_create_dataset(ctx, w.x, w.y, standardize=True)
+    for _ in range(max(1, args.warmup)):
+        cde.cde_loo_loglik(ctx, ds, h1, h2)
+    host, kms = _timed_kernel(ctx, lambda: cde.cde_loo_loglik(ctx, ds, h1, h2), args.steps)
+    pe = w.N * w.N * 1024
+    rows = np.random.default_rng(11).choice(w.N, args.grid32_rows, replace=False)
+    g = cde.cde_loo_rows(ctx, ds, h1, h2, rows)
+    oracle.build()
+    ref, _ = oracle.loo_rows(w.x, w.y, h1, h2, rows=rows, standardize_x=True)
+    from oracle.fp32_bounds import rows_within_bound
+    x64 = (w.x.astype(np.float64) - w.x.mean(0)) / w.x.astype(np.float64).std(0, ddof=1)
+    ok, worst = rows_within_bound(g, ref, x64, w.y, h1, h2, rows, gram=True)
+    par = {"rows": int(rows.size), "row_max_abs_err": float(np.max(np.abs(g - ref))),
+           "rows_within_bound": ok, "worst_excess_over_bound": worst,
+           "tolerance_row": "2e-5 + 2e-5 |ell_j| + the first-order FP32 / Gram distance bound (oracle/fp32_bounds.py)",
+           "basis": "sampled rows against the FP64 oracle; the grid's own score criterion (1e-5 of sum |ell_j|) "
+                    "is not testable on a sample, since per-row errors average out only over many rows"}
+    # the kernel's FP32 lane work against the FP32 pipe (as the default line); the Gram
+    # dot products (3 x 32 TF32 multiply-adds per pair) run on the tensor cores beside it
+    fpp = 2 * 1024 + 32 + 64 + 7
+    roof = _flop_roof(w.N * w.N * fpp, kms, "k_loo_gram")
+    roof["achieved_basis"] = "2 G1 G2 + G1 + (G1 + G2) + 7 FP32 flop per pair (outer product, denominator, " \
+                             "exponent arguments, distance from the Gram block 3, y argument 3, shift 1)"
+    pk = cde.cde_measure_peaks(ctx)
+    kp = 32
+    tf = 3 * kp * 2 * w.N * w.N / (kms * 1e-3) / 1e12
+    tpk = pk.mma_tf32_mac_per_clk_sm * pk.sm_count * 2 * 2070e6 / 1e12
+    roof["tensor_gram"] = {"achieved": tf, "peak": tpk, "unit": "TFLOP/s (TF32 mma.sync)", "frac": tf / tpk,
+                           "basis": "3 x 32 TF32 multiply-adds per pair (3xTF32 x_j.x_i) against the measured "
+                                    "mma.sync TF32 rate (cde_measure_peaks) x SMs x 2070 MHz"}
+    out = dict(workload="grid_N%d_d32_32x32" % w.N, value=pe / (kms * 1e-3), ms_per_step=kms,
+               host_ms_per_step=1e3 * float(np.median(host)), steps=args.steps, warmup=args.warmup,
+               roofline=roof, parity=par,
+               config={"workload": "grid_d32", "N": w.N, "d_x": 32, "G1": 32, "G2": 32,
+                       "data": "8 latent GMM factors x random 8x32 projection + N(0, 0.01), standardised"})
+    cde.cde_destroy_dataset(ctx, ds)
+    cde.cde_shutdown(ctx)
+    return out
+
+
+def run_grid32(args):
+    _line(**measure_grid32(args))
 
 
 def main():
@@ -921,7 +1092,7 @@ def main():
     ap.add_argument("--N", type=int, default=50000, help="dataset size (profiling runs use less)")
     ap.add_argument("--workload", default="scale",
                     choices=["scale", "tiny", "batch", "grad", "serve", "density", "select", "evaluate",
-                             "products", "dualtree"])
+                             "products", "dualtree", "grid32"])
     ap.add_argument("--select-N", type=int, default=10000)
     ap.add_argument("--select-rounds", type=int, default=8)
     ap.add_argument("--eval-N", type=int, default=0, help="0: the sizes of the paper's Table 1 sets")
@@ -936,7 +1107,12 @@ def main():
     ap.add_argument("--N-grad", type=int, default=200000)
     ap.add_argument("--ascent-steps", type=int, default=30)
     ap.add_argument("--serve-datasets", type=int, default=6)
-    ap.add_argument("--serve-N-max", type=int, default=100000)
+    ap.add_argument("--serve-N-max", type=int, default=500000)
+    ap.add_argument("--serve-loads", default="0.5,0.8,0.95", help="offered load fractions of capacity")
+    ap.add_argument("--N-grid32", type=int, default=200000)
+    ap.add_argument("--grid32-rows", type=int, default=16)
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default workload only: skip the secondary measurements")
     ap.add_argument("--serve-Q-max", type=int, default=100000)
     ap.add_argument("--serve-jobs", type=int, default=60)
     ap.add_argument("--serve-streams", type=int, default=4)
@@ -949,7 +1125,7 @@ def main():
             build()
         {"tiny": run_tiny, "batch": run_batch, "grad": run_grad, "serve": run_serve,
          "density": run_density, "select": run_select, "evaluate": run_evaluate,
-         "products": run_products, "dualtree": run_dualtree}[args.workload](args)
+         "products": run_products, "dualtree": run_dualtree, "grid32": run_grid32}[args.workload](args)
         return
     w = synth.scale_workload(N=args.N, seed=1 + 1000 * rank)
     if args.kernel == "epan":

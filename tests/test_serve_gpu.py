@@ -142,3 +142,47 @@ def test_admission_by_memory_limits_concurrency(ctx, datasets):
         srv.stop()
     for q, o in zip(xqs, outs):
         assert np.array_equal(cde.cde_density(ctx, ds, 0.3, 0.1, q, yg), o)
+
+
+def test_large_dataset_in_the_mix_and_served_results_match_oracle(ctx, datasets):
+    """A 300,000-point resident dataset next to the small ones: its density and
+    selection jobs (16 x 16 grid + 20 gradient steps) in the mix give the same
+    bits as the same jobs served alone; a served density job and a served
+    selection grid cell agree with the FP64 oracle (1e-4 of the query's
+    maximum; 1e-5 of sum_j |ell_j|)."""
+    from oracle import oracle
+    xb, yb = synth.gmm_sine(300000, 3, seed=31)
+    big = cde.cde_create_dataset(ctx, xb, yb, standardize=True)
+    h1g = synth.bandwidth_grid(0.05, 2.0, 16)
+    h2g = synth.bandwidth_grid(0.01, 1.0, 16)
+    jobs = [("d", big, (0.3, 0.1, synth.query_points(xb, 2000, seed=1), synth.y_grid(yb, 0.1, 256))),
+            ("s", big, (h1g, h2g, 20, 0.05))]
+    jobs += _jobs(datasets, 12, seed=5)
+    srv = Server(ctx, n_streams=4)
+    try:
+        mix = [_submit(srv, j) for j in jobs]
+        mix_vals = [_val(t) for t in mix]
+        st = srv.stats()
+        assert st["completed"] == len(jobs) and st["failed"] == 0 and st["peak_concurrent"] >= 2
+        alone_vals = [_val(_submit(srv, j)) for j in jobs[:2]]
+    finally:
+        srv.stop()
+    for a, b in zip(mix_vals[:2], alone_vals):
+        assert np.array_equal(a, b)
+    # the served density against the oracle on sampled queries
+    qs = np.random.default_rng(0).choice(2000, 8, replace=False)
+    _, _, (h1, h2, xq, yg) = jobs[0]
+    ref = oracle.density(xb, yb, h1, h2, xq[qs], yg, standardize_x=True)
+    f = mix_vals[0][qs]
+    assert np.max(np.abs(f - ref) / ref.max(1, keepdims=True)) <= 1e-4
+    # a served selection grid cell against the oracle's rows of a sample (score tolerance
+    # over the sampled rows is not the cell's: compare the cell with the library's grid,
+    # and the grid's sampled rows with the oracle)
+    Lgrid = mix_vals[1][4:].reshape(16, 16)
+    Lc, _ = cde.cde_loo_loglik(ctx, big, h1g, h2g)
+    assert np.array_equal(Lgrid, Lc)
+    rows = np.random.default_rng(1).choice(300000, 8, replace=False)
+    g = cde.cde_loo_rows(ctx, big, h1g, h2g, rows)
+    ref_rows, _ = oracle.loo_rows(xb, yb, h1g, h2g, rows=rows, standardize_x=True)
+    assert np.max(np.abs(g - ref_rows).sum(0) / np.abs(ref_rows).sum(0)) <= 1e-5
+    cde.cde_destroy_dataset(ctx, big)
