@@ -1010,7 +1010,8 @@ def measure_serve(args):
                unit="jobs/s", value=sat, steps=len(payload), warmup=1, ms_per_step=1e3 / sat,
                sequential={"jobs_per_s": cap, "p50_ms": 1e3 * float(np.percentile(seq_lat, 50)),
                            "p99_ms": 1e3 * float(np.percentile(seq_lat, 99)),
-                           "p50_density_ms": 1e3 * float(np.percentile(seq_den, 50)) if seq_den else None},
+                           "p50_density_ms": 1e3 * float(np.percentile(seq_den, 50)) if seq_den else None,
+                           "p99_density_ms": 1e3 * float(np.percentile(seq_den, 99)) if seq_den else None},
                speedup_vs_sequential=sat / cap, loads=loads,
                saturation={"jobs_per_s": sat, "p50_ms": sat_st["p50_ms"], "p99_ms": sat_st["p99_ms"],
                            "p50_density_ms": sat_st["p50_density_ms"], "p99_density_ms": sat_st["p99_density_ms"]},

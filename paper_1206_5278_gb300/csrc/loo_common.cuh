@@ -424,6 +424,16 @@ void fill_loo_args(LooArgs& a, const Dataset& D, const double* h1, int g1, const
 // units per tile of a grid block shape over n_rows rows (the tuned value when set; n_rows = 0:
 // the per-shape default without the small-grid reduction)
 int loo_units_per_tile(cde_ctx* ctx, int T1, int T2, int64_t n_rows);
+
+// (the launch plan behind the opaque LooChunked of cde_internal.h)
+struct LooChunked {
+    LooArgs a;
+    int T1, T2, G1, G2;
+    bool gram;
+    int n_tiles, cmax;
+    size_t part_bytes, fb_bytes, bytes;
+    int64_t N;
+};
 int loo_grid_ctas(cde_ctx* ctx, int T1, int T2);
 
 }  // namespace cde

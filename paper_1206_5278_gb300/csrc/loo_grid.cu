@@ -436,8 +436,9 @@ int loo_units_per_tile(cde_ctx* ctx, int T1, int T2, int64_t n_rows) {
     // tiles come from an atomic queue, and the last CTAs to finish decide the launch's time.
     // (N = 50,000 at 32 x 32: 70.3 ms with 8 rows per tile, 69.1 ms with 2.)
     if (ctx && n_rows > 0) {
+        const int c = ctx->tune_ctas[shape_index(T1)][shape_index(T2)];
         const int64_t units = (n_rows + JW - 1) / JW;
-        const int64_t want = 64LL * loo_grid_ctas(ctx, T1, T2);
+        const int64_t want = 64LL * (c > 0 ? c : 2) * ctx->sm_count;
         while (upt > 1 && (units + upt - 1) / upt < want) upt >>= 1;
     }
     return upt;
@@ -543,5 +544,82 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
 #ifdef CDE_CHECKS
 CDE_CHECK_READER(check_status_loo)
 #endif
+
+}  // namespace cde
+
+namespace cde {
+
+// --------------------------------------------------------------------------
+// One grid block launched in tile ranges (the request loop's selection jobs):
+// each range is its own launch, so other streams' kernels run between them.
+// Every tile writes its own partial slot whatever launch processes it, and
+// the final reduction is the one of loo_grid_enqueue, so the result is
+// bitwise the result of a single launch.
+// --------------------------------------------------------------------------
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+int loo_chunked_create(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, const double* h2, int G2,
+                       LooChunked** out) {
+    if (G1 > 32 || G2 > 32) return set_error(CDE_EINVAL, "loo_chunked_create: one grid block (<= 32 x 32) only");
+    auto* c = new LooChunked{};
+    c->T1 = loo_pad1(G1);
+    c->T2 = loo_pad2(G2);
+    c->G1 = G1;
+    c->G2 = G2;
+    LooArgs& a = c->a;
+    fill_loo_args(a, D, h1, G1, h2, G2, c->T1, c->T2);
+    const LooPlan pl = loo_plan(ctx, D, c->T1, c->T2, D.N);
+    a.rows = nullptr;
+    a.n_rows = D.N;
+    a.n_units = pl.n_units;
+    a.units_per_tile = pl.upt;
+    a.n_tiles = pl.n_tiles;
+    a.ell_rows = nullptr;
+    a.G1r = G1;
+    a.G2r = G2;
+    a.tile_base = 0;
+    c->gram = pl.gram;
+    c->n_tiles = pl.n_tiles;
+    c->cmax = pl.grid;
+    c->part_bytes = pl.part_bytes;
+    c->fb_bytes = pl.fb_bytes;
+    c->bytes = pl.bytes();
+    c->N = D.N;
+    *out = c;
+    return CDE_OK;
+}
+
+void loo_chunked_destroy(LooChunked* c) { delete c; }
+size_t loo_chunked_scratch_bytes(const LooChunked* c) { return c->bytes; }
+int loo_chunked_tiles(const LooChunked* c) { return c->n_tiles; }
+
+int loo_chunked_tiles_per_launch(const LooChunked* c, double pair_evals) {
+    const double rows = (double)c->a.units_per_tile *
+                        (c->gram ? loo_gram_rows_per_unit(c->T1, c->T2) : 1024 / (c->T1 * c->T2));
+    const double per_tile = rows * (double)c->N * c->T1 * c->T2;
+    double nt = std::ceil(pair_evals / per_tile);
+    if (nt < c->cmax) nt = c->cmax;
+    return nt > c->n_tiles ? c->n_tiles : (int)nt;
+}
+
+int loo_chunked_launch(LooChunked* c, void* scratch, int t0, int t1, cudaStream_t st) {
+    LooArgs a = c->a;
+    a.part = static_cast<double*>(scratch);
+    a.fb = reinterpret_cast<double*>(static_cast<char*>(scratch) + c->part_bytes);
+    a.work = reinterpret_cast<int*>(static_cast<char*>(scratch) + c->part_bytes + c->fb_bytes);
+    a.n_tiles = t1;   // tiles t0 .. t1-1: the queue starts at t0 and stops at t1
+    k_set_int<<<1, 1, 0, st>>>(a.work, t0);
+    CDE_CUDA(cudaGetLastError());
+    const int grid = (t1 - t0) < c->cmax ? (t1 - t0) : c->cmax;
+    return c->gram ? launch_loo_gram(c->T1, c->T2, a, grid, st) : launch_loo_tile_kernel(c->T1, c->T2, a, grid, st);
+}
+
+int loo_chunked_final(const LooChunked* c, const void* scratch, double* d_Lc, double* d_Le, cudaStream_t st) {
+    const int GG = c->T1 * c->T2;
+    k_loo_final<<<(GG * 32 + 255) / 256, 256, 0, st>>>(static_cast<const double*>(scratch), c->n_tiles, GG, c->T2,
+                                                        c->G1, c->G2, c->G2, (double)c->N, d_Lc, d_Le);
+    CDE_CUDA(cudaGetLastError());
+    return CDE_OK;
+}
 
 }  // namespace cde

@@ -4,10 +4,14 @@
 // bandwidth-selection jobs (LOO grid search, then Adam ascent on
 // (ln h1, ln h2) driven by the adjoint kernel).  One scheduler thread admits
 // queued jobs while a stream slot and the job-memory budget allow (a job that
-// does not fit waits; smaller later jobs may pass it), enqueues their kernels
+// does not fit waits; smaller later jobs may pass it; selection jobs leave the
+// last free slot to density jobs, run their grid as ~10 ms launches over tile
+// ranges, and run on low-priority streams, so density queries are not held up
+// by long selections), enqueues their kernels
 // on the slot's stream so admitted jobs overlap on the device, and polls
-// completion events.  A selection job is a small state machine: every
-// gradient step is one enqueue plus a 3-double copy; the host update between
+// completion events.  A selection job is a small state machine: every range
+// of its grid's tiles and every gradient step is one enqueue (the grid's tiles
+// write fixed partial slots, so its result is bitwise that of one launch); the host update between
 // steps happens when its event completes, so the device keeps running other
 // jobs meanwhile.  Every kernel is deterministic and partitions work by the
 // job's own sizes only, so a job's result is the same alone and in the mix.
@@ -28,6 +32,10 @@ namespace cde {
 
 using Clock = std::chrono::steady_clock;
 
+// pair evaluations (N^2 G1 G2 units) per launch of a selection job's grid: about
+// 10 ms of the grid kernel, the longest a density job waits behind it
+constexpr double kSelChunk = 2.5e11;
+
 struct Job {
     int64_t ticket = 0;
     cde_request req{};
@@ -39,6 +47,12 @@ struct Job {
     // running state
     int slot = -1;
     int phase = 0;          // selection: 0 grid, 1.. gradient steps
+    // selection grid in tile ranges (one launch per scheduling step)
+    LooChunked* gc = nullptr;
+    void* d_grid = nullptr; // the grid's partials and counters
+    bool grid_init = false;
+    int t_next = 0;         // first tile of the next range
+    bool grid_final = false;  // the final reduction has been enqueued
     cudaEvent_t ev = nullptr;
     // device / pinned buffers
     float* d_xq = nullptr;
@@ -62,10 +76,12 @@ struct Server {
     std::deque<std::shared_ptr<Job>> queue;
     std::map<int64_t, std::shared_ptr<Job>> jobs;   // all not-yet-forgotten tickets
     std::vector<std::shared_ptr<Job>> running;
-    std::vector<cudaStream_t> streams;
+    std::vector<cudaStream_t> streams;      // per slot: selection jobs (lowest priority)
+    std::vector<cudaStream_t> streams_hi;   // per slot: density jobs (highest priority)
     std::vector<int> slot_busy;
     std::vector<char*> pin;          // per-slot pinned staging (grows, reused)
     std::vector<size_t> pin_cap;
+    std::vector<char*> pin_retired;  // outgrown staging, freed at stop (cudaFreeHost waits for the device)
     size_t mem_used = 0, mem_budget = 0;
     int64_t next_ticket = 1;
     bool stop = false;
@@ -98,13 +114,24 @@ static size_t job_mem(const Job& J, int sm_count) {
     return tiles * 2 * 1024 * 8 + (size_t)J.D->N * (6 * 4 * 16 + 24) + 65536;
 }
 
+// A job's stream: density jobs run on their slot's high-priority stream, so the
+// device dispatches their blocks ahead of the waiting blocks of selection kernels.
+static cudaStream_t job_stream(const Server& S, const Job& J) {
+    if (J.slot < 0) return nullptr;
+    return J.req.kind == CDE_REQ_DENSITY ? S.streams_hi[J.slot] : S.streams[J.slot];
+}
+
 static void release(Server& S, Job& J) {
     if (J.ev) cudaEventDestroy(J.ev);
     J.ev = nullptr;
-    cudaStream_t st = J.slot >= 0 ? S.streams[J.slot] : nullptr;
+    cudaStream_t st = job_stream(S, J);
     if (J.d_xq) cudaFreeAsync(J.d_xq, st);
     if (J.d_f) cudaFreeAsync(J.d_f, st);
     if (J.d_small) cudaFreeAsync(J.d_small, st);
+    if (J.d_grid) cudaFreeAsync(J.d_grid, st);
+    J.d_grid = nullptr;
+    if (J.gc) loo_chunked_destroy(J.gc);
+    J.gc = nullptr;
     J.d_xq = J.d_yg = J.d_f = nullptr;
     J.d_small = nullptr;
     J.h_f = J.h_in = nullptr;
@@ -113,10 +140,12 @@ static void release(Server& S, Job& J) {
 
 static int slot_pinned(Server& S, int slot, size_t bytes, char** out) {
     if (S.pin_cap[slot] < bytes) {
-        if (S.pin[slot]) cudaFreeHost(S.pin[slot]);
+        // the outgrown buffer is only retired here: freeing pinned memory waits for
+        // the whole device, which would stall every job behind a long selection kernel
+        if (S.pin[slot]) S.pin_retired.push_back(S.pin[slot]);
         S.pin[slot] = nullptr;
         S.pin_cap[slot] = 0;
-        const size_t cap = std::max<size_t>(bytes, 1 << 20);
+        const size_t cap = std::max<size_t>(bytes + bytes / 2, 1 << 20);
         CDE_CUDA(cudaMallocHost((void**)&S.pin[slot], cap));
         S.pin_cap[slot] = cap;
     }
@@ -126,7 +155,7 @@ static int slot_pinned(Server& S, int slot, size_t bytes, char** out) {
 
 // Enqueue the next piece of work of a running job on its stream and record its event.
 static int advance(Server& S, Job& J) {
-    cudaStream_t st = S.streams[J.slot];
+    cudaStream_t st = job_stream(S, J);
     const cde_request& r = J.req;
     const Dataset& D = *J.D;
     if (r.kind == CDE_REQ_DENSITY) {
@@ -147,15 +176,41 @@ static int advance(Server& S, Job& J) {
         CDE_CUDA(cudaMemcpyAsync(J.h_f, J.d_f, nf * sizeof(float), cudaMemcpyDeviceToHost, st));
     } else if (J.phase == 0) {
         const size_t g = (size_t)r.G1 * r.G2;
-        char* pb = nullptr;
-        int prc = slot_pinned(S, J.slot, (g + 4) * sizeof(double), &pb);
-        if (prc != CDE_OK) return prc;
-        J.h_small = reinterpret_cast<double*>(pb);
-        CDE_CUDA(cudaMallocAsync((void**)&J.d_small, (g + 4) * sizeof(double), st));
-        int rc = loo_grid_enqueue(S.ctx, D, r.h1_grid, r.G1, r.h2_grid, r.G2, nullptr, 0, J.d_small,
-                                  nullptr, nullptr, st);
-        if (rc != CDE_OK) return rc;
-        CDE_CUDA(cudaMemcpyAsync(J.h_small, J.d_small, g * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (!J.grid_init) {
+            char* pb = nullptr;
+            int prc = slot_pinned(S, J.slot, (g + 4) * sizeof(double), &pb);
+            if (prc != CDE_OK) return prc;
+            J.h_small = reinterpret_cast<double*>(pb);
+            CDE_CUDA(cudaMallocAsync((void**)&J.d_small, (g + 4) * sizeof(double), st));
+            J.grid_init = true;
+            if (r.G1 <= 32 && r.G2 <= 32) {
+                int rc = loo_chunked_create(S.ctx, D, r.h1_grid, r.G1, r.h2_grid, r.G2, &J.gc);
+                if (rc != CDE_OK) return rc;
+                CDE_CUDA(cudaMallocAsync(&J.d_grid, loo_chunked_scratch_bytes(J.gc), st));
+            } else {
+                // wider grids: one enqueue of all its blocks
+                int rc = loo_grid_enqueue(S.ctx, D, r.h1_grid, r.G1, r.h2_grid, r.G2, nullptr, 0, J.d_small,
+                                          nullptr, nullptr, st);
+                if (rc != CDE_OK) return rc;
+                J.grid_final = true;
+            }
+        }
+        if (!J.grid_final) {
+            // the next range of tiles: about kSelChunk pair evaluations, so that density
+            // jobs queued meanwhile run between two launches of a long grid
+            const int nt = loo_chunked_tiles_per_launch(J.gc, kSelChunk);
+            const int t1 = std::min(loo_chunked_tiles(J.gc), J.t_next + nt);
+            int rc = loo_chunked_launch(J.gc, J.d_grid, J.t_next, t1, st);
+            if (rc != CDE_OK) return rc;
+            J.t_next = t1;
+            if (t1 == loo_chunked_tiles(J.gc)) {
+                rc = loo_chunked_final(J.gc, J.d_grid, J.d_small, nullptr, st);
+                if (rc != CDE_OK) return rc;
+                J.grid_final = true;
+            }
+        }
+        if (J.grid_final)
+            CDE_CUDA(cudaMemcpyAsync(J.h_small, J.d_small, g * sizeof(double), cudaMemcpyDeviceToHost, st));
     } else {
         const size_t g = (size_t)r.G1 * r.G2;
         int rc = loo_grad_enqueue(S.ctx, D, std::exp(J.th[0]), std::exp(J.th[1]), J.d_small + g, st, nullptr);
@@ -178,6 +233,7 @@ static bool on_event(Server& S, Job& J) {
     }
     const size_t g = (size_t)r.G1 * r.G2;
     const double N = (double)J.D->N;
+    if (J.phase == 0 && !J.grid_final) return false;   // more ranges of the grid to launch
     if (J.phase == 0) {
         int bk = 0;
         for (size_t c = 1; c < g; ++c)
@@ -279,16 +335,21 @@ static void loop(Server* Sp) {
                 ++k;
             }
         }
-        // 2) admissions (by free slot and job memory)
+        // 2) admissions (by free slot and job memory); the last free slot is kept
+        //    for density jobs, so that short queries never queue behind selections
         for (auto it = S.queue.begin(); it != S.queue.end();) {
-            int slot = -1;
+            int slot = -1, n_free = 0;
             for (size_t s = 0; s < S.slot_busy.size(); ++s)
                 if (!S.slot_busy[s]) {
-                    slot = (int)s;
-                    break;
+                    if (slot < 0) slot = (int)s;
+                    ++n_free;
                 }
             if (slot < 0) break;
             auto J = *it;
+            if (J->req.kind != CDE_REQ_DENSITY && n_free == 1 && S.slot_busy.size() > 1) {
+                ++it;  // a density job behind it may take the slot
+                continue;
+            }
             if (S.mem_used + J->mem > S.mem_budget && !S.running.empty()) {
                 ++it;  // does not fit now; a smaller job behind it may
                 continue;
@@ -342,13 +403,18 @@ int cde_server_start(cde_ctx* ctx, const cde_server_config* cfg) {
     const size_t avail = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
     S->mem_budget = S->cfg.job_mem_budget ? S->cfg.job_mem_budget : avail;
     cudaError_t e = cudaSetDevice(ctx->device);
+    int prio_lo = 0, prio_hi = 0;   // numerically: least and greatest priority
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     for (int s = 0; s < S->cfg.n_streams && e == cudaSuccess; ++s) {
-        cudaStream_t st;
-        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        cudaStream_t st = nullptr, sh = nullptr;
+        e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio_lo);
         if (e == cudaSuccess) S->streams.push_back(st);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sh, cudaStreamNonBlocking, prio_hi);
+        if (e == cudaSuccess) S->streams_hi.push_back(sh);
     }
     if (e != cudaSuccess) {
         for (auto st : S->streams) cudaStreamDestroy(st);
+        for (auto st : S->streams_hi) cudaStreamDestroy(st);
         delete S;
         return cuda_error(e, "cde_server_start");
     }
@@ -375,8 +441,13 @@ void cde_server_stop_internal(cde_ctx* ctx) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
+    for (auto st : S->streams_hi) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
     for (auto p : S->pin)
         if (p) cudaFreeHost(p);
+    for (auto p : S->pin_retired) cudaFreeHost(p);
     ctx->server = nullptr;
     delete S;
 }
