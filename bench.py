@@ -441,17 +441,23 @@ def run_tiny(args):
 def measure_batch(args):
     """256 datasets (N log-uniform [500, 20000], d in {1,2,4,8}, 16x16 grids):
     one graph-captured persistent launch vs one launch per dataset; parity of
-    the two smallest datasets' grids against the oracle."""
+    the two smallest datasets' grids against the oracle.  The batched call
+    tunes the 16x16 shape class on its first call (the library's default); the
+    tuned configuration is reported, and the batch is also timed with the
+    untuned defaults."""
     from oracle import oracle
     from paper_1206_5278_gb300 import cde, synth
     ws = synth.batch_workloads(n_datasets=args.n_datasets)
     ctx = cde.cde_init(0)
+    cde.cde_autotune_enable(ctx, not args.no_autotune)
     dss = [cde.cde_create_dataset(ctx, w.x, w.y, standardize=w.standardize) for w in ws]
     h1s, h2s = [w.h1 for w in ws], [w.h2 for w in ws]
-    tune = None
-    if args.autotune:
-        big = int(np.argmax([w.N for w in ws]))
-        tune = cde.cde_autotune(ctx, dss[big], ws[big].h1, ws[big].h2)
+    t0 = time.perf_counter()
+    cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s)
+    first_ms = 1e3 * (time.perf_counter() - t0)
+    u, c, tuned = cde.cde_tuning_get_ex(ctx, 16, 16)
+    tune = {"tuned": tuned, "units_per_tile": u, "rows_per_tile": u * 4, "ctas_per_sm": c,
+            "first_call_ms": first_ms, "note": "the first call tunes the shape class and captures the graph"}
     for _ in range(max(1, args.warmup)):
         cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s)
     tb = _timed(lambda: cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s), args.steps)
@@ -474,6 +480,18 @@ def measure_batch(args):
         ell, _ = oracle.loo_rows(w.x, w.y, w.h1, w.h2, standardize_x=w.standardize)
         worst = max(worst, float(np.max(np.abs(Lc[b] - ell.sum(0)) / np.abs(ell).sum(0))))
     pe = sum(w.N * w.N * w.h1.size * w.h2.size for w in ws)
+    if tuned:
+        # the same batch on the untuned defaults, for comparison
+        with tempfile.TemporaryDirectory() as td:
+            keep = os.path.join(td, "tuning.txt")
+            cde.cde_tuning_save(ctx, keep)
+            cde.cde_autotune_enable(ctx, False)
+            cde.cde_tuning_set(ctx, 16, 16, 0, 0)
+            cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s)
+            tu = _timed(lambda: cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s), max(2, args.steps // 2))
+            cde.cde_tuning_load(ctx, keep)
+        tune["untuned_value"] = pe / float(np.median(tu))
+        tune["tuned_over_untuned"] = float(np.median(tu) / np.median(tb))
     out = dict(workload="batch_%d_datasets_16x16" % len(ws), value=pe / float(np.median(tb)),
                steps=len(tb), warmup=args.warmup, ms_per_step=1e3 * float(np.median(tb)),
                latency_ms={"p50": 1e3 * float(np.percentile(tb, 50)), "p99": 1e3 * float(np.percentile(tb, 99))},
@@ -1104,7 +1122,8 @@ def main():
     ap.add_argument("--dens-N", type=int, default=100000)
     ap.add_argument("--dens-d", type=int, default=4)
     ap.add_argument("--n-datasets", type=int, default=256)
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batch workload: run the 16x16 class on the untuned defaults")
     ap.add_argument("--N-grad", type=int, default=200000)
     ap.add_argument("--ascent-steps", type=int, default=30)
     ap.add_argument("--serve-datasets", type=int, default=6)

@@ -265,26 +265,40 @@ int cde_loo_loglik_batch(cde_ctx *ctx, int n, const cde_dataset *ds, const doubl
                          double *const *L_cond_out, double *const *L_eq3_out, void *stream);
 
 /*
- * Autotuner of the LOO launch for one grid shape (grids are padded to 8, 16 or
- * 32 per axis): times units-per-tile x resident-CTAs-per-SM candidates with
- * the single-dataset launch on dataset `ds` and keeps the fastest in the
- * context.  Both cde_loo_loglik and cde_loo_loglik_batch use the kept values,
- * so their results stay bitwise identical to each other.  Outputs may be NULL.
+ * Autotuner of the LOO launch for one grid shape class (grids are padded to
+ * 16 or 32 in G1 and 8, 16 or 32 in G2).  It times every tile configuration
+ * -- units per tile (rows per tile = units x 1024 / (T1 T2); the d >= 16
+ * kernel's units are fixed) and resident CTAs per SM (1 or 2) -- with the
+ * single-dataset launch on dataset `ds`, keeps the fastest in the context and
+ * marks the class tuned.  cde_loo_loglik, the chunked and no-alloc launches
+ * and cde_loo_loglik_batch all read the kept configuration, so their results
+ * stay bitwise identical to each other.  Outputs may be NULL.
+ *
+ * cde_loo_loglik_batch tunes, by default, every shape class of its batch that
+ * is not yet tuned (on the class's largest dataset, before building the
+ * batch's graph) and then writes the tuning cache named by CDE_TUNING_CACHE,
+ * if set.  cde_autotune_enable(ctx, 0), or CDE_AUTOTUNE=0 in the environment
+ * at cde_init, turns this off (untuned classes then run the defaults).
  */
 int cde_autotune(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const double *h2, int G2,
                  int *units_per_tile, int *ctas_per_sm, double *best_ms);
+int cde_autotune_enable(cde_ctx *ctx, int on);
 /* Read / set the tile parameters for the shape of a G1 x G2 grid (0 = default:
  * 8 rows per tile, halved while a dataset's grid would give fewer than 64 tiles
- * per resident CTA; cde_tuning_get reports the 8-row value then). */
+ * per resident CTA; cde_tuning_get reports the 8-row value then).  Setting any
+ * non-zero value marks the class tuned; setting both to 0 returns it to its
+ * defaults and to untuned.  cde_tuning_get_ex also reports the tuned flag. */
 int cde_tuning_get(cde_ctx *ctx, int G1, int G2, int *units_per_tile, int *ctas_per_sm);
+int cde_tuning_get_ex(cde_ctx *ctx, int G1, int G2, int *units_per_tile, int *ctas_per_sm, int *tuned);
 int cde_tuning_set(cde_ctx *ctx, int G1, int G2, int units_per_tile, int ctas_per_sm);
 /*
  * Tuning cache on disk: cde_tuning_save writes all shape classes' parameters
- * with the device's name, compute capability and SM count (atomically, via a
- * temporary file and rename); cde_tuning_load applies a file written for the
- * same device (CDE_EINVAL for another device or a malformed file,
- * CDE_ENOTFOUND when it cannot be read).  cde_init loads the file named by
- * the environment variable CDE_TUNING_CACHE when it exists and matches.
+ * (units per tile, CTAs per SM, tuned flag) with the device's name, compute
+ * capability and SM count (atomically, via a temporary file and rename);
+ * cde_tuning_load applies a file written for the same device (CDE_EINVAL for
+ * another device, another format version or a malformed file, CDE_ENOTFOUND
+ * when it cannot be read).  cde_init loads the file named by the environment
+ * variable CDE_TUNING_CACHE when it exists and matches.
  */
 int cde_tuning_save(cde_ctx *ctx, const char *path);
 int cde_tuning_load(cde_ctx *ctx, const char *path);

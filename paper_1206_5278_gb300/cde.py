@@ -44,6 +44,7 @@ EXPORTED = [
     "cde_loo_loglik_noalloc", "cde_dataset_kernel", "cde_select_random", "cde_reference_rule",
     "cde_cond_stats", "cde_cond_interval", "cde_tuning_save", "cde_tuning_load", "cde_check_status",
     "cde_dataset_nn", "cde_dataset_nn_other", "cde_timing_enable", "cde_timing_last", "cde_selftest_wait",
+    "cde_tuning_get_ex", "cde_autotune_enable",
 ]
 
 
@@ -133,6 +134,9 @@ def lib():
                             ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cde_tuning_set": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
                            ctypes.c_int),
+        "cde_tuning_get_ex": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cde_autotune_enable": ([_vp, ctypes.c_int], ctypes.c_int),
         "cde_loo_loglik_noalloc": ([_vp, _i64, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp],
                                    ctypes.c_int),
         "cde_dataset_kernel": ([_vp, _i64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -478,6 +482,18 @@ def cde_tuning_get(ctx, G1: int, G2: int):
     u, c = ctypes.c_int(), ctypes.c_int()
     _check(lib().cde_tuning_get(ctx, int(G1), int(G2), ctypes.byref(u), ctypes.byref(c)))
     return u.value, c.value
+
+
+def cde_tuning_get_ex(ctx, G1: int, G2: int):
+    """(units_per_tile, ctas_per_sm, tuned) of the G1 x G2 shape class."""
+    u, c, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().cde_tuning_get_ex(ctx, int(G1), int(G2), ctypes.byref(u), ctypes.byref(c), ctypes.byref(t)))
+    return u.value, c.value, bool(t.value)
+
+
+def cde_autotune_enable(ctx, on: bool):
+    """Whether cde_loo_loglik_batch tunes the untuned shape classes it meets."""
+    _check(lib().cde_autotune_enable(ctx, 1 if on else 0))
 
 
 def cde_check_status(ctx):

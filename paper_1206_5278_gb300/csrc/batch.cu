@@ -351,18 +351,21 @@ void batch_plan_free(cde_ctx* ctx) {
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner: for one grid shape, time the single-dataset launch on a
-// representative dataset over units-per-tile x resident-CTAs candidates and
-// keep the fastest in the context (used by both launch paths).
+// Autotuner: for one grid shape class, time the single-dataset launch on a
+// representative dataset over every tile configuration -- units per tile and
+// resident CTAs per SM -- and keep the fastest in the context.  Both launch
+// paths read the kept configuration, so their results stay bitwise identical.
 // ---------------------------------------------------------------------------
+static int shape_class(int T) { return T <= 8 ? 0 : T <= 16 ? 1 : 2; }
+
 int autotune_shape(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, const double* h2, int G2,
                    int* best_upt, int* best_ctas, double* best_ms) {
     const int T1 = loo_pad1(G1), T2 = loo_pad2(G2);
-    const int a = T1 <= 8 ? 0 : T1 <= 16 ? 1 : 2, b = T2 <= 8 ? 0 : T2 <= 16 ? 1 : 2;
+    const int a = shape_class(T1), b = shape_class(T2);
     const int JW = 1024 / (T1 * T2);
     std::vector<int> upts;
     for (int u : {1, 2, 4, 8, 16})
-        if (u * JW >= 4 && u * JW <= 64) upts.push_back(u);
+        if (u * JW >= 2 && u * JW <= 64) upts.push_back(u);
     cudaStream_t st = ctx->stream;
     double* dout = nullptr;
     CDE_CUDA(cudaMalloc((void**)&dout, 2 * sizeof(double) * G1 * G2));
@@ -374,26 +377,27 @@ int autotune_shape(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, con
     const int save_u = ctx->tune_upt[a][b], save_c = ctx->tune_ctas[a][b];
     int rc = CDE_OK;
     for (int u : upts)
-        for (int c : {1, 2}) {
-            ctx->tune_upt[a][b] = u;
-            ctx->tune_ctas[a][b] = c;
-            float tot = 0;
-            for (int rep = 0; rep < 3 && rc == CDE_OK; ++rep) {
-                cudaEventRecord(e0, st);
-                rc = loo_grid_enqueue(ctx, D, h1, G1, h2, G2, nullptr, 0, dout, dout + G1 * G2, nullptr, st);
-                cudaEventRecord(e1, st);
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) tot += ms;
+            for (int c : {1, 2}) {
+                ctx->tune_upt[a][b] = u;
+                ctx->tune_ctas[a][b] = c;
+                // one untimed launch, then the fastest of three
+                float tmin = 1e30f;
+                for (int rep = 0; rep < 4 && rc == CDE_OK; ++rep) {
+                    cudaEventRecord(e0, st);
+                    rc = loo_grid_enqueue(ctx, D, h1, G1, h2, G2, nullptr, 0, dout, dout + G1 * G2, nullptr, st);
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess && rc == CDE_OK) rc = cuda_error(cudaGetLastError(), "autotune");
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) tmin = std::min(tmin, ms);
+                }
+                if (rc != CDE_OK) break;
+                if (tmin < best) {
+                    best = tmin;
+                    bu = u;
+                    bc = c;
+                }
             }
-            if (rc != CDE_OK) break;
-            if (tot / 2 < best) {
-                best = tot / 2;
-                bu = u;
-                bc = c;
-            }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(dout);
@@ -404,9 +408,38 @@ int autotune_shape(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, con
     }
     ctx->tune_upt[a][b] = bu;
     ctx->tune_ctas[a][b] = bc;
+    ctx->tuned[a][b] = true;
     if (best_upt) *best_upt = bu;
     if (best_ctas) *best_ctas = bc;
     if (best_ms) *best_ms = best;
+    return CDE_OK;
+}
+
+// Tune every shape class of the batch that has no configuration yet, each on
+// its largest dataset, and store the result in the tuning cache named by
+// CDE_TUNING_CACHE when there is one.
+static int autotune_batch_shapes(cde_ctx* ctx, const std::vector<BatchItem>& items) {
+    if (!ctx->autotune_batch) return CDE_OK;
+    int pick[3][3];
+    for (auto& r : pick)
+        for (int& v : r) v = -1;
+    for (int i = 0; i < (int)items.size(); ++i) {
+        const int a = shape_class(loo_pad1(items[i].G1)), b = shape_class(loo_pad2(items[i].G2));
+        if (ctx->tuned[a][b]) continue;
+        if (pick[a][b] < 0 || items[i].D->N > items[pick[a][b]].D->N) pick[a][b] = i;
+    }
+    bool any = false;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            if (pick[a][b] < 0) continue;
+            const BatchItem& it = items[pick[a][b]];
+            const int rc = autotune_shape(ctx, *it.D, it.h1, it.G1, it.h2, it.G2, nullptr, nullptr, nullptr);
+            if (rc != CDE_OK) return rc;
+            any = true;
+        }
+    if (any)
+        if (const char* tc = getenv("CDE_TUNING_CACHE"))
+            if (cde_tuning_save(ctx, tc) != CDE_OK) set_error(CDE_OK, "");
     return CDE_OK;
 }
 
@@ -445,6 +478,8 @@ extern "C" int cde_loo_loglik_batch(cde_ctx* ctx, int n, const cde_dataset* ds, 
     }
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     CDE_CUDA(cudaSetDevice(ctx->device));
+    const int rc = autotune_batch_shapes(ctx, items);
+    if (rc != CDE_OK) return rc;
     return loo_batch_run(ctx, items, Lc, Le, pick_stream(ctx, stream));
 }
 
@@ -460,17 +495,30 @@ extern "C" int cde_autotune(cde_ctx* ctx, cde_dataset ds, const double* h1, int 
     return autotune_shape(ctx, *D, h1, G1, h2, G2, units_per_tile, ctas_per_sm, best_ms);
 }
 
-extern "C" int cde_tuning_get(cde_ctx* ctx, int G1, int G2, int* units_per_tile, int* ctas_per_sm) {
+extern "C" int cde_tuning_get_ex(cde_ctx* ctx, int G1, int G2, int* units_per_tile, int* ctas_per_sm, int* tuned) {
     if (!ctx || G1 < 1 || G1 > 32 || G2 < 1 || G2 > 32) return set_error(CDE_EINVAL, "cde_tuning_get: bad arguments");
     const int T1 = loo_pad1(G1), T2 = loo_pad2(G2);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     if (units_per_tile) *units_per_tile = loo_units_per_tile(ctx, T1, T2, 0);
     if (ctas_per_sm) *ctas_per_sm = loo_grid_ctas(ctx, T1, T2) / ctx->sm_count;
+    if (tuned) *tuned = ctx->tuned[shape_class(T1)][shape_class(T2)] ? 1 : 0;
+    return CDE_OK;
+}
+
+extern "C" int cde_tuning_get(cde_ctx* ctx, int G1, int G2, int* units_per_tile, int* ctas_per_sm) {
+    return cde_tuning_get_ex(ctx, G1, G2, units_per_tile, ctas_per_sm, nullptr);
+}
+
+extern "C" int cde_autotune_enable(cde_ctx* ctx, int on) {
+    if (!ctx) return set_error(CDE_EINVAL, "cde_autotune_enable: null context");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->autotune_batch = on != 0;
     return CDE_OK;
 }
 
 // Tuning cache file: a header line with the device it was tuned on, then one
-// line "a b units_per_tile ctas_per_sm" per shape class (a, b in 0..2 for
-// padded sizes 8|16|32 of G1 and G2).
+// line "a b units_per_tile ctas_per_sm tuned" per shape class (a, b in 0..2
+// for padded sizes 8|16|32 of G1 and G2).
 static std::string tuning_device_key(cde_ctx* ctx) {
     cudaDeviceProp p;
     if (cudaGetDeviceProperties(&p, ctx->device) != cudaSuccess) return "unknown";
@@ -487,9 +535,10 @@ extern "C" int cde_tuning_save(cde_ctx* ctx, const char* path) {
     const std::string tmp = std::string(path) + ".tmp";
     FILE* f = fopen(tmp.c_str(), "w");
     if (!f) return set_error(CDE_EINVAL, std::string("cde_tuning_save: cannot write ") + path);
-    fprintf(f, "cde-tuning 1 %s\n", tuning_device_key(ctx).c_str());
+    fprintf(f, "cde-tuning 2 %s\n", tuning_device_key(ctx).c_str());
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) fprintf(f, "%d %d %d %d\n", a, b, ctx->tune_upt[a][b], ctx->tune_ctas[a][b]);
+        for (int b = 0; b < 3; ++b)
+            fprintf(f, "%d %d %d %d %d\n", a, b, ctx->tune_upt[a][b], ctx->tune_ctas[a][b], ctx->tuned[a][b] ? 1 : 0);
     const bool ok = fclose(f) == 0 && rename(tmp.c_str(), path) == 0;
     if (!ok) return set_error(CDE_EINVAL, std::string("cde_tuning_save: cannot write ") + path);
     return CDE_OK;
@@ -500,26 +549,27 @@ extern "C" int cde_tuning_load(cde_ctx* ctx, const char* path) {
     FILE* f = fopen(path, "r");
     if (!f) return set_error(CDE_ENOTFOUND, std::string("cde_tuning_load: cannot read ") + path);
     char line[512];
-    int upt[3][3], ctas[3][3], seen = 0;
+    int upt[3][3], ctas[3][3], tuned[3][3], seen = 0;
     bool ok = fgets(line, sizeof(line), f) != nullptr;
     if (ok) {
         std::string h(line);
         while (!h.empty() && (h.back() == '\n' || h.back() == '\r')) h.pop_back();
-        ok = h == "cde-tuning 1 " + tuning_device_key(ctx);
+        ok = h == "cde-tuning 2 " + tuning_device_key(ctx);
         if (!ok) {
             fclose(f);
             return set_error(CDE_EINVAL, "cde_tuning_load: file was tuned on another device or version");
         }
     }
-    int a, b, u, c;
+    int a, b, u, c, t;
     while (ok && fgets(line, sizeof(line), f)) {
-        if (sscanf(line, "%d %d %d %d", &a, &b, &u, &c) != 4 || a < 0 || a > 2 || b < 0 || b > 2 || u < 0 ||
-            u > 64 || c < 0 || c > 2 || (seen & (1 << (3 * a + b)))) {
+        if (sscanf(line, "%d %d %d %d %d", &a, &b, &u, &c, &t) != 5 || a < 0 || a > 2 || b < 0 || b > 2 || u < 0 ||
+            u > 64 || c < 0 || c > 2 || t < 0 || t > 1 || (seen & (1 << (3 * a + b)))) {
             ok = false;
             break;
         }
         upt[a][b] = u;
         ctas[a][b] = c;
+        tuned[a][b] = t;
         seen |= 1 << (3 * a + b);
     }
     fclose(f);
@@ -529,6 +579,7 @@ extern "C" int cde_tuning_load(cde_ctx* ctx, const char* path) {
         for (b = 0; b < 3; ++b) {
             ctx->tune_upt[a][b] = upt[a][b];
             ctx->tune_ctas[a][b] = ctas[a][b];
+            ctx->tuned[a][b] = tuned[a][b] != 0;
         }
     return CDE_OK;
 }
@@ -538,10 +589,11 @@ extern "C" int cde_tuning_set(cde_ctx* ctx, int G1, int G2, int units_per_tile, 
         ctas_per_sm < 0 || ctas_per_sm > 2)
         return set_error(CDE_EINVAL, "cde_tuning_set: bad arguments");
     // the classes the kernels read: G1 padded to 16 | 32, G2 to 8 | 16 | 32
-    const int T1 = loo_pad1(G1), T2 = loo_pad2(G2);
-    const int a = T1 <= 8 ? 0 : T1 <= 16 ? 1 : 2, b = T2 <= 8 ? 0 : T2 <= 16 ? 1 : 2;
+    const int a = shape_class(loo_pad1(G1)), b = shape_class(loo_pad2(G2));
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     ctx->tune_upt[a][b] = units_per_tile;
     ctx->tune_ctas[a][b] = ctas_per_sm;
+    // an explicit configuration counts as tuned; both defaults make the class untuned again
+    ctx->tuned[a][b] = units_per_tile || ctas_per_sm;
     return CDE_OK;
 }

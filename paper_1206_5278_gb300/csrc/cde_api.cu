@@ -128,6 +128,8 @@ int cde_init(cde_ctx** out, int device, size_t budget) {
         delete ctx;
         return cuda_error(e, "cde_init");
     }
+    // CDE_AUTOTUNE=0: the batched call runs untuned shape classes with the defaults
+    if (const char* at = getenv("CDE_AUTOTUNE")) ctx->autotune_batch = strcmp(at, "0") != 0;
     // a tuning cache named by the environment is applied when it matches this device
     if (const char* tc = getenv("CDE_TUNING_CACHE")) {
         if (cde_tuning_load(ctx, tc) != CDE_OK) set_error(CDE_OK, "");

@@ -113,6 +113,8 @@ struct cde_ctx {
 
     int tune_upt[3][3] = {};  // autotuned units per tile by grid shape (8/16/32), 0 = default
     int tune_ctas[3][3] = {}; // autotuned resident CTAs per SM, 0 = default (2)
+    bool tuned[3][3] = {};    // shape class tuned (autotuner, cde_tuning_set*, cde_tuning_load)
+    bool autotune_batch = true;  // cde_loo_loglik_batch tunes the untuned shape classes it meets
     void* batch_plan = nullptr;  // cached batched launch (graph), batch.cu
     // workspace of the synchronous host-output calls (they hold `mu` until their
     // stream has drained, so one call uses it at a time): device scratch and a

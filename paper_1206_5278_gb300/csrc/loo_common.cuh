@@ -117,44 +117,66 @@ constexpr float kFbEx2Fix = 7.39e-8f;
 // CTA).  For a cell (row j, k, l) let X_i = dx2_i - m_x,j, Y_i = dy2_i - m_y,j and
 // e_i = a1_k X_i + a2_l Y_i.  Then At = sum_i 2^{-e_i} = 2^{-e_*} S with
 // S = sum_i 2^{-(a1_k (dx2_i - dx2_*) + a2_l (dy2_i - dy2_*))} for the minimiser
-// i* (its term is exactly 1), and log2 At = -e_* + log2 S.  The flagged cells
-// of a row are processed together in two passes over the points:
+// i* (its term is exactly 1), and log2 At = -e_* + log2 S.  All flagged cells
+// of the unit are processed together in two passes over the points:
 //  1. the minimiser of every cell.  It is no worse than the x-nearest point
 //     (X = 0, Y = Yh) and the y-nearest point (X = Xh, Y = 0), so
 //     e_* <= min(a2 Yh, a1 Xh): only points with dx2 <= qx and dy2 <= qy
 //     (qx, qy: the dataset's stored other-coordinate distances of the two
 //     neighbours), and inside the union over the row's cells of those
-//     triangles, are tested cell by cell.  A cell keeps the smallest key
-//     (e bits, i) with a shared-memory 64-bit atomicMin: the smallest e, ties
-//     to the smallest index, whatever the order of visits.
+//     triangles, are candidates.  A cell keeps the smallest key (e bits, i):
+//     the smallest e, ties to the smallest index, whatever the order of visits.
 //  2. the sums.  A point with e_i > e_* + T adds less than 2^-T; with
 //     T = 32 + ceil(log2 N) all of them together add less than 2^-32 of S.
 //     So only points with X <= max_f (e_*f + T)/a1_f and Y <= max_f (e_*f + T)/a2_f
-//     are visited cell by cell, and each term is added as an integer in units
-//     of 2^-(62 - ceil(log2 N)) (64-bit shared-memory atomicAdd: exact, so the
-//     sum is the same in any order, and it cannot overflow).
-// Both passes compute dx2 and dy2 with the tile body's FP32 formula.
+//     (the row's box) are candidates.
+// Each warp takes chunks of 32 consecutive points (lane = point: distances to
+// every flagged row, candidate tests) and compacts a row's candidates into a
+// shared list; then lane = cell: each lane runs its cells over the list.
+// Pass 1 folds the list into the lane's (e, i) minimum and merges it with a
+// 64-bit shared atomicMin; pass 2 sums the list's terms in FP32 (list order)
+// and adds the chunk sum as an integer in units of 2^-(62 - ceil(log2 N))
+// (64-bit shared atomicAdd: exact, so the cell's sum is the same whatever the
+// order in which warps finish, and it cannot overflow).  Both passes compute
+// dx2 and dy2 with the tile body's FP32 formula.
 template <class C, class Coef>
 __device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, float* sm, int nfl) {
     constexpr int GG = C::GG, G2 = C::G2v, JW = C::JW, NT = C::kThreads, NW = C::kWarps;
     constexpr int LG2 = G2 == 8 ? 3 : (G2 == 16 ? 4 : 5);
-    static_assert(2 * JW * GG + 6 * GG <= C::COMB, "fallback scratch must fit in the combine buffer");
+    constexpr int JG = JW * GG;
+    static_assert(8 * JG <= C::COMB, "fallback scratch must fit in the combine buffer");
+    static_assert(JW <= 8, "per-row fallback parameters hold 8 rows");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int d = a.d;
     const int64_t N = a.N, Np = a.Np;
-    float* xj_s = sm + C::off_xj(d);
-    float* yj_s = sm + C::off_yj(d);
-    float* mx_s = sm + C::off_mx(d);
-    float* my_s = sm + C::off_my(d);
+    const float* xj_s = sm + C::off_xj(d);
+    const float* yj_s = sm + C::off_yj(d);
+    const float* mx_s = sm + C::off_mx(d);
+    const float* my_s = sm + C::off_my(d);
     const long long* ji_s = reinterpret_cast<const long long*>(sm + C::off_ji(d));
     int* flag_s = reinterpret_cast<int*>(sm + C::off_flag(d));
-    float* red = sm + C::off_red(d);   // 2 kWarps FB floats: per-warp reduction slots
     double* la2 = reinterpret_cast<double*>(sm);
-    // per-cell scratch after la2 (one row's cells at a time)
-    unsigned long long* best = reinterpret_cast<unsigned long long*>(sm + 2 * JW * GG);
-    unsigned long long* acc = best + GG;
-    float* dxs = reinterpret_cast<float*>(acc + GG);
-    float* dys = dxs + GG;
+    // per flagged cell f (after la2): the pass-1 key, reused for the pass-2 sum;
+    // the minimiser's distances; the cell's coefficients
+    unsigned long long* best = reinterpret_cast<unsigned long long*>(sm + 2 * JG);
+    unsigned long long* acc = best;
+    float* dxs = sm + 4 * JG;
+    float* dys = sm + 5 * JG;
+    float* As = sm + 6 * JG;
+    float* Bs = sm + 7 * JG;
+    // per warp: the candidate list of one (chunk, row); per row: bounds and cell range
+    float* fbw = sm + C::off_fbw(d);
+    float* lx = fbw + warp * 96;
+    float* ly = lx + 32;
+    int* li = reinterpret_cast<int*>(ly + 32);
+    float* rqx = fbw + NW * 96;
+    float* rqy = rqx + 8;
+    int* rlo_b = reinterpret_cast<int*>(rqy + 8);   // float bits of positive values (0: none)
+    int* rhi_b = rlo_b + 8;
+    int* rx_b = rhi_b + 8;
+    int* ry_b = rx_b + 8;
+    int* rs = ry_b + 8;                              // cells [rs, re) of the row in flag_s
+    int* re = rs + 8;
 
     // sort the (distinct) flagged cell ids in place: each thread ranks its entries
     int mine[4], rank[4];
@@ -167,6 +189,15 @@ __device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, f
         rank[nm] = r;
         ++nm;
     }
+    if (tid < JW) {
+        rs[tid] = re[tid] = 0;
+        rlo_b[tid] = 0;
+        rhi_b[tid] = __float_as_int(INFINITY);
+        rx_b[tid] = ry_b[tid] = 0;
+        const long long j = ji_s[tid];
+        rqx[tid] = a.qx[j];
+        rqy[tid] = a.qy[j];
+    }
     __syncthreads();
     for (int m = 0; m < nm; ++m) flag_s[rank[m]] = mine[m];
     __syncthreads();
@@ -177,144 +208,164 @@ __device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, f
     const int SC = 62 - lg;            // fixed-point scale of the sums
     const float scale = ldexpf(1.f, SC), inv_scale_f = ldexpf(1.f, -SC);
 
-    int q0 = 0;
-    while (q0 < nfl) {
-        const int jl = flag_s[q0] / GG;
-        int q1 = q0;
-        while (q1 < nfl && flag_s[q1] / GG == jl) ++q1;
-        const int F = q1 - q0;
-        const float mxj = mx_s[jl], myj = my_s[jl], yj = yj_s[jl];
-        const long long j = ji_s[jl];
-        const float* xjr = xj_s + jl * d;
-        const float qxj = a.qx[j], qyj = a.qy[j];
-        const float Xh = qxj - mxj, Yh = qyj - myj;
+    // cells: coefficients, row ranges, and the triangles of the argmin region --
+    // cells with rho = a2/a1 <= Xh/Yh are bounded by the x-nearest point
+    // (X + rho Y <= rho Yh; the largest rho covers the others), the rest by the
+    // y-nearest point (X + rho Y <= Xh; the smallest rho)
+    for (int f = tid; f < nfl; f += NT) {
+        const int c = flag_s[f], r = c / GG, kl = c - r * GG, k = kl >> LG2, l = kl & (G2 - 1);
+        const float A = cf.a1(k), B = cf.a2(l);
+        As[f] = A;
+        Bs[f] = B;
+        best[f] = ~0ull;
+        if (f == 0 || flag_s[f - 1] / GG != r) rs[r] = f;
+        if (f == nfl - 1 || flag_s[f + 1] / GG != r) re[r] = f + 1;
+        const float Xh = rqx[r] - mx_s[r], Yh = rqy[r] - my_s[r];
+        const float rho = B / A;
+        if (rho * Yh <= Xh) atomicMax(rlo_b + r, __float_as_int(rho));
+        else atomicMin(rhi_b + r, __float_as_int(rho));
+    }
+    __syncthreads();
 
-        // triangles of the argmin region: cells with rho = a2/a1 <= Xh/Yh are bounded
-        // by the x-nearest point (X + rho Y <= rho Yh; the largest rho covers the
-        // others), the rest by the y-nearest point (X + rho Y <= Xh; the smallest rho)
-        float rlo = -1.f, rhi = INFINITY;
-        for (int f = tid; f < F; f += NT) {
-            const int kl = flag_s[q0 + f] - jl * GG, k = kl >> LG2, l = kl & (G2 - 1);
-            const float A = cf.a1(k), B = cf.a2(l);
-            const float rho = B / A;
-            if (rho * Yh <= Xh) rlo = fmaxf(rlo, rho);
-            else rhi = fminf(rhi, rho);
-            best[f] = ~0ull;
-            acc[f] = 0ull;
-        }
+    // squared distances of a chunk's point (lane) to row r, the tile body's formula
+    const auto dist = [&](int r, const float (&xi)[8], int64_t i, float yi, float& dx2, float& dy2) {
+        const float* xjr = xj_s + r * d;
+        float s = 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            rlo = fmaxf(rlo, __shfl_xor_sync(0xffffffffu, rlo, o));
-            rhi = fminf(rhi, __shfl_xor_sync(0xffffffffu, rhi, o));
-        }
-        if (lane == 0) {
-            red[warp] = rlo;
-            red[NW + warp] = rhi;
-        }
-        __syncthreads();
-        rlo = red[0];
-        rhi = red[NW];
-        for (int w = 1; w < NW; ++w) {
-            rlo = fmaxf(rlo, red[w]);
-            rhi = fminf(rhi, red[NW + w]);
-        }
-        const float rloY = rlo * Yh;
-
-        // ---- pass 1: the minimiser of every flagged cell of the row ----
-        for (int64_t i = tid; i < N; i += NT) {
-            if (i == j) continue;
-            float dx2 = 0.f;
-#pragma unroll 4
-            for (int cc = 0; cc < d; ++cc) {
-                const float t = xjr[cc] - a.xs[(int64_t)cc * Np + i];
-                dx2 = fmaf(t, t, dx2);
+        for (int cc = 0; cc < 8; ++cc)
+            if (cc < d) {
+                const float t = xjr[cc] - xi[cc];
+                s = fmaf(t, t, s);
             }
-            const float dy = yj - a.y[i];
-            const float dy2 = dy * dy;
-            if (dx2 > qxj || dy2 > qyj) continue;
-            const float X = dx2 - mxj, Y = dy2 - myj;
-            const bool in = (rlo >= 0.f && fmaf(rlo, Y, X) <= rloY) || (rhi < INFINITY && fmaf(rhi, Y, X) <= Xh);
-            if (!in) continue;
-            for (int f = 0; f < F; ++f) {
-                const int kl = flag_s[q0 + f] - jl * GG, k = kl >> LG2, l = kl & (G2 - 1);
-                const float e = fmaxf(fmaf(cf.a1(k), X, cf.a2(l) * Y), 0.f);
-                const unsigned long long key = ((unsigned long long)__float_as_uint(e) << 32) | (unsigned int)i;
+        for (int cc = 8; cc < d; ++cc) {
+            const float t = xjr[cc] - a.xs[(int64_t)cc * Np + i];
+            s = fmaf(t, t, s);
+        }
+        dx2 = s;
+        const float dy = yj_s[r] - yi;
+        dy2 = dy * dy;
+    };
+
+    // ---- pass 1: the minimiser of every flagged cell ----
+    for (int64_t base = (int64_t)warp * 32; base < N; base += NW * 32) {
+        const int64_t i = base + lane;
+        const bool v = i < N;
+        const int64_t ic = v ? i : base;
+        float xi[8];
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) xi[cc] = cc < d ? a.xs[(int64_t)cc * Np + CDE_CK(ic, N, 108)] : 0.f;
+        const float yi = a.y[ic];
+        for (int r = 0; r < JW; ++r) {
+            const int f0 = rs[r], f1 = re[r];
+            if (f0 == f1) continue;
+            float dx2, dy2;
+            dist(r, xi, ic, yi, dx2, dy2);
+            const float mxr = mx_s[r], myr = my_s[r];
+            const float X = dx2 - mxr, Y = dy2 - myr;
+            const float Xh = rqx[r] - mxr, Yh = rqy[r] - myr;
+            const float rlo = __int_as_float(rlo_b[r]), rhi = __int_as_float(rhi_b[r]);
+            const bool in = v && i != ji_s[r] && dx2 <= rqx[r] && dy2 <= rqy[r] &&
+                            ((rlo > 0.f && fmaf(rlo, Y, X) <= rlo * Yh) || (rhi < INFINITY && fmaf(rhi, Y, X) <= Xh));
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            if (m == 0u) continue;
+            if (in) {
+                const int p = __popc(m & ((1u << lane) - 1u));
+                lx[p] = X;
+                ly[p] = Y;
+                li[p] = (int)i;
+            }
+            __syncwarp();
+            const int nc = __popc(m);
+            for (int f = f0 + lane; f < f1; f += 32) {
+                const float A = As[f], B = Bs[f];
+                float emin = INFINITY;
+                int imin = 0;
+                for (int q = 0; q < nc; ++q) {
+                    const float e = fmaxf(fmaf(A, lx[q], B * ly[q]), 0.f);
+                    if (e < emin) {
+                        emin = e;
+                        imin = li[q];
+                    }
+                }
+                const unsigned long long key = ((unsigned long long)__float_as_uint(emin) << 32) | (unsigned int)imin;
                 if (key < best[f]) atomicMin(best + f, key);
             }
+            __syncwarp();
         }
-        __syncthreads();
-
-        // ---- the minimisers' distances; the box of pass 2 ----
-        float rx = 0.f, ry = 0.f;
-        for (int f = tid; f < F; f += NT) {
-            const int kl = flag_s[q0 + f] - jl * GG, k = kl >> LG2, l = kl & (G2 - 1);
-            const unsigned long long b = best[f];
-            // no point in the region (cannot happen: the two neighbours are in it):
-            // anchor at the x-nearest bound
-            const bool none = b == ~0ull;
-            const int64_t is = none ? (j == 0 ? 1 : 0) : (int64_t)(unsigned int)b;
-            float t2 = 0.f;
-            for (int cc = 0; cc < d; ++cc) {
-                const float t = xjr[cc] - a.xs[(int64_t)cc * Np + CDE_CK(is, N, 108)];
-                t2 = fmaf(t, t, t2);
-            }
-            const float t = yj - a.y[is];
-            dxs[f] = t2;
-            dys[f] = t * t;
-            const float es = fmaxf(fmaf(cf.a1(k), t2 - mxj, cf.a2(l) * (t * t - myj)), 0.f);
-            rx = fmaxf(rx, (es + T) / cf.a1(k));
-            ry = fmaxf(ry, (es + T) / cf.a2(l));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            rx = fmaxf(rx, __shfl_xor_sync(0xffffffffu, rx, o));
-            ry = fmaxf(ry, __shfl_xor_sync(0xffffffffu, ry, o));
-        }
-        __syncthreads();   // red[] reads of the triangle step are done
-        if (lane == 0) {
-            red[warp] = rx;
-            red[NW + warp] = ry;
-        }
-        __syncthreads();
-        rx = red[0];
-        ry = red[NW];
-        for (int w = 1; w < NW; ++w) {
-            rx = fmaxf(rx, red[w]);
-            ry = fmaxf(ry, red[NW + w]);
-        }
-        const float RXd = mxj + rx, RYd = myj + ry;   // in raw squared distances
-
-        // ---- pass 2: the shifted sums over the points that can matter ----
-        for (int64_t i = tid; i < N; i += NT) {
-            if (i == j) continue;
-            float dx2 = 0.f;
-#pragma unroll 4
-            for (int cc = 0; cc < d; ++cc) {
-                const float t = xjr[cc] - a.xs[(int64_t)cc * Np + i];
-                dx2 = fmaf(t, t, dx2);
-            }
-            const float dy = yj - a.y[i];
-            const float dy2 = dy * dy;
-            if (dx2 > RXd || dy2 > RYd) continue;
-            for (int f = 0; f < F; ++f) {
-                const int kl = flag_s[q0 + f] - jl * GG, k = kl >> LG2, l = kl & (G2 - 1);
-                const float v = ex2_approx(kFbEx2Fix - (cf.a1(k) * (dx2 - dxs[f]) + cf.a2(l) * (dy2 - dys[f])));
-                const unsigned long long q = __float2ull_rn(v * scale);
-                if (q) atomicAdd(acc + f, q);
-            }
-        }
-        __syncthreads();
-        for (int f = tid; f < F; f += NT) {
-            const int c = flag_s[q0 + f];
-            const int kl = c - jl * GG, k = kl >> LG2, l = kl & (G2 - 1);
-            const float tot = (float)((double)acc[f] * (double)inv_scale_f);
-            const double es = (double)cf.a1(k) * ((double)dxs[f] - (double)mxj) +
-                              (double)cf.a2(l) * ((double)dys[f] - (double)myj);
-            la2[c] = -es + log2_wide(tot);
-        }
-        __syncthreads();
-        q0 = q1;
     }
+    __syncthreads();
+
+    // ---- the minimisers' distances; the rows' boxes of pass 2 ----
+    for (int f = tid; f < nfl; f += NT) {
+        const int r = flag_s[f] / GG;
+        const long long j = ji_s[r];
+        const unsigned long long b = best[f];
+        // no point in the region (cannot happen: the two neighbours are in it):
+        // anchor at the x-nearest bound
+        const bool none = b == ~0ull;
+        const int64_t is = none ? (j == 0 ? 1 : 0) : (int64_t)(unsigned int)b;
+        const float* xjr = xj_s + r * d;
+        float t2 = 0.f;
+        for (int cc = 0; cc < d; ++cc) {
+            const float t = xjr[cc] - a.xs[(int64_t)cc * Np + CDE_CK(is, N, 108)];
+            t2 = fmaf(t, t, t2);
+        }
+        const float t = yj_s[r] - a.y[is];
+        dxs[f] = t2;
+        dys[f] = t * t;
+        const float A = As[f], B = Bs[f];
+        const float es = fmaxf(fmaf(A, t2 - mx_s[r], B * (t * t - my_s[r])), 0.f);
+        atomicMax(rx_b + r, __float_as_int((es + T) / A));
+        atomicMax(ry_b + r, __float_as_int((es + T) / B));
+        acc[f] = 0ull;   // the key of this cell has been read
+    }
+    __syncthreads();
+
+    // ---- pass 2: the shifted sums over the points that can matter ----
+    for (int64_t base = (int64_t)warp * 32; base < N; base += NW * 32) {
+        const int64_t i = base + lane;
+        const bool v = i < N;
+        const int64_t ic = v ? i : base;
+        float xi[8];
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) xi[cc] = cc < d ? a.xs[(int64_t)cc * Np + CDE_CK(ic, N, 108)] : 0.f;
+        const float yi = a.y[ic];
+        for (int r = 0; r < JW; ++r) {
+            const int f0 = rs[r], f1 = re[r];
+            if (f0 == f1) continue;
+            float dx2, dy2;
+            dist(r, xi, ic, yi, dx2, dy2);
+            const float RXd = mx_s[r] + __int_as_float(rx_b[r]), RYd = my_s[r] + __int_as_float(ry_b[r]);
+            const bool in = v && i != ji_s[r] && dx2 <= RXd && dy2 <= RYd;
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            if (m == 0u) continue;
+            if (in) {
+                const int p = __popc(m & ((1u << lane) - 1u));
+                lx[p] = dx2;
+                ly[p] = dy2;
+            }
+            __syncwarp();
+            const int nc = __popc(m);
+            for (int f = f0 + lane; f < f1; f += 32) {
+                const float A = As[f], B = Bs[f], dxf = dxs[f], dyf = dys[f];
+                float s = 0.f;
+                for (int q = 0; q < nc; ++q)
+                    s += ex2_approx(kFbEx2Fix - (A * (lx[q] - dxf) + B * (ly[q] - dyf)));
+                const unsigned long long qv = __float2ull_rn(s * scale);
+                if (qv) atomicAdd(acc + f, qv);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int f = tid; f < nfl; f += NT) {
+        const int c = flag_s[f], r = c / GG;
+        const float tot = (float)((double)acc[f] * (double)inv_scale_f);
+        const double es = (double)As[f] * ((double)dxs[f] - (double)mx_s[r]) +
+                          (double)Bs[f] * ((double)dys[f] - (double)my_s[r]);
+        la2[c] = -es + log2_wide(tot);
+    }
+    __syncthreads();
 }
 
 // Per-unit epilogue shared by the tile bodies.  On entry At[m] holds the

@@ -71,7 +71,6 @@ struct MmaCfg {
     static constexpr int JW = 1024 / GG;     // rows per unit (all handled by every warp)
     static constexpr int MT = G1 / 16, NT = G2 / 8;
     static constexpr int IC = 32;            // points per warp chunk (4 MMA k-steps)
-    static constexpr int FB = 8;
     static constexpr int COMB = kWarps * 1024 + kWarps * JW * G1;
     // per warp: (t1, t1) and t2 for JW rows x IC points
     __host__ __device__ static int stage(int) { return kWarps * JW * IC * 3; }
@@ -90,9 +89,11 @@ struct MmaCfg {
     __host__ __device__ static int off_btl(int d) { return off_yj(d) + 96; }
     __host__ __device__ static int off_flag(int d) { return off_btl(d) + 2 * JW * G1; }
     __host__ __device__ static int off_nflag(int d) { return off_flag(d) + 1024; }
-    __host__ __device__ static int off_red(int d) { return off_nflag(d) + 4; }
-    __host__ __device__ static int off_fb(int d) { return off_red(d) + 2 * kWarps * FB; }
-    static size_t smem_bytes(int d) { return (size_t)(off_fb(d) + 2 * FB + 8) * sizeof(float); }
+    // exact recomputation: per warp a list of 32 candidate points (3 words each),
+    // then per row (at most 8) its bounds and cell range
+    static constexpr int FBW = kWarps * 96 + 8 * 8;
+    __host__ __device__ static int off_fbw(int d) { return off_nflag(d) + 4; }
+    static size_t smem_bytes(int d) { return (size_t)(off_fbw(d) + FBW) * sizeof(float); }
 };
 
 __device__ __forceinline__ uint32_t tf32_rna(float v) {

@@ -88,17 +88,60 @@ def test_batch_mixed_shapes(ctx):
         cde.cde_destroy_dataset(ctx, ds)
 
 
-def test_autotune_keeps_paths_identical(ctx):
+@pytest.fixture
+def keep_tuning(ctx, tmp_path):
+    """Restore the context's whole tuning state after the test."""
+    path = str(tmp_path / "state.txt")
+    cde.cde_tuning_save(ctx, path)
+    yield
+    cde.cde_tuning_load(ctx, path)
+
+
+def test_autotune_keeps_paths_identical(ctx, keep_tuning):
+    """The tuned configuration (rows per tile, CTAs per SM) is read by both
+    launch paths, which stay bitwise the same and meet the oracle."""
     ws = synth.batch_workloads(n_datasets=6, N_min=500, N_max=4000, seed=9)
     dss = _make(ctx, ws)
     u, c, ms = cde.cde_autotune(ctx, dss[0], ws[0].h1, ws[0].h2)
     assert u >= 1 and c in (1, 2) and ms > 0
     assert cde.cde_tuning_get(ctx, 16, 16) == (u, c)
+    assert cde.cde_tuning_get_ex(ctx, 16, 16) == (u, c, True)
     Lc, Le = cde.cde_loo_loglik_batch(ctx, dss, [w.h1 for w in ws], [w.h2 for w in ws])
     for b, (w, ds) in enumerate(zip(ws, dss)):
         sc, se = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
-        assert np.array_equal(sc, Lc[b]) and np.array_equal(se, Le[b])
+        assert np.array_equal(sc, Lc[b]) and np.array_equal(se, Le[b]), w.name
+    for b in range(2):
+        w = ws[b]
+        ell, _ = oracle.loo_rows(w.x, w.y, w.h1, w.h2, standardize_x=w.standardize)
+        err = np.abs(Lc[b] - ell.sum(0)) / np.abs(ell).sum(0)
+        assert err.max() <= 1e-5, err.max()
+    for ds in dss:
+        cde.cde_destroy_dataset(ctx, ds)
+
+
+def test_batch_tunes_untuned_shapes_by_default(ctx, keep_tuning):
+    """cde_loo_loglik_batch tunes a shape class it meets untuned, keeps the
+    result for the single launches, and leaves tuned classes alone; with
+    tuning off the class stays untuned."""
+    ws = synth.batch_workloads(n_datasets=5, N_min=400, N_max=2500, seed=11)
+    dss = _make(ctx, ws)
+    h1s, h2s = [w.h1 for w in ws], [w.h2 for w in ws]
+    cde.cde_autotune_enable(ctx, False)
     cde.cde_tuning_set(ctx, 16, 16, 0, 0)
+    assert cde.cde_tuning_get_ex(ctx, 16, 16)[2] is False
+    cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s)
+    assert cde.cde_tuning_get_ex(ctx, 16, 16)[2] is False
+    cde.cde_autotune_enable(ctx, True)
+    Lc, Le = cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s)
+    u, c, tuned = cde.cde_tuning_get_ex(ctx, 16, 16)
+    assert tuned and u >= 1 and c in (1, 2)
+    for b, (w, ds) in enumerate(zip(ws, dss)):
+        sc, se = cde.cde_loo_loglik(ctx, ds, w.h1, w.h2)
+        assert np.array_equal(sc, Lc[b]) and np.array_equal(se, Le[b])
+    # a tuned class is not tuned again: an explicit configuration stays
+    cde.cde_tuning_set(ctx, 16, 16, 7, 1)
+    cde.cde_loo_loglik_batch(ctx, dss, h1s, h2s)
+    assert cde.cde_tuning_get_ex(ctx, 16, 16) == (7, 1, True)
     for ds in dss:
         cde.cde_destroy_dataset(ctx, ds)
 
@@ -113,48 +156,51 @@ def test_batch_rejects_bad_grids(ctx):
     cde.cde_destroy_dataset(ctx, ds)
 
 
-def test_tuning_cache_roundtrip(ctx, tmp_path):
-    """cde_tuning_save / cde_tuning_load: same values back, atomic file, and a
-    file written for another device (or malformed) is refused."""
-    saved = {(g1, g2): cde.cde_tuning_get(ctx, g1, g2) for g1 in (8, 16, 32) for g2 in (8, 16, 32)}
-    try:
-        cde.cde_tuning_set(ctx, 32, 32, 5, 1)
-        cde.cde_tuning_set(ctx, 8, 16, 3, 2)
-        path = str(tmp_path / "tune.txt")
-        cde.cde_tuning_save(ctx, path)
-        cde.cde_tuning_set(ctx, 32, 32, 0, 0)
-        cde.cde_tuning_set(ctx, 8, 16, 0, 0)
-        cde.cde_tuning_load(ctx, path)
-        assert tuple(cde.cde_tuning_get(ctx, 32, 32)) == (5, 1)
-        assert tuple(cde.cde_tuning_get(ctx, 8, 16)) == (3, 2)
-        lines = open(path).read().splitlines()
+def test_tuning_cache_roundtrip(ctx, keep_tuning, tmp_path):
+    """cde_tuning_save / cde_tuning_load: same values back (tuned flag
+    included), atomic file, and a file written for another device, in another
+    format version, or malformed is refused."""
+    cde.cde_tuning_set(ctx, 32, 32, 5, 1)
+    cde.cde_tuning_set(ctx, 8, 16, 3, 2)
+    cde.cde_tuning_set(ctx, 16, 8, 0, 0)
+    path = str(tmp_path / "tune.txt")
+    cde.cde_tuning_save(ctx, path)
+    cde.cde_tuning_set(ctx, 32, 32, 0, 0)
+    cde.cde_tuning_set(ctx, 8, 16, 0, 0)
+    cde.cde_tuning_set(ctx, 16, 8, 2, 2)
+    assert cde.cde_tuning_get_ex(ctx, 32, 32)[2] is False
+    cde.cde_tuning_load(ctx, path)
+    assert cde.cde_tuning_get_ex(ctx, 32, 32) == (5, 1, True)
+    assert cde.cde_tuning_get_ex(ctx, 8, 16) == (3, 2, True)
+    assert cde.cde_tuning_get_ex(ctx, 16, 8)[2] is False
+    lines = open(path).read().splitlines()
+    assert lines[0].startswith("cde-tuning 2 ")
+    for head in ("cde-tuning 2 some other device sm_90 sms=132", lines[0].replace("cde-tuning 2", "cde-tuning 1")):
         other = tmp_path / "other.txt"
-        other.write_text("\n".join(["cde-tuning 1 some other device sm_90 sms=132"] + lines[1:]) + "\n")
+        other.write_text("\n".join([head] + lines[1:]) + "\n")
         with pytest.raises(cde.CdeError):
             cde.cde_tuning_load(ctx, str(other))
-        bad = tmp_path / "bad.txt"
-        bad.write_text("\n".join(lines[:-1]) + "\n")
-        with pytest.raises(cde.CdeError):
-            cde.cde_tuning_load(ctx, str(bad))
-        with pytest.raises(cde.CdeError):
-            cde.cde_tuning_load(ctx, str(tmp_path / "missing.txt"))
-    finally:
-        for (g1, g2), (u, c) in saved.items():
-            cde.cde_tuning_set(ctx, g1, g2, u, c)
+    bad = tmp_path / "bad.txt"
+    bad.write_text("\n".join(lines[:-1]) + "\n")
+    with pytest.raises(cde.CdeError):
+        cde.cde_tuning_load(ctx, str(bad))
+    f = lines[-1].split()
+    f[4] = "9"  # a tuned flag is 0 or 1
+    bad.write_text("\n".join(lines[:-1] + [" ".join(f)]) + "\n")
+    with pytest.raises(cde.CdeError):
+        cde.cde_tuning_load(ctx, str(bad))
+    with pytest.raises(cde.CdeError):
+        cde.cde_tuning_load(ctx, str(tmp_path / "missing.txt"))
 
 
-def test_tuning_cache_applied_at_init(ctx, tmp_path):
+def test_tuning_cache_applied_at_init(ctx, keep_tuning, tmp_path):
     """cde_init loads the file named by CDE_TUNING_CACHE (fresh process)."""
     import os
     import subprocess
     import sys
-    saved = cde.cde_tuning_get(ctx, 32, 32)
     path = str(tmp_path / "tune.txt")
-    try:
-        cde.cde_tuning_set(ctx, 32, 32, 6, 1)
-        cde.cde_tuning_save(ctx, path)
-    finally:
-        cde.cde_tuning_set(ctx, 32, 32, *saved)
+    cde.cde_tuning_set(ctx, 32, 32, 6, 1)
+    cde.cde_tuning_save(ctx, path)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     code = ("import sys; sys.path.insert(0, %r)\n"
             "from paper_1206_5278_gb300 import cde\n"
