@@ -38,8 +38,9 @@
 // grid: mean per-row error of L_cond -1.8e-7 before, ~0 after.  Each lane takes
 // the points (2t, 2t+1) of a k-step so the TF32 and BF16 fragment layouts hold
 // the same points.  The tensor core's FP32 accumulation is kept short: each
-// chunk of 32 points (8 MMAs per accumulator) starts from zero and is then
-// added to an FP32 running total with a rounded add.
+// chunk of 64 points (128 at 32 x 32: 16 or 32 MMAs per accumulator) starts
+// from zero and is then added to an FP32 running total with a rounded add; the
+// running totals live in shared memory.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -70,7 +71,9 @@ struct MmaCfg {
     static constexpr int GG = G1 * G2;
     static constexpr int JW = 1024 / GG;     // rows per unit (all handled by every warp)
     static constexpr int MT = G1 / 16, NT = G2 / 8;
-    static constexpr int IC = 32;            // points per warp chunk (4 MMA k-steps)
+    // points per warp chunk (IC / 8 MMA k-steps): the chunk sums start from zero
+    // and are added to the FP32 running totals once per chunk
+    static constexpr int IC = 64;
     static constexpr int COMB = kWarps * 1024 + kWarps * JW * G1;
     // per warp: (t1, t1) and t2 for JW rows x IC points
     __host__ __device__ static int stage(int) { return kWarps * JW * IC * 3; }
@@ -93,7 +96,10 @@ struct MmaCfg {
     // then per row (at most 8) its bounds and cell range
     static constexpr int FBW = kWarps * 96 + 8 * 8;
     __host__ __device__ static int off_fbw(int d) { return off_nflag(d) + 4; }
-    static size_t smem_bytes(int d) { return (size_t)(off_fbw(d) + FBW) * sizeof(float); }
+    // per warp the FP32 running totals of its 1024 cells in MMA fragment order
+    // (lane-contiguous float4 per (row, M tile, N tile): conflict-free)
+    __host__ __device__ static int off_dts(int d) { return (off_fbw(d) + FBW + 3) & ~3; }
+    static size_t smem_bytes(int d) { return (size_t)(off_dts(d) + kWarps * 1024) * sizeof(float); }
 };
 
 __device__ __forceinline__ uint32_t tf32_rna(float v) {
@@ -185,7 +191,9 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
         }
         __syncthreads();
 
-        float Dt[JW][MT][NT][4];
+        // running totals in shared memory (keeping them in registers costs 32 per
+        // thread, which the compiler then takes from the software pipeline)
+        float4* dts = reinterpret_cast<float4*>(sm + C::off_dts(d)) + warp * 256;
         float2 bt[JW][MT];  // denominator partials of k = 16 mt + g and k + 8
 #pragma unroll
         for (int r = 0; r < JW; ++r)
@@ -193,19 +201,22 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
             for (int mt = 0; mt < MT; ++mt) {
                 bt[r][mt] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) Dt[r][mt][nt][q] = 0.f;
+                for (int nt = 0; nt < NT; ++nt) dts[((r * MT + mt) * NT + nt) * 32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
 
-        // point coordinates of the first chunk (lane = point), prefetched one chunk ahead
-        float xin[8], yin = 0.f;
+        // point coordinates of the first chunk (lane = point of each 32-point half),
+        // prefetched one chunk ahead
+        constexpr int HH = IC / 32;
+        float xin[HH][8], yin[HH];
         int64_t ch = warp;
         if (ch < n_chunks) {
-            const int64_t i = CDE_CK(ch * IC + lane, Np, 103);  // < Np
 #pragma unroll
-            for (int c = 0; c < 8; ++c) xin[c] = c < d ? a.xs[(int64_t)c * Np + i] : 0.f;
-            yin = a.y[i];
+            for (int h = 0; h < HH; ++h) {
+                const int64_t i = CDE_CK(ch * IC + h * 32 + lane, Np, 103);  // < Np
+#pragma unroll
+                for (int c = 0; c < 8; ++c) xin[h][c] = c < d ? a.xs[(int64_t)c * Np + i] : 0.f;
+                yin[h] = a.y[i];
+            }
         }
         // one row per unit (G1 G2 = 1024): its constants stay in registers for
         // the whole chunk loop instead of being re-read from shared memory
@@ -219,43 +230,64 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
         }
         const int N32 = (int)N;  // N < 2^31
         for (; ch < n_chunks; ch += C::kWarps) {
-            const int64_t i = ch * IC + lane;
-            const int i32 = (int)i;
-            // ---- distance pass: lane = point; masked pairs get t1 = -inf ----
+            // ---- distance pass: lane = the points (h = 0, 1) of the chunk's halves,
+            //      packed FP32x2; masked pairs get t1 = -inf ----
+            static_assert(IC == 64, "two points per lane");
             __syncwarp();
+            {
+              const int64_t i0 = ch * IC + lane, i1 = i0 + 32;
 #pragma unroll
-            for (int r = 0; r < JW; ++r) {
+              for (int r = 0; r < JW; ++r) {
                 const float* xjr = xj_s + r * d;
-                float dx2 = 0.f;
+                float2 dx2 = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
                     if (c < d) {
-                        const float q = xjr[c] - xin[c];
-                        dx2 = fmaf(q, q, dx2);
+                        const float2 q = __fadd2_rn(make_float2(xjr[c], xjr[c]), make_float2(-xin[0][c], -xin[1][c]));
+                        dx2 = __ffma2_rn(q, q, dx2);
                     }
                 for (int c = 8; c < d; ++c) {
-                    const float q = xjr[c] - a.xs[(int64_t)c * Np + CDE_CK(i, Np, 104)];
-                    dx2 = fmaf(q, q, dx2);
+                    const float2 q = __fadd2_rn(make_float2(xjr[c], xjr[c]),
+                                                make_float2(-a.xs[(int64_t)c * Np + CDE_CK(i0, Np, 104)],
+                                                            -a.xs[(int64_t)c * Np + CDE_CK(i1, Np, 104)]));
+                    dx2 = __ffma2_rn(q, q, dx2);
                 }
-                const float dy = (JW == 1 ? yr1 : yj_s[r]) - yin;
-                const bool ok = i32 < N32 && i32 != (JW == 1 ? jr1 : (int)ji_s[r]);
+                const float yr = JW == 1 ? yr1 : yj_s[r];
+                const float2 dy = __fadd2_rn(make_float2(yr, yr), make_float2(-yin[0], -yin[1]));
+                const float2 dy2 = __fmul2_rn(dy, dy);
+                const int jr = JW == 1 ? jr1 : (int)ji_s[r];
+                const bool ok0 = (int)i0 < N32 && (int)i0 != jr, ok1 = (int)i1 < N32 && (int)i1 != jr;
                 // Gaussian: shifted exponents (masked pairs -inf); Epanechnikov:
                 // squared distances (masked pairs +inf)
                 const float mxv = JW == 1 ? mxr1 : mx_s[r], myv = JW == 1 ? myr1 : my_s[r];
-                const float t1 = KERN == 0 ? (ok ? mxv - dx2 : -INFINITY) : (ok ? dx2 : INFINITY);
-                // masked pairs: w = 0 as well (at i = j, m_y - 0 could overflow 2^{a2 t2})
-                const float t2 = KERN == 0 ? (ok ? myv - dy * dy : -INFINITY) : dy * dy;
-                reinterpret_cast<float2*>(tt + r * 3 * IC)[lane] = make_float2(t1, t1);
-                tt[r * 3 * IC + 2 * IC + lane] = t2;
+                float2 t1, t2;
+                if constexpr (KERN == 0) {
+                    t1 = __fadd2_rn(make_float2(mxv, mxv), make_float2(-dx2.x, -dx2.y));
+                    t2 = __fadd2_rn(make_float2(myv, myv), make_float2(-dy2.x, -dy2.y));
+                    // masked pairs: w = 0 as well (at i = j, m_y - 0 could overflow 2^{a2 t2})
+                    t1.x = ok0 ? t1.x : -INFINITY;  t1.y = ok1 ? t1.y : -INFINITY;
+                    t2.x = ok0 ? t2.x : -INFINITY;  t2.y = ok1 ? t2.y : -INFINITY;
+                } else {
+                    t1 = make_float2(ok0 ? dx2.x : INFINITY, ok1 ? dx2.y : INFINITY);
+                    t2 = dy2;
+                }
+                reinterpret_cast<float2*>(tt + r * 3 * IC)[lane] = make_float2(t1.x, t1.x);
+                reinterpret_cast<float2*>(tt + r * 3 * IC)[32 + lane] = make_float2(t1.y, t1.y);
+                tt[r * 3 * IC + 2 * IC + lane] = t2.x;
+                tt[r * 3 * IC + 2 * IC + 32 + lane] = t2.y;
+              }
             }
             if (ch + C::kWarps < n_chunks) {
-                const int64_t i2 = CDE_CK((ch + C::kWarps) * IC + lane, Np, 105);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) xin[c] = c < d ? a.xs[(int64_t)c * Np + i2] : 0.f;
-                yin = a.y[i2];
+                for (int h = 0; h < HH; ++h) {
+                    const int64_t i2 = CDE_CK((ch + C::kWarps) * IC + h * 32 + lane, Np, 105);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) xin[h][c] = c < d ? a.xs[(int64_t)c * Np + i2] : 0.f;
+                    yin[h] = a.y[i2];
+                }
             }
             __syncwarp();
-            // ---- MMA pass: 4 k-steps of 8 points ----
+            // ---- MMA pass: IC / 8 k-steps of 8 points ----
             float D[JW][MT][NT][4];
 #pragma unroll
             for (int r = 0; r < JW; ++r)
@@ -333,12 +365,11 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                 for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
                     for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                        for (int q = 0; q < 4; q += 2) {
-                            const float2 s2 = __fadd2_rn(make_float2(Dt[r][mt][nt][q], Dt[r][mt][nt][q + 1]),
-                                                         make_float2(D[r][mt][nt][q], D[r][mt][nt][q + 1]));
-                            Dt[r][mt][nt][q] = s2.x;
-                            Dt[r][mt][nt][q + 1] = s2.y;
+                        {
+                            float4 o = dts[((r * MT + mt) * NT + nt) * 32 + lane];
+                            const float2 s0 = __fadd2_rn(make_float2(o.x, o.y), make_float2(D[r][mt][nt][0], D[r][mt][nt][1]));
+                            const float2 s1 = __fadd2_rn(make_float2(o.z, o.w), make_float2(D[r][mt][nt][2], D[r][mt][nt][3]));
+                            dts[((r * MT + mt) * NT + nt) * 32 + lane] = make_float4(s0.x, s0.y, s1.x, s1.y);
                         }
         }
 
@@ -351,12 +382,15 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
 #pragma unroll
             for (int mt = 0; mt < MT; ++mt) {
 #pragma unroll
-                for (int nt = 0; nt < NT; ++nt)
+                for (int nt = 0; nt < NT; ++nt) {
+                    const float4 o = dts[((r * MT + mt) * NT + nt) * 32 + lane];
+                    const float ov[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int k = 16 * mt + g + 8 * (q >> 1), l = 8 * nt + 2 * t + (q & 1);
-                        accS[warp * 1024 + r * GG + k * G2 + l] = Dt[r][mt][nt][q];
+                        accS[warp * 1024 + r * GG + k * G2 + l] = ov[q];
                     }
+                }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     float v = h ? bt[r][mt].y : bt[r][mt].x;
