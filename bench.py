@@ -33,6 +33,11 @@ def _env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+# DRAM bytes (read + write) of one k_loo_mma<32,32> launch at N = 50,000 from an ncu
+# capture of the current tile body (9,648,640 read + 356,306,944 written)
+LOO_MMA_TRAFFIC = 365955584
+
+
 def flops_per_pair(G1: int, G2: int, d: int) -> int:
     """Algorithmic FP32 flops per pair (j, i) for a G1 x G2 grid, FMA = 2:
     distance 3d+2, shift subtractions 2, exp2 arguments G1+G2 multiplies,
@@ -231,13 +236,16 @@ def run_ours(args, w):
         p = None
     lanes = 128.0
     peak_max = 2 * lanes * sms * 2070e6 / 1e12
-    # DRAM bytes of one k_loo_mma<32,32> launch at N=50,000 (2-row tiles) from an ncu
-    # capture (profiles/k_loo_mma_32x32_N50000.md): 10.3 MB read, 357.5 MB of FP64 tile
-    # partials written; not measured for other sizes.
-    traffic = 367792640 if (w.N == 50000 and G1 == 32 and G2 == 32 and args.kernel == "gauss") else None
+    # DRAM bytes of one k_loo_mma<32,32> launch at N=50,000 from an ncu capture of the
+    # current tile body (profiles/k_loo_mma_32x32_N50000.md); not measured for other sizes.
+    traffic = LOO_MMA_TRAFFIC if (w.N == 50000 and G1 == 32 and G2 == 32 and args.kernel == "gauss") else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
             "frac": achieved / peak_max, "traffic": traffic, "kernel": "k_loo_mma", "kernel_ms": kms,
-            "peak_basis": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x 2070 MHz (max clock)" % sms}
+            "peak_basis": "FP32 FMA pipe: %d SMs x 128 lanes x 2 flop x 2070 MHz (max clock)" % sms,
+            "note": "the algorithm's FP32 flops against the FP32 lanes: the ceiling of an FP32-lane "
+                    "evaluation of the separable method. The kernel runs the 2 G1 G2 outer-product "
+                    "flops per pair on the tensor cores (mma.sync), so it can exceed 1; the pipe it "
+                    "is bound by is in pipe_fractions"}
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (2 * lanes * sms * clocks["sm_mhz"] * 1e6 / 1e12)
     # the naive form's ceiling: one kernel evaluation per (pair, bandwidth pair) (Gaussian:
