@@ -34,8 +34,8 @@ def _env_rank():
 
 
 # DRAM bytes (read + write) of one k_loo_mma<32,32> launch at N = 50,000 from an ncu
-# capture of the current tile body (9,648,640 read + 356,306,944 written)
-LOO_MMA_TRAFFIC = 365955584
+# capture of the current tile body and tile partition (2,577,664 read + 35,840 written)
+LOO_MMA_TRAFFIC = 2613504
 
 
 def flops_per_pair(G1: int, G2: int, d: int) -> int:

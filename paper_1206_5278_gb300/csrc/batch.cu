@@ -177,7 +177,14 @@ static int build_plan(cde_ctx* ctx, const std::vector<BatchItem>& items, BatchPl
         a.n_rows = it.D->N;
         a.n_units = (int)((it.D->N + JW - 1) / JW);
         a.units_per_tile = loo_units_per_tile(ctx, T1, T2, it.D->N);
-        a.n_tiles = (a.n_units + a.units_per_tile - 1) / a.units_per_tile;
+        // the single launch's partition (its grid size), so that the partials agree
+        const LooTiles tp = loo_tiles(a.n_units, a.units_per_tile, loo_grid_ctas(ctx, T1, T2));
+        a.n_tiles = tp.n_tiles;
+        a.big_g = tp.big_g;
+        a.big_levels = tp.big_levels;
+        a.big_s0 = tp.big_s0;
+        a.win0 = 0;
+        a.win1 = INT_MAX;
         a.G1r = it.G1;
         a.G2r = it.G2;
         a.ell_rows = nullptr;

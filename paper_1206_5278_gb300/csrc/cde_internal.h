@@ -186,8 +186,9 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
                      size_t scratch_bytes = 0);
 size_t loo_grid_scratch_bytes(cde_ctx* ctx, const Dataset& D, int G1, int G2, int64_t n_rows);
 
-// One grid block (G1, G2 <= 32) launched in ranges of its tiles, each range its
-// own launch; every tile writes a fixed partial slot and the final reduction is
+// One grid block (G1, G2 <= 32) launched in parts, each its own launch: windows
+// of units of the large tiles, then ranges of the small tiles.  Every tile adds
+// its units to a fixed partial slot in unit order and the final reduction is
 // loo_grid_enqueue's, so the result is bitwise that of one launch (the request
 // loop runs selection grids this way, so queued density jobs run in between).
 // Scratch: loo_chunked_scratch_bytes, stream-ordered, the caller's for the whole sequence.
@@ -196,10 +197,9 @@ int loo_chunked_create(cde_ctx* ctx, const Dataset& D, const double* h1, int G1,
                        LooChunked** out);
 void loo_chunked_destroy(LooChunked* c);
 size_t loo_chunked_scratch_bytes(const LooChunked* c);
-int loo_chunked_tiles(const LooChunked* c);
-// tiles of a launch of about `pair_evals` pair evaluations (at least the launch's CTAs)
-int loo_chunked_tiles_per_launch(const LooChunked* c, double pair_evals);
-int loo_chunked_launch(LooChunked* c, void* scratch, int t0, int t1, cudaStream_t st);
+// the next part, about `pair_evals` pair evaluations (at least one unit per large
+// tile, or one small tile per CTA); *done = 1 once every unit has been launched
+int loo_chunked_next(LooChunked* c, void* scratch, double pair_evals, cudaStream_t st, int* done);
 int loo_chunked_final(const LooChunked* c, const void* scratch, double* d_Lc, double* d_Le, cudaStream_t st);
 
 constexpr size_t kWorkspaceMax = (size_t)64 << 20;

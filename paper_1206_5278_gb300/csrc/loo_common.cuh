@@ -6,6 +6,7 @@
 // the method.
 #pragma once
 
+#include <climits>
 #include <cstdint>
 
 #include "cde_internal.h"
@@ -29,6 +30,11 @@ struct LooArgs {
     int64_t N, Np, n_rows;
     int d;
     int n_units, units_per_tile, n_tiles;
+    // tile partition (LooTiles): big_levels levels of big_g tiles each, the tiles of
+    // level l holding big_s0 >> l units; the rest hold units_per_tile consecutive
+    // units.  big_levels = 0: all tiles are small.
+    int big_g, big_levels, big_s0;
+    int win0, win1;         // units m of each tile processed by this launch: [win0, win1)
     int tile_base;          // batched launch: first global tile of this item
     int* work;              // batched launch: queue counter
     int kern;               // CDE_KERNEL_GAUSS or CDE_KERNEL_EPAN
@@ -90,6 +96,59 @@ __device__ __forceinline__ void loo_final_cell(const double* __restrict__ part, 
     for (int o = 16; o > 0; o >>= 1) {
         sc += __shfl_xor_sync(0xffffffffu, sc, o);
         se += __shfl_xor_sync(0xffffffffu, se, o);
+    }
+}
+
+// Tile partition of a launch's units.  One partial slot per tile; a tile's units
+// are added to its slot in order, and the slots are reduced in a fixed order, so
+// the result depends on the partition only, not on which CTA runs which tile or
+// in which launch.  With enough work the tiles shrink as the launch proceeds
+// (guided self-scheduling): level l holds G tiles (one per resident CTA) of
+// s0 >> l units, s0 = n_units / 2G, interleaved with stride G inside the level's
+// range so that every tile samples the whole dataset; levels stop before the
+// size falls under 2 units_per_tile, and small tiles of units_per_tile
+// consecutive units take the rest.  The atomic queue hands tiles out in index
+// order, so the launch ends on small tiles as with uniform ones, with
+// G log2(n_units / G) + 2G slots instead of one per small tile.
+struct LooTiles {
+    int big_g, big_levels, big_s0, n_tiles;
+};
+
+__host__ __device__ inline LooTiles loo_tiles(int n_units, int upt, int G) {
+    LooTiles p{0, 0, 0, 0};
+    if (G > 0 && (int64_t)n_units >= 8LL * G * upt) {
+        p.big_g = G;
+        p.big_s0 = n_units / (2 * G);
+        while (p.big_levels < 16 && (p.big_s0 >> p.big_levels) >= 2 * upt) ++p.big_levels;
+        int64_t covered = 0;
+        for (int l = 0; l < p.big_levels; ++l) covered += p.big_s0 >> l;
+        const int rest = n_units - (int)(covered * G);
+        p.n_tiles = p.big_levels * G + (rest + upt - 1) / upt;
+    } else {
+        p.n_tiles = (n_units + upt - 1) / upt;
+    }
+    return p;
+}
+
+// first unit of level l (the units of levels 0 .. l-1 come before it)
+__device__ __forceinline__ int loo_level_base(const LooArgs& a, int l) {
+    int s = 0;
+    for (int i = 0; i < l; ++i) s += a.big_s0 >> i;
+    return s * a.big_g;
+}
+
+// tile t's units: u0 + m stride for m < len
+__device__ __forceinline__ void loo_tile_span(const LooArgs& a, int t, int& u0, int& stride, int& len) {
+    const int nb = a.big_levels * a.big_g;
+    if (t < nb) {
+        const int l = t / a.big_g;
+        u0 = loo_level_base(a, l) + (t - l * a.big_g);
+        stride = a.big_g;
+        len = a.big_s0 >> l;
+    } else {
+        u0 = loo_level_base(a, a.big_levels) + (t - nb) * a.units_per_tile;
+        stride = 1;
+        len = min(a.units_per_tile, a.n_units - u0);
     }
 }
 
@@ -373,10 +432,10 @@ __device__ __forceinline__ void loo_fallback(const LooArgs& a, const Coef& cf, f
 // of the shifted denominators; `big` (the first BIG floats of shared memory)
 // is free.  Flags cells below the threshold, recomputes them exactly, and adds
 // the FP64 log-ratios of the unit's rows into the tile partial (thread-owned
-// cells, rows in order).
+// cells, rows in order; `first`: the tile's first unit, which stores instead).
 template <class C, int KERN, class Coef>
 __device__ __forceinline__ void loo_unit_epilogue(const LooArgs& a, const Coef& cf, float* sm, int u,
-                                                  int u_begin, int tile, const float (&At)[4]) {
+                                                  bool first, int tile, const float (&At)[4]) {
     constexpr int JW = C::JW, GG = C::GG, G1 = C::G1v, G2 = C::G2v;
     constexpr double LN2 = 0.69314718055994530942;
     const int tid = threadIdx.x;
@@ -418,7 +477,6 @@ __device__ __forceinline__ void loo_unit_epilogue(const LooArgs& a, const Coef& 
         // ---- FP64 log-ratio; each thread owns whole grid cells (all rows of
         //      the unit, in row order) and adds them to the tile partial ----
         {
-            const bool first = (u == u_begin);
             double* part = a.part + CDE_CK(tile, a.n_tiles, 106) * 2 * GG;
             constexpr int NOWN = GG >= 256 ? GG / 256 : 1;
 #pragma unroll
@@ -484,6 +542,9 @@ struct LooChunked {
     int n_tiles, cmax;
     size_t part_bytes, fb_bytes, bytes;
     int64_t N;
+    int next_l;     // levels < next_l are done
+    int next_m;     // level next_l: units m < next_m of its tiles are done
+    int next_t;     // small tiles: tiles < next_t are done
 };
 int loo_grid_ctas(cde_ctx* ctx, int T1, int T2);
 

@@ -455,7 +455,8 @@ __device__ __forceinline__ void gram_fb_scan(const LooArgs& a, float* sm, int64_
 }
 
 template <int G1, int G2, int KERN, class Coef>
-__device__ __forceinline__ void gram_unit(const LooArgs& a, const Coef& cf, int u, float* sm) {
+__device__ __forceinline__ void gram_unit(const LooArgs& a, const Coef& cf, int u, int tile, bool first,
+                                          float* sm) {
     using C = GramCfg<G1, G2>;
     constexpr int R = C::R, P = C::P, JW = C::JW, MT = C::MT, NT = C::NT, GG = C::GG, NTH = C::kThreads;
     constexpr int LG2 = G2 == 8 ? 3 : (G2 == 16 ? 4 : 5);
@@ -774,13 +775,19 @@ __device__ __forceinline__ void gram_unit(const LooArgs& a, const Coef& cf, int 
             }
         }
     }
-    double* part = a.part + (size_t)CDE_CK(u, a.n_tiles, 126) * 2 * GG;
+    // the tile's partial slot: its first unit stores, the others add in order
+    double* part = a.part + (size_t)CDE_CK(tile, a.n_tiles, 126) * 2 * GG;
 #pragma unroll
     for (int s = 0; s < NOWN; ++s) {
         const int kl = tid + NTH * s;
         if (kl >= GG) continue;
-        part[kl] = sc[s];
-        part[GG + kl] = se[s];
+        if (first) {
+            part[kl] = sc[s];
+            part[GG + kl] = se[s];
+        } else {
+            part[kl] += sc[s];
+            part[GG + kl] += se[s];
+        }
     }
 }
 
@@ -788,6 +795,7 @@ template <int G1, int G2, int KERN>
 __global__ void __launch_bounds__(512, 1) k_loo_gram(const LooArgs a) {
     extern __shared__ float4 sm4[];
     __shared__ int next_tile;
+    __shared__ int ls_u, ls_end, ls_stride, ls_first;
     const CoefParam cf{a};
     for (int t0 = blockIdx.x;; t0 += gridDim.x) {
         __syncthreads();
@@ -795,7 +803,24 @@ __global__ void __launch_bounds__(512, 1) k_loo_gram(const LooArgs a) {
         __syncthreads();
         const int t = next_tile;
         if (t >= a.n_tiles) break;
-        gram_unit<G1, G2, KERN>(a, cf, t, reinterpret_cast<float*>(sm4));
+        // the tile's units; the loop state lives in shared memory (thread 0 advances
+        // it, every thread reads it after a barrier), not in registers through the body
+        if (threadIdx.x == 0) {
+            int u_first, u_stride, u_len;
+            loo_tile_span(a, t, u_first, u_stride, u_len);
+            ls_u = u_first + max(a.win0, 0) * u_stride;
+            ls_end = u_first + min(u_len, a.win1) * u_stride;
+            ls_stride = u_stride;
+            ls_first = u_first;
+        }
+        for (;;) {
+            __syncthreads();
+            const int u = ls_u;
+            if (u >= ls_end) break;
+            gram_unit<G1, G2, KERN>(a, cf, u, next_tile, u == ls_first, reinterpret_cast<float*>(sm4));
+            // (every thread read ls_u before the barriers of the unit's body)
+            if (threadIdx.x == 0) ls_u += ls_stride;
+        }
     }
 }
 

@@ -455,6 +455,7 @@ int loo_grid_ctas(cde_ctx* ctx, int T1, int T2) {
 struct LooPlan {
     bool gram;
     int rpu, upt, n_units, n_tiles, grid;
+    LooTiles tiles;
     size_t part_bytes, fb_bytes;
     size_t bytes() const { return part_bytes + fb_bytes + 256; }
 };
@@ -465,8 +466,9 @@ static LooPlan loo_plan(cde_ctx* ctx, const Dataset& D, int T1, int T2, int64_t 
     p.rpu = p.gram ? loo_gram_rows_per_unit(T1, T2) : 1024 / (T1 * T2);
     p.upt = p.gram ? 1 : loo_units_per_tile(ctx, T1, T2, n_rows);
     p.n_units = (int)((n_rows + p.rpu - 1) / p.rpu);
-    p.n_tiles = (p.n_units + p.upt - 1) / p.upt;
     const int cmax = p.gram ? ctx->sm_count : loo_grid_ctas(ctx, T1, T2);
+    p.tiles = loo_tiles(p.n_units, p.upt, cmax);
+    p.n_tiles = p.tiles.n_tiles;
     p.grid = p.n_tiles < cmax ? p.n_tiles : cmax;
     p.part_bytes = (size_t)p.n_tiles * 2 * T1 * T2 * sizeof(double);
     p.fb_bytes = p.gram ? (size_t)p.grid * loo_gram_fb_bytes_per_cta() : 0;
@@ -505,6 +507,11 @@ int loo_grid_enqueue(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, c
             a.n_units = pl.n_units;
             a.units_per_tile = pl.upt;
             a.n_tiles = pl.n_tiles;
+            a.big_g = pl.tiles.big_g;
+            a.big_levels = pl.tiles.big_levels;
+            a.big_s0 = pl.tiles.big_s0;
+            a.win0 = 0;
+            a.win1 = INT_MAX;
             a.ell_rows = d_ell_rows ? d_ell_rows + (size_t)k0 * G2 + l0 : nullptr;
             a.ell_ld_row = (int64_t)G1 * G2;
             a.ell_ld_k = G2;
@@ -574,10 +581,18 @@ int loo_chunked_create(cde_ctx* ctx, const Dataset& D, const double* h1, int G1,
     a.n_units = pl.n_units;
     a.units_per_tile = pl.upt;
     a.n_tiles = pl.n_tiles;
+    a.big_g = pl.tiles.big_g;
+    a.big_levels = pl.tiles.big_levels;
+    a.big_s0 = pl.tiles.big_s0;
+    a.win0 = 0;
+    a.win1 = INT_MAX;
     a.ell_rows = nullptr;
     a.G1r = G1;
     a.G2r = G2;
     a.tile_base = 0;
+    c->next_l = 0;
+    c->next_m = 0;
+    c->next_t = a.big_levels * a.big_g;
     c->gram = pl.gram;
     c->n_tiles = pl.n_tiles;
     c->cmax = pl.grid;
@@ -591,26 +606,61 @@ int loo_chunked_create(cde_ctx* ctx, const Dataset& D, const double* h1, int G1,
 
 void loo_chunked_destroy(LooChunked* c) { delete c; }
 size_t loo_chunked_scratch_bytes(const LooChunked* c) { return c->bytes; }
-int loo_chunked_tiles(const LooChunked* c) { return c->n_tiles; }
 
-int loo_chunked_tiles_per_launch(const LooChunked* c, double pair_evals) {
-    const double rows = (double)c->a.units_per_tile *
-                        (c->gram ? loo_gram_rows_per_unit(c->T1, c->T2) : 1024 / (c->T1 * c->T2));
-    const double per_tile = rows * (double)c->N * c->T1 * c->T2;
-    double nt = std::ceil(pair_evals / per_tile);
-    if (nt < c->cmax) nt = c->cmax;
-    return nt > c->n_tiles ? c->n_tiles : (int)nt;
-}
-
-int loo_chunked_launch(LooChunked* c, void* scratch, int t0, int t1, cudaStream_t st) {
+// The next launch of the sequence, about `pair_evals` evaluations: the levels of
+// large tiles in order, each either whole (with the levels after it that still
+// fit) or a window of units m at a time in all of its tiles (one CTA per tile,
+// each adding its window to its slot in unit order), then the small tiles in
+// index ranges.  *done is set by the launch that processes the last units.
+int loo_chunked_next(LooChunked* c, void* scratch, double pair_evals, cudaStream_t st, int* done) {
     LooArgs a = c->a;
     a.part = static_cast<double*>(scratch);
     a.fb = reinterpret_cast<double*>(static_cast<char*>(scratch) + c->part_bytes);
     a.work = reinterpret_cast<int*>(static_cast<char*>(scratch) + c->part_bytes + c->fb_bytes);
+    const double rows_per_unit = c->gram ? loo_gram_rows_per_unit(c->T1, c->T2) : 1024.0 / (c->T1 * c->T2);
+    const double per_unit = rows_per_unit * (double)c->N * c->T1 * c->T2;
+    const int G = a.big_g, L = a.big_levels;
+    int t0, t1, grid;
+    if (c->next_l < L) {
+        const int s = a.big_s0 >> c->next_l;
+        if (c->next_m == 0 && per_unit * s * G <= pair_evals) {
+            // whole levels while they fit
+            double budget = pair_evals;
+            int l = c->next_l;
+            while (l < L && per_unit * (a.big_s0 >> l) * G <= budget) budget -= per_unit * (a.big_s0 >> l) * G, ++l;
+            t0 = c->next_l * G;
+            t1 = l * G;
+            c->next_l = l;
+        } else {
+            // a window of units in every tile of the level
+            int w = (int)std::ceil(pair_evals / (per_unit * G));
+            if (w < 1) w = 1;
+            a.win0 = c->next_m;
+            a.win1 = std::min(s, c->next_m + w);
+            t0 = c->next_l * G;
+            t1 = t0 + G;
+            c->next_m = a.win1;
+            if (c->next_m >= s) {
+                ++c->next_l;
+                c->next_m = 0;
+            }
+        }
+        grid = std::min(t1 - t0, c->cmax);
+    } else {
+        // a range of small tiles, at least one per CTA of the full launch
+        const double per_tile = per_unit * a.units_per_tile;
+        double nt = std::ceil(pair_evals / per_tile);
+        if (nt < c->cmax) nt = c->cmax;
+        t0 = c->next_t;
+        t1 = (int)std::min<double>(c->n_tiles, c->next_t + nt);
+        grid = std::min(t1 - t0, c->cmax);
+        c->next_t = t1;
+    }
+    *done = c->next_l >= L && c->next_t >= c->n_tiles;
+    if (t1 <= t0) return CDE_OK;
     a.n_tiles = t1;   // tiles t0 .. t1-1: the queue starts at t0 and stops at t1
     k_set_int<<<1, 1, 0, st>>>(a.work, t0);
     CDE_CUDA(cudaGetLastError());
-    const int grid = (t1 - t0) < c->cmax ? (t1 - t0) : c->cmax;
     return c->gram ? launch_loo_gram(c->T1, c->T2, a, grid, st) : launch_loo_tile_kernel(c->T1, c->T2, a, grid, st);
 }
 

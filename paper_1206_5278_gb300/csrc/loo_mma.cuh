@@ -165,13 +165,27 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt) ca2[nt] = make_float2(cf.a2(8 * nt + g), cf.a2(8 * nt + g));
 
-    const int u_begin = tile * a.units_per_tile;
-    const int u_end = min(a.n_units, u_begin + a.units_per_tile);
+    // this launch's units of the tile (all of them unless a chunked launch gives a
+    // window).  The loop's state lives in shared memory: thread 0 advances it, every
+    // thread reads it after the barrier at the top of the loop, so it holds no
+    // registers through the unit's body (the body runs at the register limit).
+    __shared__ int ls_u, ls_end, ls_stride, ls_first;
+    if (tid == 0) {
+        int u_first, u_stride, u_len;
+        loo_tile_span(a, tile, u_first, u_stride, u_len);
+        ls_u = u_first + max(a.win0, 0) * u_stride;
+        ls_end = u_first + min(u_len, a.win1) * u_stride;
+        ls_stride = u_stride;
+        ls_first = u_first;
+    }
     const int64_t N = a.N, Np = a.Np;
     const int64_t n_chunks = (N + IC - 1) / IC;
 
-    for (int u = u_begin; u < u_end; ++u) {
+    for (;;) {
         __syncthreads();
+        const int u = ls_u;
+        if (u >= ls_end) break;
+        const bool first_u = u == ls_first;
         if (tid < JW) {
             const int64_t r = (int64_t)u * JW + tid;
             const bool v = r < a.n_rows;
@@ -415,7 +429,9 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
             btl_s[e] = log2_wide(s);
         }
         __syncthreads();
-        loo_unit_epilogue<C, KERN>(a, cf, sm, u, u_begin, tile, At);
+        loo_unit_epilogue<C, KERN>(a, cf, sm, u, first_u, tile, At);
+        // (every thread read ls_u before the barriers of the unit's body)
+        if (tid == 0) ls_u += ls_stride;
     }
 }
 

@@ -79,13 +79,24 @@ extern "C" int cde_loo_loglik_noalloc(cde_ctx* ctx, cde_dataset ds, const double
     a.rows = nullptr;
     a.n_rows = D->N;
     a.n_units = (int)((D->N + JW - 1) / JW);
-    // as many tile slots as the scratch holds; tiles grow with N to fit
+    // the tile partition of cde_loo_loglik (at most 3 slots per CTA once N is large);
+    // where its small tiles need more slots than the scratch holds, they grow to fit
     const size_t slot_bytes = (size_t)2 * T1 * T2 * sizeof(double);
     const int max_tiles = (int)((kNoAllocScratchBytes - kNoAllocCounterBytes) / slot_bytes);
+    const int cmax = loo_grid_ctas(ctx, T1, T2);
     int upt = loo_units_per_tile(ctx, T1, T2, D->N);
-    if ((a.n_units + upt - 1) / upt > max_tiles) upt = (a.n_units + max_tiles - 1) / max_tiles;
+    LooTiles tp = loo_tiles(a.n_units, upt, cmax);
+    if (tp.n_tiles > max_tiles) {
+        upt = (a.n_units + max_tiles - 1) / max_tiles;
+        tp = LooTiles{0, 0, 0, (a.n_units + upt - 1) / upt};
+    }
     a.units_per_tile = upt;
-    a.n_tiles = (a.n_units + upt - 1) / upt;
+    a.n_tiles = tp.n_tiles;
+    a.big_g = tp.big_g;
+    a.big_levels = tp.big_levels;
+    a.big_s0 = tp.big_s0;
+    a.win0 = 0;
+    a.win1 = INT_MAX;
     a.ell_rows = nullptr;
     a.G1r = G1;
     a.G2r = G2;
@@ -94,7 +105,6 @@ extern "C" int cde_loo_loglik_noalloc(cde_ctx* ctx, cde_dataset ds, const double
     a.work = reinterpret_cast<int*>(static_cast<char*>(scratch) + kNoAllocScratchBytes - kNoAllocCounterBytes);
     // the array keeps the previous call's contents: the tile counter must start at zero
     CDE_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));
-    const int cmax = loo_grid_ctas(ctx, T1, T2);
     const int grid = a.n_tiles < cmax ? a.n_tiles : cmax;
     // kernel timing (cde_timing_last) covers this call's tile kernel, as in cde_loo_loglik
     timing_reset(ctx);

@@ -51,7 +51,6 @@ struct Job {
     LooChunked* gc = nullptr;
     void* d_grid = nullptr; // the grid's partials and counters
     bool grid_init = false;
-    int t_next = 0;         // first tile of the next range
     bool grid_final = false;  // the final reduction has been enqueued
     cudaEvent_t ev = nullptr;
     // device / pinned buffers
@@ -196,14 +195,12 @@ static int advance(Server& S, Job& J) {
             }
         }
         if (!J.grid_final) {
-            // the next range of tiles: about kSelChunk pair evaluations, so that density
-            // jobs queued meanwhile run between two launches of a long grid
-            const int nt = loo_chunked_tiles_per_launch(J.gc, kSelChunk);
-            const int t1 = std::min(loo_chunked_tiles(J.gc), J.t_next + nt);
-            int rc = loo_chunked_launch(J.gc, J.d_grid, J.t_next, t1, st);
+            // the next part: about kSelChunk pair evaluations, so that density jobs
+            // queued meanwhile run between two launches of a long grid
+            int done = 0;
+            int rc = loo_chunked_next(J.gc, J.d_grid, kSelChunk, st, &done);
             if (rc != CDE_OK) return rc;
-            J.t_next = t1;
-            if (t1 == loo_chunked_tiles(J.gc)) {
+            if (done) {
                 rc = loo_chunked_final(J.gc, J.d_grid, J.d_small, nullptr, st);
                 if (rc != CDE_OK) return rc;
                 J.grid_final = true;
