@@ -216,6 +216,16 @@ int pack_enqueue(Dataset& D, const float* d_x_rowmajor, const float* d_y, cudaSt
 
 // ---- gradient (loo_grad.cu) ----
 // d_rowv (optional, N x 3 doubles) receives per-row {ell_j, d ell_j/d ln h1, d ell_j/d ln h2}.
+// A gradient evaluation in launches over ranges of row blocks (bitwise the
+// single launch's result): create (scratch, stream-ordered), next until *done,
+// then finish (per-row merge, sums into d_out3 if given; frees the sequence) or
+// free on an error.
+struct GradChunked;
+int grad_chunked_create(cde_ctx* ctx, const Dataset& D, double h1, double h2, cudaStream_t st, double* d_rowv_ext,
+                        GradChunked** out);
+int grad_chunked_next(GradChunked* c, double pair_evals, cudaStream_t st, int* done);
+int grad_chunked_finish(cde_ctx* ctx, GradChunked* c, double* d_out3, cudaStream_t st);
+void grad_chunked_free(GradChunked* c, cudaStream_t st);
 int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, double* d_out3,
                      cudaStream_t st, double* d_rowv);
 

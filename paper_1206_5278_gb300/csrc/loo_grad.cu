@@ -54,6 +54,7 @@ struct GradArgs {
     const uint32_t* xsplit;   // d >= 16: TF32 hi words [Np][DK] in the MMA core-matrix layout, then lo
     const float* xnorm;       // d >= 16: |x_i|^2 [Np]
     int* err;                 // the context's device-wait word (k_grad_tc)
+    int64_t bx0;              // first row block of this launch (grid x covers row blocks bx0 ...)
 };
 
 constexpr int kGradThreads = 128;
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
     __shared__ __align__(16) float xt[kGradThreads][DREG];  // point-major: 128-bit broadcast loads
     __shared__ float yt[kGradThreads];
     const int tid = threadIdx.x;
-    const int64_t jbase = (int64_t)blockIdx.x * kGradThreads * JB + tid;
+    const int64_t jbase = ((int64_t)blockIdx.x + g.bx0) * kGradThreads * JB + tid;
     const int64_t i0 = (int64_t)blockIdx.y * g.i_per_split;
     const int64_t i1 = min(g.N, i0 + g.i_per_split);
     const int d = g.d;
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kGradThreads) k_loo_grad(const GradArgs g) {
         __syncthreads();
         const int n = (int)min((int64_t)kGradThreads, i1 - t0);
         // the leave-one-out test is needed only where the tile meets this CTA's rows
-        const int64_t r0 = (int64_t)blockIdx.x * kGradThreads * JB;
+        const int64_t r0 = ((int64_t)blockIdx.x + g.bx0) * kGradThreads * JB;
         const auto body = [&](auto masked) {
             for (int t = 0; t < n; ++t) {
                 const int i32 = (int)(t0 + t);  // N < 2^31
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(kGTThreads, 1) k_grad_tc(const GradArgs g) {
     GradTcSmem<DK>& S = *reinterpret_cast<GradTcSmem<DK>*>(gt_dyn);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t N = g.N, Np = g.Np;
-    const int64_t r0 = (int64_t)blockIdx.x * kGTRows;
+    const int64_t r0 = ((int64_t)blockIdx.x + g.bx0) * kGTRows;
     const int64_t i0 = (int64_t)blockIdx.y * g.i_per_split, i1 = min(N, i0 + g.i_per_split);
     const int ntiles = i0 < i1 ? (int)((i1 - i0 + C::PT - 1) / C::PT) : 0;
     const uint32_t* xh = g.xsplit;
@@ -686,10 +687,27 @@ static int64_t grad_splits(int64_t row_ctas, int64_t tiles, int64_t slots) {
     return best;
 }
 
-int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, double* d_out3,
-                     cudaStream_t st, double* d_rowv_ext) {
-    timing_reset(ctx);
-    GradArgs g{};
+// A gradient evaluation as a sequence of launches over ranges of row blocks.
+// Every (row block, point split) writes its own partial and the per-row
+// merge and the sums run once at the end, so the result does not depend on
+// how the row blocks are split over launches (the request loop runs
+// gradient steps this way, so queued density jobs run in between).
+struct GradChunked {
+    GradArgs g;
+    bool tc, epan;
+    int DREG, DK;
+    int64_t gx, ns, next_bx;
+    int64_t slots;     // resident CTAs of the GPU for this kernel
+    double h1, h2;
+    double* rowv;
+    bool own_rowv;
+    int* fb;
+};
+
+int grad_chunked_create(cde_ctx* ctx, const Dataset& D, double h1, double h2, cudaStream_t st, double* d_rowv_ext,
+                        GradChunked** out) {
+    auto* c = new GradChunked{};
+    GradArgs& g = c->g;
     g.xs = D.xs;
     g.y = D.y;
     g.mx = D.mx;
@@ -698,84 +716,148 @@ int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, doubl
     g.Np = D.Np;
     g.d = D.d;
     const double L2E = 1.4426950408889634074;
-    const bool epan = D.kernel == CDE_KERNEL_EPAN;
-    g.a1 = (float)(epan ? 1.0 / (h1 * h1) : L2E / (2 * h1 * h1));
-    g.a2 = (float)(epan ? 1.0 / (h2 * h2) : L2E / (2 * h2 * h2));
-    const bool tc = D.d >= 16;   // tensor-core cross term
-    const int DREG = D.d <= 4 ? 4 : D.d <= 8 ? 8 : D.d <= 16 ? 16 : D.d <= 32 ? 32 : 64;
-    const int JB = DREG <= 8 ? 4 : DREG <= 32 ? 2 : 1;
-    const int DK = D.d <= 16 ? 16 : D.d <= 32 ? 32 : 64;
-    const int64_t rows_per_cta = tc ? (int64_t)kGTRows : (int64_t)kGradThreads * JB;
-    const int tile = tc ? (DK <= 32 ? 256 : 128) : kGradThreads;
-    const int64_t gx = (D.N + rows_per_cta - 1) / rows_per_cta;
+    c->epan = D.kernel == CDE_KERNEL_EPAN;
+    c->h1 = h1;
+    c->h2 = h2;
+    g.a1 = (float)(c->epan ? 1.0 / (h1 * h1) : L2E / (2 * h1 * h1));
+    g.a2 = (float)(c->epan ? 1.0 / (h2 * h2) : L2E / (2 * h2 * h2));
+    c->tc = D.d >= 16;   // tensor-core cross term
+    c->DREG = D.d <= 4 ? 4 : D.d <= 8 ? 8 : D.d <= 16 ? 16 : D.d <= 32 ? 32 : 64;
+    c->DK = D.d <= 16 ? 16 : D.d <= 32 ? 32 : 64;
+    const int JB = c->DREG <= 8 ? 4 : c->DREG <= 32 ? 2 : 1;
+    const int64_t rows_per_cta = c->tc ? (int64_t)kGTRows : (int64_t)kGradThreads * JB;
+    const int tile = c->tc ? (c->DK <= 32 ? 256 : 128) : kGradThreads;
+    c->gx = (D.N + rows_per_cta - 1) / rows_per_cta;
     const int64_t tiles = (D.N + tile - 1) / tile;
     int64_t ns;
-    if (tc) {
-        ns = grad_splits(gx, tiles, ctx->sm_count);
+    if (c->tc) {
+        c->slots = ctx->sm_count;
     } else {
-        const int per_sm = DREG == 4 ? grad_simt_ctas_per_sm<4, 4>()
-                           : DREG == 8 ? grad_simt_ctas_per_sm<4, 8>() : grad_simt_ctas_per_sm<2, 16>();
-        ns = grad_splits(gx, tiles, (int64_t)per_sm * ctx->sm_count);
+        const int per_sm = c->DREG == 4 ? grad_simt_ctas_per_sm<4, 4>()
+                           : c->DREG == 8 ? grad_simt_ctas_per_sm<4, 8>() : grad_simt_ctas_per_sm<2, 16>();
+        c->slots = (int64_t)per_sm * ctx->sm_count;
     }
+    ns = grad_splits(c->gx, tiles, c->slots);
     if (ns > tiles) ns = tiles;
     if (ns < 1) ns = 1;
     const int64_t tiles_per = (tiles + ns - 1) / ns;
     g.i_per_split = tiles_per * tile;
-    ns = (tiles + tiles_per - 1) / tiles_per;
-    float* part = nullptr;
-    double* rowv = d_rowv_ext;
-    int* fb = nullptr;  // [0] count, then the listed rows
-    CDE_CUDA(cudaMallocAsync((void**)&part, (size_t)ns * D.N * 6 * sizeof(float), st));
-    CDE_CUDA(cudaMallocAsync((void**)&fb, (size_t)(D.N + 1) * sizeof(int), st));
-    CDE_CUDA(cudaMemsetAsync(fb, 0, sizeof(int), st));
-    if (!rowv) CDE_CUDA(cudaMallocAsync((void**)&rowv, (size_t)D.N * 3 * sizeof(double), st));
-    g.part = part;
-    dim3 grid((unsigned)gx, (unsigned)ns);
-    uint32_t* xsplit = nullptr;
-    float* xnorm = nullptr;
-    if (tc) {
-        CDE_CUDA(cudaMallocAsync((void**)&xsplit, (size_t)2 * D.Np * DK * sizeof(uint32_t), st));
-        CDE_CUDA(cudaMallocAsync((void**)&xnorm, (size_t)D.Np * sizeof(float), st));
+    c->ns = (tiles + tiles_per - 1) / tiles_per;
+    c->next_bx = 0;
+    c->rowv = d_rowv_ext;
+    c->own_rowv = d_rowv_ext == nullptr;
+    int rc = CDE_OK;
+    auto fail = [&](cudaError_t e, const char* what) {
+        rc = cuda_error(e, what);
+        return rc;
+    };
+    cudaError_t e = cudaMallocAsync((void**)&g.part, (size_t)c->ns * D.N * 6 * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&c->fb, (size_t)(D.N + 1) * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->fb, 0, sizeof(int), st);
+    if (e == cudaSuccess && c->own_rowv) e = cudaMallocAsync((void**)&c->rowv, (size_t)D.N * 3 * sizeof(double), st);
+    if (e == cudaSuccess && c->tc) {
+        uint32_t* xsplit = nullptr;
+        float* xnorm = nullptr;
+        e = cudaMallocAsync((void**)&xsplit, (size_t)2 * D.Np * c->DK * sizeof(uint32_t), st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&xnorm, (size_t)D.Np * sizeof(float), st);
         g.xsplit = xsplit;
         g.xnorm = xnorm;
         g.err = ctx->d_err + kErrTensorWait;
-        const unsigned sb = (unsigned)(D.Np / 32);
-        if (DK == 16) k_grad_split_tc<16><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
-        else if (DK == 32) k_grad_split_tc<32><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
-        else k_grad_split_tc<64><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
-        CDE_CUDA(cudaGetLastError());
-        timing_begin(ctx, st);
-        const int rl = DK == 16 ? launch_grad_tc<16>(g, grid, st, epan)
-                       : DK == 32 ? launch_grad_tc<32>(g, grid, st, epan)
-                                  : launch_grad_tc<64>(g, grid, st, epan);
-        timing_end(ctx, st);
+        if (e == cudaSuccess) {
+            const unsigned sb = (unsigned)(D.Np / 32);
+            if (c->DK == 16) k_grad_split_tc<16><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
+            else if (c->DK == 32) k_grad_split_tc<32><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
+            else k_grad_split_tc<64><<<sb, 256, 0, st>>>(D.xs, D.Np, D.d, xsplit, xnorm);
+            e = cudaGetLastError();
+        }
+    }
+    if (e != cudaSuccess) {
+        fail(e, "gradient: scratch");
+        grad_chunked_free(c, st);
+        return rc;
+    }
+    *out = c;
+    return CDE_OK;
+}
+
+// Launch the next range of row blocks: about `pair_evals` pairs, and at least
+// enough row blocks to fill the GPU with their point splits; pair_evals <= 0:
+// all the rest.  *done once every row block has been launched.
+int grad_chunked_next(GradChunked* c, double pair_evals, cudaStream_t st, int* done) {
+    const int64_t rows_per_block = c->tc ? (int64_t)kGTRows : (int64_t)kGradThreads * (c->DREG <= 8 ? 4 : c->DREG <= 32 ? 2 : 1);
+    const double per_block = (double)rows_per_block * (double)c->g.N;
+    int64_t nb = c->gx - c->next_bx;
+    if (pair_evals > 0 && pair_evals < per_block * (double)nb) {
+        const int64_t fill = (c->slots + c->ns - 1) / c->ns;
+        nb = std::max<int64_t>((int64_t)std::ceil(pair_evals / per_block), fill);
+        nb = std::min(nb, c->gx - c->next_bx);
+    }
+    GradArgs g = c->g;
+    g.bx0 = c->next_bx;
+    const dim3 grid((unsigned)nb, (unsigned)c->ns);
+    if (c->tc) {
+        const int rl = c->DK == 16 ? launch_grad_tc<16>(g, grid, st, c->epan)
+                       : c->DK == 32 ? launch_grad_tc<32>(g, grid, st, c->epan)
+                                     : launch_grad_tc<64>(g, grid, st, c->epan);
         if (rl != CDE_OK) return rl;
     } else {
-        timing_begin(ctx, st);
-        if (DREG == 4) launch_grad<4, 4>(g, grid, st, epan);
-        else if (DREG == 8) launch_grad<4, 8>(g, grid, st, epan);
-        else launch_grad<2, 16>(g, grid, st, epan);
-        timing_end(ctx, st);
+        if (c->DREG == 4) launch_grad<4, 4>(g, grid, st, c->epan);
+        else if (c->DREG == 8) launch_grad<4, 8>(g, grid, st, c->epan);
+        else launch_grad<2, 16>(g, grid, st, c->epan);
     }
     CDE_CUDA(cudaGetLastError());
-    k_grad_rows<<<(unsigned)((D.N + 255) / 256), 256, 0, st>>>(part, (int)ns, D.N, D.my, g.a2, h1, h2,
-                                                             epan ? 1 : 0, epan_log_norm(1), rowv, fb, fb + 1);
-    CDE_CUDA(cudaGetLastError());
-    if (!epan) {
-        // listed rows only; exits at once when the list is empty
-        k_grad_fallback<<<2 * ctx->sm_count, kFbThreads, 0, st>>>(g, fb, fb + 1, h1, h2, rowv);
-        CDE_CUDA(cudaGetLastError());
-    }
-    if (d_out3) {
-        k_sum_rows3<<<1, 1024, 0, st>>>(rowv, D.N, d_out3);
-        CDE_CUDA(cudaGetLastError());
-    }
-    CDE_CUDA(cudaFreeAsync(part, st));
-    CDE_CUDA(cudaFreeAsync(fb, st));
-    if (xsplit) CDE_CUDA(cudaFreeAsync(xsplit, st));
-    if (xnorm) CDE_CUDA(cudaFreeAsync(xnorm, st));
-    if (!d_rowv_ext) CDE_CUDA(cudaFreeAsync(rowv, st));
+    c->next_bx += nb;
+    *done = c->next_bx >= c->gx;
     return CDE_OK;
+}
+
+void grad_chunked_free(GradChunked* c, cudaStream_t st) {
+    if (!c) return;
+    if (c->g.part) cudaFreeAsync(c->g.part, st);
+    if (c->fb) cudaFreeAsync(c->fb, st);
+    if (c->g.xsplit) cudaFreeAsync(const_cast<uint32_t*>(c->g.xsplit), st);
+    if (c->g.xnorm) cudaFreeAsync(const_cast<float*>(c->g.xnorm), st);
+    if (c->own_rowv && c->rowv) cudaFreeAsync(c->rowv, st);
+    delete c;
+}
+
+// After the last range: the per-row merge, the exact recomputation of listed
+// rows, and (d_out3) the fixed-order sums; frees the sequence.
+int grad_chunked_finish(cde_ctx* ctx, GradChunked* c, double* d_out3, cudaStream_t st) {
+    const GradArgs& g = c->g;
+    k_grad_rows<<<(unsigned)((g.N + 255) / 256), 256, 0, st>>>(g.part, (int)c->ns, g.N, g.my, g.a2, c->h1, c->h2,
+                                                             c->epan ? 1 : 0, epan_log_norm(1), c->rowv, c->fb,
+                                                             c->fb + 1);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !c->epan) {
+        // listed rows only; exits at once when the list is empty
+        k_grad_fallback<<<2 * ctx->sm_count, kFbThreads, 0, st>>>(g, c->fb, c->fb + 1, c->h1, c->h2, c->rowv);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && d_out3) {
+        k_sum_rows3<<<1, 1024, 0, st>>>(c->rowv, g.N, d_out3);
+        e = cudaGetLastError();
+    }
+    grad_chunked_free(c, st);
+    if (e != cudaSuccess) return cuda_error(e, "gradient: final kernels");
+    return CDE_OK;
+}
+
+int loo_grad_enqueue(cde_ctx* ctx, const Dataset& D, double h1, double h2, double* d_out3,
+                     cudaStream_t st, double* d_rowv_ext) {
+    timing_reset(ctx);
+    GradChunked* c = nullptr;
+    int rc = grad_chunked_create(ctx, D, h1, h2, st, d_rowv_ext, &c);
+    if (rc != CDE_OK) return rc;
+    int done = 0;
+    timing_begin(ctx, st);
+    rc = grad_chunked_next(c, 0.0, st, &done);   // all row blocks in one launch
+    timing_end(ctx, st);
+    if (rc != CDE_OK) {
+        grad_chunked_free(c, st);
+        return rc;
+    }
+    return grad_chunked_finish(ctx, c, d_out3, st);
 }
 
 #ifdef CDE_CHECKS

@@ -35,6 +35,8 @@ using Clock = std::chrono::steady_clock;
 // pair evaluations (N^2 G1 G2 units) per launch of a selection job's grid: about
 // 10 ms of the grid kernel, the longest a density job waits behind it
 constexpr double kSelChunk = 2.5e11;
+// pairs per launch of a gradient step (about 10 ms of the gradient kernel at d = 8)
+constexpr double kGradChunk = 1.2e10;
 
 struct Job {
     int64_t ticket = 0;
@@ -52,6 +54,9 @@ struct Job {
     void* d_grid = nullptr; // the grid's partials and counters
     bool grid_init = false;
     bool grid_final = false;  // the final reduction has been enqueued
+    // the running gradient step in ranges of row blocks (one launch per scheduling step)
+    GradChunked* gr = nullptr;
+    bool step_final = false;  // the step's per-row merge and sums have been enqueued
     cudaEvent_t ev = nullptr;
     // device / pinned buffers
     float* d_xq = nullptr;
@@ -131,6 +136,8 @@ static void release(Server& S, Job& J) {
     J.d_grid = nullptr;
     if (J.gc) loo_chunked_destroy(J.gc);
     J.gc = nullptr;
+    if (J.gr) grad_chunked_free(J.gr, st);
+    J.gr = nullptr;
     J.d_xq = J.d_yg = J.d_f = nullptr;
     J.d_small = nullptr;
     J.h_f = J.h_in = nullptr;
@@ -209,10 +216,24 @@ static int advance(Server& S, Job& J) {
         if (J.grid_final)
             CDE_CUDA(cudaMemcpyAsync(J.h_small, J.d_small, g * sizeof(double), cudaMemcpyDeviceToHost, st));
     } else {
+        // a gradient step in ranges of row blocks of about kGradChunk pairs each
         const size_t g = (size_t)r.G1 * r.G2;
-        int rc = loo_grad_enqueue(S.ctx, D, std::exp(J.th[0]), std::exp(J.th[1]), J.d_small + g, st, nullptr);
+        if (!J.gr) {
+            int rc = grad_chunked_create(S.ctx, D, std::exp(J.th[0]), std::exp(J.th[1]), st, nullptr, &J.gr);
+            if (rc != CDE_OK) return rc;
+            J.step_final = false;
+        }
+        int done = 0;
+        int rc = grad_chunked_next(J.gr, kGradChunk, st, &done);
         if (rc != CDE_OK) return rc;
-        CDE_CUDA(cudaMemcpyAsync(J.h_small + g, J.d_small + g, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (done) {
+            GradChunked* c = J.gr;
+            J.gr = nullptr;
+            rc = grad_chunked_finish(S.ctx, c, J.d_small + g, st);
+            if (rc != CDE_OK) return rc;
+            J.step_final = true;
+            CDE_CUDA(cudaMemcpyAsync(J.h_small + g, J.d_small + g, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
     }
     CDE_CUDA(cudaEventCreateWithFlags(&J.ev, cudaEventDisableTiming));
     CDE_CUDA(cudaEventRecord(J.ev, st));
@@ -231,6 +252,7 @@ static bool on_event(Server& S, Job& J) {
     const size_t g = (size_t)r.G1 * r.G2;
     const double N = (double)J.D->N;
     if (J.phase == 0 && !J.grid_final) return false;   // more ranges of the grid to launch
+    if (J.phase > 0 && !J.step_final) return false;    // more row blocks of the gradient step
     if (J.phase == 0) {
         int bk = 0;
         for (size_t c = 1; c < g; ++c)

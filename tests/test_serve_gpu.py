@@ -183,6 +183,13 @@ def test_large_dataset_in_the_mix_and_served_results_match_oracle(ctx, datasets)
     Lgrid = mix_vals[1][4:].reshape(16, 16)
     Lc, _ = cde.cde_loo_loglik(ctx, big, h1g, h2g)
     assert np.array_equal(Lgrid, Lc)
+    # the gradient steps run in launches over ranges of row blocks: where the best L
+    # came from a step, it is the single-launch gradient's L at those bandwidths
+    h1b, h2b, Lb, Lgb = mix_vals[1][:4]
+    if Lb > Lgb:
+        assert cde.cde_loo_grad(ctx, big, h1b, h2b)[0] == Lb
+    else:
+        assert Lb == Lgb == Lc.max()
     rows = np.random.default_rng(1).choice(300000, 8, replace=False)
     g = cde.cde_loo_rows(ctx, big, h1g, h2g, rows)
     ref_rows, _ = oracle.loo_rows(xb, yb, h1g, h2g, rows=rows, standardize_x=True)
