@@ -319,58 +319,110 @@ __device__ __forceinline__ void loo_tile_mma(const LooArgs& a, const Coef& cf, i
                     const float4 q1 = *reinterpret_cast<const float4*>(tt + r * 3 * IC + 2 * (8 * s + 2 * t));
                     const float2 t1p0 = make_float2(q1.x, q1.y), t1p1 = make_float2(q1.z, q1.w);
                     const float2 t2p = *reinterpret_cast<const float2*>(tt + r * 3 * IC + 2 * IC + 8 * s + 2 * t);
-                    // B fragments: w(l, p0) in register 0, w(l, p1) in register 1 (TF32);
-                    // BF16: register 0 = lo w at (p0, p1), register 1 = hi w at (p0, p1)
-                    uint32_t bh[NT][2], bx[NT][2];
+                    // Two orders of the k-step, the faster one per kernel and shape (measured at
+                    // N = 50,000): all B fragments, all A fragments, then the 16 MMAs; or the A
+                    // fragments, then per N tile its B fragment and its MMAs, which spreads the
+                    // MMAs over the factor work (Epanechnikov 32 x 32: 57.6 -> 55.2 ms; Gaussian
+                    // 16 x 16: 23.25 -> 23.0 ms; Gaussian 32 x 32 59.1 -> 59.9 ms, so not there)
+                    constexpr bool kSpread = KERN == 1 || GG == 256;
+                    if constexpr (!kSpread) {
+                        // B fragments: w(l, p0) in register 0, w(l, p1) in register 1 (TF32);
+                        // BF16: register 0 = lo w at (p0, p1), register 1 = hi w at (p0, p1)
+                        uint32_t bh[NT][2], bx[NT][2];
+    #pragma unroll
+                        for (int nt = 0; nt < NT; ++nt) {
+                            // Gaussian: w' = w / r, lo = w' r - hi (signed); Epanechnikov: lo = w - hi
+                            const float2 w = KERN == 0 ? gauss_factor2(ca2[nt], t2p, kWc)
+                                                       : kernel_factor2<KERN>(ca2[nt], t2p);
+                            const float2 h = make_float2(__uint_as_float(__float_as_uint(w.x) & 0xffffe000u),
+                                                         __uint_as_float(__float_as_uint(w.y) & 0xffffe000u));
+                            const float2 l = KERN == 0 ? __ffma2_rn(w, make_float2(kWr, kWr), make_float2(-h.x, -h.y))
+                                                       : __ffma2_rn(h, make_float2(-1.f, -1.f), w);
+                            bh[nt][0] = __float_as_uint(h.x);
+                            bh[nt][1] = __float_as_uint(h.y);
+                            bx[nt][0] = pack_bf16x2(l.x, l.y);
+                            bx[nt][1] = pack_bf16x2(h.x, h.y);
+                        }
+                        // A fragments: TF32 (k, p0), (k+8, p0), (k, p1), (k+8, p1);
+                        // BF16 columns 2t, 2t+1 hold hi u at (p0, p1), columns 2t+8, 2t+9 lo u
+                        uint32_t ah[MT][4], ax[MT][4];
+    #pragma unroll
+                        for (int mt = 0; mt < MT; ++mt) {
+                            // (k, p0), (k+8, p0) and (k, p1), (k+8, p1)
+                            const float2 u0 = KERN == 0 ? gauss_factor2(ca1[mt], t1p0, kEx2Fix)
+                                                        : kernel_factor2<KERN>(ca1[mt], t1p0);
+                            const float2 u1 = KERN == 0 ? gauss_factor2(ca1[mt], t1p1, kEx2Fix)
+                                                        : kernel_factor2<KERN>(ca1[mt], t1p1);
+                            bt[r][mt] = __fadd2_rn(bt[r][mt], __fadd2_rn(u0, u1));
+                            const float2 h0 = make_float2(__uint_as_float(__float_as_uint(u0.x) & 0xffffe000u),
+                                                          __uint_as_float(__float_as_uint(u0.y) & 0xffffe000u));
+                            const float2 h1 = make_float2(__uint_as_float(__float_as_uint(u1.x) & 0xffffe000u),
+                                                          __uint_as_float(__float_as_uint(u1.y) & 0xffffe000u));
+                            const float2 l0 = __ffma2_rn(h0, make_float2(-1.f, -1.f), u0);
+                            const float2 l1 = __ffma2_rn(h1, make_float2(-1.f, -1.f), u1);
+                            ah[mt][0] = __float_as_uint(h0.x);
+                            ah[mt][1] = __float_as_uint(h0.y);
+                            ah[mt][2] = __float_as_uint(h1.x);
+                            ah[mt][3] = __float_as_uint(h1.y);
+                            ax[mt][0] = pack_bf16x2(h0.x, h1.x);
+                            ax[mt][1] = pack_bf16x2(h0.y, h1.y);
+                            ax[mt][2] = pack_bf16x2(l0.x, l1.x);
+                            ax[mt][3] = pack_bf16x2(l0.y, l1.y);
+                        }
+                        // hi*hi on TF32; hi*lo + lo*hi together on one BF16 k16 MMA
+    #pragma unroll
+                        for (int mt = 0; mt < MT; ++mt)
+    #pragma unroll
+                            for (int nt = 0; nt < NT; ++nt) mma_tf32(D[r][mt][nt], ah[mt], bh[nt][0], bh[nt][1]);
+    #pragma unroll
+                        for (int mt = 0; mt < MT; ++mt)
+    #pragma unroll
+                            for (int nt = 0; nt < NT; ++nt) mma_bf16(D[r][mt][nt], ax[mt], bx[nt][0], bx[nt][1]);
+                    } else {
+                        // A fragments: TF32 (k, p0), (k+8, p0), (k, p1), (k+8, p1);
+                        // BF16 columns 2t, 2t+1 hold hi u at (p0, p1), columns 2t+8, 2t+9 lo u
+                        uint32_t ah[MT][4], ax[MT][4];
+    #pragma unroll
+                        for (int mt = 0; mt < MT; ++mt) {
+                            // (k, p0), (k+8, p0) and (k, p1), (k+8, p1)
+                            const float2 u0 = KERN == 0 ? gauss_factor2(ca1[mt], t1p0, kEx2Fix)
+                                                        : kernel_factor2<KERN>(ca1[mt], t1p0);
+                            const float2 u1 = KERN == 0 ? gauss_factor2(ca1[mt], t1p1, kEx2Fix)
+                                                        : kernel_factor2<KERN>(ca1[mt], t1p1);
+                            bt[r][mt] = __fadd2_rn(bt[r][mt], __fadd2_rn(u0, u1));
+                            const float2 h0 = make_float2(__uint_as_float(__float_as_uint(u0.x) & 0xffffe000u),
+                                                          __uint_as_float(__float_as_uint(u0.y) & 0xffffe000u));
+                            const float2 h1 = make_float2(__uint_as_float(__float_as_uint(u1.x) & 0xffffe000u),
+                                                          __uint_as_float(__float_as_uint(u1.y) & 0xffffe000u));
+                            const float2 l0 = __ffma2_rn(h0, make_float2(-1.f, -1.f), u0);
+                            const float2 l1 = __ffma2_rn(h1, make_float2(-1.f, -1.f), u1);
+                            ah[mt][0] = __float_as_uint(h0.x);
+                            ah[mt][1] = __float_as_uint(h0.y);
+                            ah[mt][2] = __float_as_uint(h1.x);
+                            ah[mt][3] = __float_as_uint(h1.y);
+                            ax[mt][0] = pack_bf16x2(h0.x, h1.x);
+                            ax[mt][1] = pack_bf16x2(h0.y, h1.y);
+                            ax[mt][2] = pack_bf16x2(l0.x, l1.x);
+                            ax[mt][3] = pack_bf16x2(l0.y, l1.y);
+                        }
+                        // per N tile: its B fragments, then its MMAs (same order per accumulator:
+                        // TF32 hi*hi, then the BF16 cross terms)
 #pragma unroll
-                    for (int nt = 0; nt < NT; ++nt) {
-                        // Gaussian: w' = w / r, lo = w' r - hi (signed); Epanechnikov: lo = w - hi
-                        const float2 w = KERN == 0 ? gauss_factor2(ca2[nt], t2p, kWc)
-                                                   : kernel_factor2<KERN>(ca2[nt], t2p);
-                        const float2 h = make_float2(__uint_as_float(__float_as_uint(w.x) & 0xffffe000u),
-                                                     __uint_as_float(__float_as_uint(w.y) & 0xffffe000u));
-                        const float2 l = KERN == 0 ? __ffma2_rn(w, make_float2(kWr, kWr), make_float2(-h.x, -h.y))
-                                                   : __ffma2_rn(h, make_float2(-1.f, -1.f), w);
-                        bh[nt][0] = __float_as_uint(h.x);
-                        bh[nt][1] = __float_as_uint(h.y);
-                        bx[nt][0] = pack_bf16x2(l.x, l.y);
-                        bx[nt][1] = pack_bf16x2(h.x, h.y);
+                        for (int nt = 0; nt < NT; ++nt) {
+                            const float2 w = KERN == 0 ? gauss_factor2(ca2[nt], t2p, kWc)
+                                                       : kernel_factor2<KERN>(ca2[nt], t2p);
+                            const float2 h = make_float2(__uint_as_float(__float_as_uint(w.x) & 0xffffe000u),
+                                                         __uint_as_float(__float_as_uint(w.y) & 0xffffe000u));
+                            const float2 l = KERN == 0 ? __ffma2_rn(w, make_float2(kWr, kWr), make_float2(-h.x, -h.y))
+                                                       : __ffma2_rn(h, make_float2(-1.f, -1.f), w);
+                            const uint32_t bh0 = __float_as_uint(h.x), bh1 = __float_as_uint(h.y);
+                            const uint32_t bx0 = pack_bf16x2(l.x, l.y), bx1 = pack_bf16x2(h.x, h.y);
+#pragma unroll
+                            for (int mt = 0; mt < MT; ++mt) mma_tf32(D[r][mt][nt], ah[mt], bh0, bh1);
+#pragma unroll
+                            for (int mt = 0; mt < MT; ++mt) mma_bf16(D[r][mt][nt], ax[mt], bx0, bx1);
+                        }
                     }
-                    // A fragments: TF32 (k, p0), (k+8, p0), (k, p1), (k+8, p1);
-                    // BF16 columns 2t, 2t+1 hold hi u at (p0, p1), columns 2t+8, 2t+9 lo u
-                    uint32_t ah[MT][4], ax[MT][4];
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt) {
-                        // (k, p0), (k+8, p0) and (k, p1), (k+8, p1)
-                        const float2 u0 = KERN == 0 ? gauss_factor2(ca1[mt], t1p0, kEx2Fix)
-                                                    : kernel_factor2<KERN>(ca1[mt], t1p0);
-                        const float2 u1 = KERN == 0 ? gauss_factor2(ca1[mt], t1p1, kEx2Fix)
-                                                    : kernel_factor2<KERN>(ca1[mt], t1p1);
-                        bt[r][mt] = __fadd2_rn(bt[r][mt], __fadd2_rn(u0, u1));
-                        const float2 h0 = make_float2(__uint_as_float(__float_as_uint(u0.x) & 0xffffe000u),
-                                                      __uint_as_float(__float_as_uint(u0.y) & 0xffffe000u));
-                        const float2 h1 = make_float2(__uint_as_float(__float_as_uint(u1.x) & 0xffffe000u),
-                                                      __uint_as_float(__float_as_uint(u1.y) & 0xffffe000u));
-                        const float2 l0 = __ffma2_rn(h0, make_float2(-1.f, -1.f), u0);
-                        const float2 l1 = __ffma2_rn(h1, make_float2(-1.f, -1.f), u1);
-                        ah[mt][0] = __float_as_uint(h0.x);
-                        ah[mt][1] = __float_as_uint(h0.y);
-                        ah[mt][2] = __float_as_uint(h1.x);
-                        ah[mt][3] = __float_as_uint(h1.y);
-                        ax[mt][0] = pack_bf16x2(h0.x, h1.x);
-                        ax[mt][1] = pack_bf16x2(h0.y, h1.y);
-                        ax[mt][2] = pack_bf16x2(l0.x, l1.x);
-                        ax[mt][3] = pack_bf16x2(l0.y, l1.y);
-                    }
-                    // hi*hi on TF32; hi*lo + lo*hi together on one BF16 k16 MMA
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < NT; ++nt) mma_tf32(D[r][mt][nt], ah[mt], bh[nt][0], bh[nt][1]);
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < NT; ++nt) mma_bf16(D[r][mt][nt], ax[mt], bx[nt][0], bx[nt][1]);
                 }
             }
 #pragma unroll
