@@ -431,6 +431,8 @@ typedef struct {
     double p50_density_ms, p99_density_ms, p50_select_ms, p99_select_ms;
     double busy_s;                       /* wall time with >= 1 job on the device */
     int64_t peak_concurrent;             /* most jobs admitted at once */
+    int64_t peak_selection;              /* most selection jobs admitted at once (at most half
+                                            of the stream slots, at least one) */
 } cde_server_stats;
 
 int cde_server_stats_get(cde_ctx *ctx, cde_server_stats *out);

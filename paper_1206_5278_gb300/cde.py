@@ -73,7 +73,7 @@ class cde_server_stats(ctypes.Structure):
                 ("mean_ms", ctypes.c_double), ("p50_density_ms", ctypes.c_double),
                 ("p99_density_ms", ctypes.c_double), ("p50_select_ms", ctypes.c_double),
                 ("p99_select_ms", ctypes.c_double), ("busy_s", ctypes.c_double),
-                ("peak_concurrent", _i64)]
+                ("peak_concurrent", _i64), ("peak_selection", _i64)]
 
 
 class cde_peaks(ctypes.Structure):

@@ -4,14 +4,14 @@
 // bandwidth-selection jobs (LOO grid search, then Adam ascent on
 // (ln h1, ln h2) driven by the adjoint kernel).  One scheduler thread admits
 // queued jobs while a stream slot and the job-memory budget allow (a job that
-// does not fit waits; smaller later jobs may pass it; selection jobs leave the
-// last free slot to density jobs, run their grid as ~10 ms launches over tile
-// ranges, and run on low-priority streams, so density queries are not held up
-// by long selections), enqueues their kernels
+// does not fit waits; smaller later jobs may pass it; selection jobs take at
+// most half of the slots and never the last free one, run their grid and
+// their gradient steps as ~10 ms launches, and run on low-priority streams, so
+// density queries are not held up by long selections), enqueues their kernels
 // on the slot's stream so admitted jobs overlap on the device, and polls
-// completion events.  A selection job is a small state machine: every range
-// of its grid's tiles and every gradient step is one enqueue (the grid's tiles
-// write fixed partial slots, so its result is bitwise that of one launch); the host update between
+// completion events.  A selection job is a small state machine: every part
+// of its grid and of each gradient step is one enqueue (each writes fixed
+// partial slots, so the result is bitwise that of one launch); the host update between
 // steps happens when its event completes, so the device keeps running other
 // jobs meanwhile.  Every kernel is deterministic and partitions work by the
 // job's own sizes only, so a job's result is the same alone and in the mix.
@@ -92,7 +92,7 @@ struct Server {
     std::thread th;
     // stats
     std::vector<double> lat_all, lat_den, lat_sel;
-    int64_t completed = 0, cancelled = 0, failed = 0, peak = 0;
+    int64_t completed = 0, cancelled = 0, failed = 0, peak = 0, peak_sel = 0;
     double busy_s = 0;
     Clock::time_point busy_since;
 };
@@ -354,8 +354,11 @@ static void loop(Server* Sp) {
                 ++k;
             }
         }
-        // 2) admissions (by free slot and job memory); the last free slot is kept
-        //    for density jobs, so that short queries never queue behind selections
+        // 2) admissions (by free slot and job memory).  Selection jobs take at most
+        //    half of the slots (at least one): they are GPU-bound for seconds and gain
+        //    little from running side by side, while density jobs arriving meanwhile
+        //    then find a slot, and several of them can run at once
+        const int sel_cap = std::max<int>(1, (int)S.slot_busy.size() / 2);
         for (auto it = S.queue.begin(); it != S.queue.end();) {
             int slot = -1, n_free = 0;
             for (size_t s = 0; s < S.slot_busy.size(); ++s)
@@ -365,9 +368,13 @@ static void loop(Server* Sp) {
                 }
             if (slot < 0) break;
             auto J = *it;
-            if (J->req.kind != CDE_REQ_DENSITY && n_free == 1 && S.slot_busy.size() > 1) {
-                ++it;  // a density job behind it may take the slot
-                continue;
+            if (J->req.kind != CDE_REQ_DENSITY) {
+                int n_sel = 0;
+                for (const auto& R : S.running) n_sel += R->req.kind != CDE_REQ_DENSITY;
+                if (n_sel >= sel_cap || (n_free == 1 && S.slot_busy.size() > 1)) {
+                    ++it;  // a density job behind it may take the slot
+                    continue;
+                }
             }
             if (S.mem_used + J->mem > S.mem_budget && !S.running.empty()) {
                 ++it;  // does not fit now; a smaller job behind it may
@@ -390,6 +397,9 @@ static void loop(Server* Sp) {
             }
             S.running.push_back(J);
             S.peak = std::max<int64_t>(S.peak, (int64_t)S.running.size());
+            int64_t n_sel = 0;
+            for (const auto& R : S.running) n_sel += R->req.kind != CDE_REQ_DENSITY;
+            S.peak_sel = std::max(S.peak_sel, n_sel);
         }
         if (S.stop && S.running.empty()) break;
         // 3) wait: briefly when jobs run (poll their events), else for work
@@ -585,6 +595,7 @@ int cde_server_stats_get(cde_ctx* ctx, cde_server_stats* out) {
     if (!S->running.empty()) busy += std::chrono::duration<double>(Clock::now() - S->busy_since).count();
     out->busy_s = busy;
     out->peak_concurrent = S->peak;
+    out->peak_selection = S->peak_sel;
     return CDE_OK;
 }
 
@@ -596,7 +607,7 @@ int cde_server_stats_reset(cde_ctx* ctx) {
     S->lat_all.clear();
     S->lat_den.clear();
     S->lat_sel.clear();
-    S->completed = S->cancelled = S->failed = S->peak = 0;
+    S->completed = S->cancelled = S->failed = S->peak = S->peak_sel = 0;
     S->busy_s = 0;
     if (!S->running.empty()) S->busy_since = Clock::now();
     // forget finished tickets

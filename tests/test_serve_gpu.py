@@ -123,6 +123,27 @@ def test_queue_full_cancel_timeout_and_budget(ctx, datasets):
         srv.stop()
 
 
+def test_selections_take_at_most_half_of_the_slots(ctx, datasets):
+    """Four selection jobs and density jobs on a 4-slot server: at most two
+    selections run at once, density jobs still run beside them, and every job
+    completes with the result it has alone."""
+    jobs = [("s", datasets[b % len(datasets)][0], (synth.bandwidth_grid(0.05, 2.0, 8),
+                                               synth.bandwidth_grid(0.01, 1.0, 8), 3, 0.05)) for b in range(4)]
+    jobs += _jobs(datasets, 6, seed=21)
+    srv = Server(ctx, n_streams=4)
+    try:
+        mix = [_submit(srv, j) for j in jobs]
+        mix_vals = [_val(t) for t in mix]
+        st = srv.stats()
+        assert st["completed"] == len(jobs) and st["failed"] == 0
+        assert 1 <= st["peak_selection"] <= 2
+        alone_vals = [_val(_submit(srv, j)) for j in jobs[:4]]
+    finally:
+        srv.stop()
+    for a, b in zip(mix_vals[:4], alone_vals):
+        assert np.array_equal(a, b)
+
+
 def test_admission_by_memory_limits_concurrency(ctx, datasets):
     import torch
     ds, (x, y) = datasets[0]
