@@ -258,7 +258,9 @@ int cde_density(cde_ctx *ctx, cde_dataset ds, double h1, double h2, const float 
  *   doubles), outputs L_cond_out[b] / L_eq3_out[b] (G1[b] x G2[b] doubles, host;
  *   either array of pointers, or an entry, may be NULL).  Every G must be
  *   <= 32.  The result of each dataset is bitwise identical to
- *   cde_loo_loglik on that dataset alone.
+ *   cde_loo_loglik on that dataset alone.  Datasets with d_x >= 16 (whose
+ *   single launch uses the Gram-form distance kernel) are run by that launch,
+ *   one per dataset, before the batched graph of the others.
  */
 int cde_loo_loglik_batch(cde_ctx *ctx, int n, const cde_dataset *ds, const double *const *h1,
                          const int *G1, const double *const *h2, const int *G2,

@@ -498,9 +498,25 @@ extern "C" int cde_loo_loglik_batch(cde_ctx* ctx, int n, const cde_dataset* ds, 
     }
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     CDE_CUDA(cudaSetDevice(ctx->device));
-    const int rc = autotune_batch_shapes(ctx, items);
+    // Datasets whose single launch runs on the d >= 16 kernel (Gram-form distances)
+    // take that launch, one per dataset, so that their results stay those of
+    // cde_loo_loglik; the others share the batched graph of the direct tile body.
+    std::vector<BatchItem> bitems;
+    std::vector<double*> bLc, bLe;
+    for (int b = 0; b < n; ++b) {
+        if (loo_use_gram(*items[b].D, loo_pad1(G1[b]), loo_pad2(G2[b]))) {
+            const int rc = cde_loo_loglik(ctx, ds[b], h1[b], G1[b], h2[b], G2[b], Lc[b], Le[b], 0, stream);
+            if (rc != CDE_OK) return rc;
+        } else {
+            bitems.push_back(items[b]);
+            bLc.push_back(Lc[b]);
+            bLe.push_back(Le[b]);
+        }
+    }
+    if (bitems.empty()) return CDE_OK;
+    const int rc = autotune_batch_shapes(ctx, bitems);
     if (rc != CDE_OK) return rc;
-    return loo_batch_run(ctx, items, Lc, Le, pick_stream(ctx, stream));
+    return loo_batch_run(ctx, bitems, bLc, bLe, pick_stream(ctx, stream));
 }
 
 extern "C" int cde_autotune(cde_ctx* ctx, cde_dataset ds, const double* h1, int G1, const double* h2, int G2,

@@ -97,6 +97,27 @@ def keep_tuning(ctx, tmp_path):
     cde.cde_tuning_load(ctx, path)
 
 
+def test_batch_with_high_dimensional_datasets(ctx):
+    """Datasets with d_x >= 16 (their single launch uses the Gram-form kernel)
+    next to low-dimensional ones: every member bitwise equal to its single
+    launch, and a d = 20 member's grid against the oracle."""
+    items = []
+    for b, (N, d) in enumerate([(900, 20), (1500, 3), (700, 16), (1200, 8)]):
+        x, y = synth.gmm_sine(N, d, seed=40 + b)
+        items.append((x, y, synth.bandwidth_grid(0.1, 2.0, 16), synth.bandwidth_grid(0.02, 1.0, 16)))
+    dss = [cde.cde_create_dataset(ctx, x, y, standardize=True) for x, y, _, _ in items]
+    Lc, Le = cde.cde_loo_loglik_batch(ctx, dss, [it[2] for it in items], [it[3] for it in items])
+    for b, (ds, it) in enumerate(zip(dss, items)):
+        sc, se = cde.cde_loo_loglik(ctx, ds, it[2], it[3])
+        assert np.array_equal(sc, Lc[b]) and np.array_equal(se, Le[b]), b
+    x, y, h1, h2 = items[0]
+    ell, _ = oracle.loo_rows(x, y, h1, h2, standardize_x=True)
+    err = np.abs(Lc[0] - ell.sum(0)) / np.abs(ell).sum(0)
+    assert err.max() <= 1e-5, err.max()
+    for ds in dss:
+        cde.cde_destroy_dataset(ctx, ds)
+
+
 def test_autotune_keeps_paths_identical(ctx, keep_tuning):
     """The tuned configuration (rows per tile, CTAs per SM) is read by both
     launch paths, which stay bitwise the same and meet the oracle."""
