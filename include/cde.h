@@ -194,7 +194,10 @@ int cde_loo_loglik(cde_ctx *ctx, cde_dataset ds, const double *h1, int G1, const
  * loop in which cudaMalloc/cudaFree may synchronise the device and stall other
  * work, or a host that forbids allocation calls to the plugins it loads.
  *   Same scores as cde_loo_loglik (up to the order of FP64 additions) for one
- *   grid of at most 32 x 32 bandwidths; larger grids give CDE_EINVAL.
+ *   grid of at most 32 x 32 bandwidths; larger grids give CDE_EINVAL.  For
+ *   d_x >= 16 this entry point forms the squared distances directly (the
+ *   Gram-form kernel of cde_loo_loglik needs a per-CTA buffer larger than the
+ *   fixed scratch), so the two agree within the FP32 distance precision there.
  *   d_L_cond, d_L_eq3: caller-owned DEVICE arrays of G1 x G2 doubles (either
  *   may be NULL); the call only enqueues work on `stream` (NULL: the context's
  *   stream) and returns.

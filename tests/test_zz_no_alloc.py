@@ -54,6 +54,28 @@ def test_noalloc_matches_existing_entry_point_twice(ctx, N, G1, G2, std):
     cde.cde_destroy_dataset(ctx, ds)
 
 
+def test_noalloc_high_dimension_matches_oracle(ctx):
+    """d_x = 20: the allocation-free launch forms distances directly (the
+    Gram-form kernel's buffer does not fit its scratch); its grid against the
+    FP64 oracle and against cde_loo_loglik, within the score tolerance."""
+    import torch
+    from oracle import oracle
+    x, y = synth.gmm_sine(1100, 20, seed=77)
+    h1, h2 = synth.bandwidth_grid(0.1, 2.0, 16), synth.bandwidth_grid(0.02, 1.0, 16)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    Lc = torch.empty(16 * 16, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    cde.cde_loo_loglik_noalloc(ctx, ds, h1, h2, Lc, None, stream=s)
+    s.synchronize()
+    got = Lc.cpu().numpy().reshape(16, 16)
+    ell, _ = oracle.loo_rows(x, y, h1, h2, standardize_x=True)
+    scale = np.abs(ell).sum(0)
+    assert np.max(np.abs(got - ell.sum(0)) / scale) <= 1e-5
+    ref, _ = cde.cde_loo_loglik(ctx, ds, h1, h2)
+    assert np.max(np.abs(got - ref) / scale) <= 1e-5
+    cde.cde_destroy_dataset(ctx, ds)
+
+
 def test_noalloc_rejects_grid_beyond_limit(ctx):
     import torch
     x, y = synth.random_small(100, 2, 1)
