@@ -152,6 +152,18 @@ int cde_dataset_nn(cde_ctx *ctx, cde_dataset ds, float *nn_x2, float *nn_y2);
 int cde_dataset_nn_other(cde_ctx *ctx, cde_dataset ds, float *other_x2, float *other_y2);
 
 /*
+ * The tile partition of a LOO launch (host query, no GPU needed): n_units units
+ * (rows / rows per unit), units_per_tile units per small tile, ctas resident
+ * CTAs of the launch.  Writes the number of tiles; for tile >= 0 also its units
+ * unit_first + m * unit_stride, m < unit_count, added to the tile's FP64 slot in
+ * that order.  Every tile's units are distinct and together they are 0 ..
+ * n_units - 1.  Any output may be NULL.  (The same code the kernels run; the
+ * result of a launch depends on this partition only.)
+ */
+int cde_loo_tile_partition(int64_t n_units, int units_per_tile, int ctas, int tile, int *n_tiles,
+                           int *unit_first, int *unit_stride, int *unit_count);
+
+/*
  * Kernel timing (a profiling aid).  With timing on, these calls record CUDA
  * events on their stream around their dominant kernel: cde_loo_loglik and
  * cde_loo_rows (the exact-LOO tile kernel, from the first to the last launch

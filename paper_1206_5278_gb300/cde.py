@@ -44,7 +44,7 @@ EXPORTED = [
     "cde_loo_loglik_noalloc", "cde_dataset_kernel", "cde_select_random", "cde_reference_rule",
     "cde_cond_stats", "cde_cond_interval", "cde_tuning_save", "cde_tuning_load", "cde_check_status",
     "cde_dataset_nn", "cde_dataset_nn_other", "cde_timing_enable", "cde_timing_last", "cde_selftest_wait",
-    "cde_tuning_get_ex", "cde_autotune_enable",
+    "cde_tuning_get_ex", "cde_autotune_enable", "cde_loo_tile_partition",
 ]
 
 
@@ -137,6 +137,9 @@ def lib():
         "cde_tuning_get_ex": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cde_autotune_enable": ([_vp, ctypes.c_int], ctypes.c_int),
+        "cde_loo_tile_partition": ([_i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cde_loo_loglik_noalloc": ([_vp, _i64, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp],
                                    ctypes.c_int),
         "cde_dataset_kernel": ([_vp, _i64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -489,6 +492,22 @@ def cde_tuning_get_ex(ctx, G1: int, G2: int):
     u, c, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().cde_tuning_get_ex(ctx, int(G1), int(G2), ctypes.byref(u), ctypes.byref(c), ctypes.byref(t)))
     return u.value, c.value, bool(t.value)
+
+
+def cde_loo_tile_partition(n_units: int, units_per_tile: int, ctas: int):
+    """The LOO launch's tile partition: a list of (unit_first, unit_stride,
+    unit_count) per tile (host query, no GPU)."""
+    L = lib()
+    nt = ctypes.c_int()
+    _check(L.cde_loo_tile_partition(int(n_units), int(units_per_tile), int(ctas), -1, ctypes.byref(nt),
+                                    None, None, None))
+    out = []
+    u0, st, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    for t in range(nt.value):
+        _check(L.cde_loo_tile_partition(int(n_units), int(units_per_tile), int(ctas), t, None,
+                                        ctypes.byref(u0), ctypes.byref(st), ctypes.byref(n)))
+        out.append((u0.value, st.value, n.value))
+    return out
 
 
 def cde_autotune_enable(ctx, on: bool):

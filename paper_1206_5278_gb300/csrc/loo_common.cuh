@@ -131,14 +131,14 @@ __host__ __device__ inline LooTiles loo_tiles(int n_units, int upt, int G) {
 }
 
 // first unit of level l (the units of levels 0 .. l-1 come before it)
-__device__ __forceinline__ int loo_level_base(const LooArgs& a, int l) {
+__host__ __device__ __forceinline__ int loo_level_base(const LooArgs& a, int l) {
     int s = 0;
     for (int i = 0; i < l; ++i) s += a.big_s0 >> i;
     return s * a.big_g;
 }
 
 // tile t's units: u0 + m stride for m < len
-__device__ __forceinline__ void loo_tile_span(const LooArgs& a, int t, int& u0, int& stride, int& len) {
+__host__ __device__ __forceinline__ void loo_tile_span(const LooArgs& a, int t, int& u0, int& stride, int& len) {
     const int nb = a.big_levels * a.big_g;
     if (t < nb) {
         const int l = t / a.big_g;
@@ -148,7 +148,7 @@ __device__ __forceinline__ void loo_tile_span(const LooArgs& a, int t, int& u0, 
     } else {
         u0 = loo_level_base(a, a.big_levels) + (t - nb) * a.units_per_tile;
         stride = 1;
-        len = min(a.units_per_tile, a.n_units - u0);
+        len = a.units_per_tile < a.n_units - u0 ? a.units_per_tile : a.n_units - u0;
     }
 }
 

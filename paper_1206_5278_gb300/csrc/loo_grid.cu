@@ -673,3 +673,28 @@ int loo_chunked_final(const LooChunked* c, const void* scratch, double* d_Lc, do
 }
 
 }  // namespace cde
+
+// The tile partition of n_units units (units_per_tile small-tile units, G CTAs),
+// as every LOO launch forms it: the same host/device code the kernels run.
+extern "C" int cde_loo_tile_partition(int64_t n_units, int units_per_tile, int ctas, int tile, int* n_tiles,
+                                      int* unit_first, int* unit_stride, int* unit_count) {
+    if (n_units < 1 || n_units >= (1LL << 31) || units_per_tile < 1 || ctas < 0)
+        return cde::set_error(CDE_EINVAL, "cde_loo_tile_partition: bad arguments");
+    const cde::LooTiles p = cde::loo_tiles((int)n_units, units_per_tile, ctas);
+    if (n_tiles) *n_tiles = p.n_tiles;
+    if (tile < 0) return CDE_OK;
+    if (tile >= p.n_tiles) return cde::set_error(CDE_EINVAL, "cde_loo_tile_partition: no such tile");
+    cde::LooArgs a{};
+    a.n_units = (int)n_units;
+    a.units_per_tile = units_per_tile;
+    a.big_g = p.big_g;
+    a.big_levels = p.big_levels;
+    a.big_s0 = p.big_s0;
+    int u0, st, len;
+    cde::loo_tile_span(a, tile, u0, st, len);
+    if (unit_first) *unit_first = u0;
+    if (unit_stride) *unit_stride = st;
+    if (unit_count) *unit_count = len;
+    return CDE_OK;
+}
+
