@@ -381,7 +381,6 @@ int autotune_shape(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, con
     cudaEventCreate(&e1);
     double best = 1e300;
     int bu = 0, bc = 0;
-    const int save_u = ctx->tune_upt[a][b], save_c = ctx->tune_ctas[a][b];
     int rc = CDE_OK;
     struct Cand {
         int u, c;
@@ -390,8 +389,7 @@ int autotune_shape(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, con
     std::vector<Cand> timed;
     for (int u : upts)
             for (int c : {1, 2}) {
-                ctx->tune_upt[a][b] = u;
-                ctx->tune_ctas[a][b] = c;
+                tuning_candidate(T1, T2, u, c);
                 // one untimed launch, then the fastest of three
                 float tmin = 1e30f;
                 for (int rep = 0; rep < 4 && rc == CDE_OK; ++rep) {
@@ -418,14 +416,11 @@ int autotune_shape(cde_ctx* ctx, const Dataset& D, const double* h1, int G1, con
             bc = k.c;
             kept = k.ms;
         }
+    tuning_candidate_clear();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(dout);
-    if (rc != CDE_OK) {
-        ctx->tune_upt[a][b] = save_u;
-        ctx->tune_ctas[a][b] = save_c;
-        return rc;
-    }
+    if (rc != CDE_OK) return rc;
     ctx->tune_upt[a][b] = bu;
     ctx->tune_ctas[a][b] = bc;
     ctx->tuned[a][b] = true;

@@ -533,6 +533,9 @@ void fill_loo_args(LooArgs& a, const Dataset& D, const double* h1, int g1, const
 // units per tile of a grid block shape over n_rows rows (the tuned value when set; n_rows = 0:
 // the per-shape default without the small-grid reduction)
 int loo_units_per_tile(cde_ctx* ctx, int T1, int T2, int64_t n_rows);
+// the autotuner's candidate for a shape class, used by this thread's launches only
+void tuning_candidate(int T1, int T2, int units_per_tile, int ctas_per_sm);
+void tuning_candidate_clear();
 
 // (the launch plan behind the opaque LooChunked of cde_internal.h)
 struct LooChunked {

@@ -427,8 +427,34 @@ static int shape_index(int T) { return T <= 8 ? 0 : T <= 16 ? 1 : 2; }
 // Units per tile: the autotuned value for this grid shape when the context has
 // one, else enough units for 8 rows per tile.  Both the single-dataset and the
 // batched launch use this, so they form identical tile partials.
+// The autotuner's candidate of one shape class, seen by the launches of the
+// tuning thread only: the context's table changes once, to the kept values, so
+// other threads (the request loop) never plan with a candidate.
+static thread_local int t_cand_a = -1, t_cand_b = -1, t_cand_upt = 0, t_cand_ctas = 0;
+
+void tuning_candidate(int T1, int T2, int units_per_tile, int ctas_per_sm) {
+    t_cand_a = shape_index(T1);
+    t_cand_b = shape_index(T2);
+    t_cand_upt = units_per_tile;
+    t_cand_ctas = ctas_per_sm;
+}
+
+void tuning_candidate_clear() { t_cand_a = t_cand_b = -1; }
+
+static int tuned_upt(cde_ctx* ctx, int T1, int T2) {
+    const int a = shape_index(T1), b = shape_index(T2);
+    if (a == t_cand_a && b == t_cand_b) return t_cand_upt;
+    return ctx ? ctx->tune_upt[a][b] : 0;
+}
+
+static int tuned_ctas(cde_ctx* ctx, int T1, int T2) {
+    const int a = shape_index(T1), b = shape_index(T2);
+    if (a == t_cand_a && b == t_cand_b) return t_cand_ctas;
+    return ctx ? ctx->tune_ctas[a][b] : 0;
+}
+
 int loo_units_per_tile(cde_ctx* ctx, int T1, int T2, int64_t n_rows) {
-    const int t = ctx ? ctx->tune_upt[shape_index(T1)][shape_index(T2)] : 0;
+    const int t = tuned_upt(ctx, T1, T2);
     if (t > 0) return t;
     const int JW = 1024 / (T1 * T2);
     int upt = JW >= 8 ? 1 : 8 / JW;
@@ -436,7 +462,7 @@ int loo_units_per_tile(cde_ctx* ctx, int T1, int T2, int64_t n_rows) {
     // tiles come from an atomic queue, and the last CTAs to finish decide the launch's time.
     // (N = 50,000 at 32 x 32: 70.3 ms with 8 rows per tile, 69.1 ms with 2.)
     if (ctx && n_rows > 0) {
-        const int c = ctx->tune_ctas[shape_index(T1)][shape_index(T2)];
+        const int c = tuned_ctas(ctx, T1, T2);
         const int64_t units = (n_rows + JW - 1) / JW;
         const int64_t want = 64LL * (c > 0 ? c : 2) * ctx->sm_count;
         while (upt > 1 && (units + upt - 1) / upt < want) upt >>= 1;
@@ -445,7 +471,7 @@ int loo_units_per_tile(cde_ctx* ctx, int T1, int T2, int64_t n_rows) {
 }
 
 int loo_grid_ctas(cde_ctx* ctx, int T1, int T2) {
-    const int c = ctx->tune_ctas[shape_index(T1)][shape_index(T2)];
+    const int c = tuned_ctas(ctx, T1, T2);
     return (c > 0 ? c : 2) * ctx->sm_count;
 }
 
