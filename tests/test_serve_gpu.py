@@ -218,3 +218,21 @@ def test_large_dataset_in_the_mix_and_served_results_match_oracle(ctx, datasets)
     ok, worst = rows_within_bound(g, ref_rows, x64, yb, h1g, h2g, rows, gram=False)
     assert ok, "a sampled row is off by %g beyond its bound" % worst
     cde.cde_destroy_dataset(ctx, big)
+
+
+def test_served_grid_on_the_d16_kernel_matches_single_launch(ctx):
+    """A selection job on a d_x = 20 dataset of 100,000 points: its grid runs on
+    the Gram-form kernel in the request loop's chunked launches (level windows,
+    then small tiles) and is the single launch's grid bit for bit."""
+    x, y = synth.gmm_sine(100000, 20, seed=57)
+    ds = cde.cde_create_dataset(ctx, x, y, standardize=True)
+    h1g = synth.bandwidth_grid(0.3, 3.0, 16)
+    h2g = synth.bandwidth_grid(0.02, 1.0, 16)
+    srv = Server(ctx, n_streams=2)
+    try:
+        r = _val(_submit(srv, ("s", ds, (h1g, h2g, 1, 0.05))))
+    finally:
+        srv.stop()
+    Lc, _ = cde.cde_loo_loglik(ctx, ds, h1g, h2g)
+    assert np.array_equal(r[4:].reshape(16, 16), Lc)
+    cde.cde_destroy_dataset(ctx, ds)
