@@ -108,13 +108,6 @@ __device__ __forceinline__ uint32_t tf32_rna(float v) {
     return r;
 }
 
-// split v into hi (v with the 13 low mantissa bits cleared: a TF32 value) and
-// lo = v - hi (exact in FP32; the MMA reads its leading 10 mantissa bits)
-__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
-    hi = __float_as_uint(v) & 0xffffe000u;
-    lo = __float_as_uint(v - __uint_as_float(hi));
-}
-
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
                                          uint32_t b1) {
     asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
