@@ -203,8 +203,11 @@ __global__ void __launch_bounds__(kNnThreads) k_nn_shift_split(const float* __re
     const int64_t jbase = (int64_t)blockIdx.x * kNnThreads * kNnJB + tid;
     const int64_t i0 = (int64_t)blockIdx.y * i_per_split;
     const int64_t i1 = min(N, i0 + i_per_split);
-    // b*: running minima, a*: the other coordinate's distance of the minimiser
-    float xj[kNnJB][DREG], yj[kNnJB], bx[kNnJB], by[kNnJB], ax[kNnJB], ay[kNnJB];
+    // running lexicographic minima as keys (minimum bits, other coordinate's bits):
+    // non-negative floats order like their bit patterns, so one 64-bit compare is
+    // the (minimum, then other distance) order
+    float xj[kNnJB][DREG], yj[kNnJB];
+    unsigned long long mkx[kNnJB], mky[kNnJB];
     int jj[kNnJB];
 #pragma unroll
     for (int b = 0; b < kNnJB; ++b) {
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(kNnThreads) k_nn_shift_split(const float* __re
 #pragma unroll
         for (int c = 0; c < DREG; ++c) xj[b][c] = c < d ? xs[(int64_t)c * Np + jc] : 0.f;
         yj[b] = y[jc];
-        bx[b] = by[b] = ax[b] = ay[b] = INFINITY;
+        mkx[b] = mky[b] = nn_key(INFINITY, INFINITY);
     }
     for (int64_t t0 = i0; t0 < i1; t0 += kNnThreads) {
         __syncthreads();
@@ -250,18 +253,12 @@ __global__ void __launch_bounds__(kNnThreads) k_nn_shift_split(const float* __re
                 const float2 dy = __ffma2_rn(make_float2(yi, yi), m1, make_float2(yj[b], yj[b + 1]));
                 const float2 dy2 = __fmul2_rn(dy, dy);
                 const bool o0 = i32 != jj[b], o1 = i32 != jj[b + 1];
-                const bool px0 = o0 && lex_less(dx2.x, dy2.x, bx[b], ax[b]);
-                const bool px1 = o1 && lex_less(dx2.y, dy2.y, bx[b + 1], ax[b + 1]);
-                const bool py0 = o0 && lex_less(dy2.x, dx2.x, by[b], ay[b]);
-                const bool py1 = o1 && lex_less(dy2.y, dx2.y, by[b + 1], ay[b + 1]);
-                bx[b] = px0 ? dx2.x : bx[b];
-                ax[b] = px0 ? dy2.x : ax[b];
-                bx[b + 1] = px1 ? dx2.y : bx[b + 1];
-                ax[b + 1] = px1 ? dy2.y : ax[b + 1];
-                by[b] = py0 ? dy2.x : by[b];
-                ay[b] = py0 ? dx2.x : ay[b];
-                by[b + 1] = py1 ? dy2.y : by[b + 1];
-                ay[b + 1] = py1 ? dx2.y : ay[b + 1];
+                const unsigned long long x0 = nn_key(dx2.x, dy2.x), x1 = nn_key(dx2.y, dy2.y);
+                const unsigned long long y0 = nn_key(dy2.x, dx2.x), y1 = nn_key(dy2.y, dx2.y);
+                if (o0 && x0 < mkx[b]) mkx[b] = x0;
+                if (o1 && x1 < mkx[b + 1]) mkx[b + 1] = x1;
+                if (o0 && y0 < mky[b]) mky[b] = y0;
+                if (o1 && y1 < mky[b + 1]) mky[b + 1] = y1;
             }
         }
     }
@@ -269,8 +266,8 @@ __global__ void __launch_bounds__(kNnThreads) k_nn_shift_split(const float* __re
     for (int b = 0; b < kNnJB; ++b) {
         const int64_t j = jbase + (int64_t)b * kNnThreads;
         if (j >= N) continue;
-        atomicMin(kx + j, nn_key(bx[b], ax[b]));
-        atomicMin(ky + j, nn_key(by[b], ay[b]));
+        atomicMin(kx + j, mkx[b]);
+        atomicMin(ky + j, mky[b]);
     }
 }
 
